@@ -1,0 +1,303 @@
+"""FP64 CPU oracle of the tree-code force evaluation (numpy + ctypes over oracle.c).
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+benchmark's CPU-baseline leg may import this package; the product library and
+its Python binding never do, and share no code with it.
+
+Each wrapper names the passage of N. Nakasato, "Implementation of a Parallel
+Tree Method on a GPU", that its C function follows.  Inputs are FP32
+particle arrays (x, y, z, m) exactly as the GPU path receives them; all force
+arithmetic is FP64.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+_f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+_u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+_i64 = ctypes.c_int64
+_vp = ctypes.c_void_p
+
+
+def lib():
+    """Load (building first if needed) the oracle shared library."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.or_direct.argtypes = [_i64, _f32p, _i64, _f32p, _vp, ctypes.c_double, _f64p]
+        L.or_bbox.argtypes = [_i64, _f32p, _f32p]
+        L.or_keys.argtypes = [_i64, _f32p, _f32p, _u32p]
+        L.or_sort.argtypes = [_i64, _u32p, _u32p]
+        L.or_sort.restype = ctypes.c_int
+        L.or_tree_build.argtypes = [_i64, _u32p, ctypes.c_int, _i64] + [_i32p] * 5
+        L.or_tree_build.restype = _i64
+        L.or_moments.argtypes = [_i64, _f32p, _u32p, _i32p, _i32p, _i32p, _f32p,
+                                 ctypes.c_double, _f64p, _vp, _f64p, _f64p]
+        L.or_groups.argtypes = [_i64, _i32p, _i32p, _i32p, _i32p, ctypes.c_int, _i64, _i32p, _i32p]
+        L.or_groups.restype = _i64
+        L.or_force_groups.argtypes = [_i64, _f32p, _u32p, _i64, _i32p, _i32p, _i32p, _i32p,
+                                      _f64p, _vp, _f64p, _i64, _i32p, _i32p, _vp,
+                                      ctypes.c_double, _f64p, _vp, _vp, _vp]
+        L.or_force_groups.restype = ctypes.c_int
+        L.or_group_lists.argtypes = [_i64, _f32p, _i32p, _i32p, _i32p, _i32p, _f64p, _f64p,
+                                     ctypes.c_int32, ctypes.c_int32, _i32p,
+                                     ctypes.POINTER(ctypes.c_int64), _i32p,
+                                     ctypes.POINTER(ctypes.c_int64)]
+        L.or_group_lists.restype = _i64
+        L.or_force_particles.argtypes = [_i64, _f32p, _u32p, _i64, _i32p, _i32p, _i32p, _i32p,
+                                         _f64p, _vp, _f64p, _i64, _i64, ctypes.c_double,
+                                         ctypes.c_int, _f64p, _vp, _vp]
+        L.or_force_particles.restype = ctypes.c_int
+        L.or_pc_eval.argtypes = [_f64p, _f64p, _vp, ctypes.c_double, _f64p]
+        L.or_num_threads.restype = ctypes.c_int
+        L.or_set_threads.argtypes = [ctypes.c_int]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _pos(pos):
+    pos = np.ascontiguousarray(pos, dtype=np.float32)
+    if pos.ndim != 2 or pos.shape[1] != 4:
+        raise ValueError("particles must be an (n, 4) array of x, y, z, m")
+    return pos
+
+
+def num_threads():
+    return lib().or_num_threads()
+
+
+def set_threads(t):
+    lib().or_set_threads(int(t))
+
+
+def direct(src, tgt=None, self_idx=None, eps=0.0):
+    """Eq. (1): softened direct sum.  Returns (n_tgt, 4) FP64 (ax, ay, az, phi).
+
+    With tgt=None the targets are the sources and target i skips source i.
+    """
+    src = _pos(src)
+    if tgt is None:
+        tgt = src
+        self_idx = np.arange(src.shape[0], dtype=np.int64)
+    tgt = _pos(tgt)
+    if self_idx is not None:
+        self_idx = np.ascontiguousarray(self_idx, dtype=np.int64)
+    out = np.zeros((tgt.shape[0], 4), dtype=np.float64)
+    lib().or_direct(src.shape[0], src, tgt.shape[0], tgt, _ptr(self_idx), float(eps), out)
+    return out
+
+
+def bbox(pos):
+    """Sec. 4.1 root cube: (xmin, ymin, zmin, L) in FP32."""
+    pos = _pos(pos)
+    box = np.zeros(4, dtype=np.float32)
+    lib().or_bbox(pos.shape[0], pos, box)
+    return box
+
+
+def keys(pos, box):
+    """Sec. 5 Morton ordering: 30-bit keys (10 bits per axis)."""
+    pos = _pos(pos)
+    k = np.zeros(pos.shape[0], dtype=np.uint32)
+    lib().or_keys(pos.shape[0], pos, np.ascontiguousarray(box, dtype=np.float32), k)
+    return k
+
+
+def sort(k):
+    """Stable sort by key; returns perm with perm[rank] = original index."""
+    k = np.ascontiguousarray(k, dtype=np.uint32)
+    perm = np.zeros(k.shape[0], dtype=np.uint32)
+    if lib().or_sort(k.shape[0], k, perm) != 0:
+        raise MemoryError("oracle sort")
+    return perm
+
+
+def node_capacity(n, n_leaf):
+    """Upper bound on the node count: <= n leaves plus, on each of levels 0..9,
+    at most n // (n_leaf + 1) internal nodes."""
+    return int(n + 10 * (n // (n_leaf + 1)) + 1)
+
+
+class Tree:
+    """Nodes in breadth-first order (sorted by level, then first particle)."""
+
+    def __init__(self, level, first, count, child_first, nchild):
+        self.level, self.first, self.count = level, first, count
+        self.child_first, self.nchild = child_first, nchild
+
+    @property
+    def n_nodes(self):
+        return self.level.shape[0]
+
+    def as_dict(self):
+        return dict(level=self.level, first=self.first, count=self.count,
+                    child_first=self.child_first, nchild=self.nchild)
+
+
+def tree_build(skeys, n_leaf):
+    """Sec. 4.1 octree over Morton-sorted keys (leaf: <= n_leaf or level 10)."""
+    skeys = np.ascontiguousarray(skeys, dtype=np.uint32)
+    n = skeys.shape[0]
+    cap = max(node_capacity(n, n_leaf), 1)
+    arrs = [np.zeros(cap, dtype=np.int32) for _ in range(5)]
+    nn = lib().or_tree_build(n, skeys, int(n_leaf), cap, *arrs)
+    if nn < 0:
+        raise RuntimeError("oracle tree_build: capacity exceeded")
+    return Tree(*[a[:nn].copy() for a in arrs])
+
+
+class Moments:
+    def __init__(self, com_m, quad, s_eff, side):
+        self.com_m, self.quad, self.s_eff, self.side = com_m, quad, s_eff, side
+
+
+def moments(spos, skeys, tree, box, theta, order=1):
+    """Sec. 4.4 cell data: mass, centre of mass, Eq. (2) S_eff; quadrupole if order 2."""
+    spos = _pos(spos)
+    nn = tree.n_nodes
+    com_m = np.zeros((nn, 4), dtype=np.float64)
+    quad = np.zeros((nn, 6), dtype=np.float64) if order >= 2 else None
+    s_eff = np.zeros(nn, dtype=np.float64)
+    side = np.zeros(nn, dtype=np.float64)
+    lib().or_moments(nn, spos, np.ascontiguousarray(skeys, dtype=np.uint32), tree.level,
+                     tree.first, tree.count, np.ascontiguousarray(box, dtype=np.float32),
+                     float(theta), com_m, _ptr(quad), s_eff, side)
+    return Moments(com_m, quad, s_eff, side)
+
+
+def groups(tree, G):
+    """Particle groups for the group walk (sibling packing, chunks of oversized leaves)."""
+    nn = tree.n_nodes
+    if nn == 0:
+        return np.zeros(0, np.int32), np.zeros(0, np.int32)
+    n = int(tree.count[0])
+    cap = n + 1
+    gf = np.zeros(cap, dtype=np.int32)
+    gc = np.zeros(cap, dtype=np.int32)
+    ng = lib().or_groups(nn, tree.first, tree.count, tree.child_first, tree.nchild, int(G), cap, gf, gc)
+    if ng < 0:
+        raise RuntimeError("oracle groups: capacity exceeded")
+    return gf[:ng].copy(), gc[:ng].copy()
+
+
+def force_groups(spos, perm, tree, mom, g_first, g_count, eps, group_mask=None, want_quad=None):
+    """Group walk with the conservative group form of Eq. (2).
+
+    Returns dict(out=(n,4) caller order, margin=(n,), n_pp=(n,), n_pc=(n,)).
+    """
+    spos = _pos(spos)
+    n = spos.shape[0]
+    out = np.zeros((n, 4), dtype=np.float64)
+    margin = np.full(n, np.inf, dtype=np.float64)
+    n_pp = np.zeros(n, dtype=np.int64)
+    n_pc = np.zeros(n, dtype=np.int64)
+    quad = mom.quad if want_quad is None or want_quad else None
+    if group_mask is not None:
+        group_mask = np.ascontiguousarray(group_mask, dtype=np.uint8)
+    rc = lib().or_force_groups(n, spos, np.ascontiguousarray(perm, dtype=np.uint32), tree.n_nodes,
+                               tree.first, tree.count, tree.child_first, tree.nchild,
+                               np.ascontiguousarray(mom.com_m), _ptr(quad), mom.s_eff,
+                               g_first.shape[0], g_first, g_count, _ptr(group_mask), float(eps),
+                               out, _ptr(margin), _ptr(n_pp), _ptr(n_pc))
+    if rc != 0:
+        raise MemoryError("oracle force_groups")
+    return dict(out=out, margin=margin, n_pp=n_pp, n_pc=n_pc)
+
+
+def group_lists(spos, tree, mom, gfirst, gcount):
+    """Accepted nodes and opened leaves of one group."""
+    spos = _pos(spos)
+    nn = tree.n_nodes
+    pc = np.zeros(nn, dtype=np.int32)
+    pp = np.zeros(nn, dtype=np.int32)
+    npc = ctypes.c_int64(0)
+    npp = ctypes.c_int64(0)
+    lib().or_group_lists(nn, spos, tree.first, tree.count, tree.child_first, tree.nchild,
+                         np.ascontiguousarray(mom.com_m), mom.s_eff, int(gfirst), int(gcount),
+                         pc, ctypes.byref(npc), pp, ctypes.byref(npp))
+    return pc[:npc.value].copy(), pp[:npp.value].copy()
+
+
+def force_particles(spos, perm, tree, mom, eps, t0=0, t1=None, unsoftened_pc=False,
+                    want_quad=None):
+    """Per-particle walk of Fig. 3 / Fig. 5 with Eq. (2)'s criterion."""
+    spos = _pos(spos)
+    n = spos.shape[0]
+    t1 = n if t1 is None else t1
+    out = np.zeros((n, 4), dtype=np.float64)
+    n_pp = np.zeros(n, dtype=np.int64)
+    n_pc = np.zeros(n, dtype=np.int64)
+    quad = mom.quad if want_quad is None or want_quad else None
+    rc = lib().or_force_particles(n, spos, np.ascontiguousarray(perm, dtype=np.uint32),
+                                  tree.n_nodes, tree.first, tree.count, tree.child_first,
+                                  tree.nchild, np.ascontiguousarray(mom.com_m), _ptr(quad),
+                                  mom.s_eff, int(t0), int(t1), float(eps), int(bool(unsoftened_pc)),
+                                  out, _ptr(n_pp), _ptr(n_pc))
+    if rc != 0:
+        raise MemoryError("oracle force_particles")
+    return dict(out=out, n_pp=n_pp, n_pc=n_pc)
+
+
+class Built:
+    """Everything the oracle derives from one particle set before the walk."""
+
+    def __init__(self, pos, n_leaf, G, theta, order):
+        self.pos = _pos(pos)
+        self.box = bbox(self.pos)
+        self.keys = keys(self.pos, self.box)
+        self.perm = sort(self.keys)
+        self.skeys = self.keys[self.perm]
+        self.spos = self.pos[self.perm]
+        self.tree = tree_build(self.skeys, n_leaf)
+        self.mom = moments(self.spos, self.skeys, self.tree, self.box, theta, order)
+        self.g_first, self.g_count = groups(self.tree, G)
+        self.order = order
+
+
+def tree_force(pos, theta, eps, n_leaf=8, G=32, order=1, walk="group", group_mask=None):
+    """Whole force evaluation: box, keys, sort, tree, moments, groups, walk.
+
+    walk="group" (the GPU path's criterion) or "particle" (the paper's).
+    Returns (result dict, Built).
+    """
+    b = Built(pos, n_leaf, G, theta, order)
+    if walk == "group":
+        res = force_groups(b.spos, b.perm, b.tree, b.mom, b.g_first, b.g_count, eps,
+                           group_mask=group_mask)
+    elif walk == "particle":
+        res = force_particles(b.spos, b.perm, b.tree, b.mom, eps)
+    else:
+        raise ValueError(walk)
+    return res, b
+
+
+def pc_eval(x, com_m, quad=None, eps=0.0):
+    """One particle-cell term (monopole, plus quadrupole when quad is given)."""
+    out = np.zeros(4, dtype=np.float64)
+    q = None if quad is None else np.ascontiguousarray(quad, dtype=np.float64)
+    lib().or_pc_eval(np.ascontiguousarray(x, dtype=np.float64),
+                     np.ascontiguousarray(com_m, dtype=np.float64), _ptr(q), float(eps), out)
+    return out
+
+
+def rel_err(a, ref):
+    """Per-target relative errors of accelerations and potentials (Sec. 5 a_error form)."""
+    a = np.asarray(a, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    ea = np.linalg.norm(a[:, :3] - ref[:, :3], axis=1) / np.linalg.norm(ref[:, :3], axis=1)
+    ep = np.abs(a[:, 3] - ref[:, 3]) / np.abs(ref[:, 3])
+    return ea, ep

@@ -1,0 +1,646 @@
+/*
+ * oracle.c -- plain, slow, FP64 CPU oracle of the tree-code force evaluation
+ * (N. Nakasato, "Implementation of a Parallel Tree Method on a GPU").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file: only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark use it.  It shares no code, header, table or constant
+ * generator with the CUDA library.
+ *
+ * Every function below is written from the paper's definitions (cited per
+ * function) in the most direct form: no blocking, no fusion, no reordering.
+ * Floating point is FP64 except where a floating-point result decides an
+ * integer (root box, Morton keys): there the decision is taken in FP32 with
+ * IEEE round-to-nearest and no contraction, exactly as the GPU kernel does
+ * (this file must be compiled with -ffp-contract=off).
+ *
+ * Conventions (readings of the paper, listed in the design notes):
+ *   - sign: accelerations are attractive and the potential is negative,
+ *     phi_i = -sum m_j / sqrt(r^2 + eps^2)  (the paper's p_i is -phi_i);
+ *   - the self term is excluded by index (Eq. 1, j != i);
+ *   - particle-cell terms are softened with the same eps as particle-particle
+ *     terms unless `unsoftened_pc` is set (the Appendix A kernel's form);
+ *   - tree: node = non-empty cell of the 2^l grid (l = 0..10) whose parent cell
+ *     holds more than n_leaf particles; a node is a leaf when it holds at most
+ *     n_leaf particles or l == 10; nodes are stored breadth first, i.e. sorted
+ *     by (level, first particle), so the children of a node are contiguous.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_MAX_LEVEL 10
+
+int or_version(void) { return 3; }
+
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void or_set_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
+/* ------------------------------------------------------------------------
+ * Eq. (1), Sec. 3: softened direct summation over all j != i.
+ * src: n_src x (x,y,z,m) FP32;  tgt: n_tgt x (x,y,z,*) FP32;
+ * self: optional index into src excluded for each target (-1 = none);
+ * out:  n_tgt x (ax,ay,az,phi) FP64.
+ * ---------------------------------------------------------------------- */
+void or_direct(int64_t n_src, const float* src, int64_t n_tgt, const float* tgt,
+               const int64_t* self, double eps, double* out)
+{
+    const double e2 = eps * eps;
+    int64_t i;
+#pragma omp parallel for schedule(dynamic, 8)
+    for (i = 0; i < n_tgt; i++) {
+        const double xi = tgt[4 * i], yi = tgt[4 * i + 1], zi = tgt[4 * i + 2];
+        const int64_t skip = self ? self[i] : -1;
+        double ax = 0, ay = 0, az = 0, phi = 0;
+        for (int64_t j = 0; j < n_src; j++) {
+            if (j == skip) continue;
+            const double dx = (double)src[4 * j] - xi;
+            const double dy = (double)src[4 * j + 1] - yi;
+            const double dz = (double)src[4 * j + 2] - zi;
+            const double m = src[4 * j + 3];
+            const double r2 = dx * dx + dy * dy + dz * dz + e2;
+            const double rinv = 1.0 / sqrt(r2);
+            const double mr3 = m * rinv * rinv * rinv;
+            ax += mr3 * dx;
+            ay += mr3 * dy;
+            az += mr3 * dz;
+            phi -= m * rinv;
+        }
+        out[4 * i] = ax;
+        out[4 * i + 1] = ay;
+        out[4 * i + 2] = az;
+        out[4 * i + 3] = phi;
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Sec. 4.1: the root cell is a cube enclosing all particles.  Origin = the
+ * per-axis minimum, side L = the largest per-axis extent (FP32, exact min/max,
+ * one rounded subtraction).  A degenerate side (0, or one whose 1024/L is not
+ * finite) is replaced by 1.  box = (xmin, ymin, zmin, L).
+ * ---------------------------------------------------------------------- */
+void or_bbox(int64_t n, const float* pos, float* box)
+{
+    float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int64_t i = 0; i < n; i++)
+        for (int a = 0; a < 3; a++) {
+            const float v = pos[4 * i + a];
+            if (i == 0 || v < lo[a]) lo[a] = v;
+            if (i == 0 || v > hi[a]) hi[a] = v;
+        }
+    float L = 0.0f;
+    for (int a = 0; a < 3; a++) {
+        const float d = hi[a] - lo[a];
+        if (d > L) L = d;
+    }
+    const float inv = 1024.0f / L;
+    if (!(L > 0.0f) || !isfinite(inv)) L = 1.0f;
+    box[0] = lo[0];
+    box[1] = lo[1];
+    box[2] = lo[2];
+    box[3] = L;
+}
+
+/* Spread the low 10 bits of v so that bit k moves to bit 3k. */
+static uint32_t or_spread3(uint32_t v)
+{
+    uint32_t r = 0;
+    for (int k = 0; k < 10; k++) r |= ((v >> k) & 1u) << (3 * k);
+    return r;
+}
+
+/* Inverse of or_spread3 restricted to `nbits` triples. */
+static uint32_t or_compact3(uint32_t v, int nbits)
+{
+    uint32_t r = 0;
+    for (int k = 0; k < nbits; k++) r |= ((v >> (3 * k)) & 1u) << k;
+    return r;
+}
+
+/* ------------------------------------------------------------------------
+ * Sec. 5 (Morton ordering): 30-bit Morton key, 10 bits per axis.
+ * q = (x - xmin) * (1024/L) in FP32 (two rounded ops), integer cell
+ * c = min(trunc(q), 1023); bit k of cx, cy, cz goes to key bit 3k+2, 3k+1, 3k.
+ * ---------------------------------------------------------------------- */
+void or_keys(int64_t n, const float* pos, const float* box, uint32_t* keys)
+{
+    const float inv = 1024.0f / box[3];
+    for (int64_t i = 0; i < n; i++) {
+        uint32_t c[3];
+        for (int a = 0; a < 3; a++) {
+            const float t = pos[4 * i + a] - box[a];
+            const float q = t * inv;
+            uint32_t ci = (uint32_t)q;
+            if (ci > 1023u) ci = 1023u;
+            c[a] = ci;
+        }
+        keys[i] = (or_spread3(c[0]) << 2) | (or_spread3(c[1]) << 1) | or_spread3(c[2]);
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Stable sort of indices 0..n-1 by key (plain top-down merge sort).
+ * perm[k] = original index of the k-th particle in Morton order.
+ * ---------------------------------------------------------------------- */
+static void or_merge_sort(uint32_t* a, uint32_t* tmp, int64_t lo, int64_t hi, const uint32_t* keys)
+{
+    if (hi - lo < 2) return;
+    const int64_t mid = lo + (hi - lo) / 2;
+    or_merge_sort(a, tmp, lo, mid, keys);
+    or_merge_sort(a, tmp, mid, hi, keys);
+    int64_t i = lo, j = mid, k = lo;
+    while (i < mid && j < hi) {
+        if (keys[a[j]] < keys[a[i]]) tmp[k++] = a[j++];
+        else tmp[k++] = a[i++];
+    }
+    while (i < mid) tmp[k++] = a[i++];
+    while (j < hi) tmp[k++] = a[j++];
+    memcpy(a + lo, tmp + lo, (size_t)(hi - lo) * sizeof(uint32_t));
+}
+
+int or_sort(int64_t n, const uint32_t* keys, uint32_t* perm)
+{
+    uint32_t* tmp = (uint32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(uint32_t));
+    if (!tmp) return -1;
+    for (int64_t i = 0; i < n; i++) perm[i] = (uint32_t)i;
+    or_merge_sort(perm, tmp, 0, n, keys);
+    free(tmp);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Sec. 4.1 tree construction: recursively split a cube into 8 equal
+ * sub-cells.  Here the recursion stops at a cell holding <= n_leaf particles
+ * or at level 10 (the resolution of a 30-bit key).  Nodes are emitted level
+ * by level, children in octant order, so node order = (level, first).
+ * Returns the node count, or -1 if `cap` is too small.
+ * ---------------------------------------------------------------------- */
+int64_t or_tree_build(int64_t n, const uint32_t* skeys, int n_leaf, int64_t cap,
+                      int32_t* level, int32_t* first, int32_t* count,
+                      int32_t* child_first, int32_t* nchild)
+{
+    if (n <= 0) return 0;
+    if (cap < 1) return -1;
+    int64_t nn = 1;
+    level[0] = 0;
+    first[0] = 0;
+    count[0] = (int32_t)n;
+    int64_t lev_begin = 0, lev_end = 1;
+    for (int l = 0; l <= OR_MAX_LEVEL; l++) {
+        for (int64_t v = lev_begin; v < lev_end; v++) {
+            if (count[v] <= n_leaf || l == OR_MAX_LEVEL) {
+                child_first[v] = -1;
+                nchild[v] = 0;
+                continue;
+            }
+            /* digit of the sub-cell at level l+1 */
+            const int shift = 3 * (OR_MAX_LEVEL - 1 - l);
+            child_first[v] = (int32_t)nn;
+            nchild[v] = 0;
+            int64_t k = first[v];
+            const int64_t end = (int64_t)first[v] + count[v];
+            while (k < end) {
+                const uint32_t d = (skeys[k] >> shift) & 7u;
+                int64_t e = k;
+                while (e < end && ((skeys[e] >> shift) & 7u) == d) e++;
+                if (nn >= cap) return -1;
+                level[nn] = l + 1;
+                first[nn] = (int32_t)k;
+                count[nn] = (int32_t)(e - k);
+                nn++;
+                nchild[v]++;
+                k = e;
+            }
+        }
+        lev_begin = lev_end;
+        lev_end = nn;
+        if (lev_begin == lev_end) break;
+    }
+    return nn;
+}
+
+/* ------------------------------------------------------------------------
+ * Sec. 4.4 cell data: total mass, centre of mass, and Eq. (2)'s effective
+ * size S_eff = (l/theta + s)^2, where l is the side of the node's cube and s
+ * the distance from the cube's centre to the centre of mass.  For order 2
+ * also the raw second moment about the centre of mass,
+ * I_ab = sum m (x_a - c_a)(x_b - c_b), stored (xx, yy, zz, xy, xz, yz).
+ * Every node is summed directly over its own particles (not from its
+ * children).  A massless node takes its geometric centre as centre of mass.
+ * spos: particles in Morton order (x,y,z,m) FP32; skeys: their keys.
+ * Outputs per node: com_m (cx,cy,cz,M), quad[6] (may be NULL), s_eff, side.
+ * ---------------------------------------------------------------------- */
+void or_moments(int64_t nn, const float* spos, const uint32_t* skeys,
+                const int32_t* level, const int32_t* first, const int32_t* count,
+                const float* box, double theta, double* com_m, double* quad,
+                double* s_eff, double* side)
+{
+    int64_t v;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (v = 0; v < nn; v++) {
+        const int l = level[v];
+        const int64_t b = first[v], e = (int64_t)first[v] + count[v];
+        double M = 0, sx = 0, sy = 0, sz = 0;
+        for (int64_t k = b; k < e; k++) {
+            const double m = spos[4 * k + 3];
+            M += m;
+            sx += m * spos[4 * k];
+            sy += m * spos[4 * k + 1];
+            sz += m * spos[4 * k + 2];
+        }
+        /* geometric centre of the level-l cell containing the node */
+        const double lside = (double)box[3] / (double)(1u << l);
+        const uint32_t prefix = (l == 0) ? 0u : (skeys[b] >> (3 * (OR_MAX_LEVEL - l)));
+        const double px = or_compact3(prefix >> 2, l), py = or_compact3(prefix >> 1, l),
+                     pz = or_compact3(prefix, l);
+        const double gx = (double)box[0] + (px + 0.5) * lside;
+        const double gy = (double)box[1] + (py + 0.5) * lside;
+        const double gz = (double)box[2] + (pz + 0.5) * lside;
+        double cx, cy, cz;
+        if (M > 0) {
+            cx = sx / M;
+            cy = sy / M;
+            cz = sz / M;
+        } else {
+            cx = gx;
+            cy = gy;
+            cz = gz;
+        }
+        com_m[4 * v] = cx;
+        com_m[4 * v + 1] = cy;
+        com_m[4 * v + 2] = cz;
+        com_m[4 * v + 3] = M;
+        if (quad) {
+            double q[6] = {0, 0, 0, 0, 0, 0};
+            for (int64_t k = b; k < e; k++) {
+                const double m = spos[4 * k + 3];
+                const double y0 = spos[4 * k] - cx, y1 = spos[4 * k + 1] - cy, y2 = spos[4 * k + 2] - cz;
+                q[0] += m * y0 * y0;
+                q[1] += m * y1 * y1;
+                q[2] += m * y2 * y2;
+                q[3] += m * y0 * y1;
+                q[4] += m * y0 * y2;
+                q[5] += m * y1 * y2;
+            }
+            for (int c = 0; c < 6; c++) quad[6 * v + c] = q[c];
+        }
+        const double s = sqrt((gx - cx) * (gx - cx) + (gy - cy) * (gy - cy) + (gz - cz) * (gz - cz));
+        const double t = lside / theta + s;
+        s_eff[v] = t * t;
+        if (side) side[v] = lside;
+    }
+}
+
+/* ------------------------------------------------------------------------
+ * Particle groups for the group walk (an extension in the spirit of the
+ * GRAPE interaction lists of Sec. 4.2: one list shared by nearby targets).
+ * Groups partition the Morton-ordered particles:
+ *   - if the root holds <= G particles it is the only group;
+ *   - for every internal node P holding > G particles, its children are
+ *     visited in octant order; children holding <= G particles are packed
+ *     greedily, in order, into runs of total <= G (a child holding > G
+ *     particles ends the current run); a leaf holding > G particles
+ *     (possible only at level 10, or when n_leaf > G) is cut into chunks of G.
+ * Groups are returned sorted by first particle.  Returns the group count or
+ * -1 if `cap` is too small.
+ * ---------------------------------------------------------------------- */
+static int or_cmp_i64(const void* a, const void* b)
+{
+    const int64_t x = *(const int64_t*)a, y = *(const int64_t*)b;
+    return (x > y) - (x < y);
+}
+
+int64_t or_groups(int64_t nn, const int32_t* first, const int32_t* count,
+                  const int32_t* child_first, const int32_t* nchild, int G, int64_t cap,
+                  int32_t* g_first, int32_t* g_count)
+{
+    if (nn <= 0) return 0;
+    /* (first << 32 | count) pairs, sorted at the end */
+    int64_t* tmp = (int64_t*)malloc((size_t)(cap > 0 ? cap : 1) * sizeof(int64_t));
+    if (!tmp) return -1;
+    int64_t ng = 0;
+#define OR_EMIT(F, C)                                                  \
+    do {                                                               \
+        if (ng >= cap) { free(tmp); return -1; }                       \
+        tmp[ng++] = ((int64_t)(F) << 32) | (int64_t)(uint32_t)(C);     \
+    } while (0)
+    if (count[0] <= G) {
+        OR_EMIT(first[0], count[0]);
+    } else if (nchild[0] == 0) {
+        for (int64_t k = 0; k < count[0]; k += G)
+            OR_EMIT(first[0] + k, (count[0] - k < G) ? (count[0] - k) : G);
+    } else {
+        for (int64_t p = 0; p < nn; p++) {
+            if (nchild[p] == 0 || count[p] <= G) continue;
+            int64_t run_first = -1, run_count = 0;
+            for (int c = 0; c < nchild[p]; c++) {
+                const int64_t ch = child_first[p] + c;
+                if (count[ch] <= G) {
+                    if (run_first >= 0 && run_count + count[ch] <= G) {
+                        run_count += count[ch];
+                    } else {
+                        if (run_first >= 0) OR_EMIT(run_first, run_count);
+                        run_first = first[ch];
+                        run_count = count[ch];
+                    }
+                } else {
+                    if (run_first >= 0) OR_EMIT(run_first, run_count);
+                    run_first = -1;
+                    run_count = 0;
+                    if (nchild[ch] == 0)
+                        for (int64_t k = 0; k < count[ch]; k += G)
+                            OR_EMIT(first[ch] + k, (count[ch] - k < G) ? (count[ch] - k) : G);
+                }
+            }
+            if (run_first >= 0) OR_EMIT(run_first, run_count);
+        }
+    }
+#undef OR_EMIT
+    qsort(tmp, (size_t)ng, sizeof(int64_t), or_cmp_i64);
+    for (int64_t g = 0; g < ng; g++) {
+        g_first[g] = (int32_t)(tmp[g] >> 32);
+        g_count[g] = (int32_t)(tmp[g] & 0xffffffff);
+    }
+    free(tmp);
+    return ng;
+}
+
+/* ------------------------------------------------------------------------
+ * Interaction kernels (Eq. 1 and its multipole generalisation).
+ * r = x_i - c,  h^2 = |r|^2 + eps^2,  g_n = h^-n.
+ * Monopole: phi = -M g1,  a = -M g3 r.
+ * Quadrupole (second-order Taylor term of the softened kernel about the
+ * centre of mass, where the dipole vanishes):
+ *   phi += -(3 q g5 - T g3)/2,   a += 3 g5 (I r) + (1.5 T g5 - 7.5 q g7) r,
+ * with T = tr I and q = r.I.r.  At eps = 0 this is the traceless form
+ * -r.Q.r / (2 |r|^5) with Q = 3I - T 1.
+ * ---------------------------------------------------------------------- */
+static void or_pc(double xi, double yi, double zi, const double* cm, const double* qd,
+                  double e2, double* acc)
+{
+    const double rx = xi - cm[0], ry = yi - cm[1], rz = zi - cm[2], M = cm[3];
+    const double h2 = rx * rx + ry * ry + rz * rz + e2;
+    const double g1 = 1.0 / sqrt(h2);
+    const double g2 = g1 * g1;
+    const double g3 = g1 * g2;
+    acc[0] -= M * g3 * rx;
+    acc[1] -= M * g3 * ry;
+    acc[2] -= M * g3 * rz;
+    acc[3] -= M * g1;
+    if (qd) {
+        const double g5 = g3 * g2, g7 = g5 * g2;
+        const double Ir0 = qd[0] * rx + qd[3] * ry + qd[4] * rz;
+        const double Ir1 = qd[3] * rx + qd[1] * ry + qd[5] * rz;
+        const double Ir2 = qd[4] * rx + qd[5] * ry + qd[2] * rz;
+        const double T = qd[0] + qd[1] + qd[2];
+        const double q = rx * Ir0 + ry * Ir1 + rz * Ir2;
+        const double c = 1.5 * T * g5 - 7.5 * q * g7;
+        acc[0] += 3.0 * g5 * Ir0 + c * rx;
+        acc[1] += 3.0 * g5 * Ir1 + c * ry;
+        acc[2] += 3.0 * g5 * Ir2 + c * rz;
+        acc[3] -= 0.5 * (3.0 * q * g5 - T * g3);
+    }
+}
+
+static void or_pp(double xi, double yi, double zi, const float* pj, double e2, double* acc)
+{
+    const double dx = (double)pj[0] - xi, dy = (double)pj[1] - yi, dz = (double)pj[2] - zi;
+    const double m = pj[3];
+    const double r2 = dx * dx + dy * dy + dz * dz + e2;
+    const double rinv = 1.0 / sqrt(r2);
+    const double mr3 = m * rinv * rinv * rinv;
+    acc[0] += mr3 * dx;
+    acc[1] += mr3 * dy;
+    acc[2] += mr3 * dz;
+    acc[3] -= m * rinv;
+}
+
+/* ------------------------------------------------------------------------
+ * Group walk (group form of Fig. 3's tree walk, with Eq. 2's criterion
+ * applied conservatively to the whole group): a node is accepted for the
+ * group when the squared distance from its centre of mass to the group's
+ * axis-aligned bounding box exceeds S_eff (strict, as the Appendix A kernel's
+ * `s < r2`); an accepted node gives a particle-cell term to every member; a
+ * rejected leaf gives particle-particle terms with all its particles (the
+ * target itself excluded by index); a rejected internal node is opened.
+ *
+ * spos: Morton-ordered particles; perm: Morton position -> caller index.
+ * out (caller order, n x 4): ax, ay, az, phi.
+ * margin (caller order, optional): min over the group's decisions of
+ *   |d^2 - S_eff| / S_eff, so near-tie decisions can be recognised.
+ * n_pp, n_pc (caller order, optional): interactions evaluated per target.
+ * group_mask (optional, per group): walk only groups whose mask is non-zero;
+ *   the other targets are left untouched.
+ * ---------------------------------------------------------------------- */
+int or_force_groups(int64_t n, const float* spos, const uint32_t* perm, int64_t nn,
+                    const int32_t* first, const int32_t* count, const int32_t* child_first,
+                    const int32_t* nchild, const double* com_m, const double* quad,
+                    const double* s_eff, int64_t ng, const int32_t* g_first, const int32_t* g_count,
+                    const uint8_t* group_mask, double eps, double* out, double* margin,
+                    int64_t* n_pp, int64_t* n_pc)
+{
+    const double e2 = eps * eps;
+    int err = 0;
+    (void)n;
+    int64_t g;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (g = 0; g < ng; g++) {
+        if (group_mask && !group_mask[g]) continue;
+        const int64_t gb = g_first[g], ge = (int64_t)g_first[g] + g_count[g];
+        double lo[3], hi[3];
+        for (int a = 0; a < 3; a++) lo[a] = hi[a] = spos[4 * gb + a];
+        for (int64_t k = gb; k < ge; k++)
+            for (int a = 0; a < 3; a++) {
+                const double v = spos[4 * k + a];
+                if (v < lo[a]) lo[a] = v;
+                if (v > hi[a]) hi[a] = v;
+            }
+        int32_t* stack = (int32_t*)malloc((size_t)nn * sizeof(int32_t));
+        int32_t* pc = (int32_t*)malloc((size_t)nn * sizeof(int32_t));
+        int32_t* pp = (int32_t*)malloc((size_t)nn * sizeof(int32_t));
+        if (!stack || !pc || !pp) {
+            free(stack); free(pc); free(pp);
+#pragma omp atomic write
+            err = -1;
+            continue;
+        }
+        int64_t sp = 0, npc = 0, npp = 0;
+        double mmin = INFINITY;
+        stack[sp++] = 0;
+        while (sp > 0) {
+            const int32_t v = stack[--sp];
+            const double* c = com_m + 4 * v;
+            double d2 = 0;
+            for (int a = 0; a < 3; a++) {
+                double t = 0;
+                if (c[a] < lo[a]) t = lo[a] - c[a];
+                else if (c[a] > hi[a]) t = c[a] - hi[a];
+                d2 += t * t;
+            }
+            const double S = s_eff[v];
+            const double mg = fabs(d2 - S) / S;
+            if (mg < mmin) mmin = mg;
+            if (d2 > S) pc[npc++] = v;
+            else if (nchild[v] == 0) pp[npp++] = v;
+            else
+                for (int ch = nchild[v] - 1; ch >= 0; ch--) stack[sp++] = child_first[v] + ch;
+        }
+        for (int64_t i = gb; i < ge; i++) {
+            const double xi = spos[4 * i], yi = spos[4 * i + 1], zi = spos[4 * i + 2];
+            double acc[4] = {0, 0, 0, 0};
+            int64_t cnt_pp = 0;
+            for (int64_t t = 0; t < npc; t++)
+                or_pc(xi, yi, zi, com_m + 4 * pc[t], quad ? quad + 6 * pc[t] : NULL, e2, acc);
+            for (int64_t t = 0; t < npp; t++) {
+                const int64_t b = first[pp[t]], e = b + count[pp[t]];
+                for (int64_t j = b; j < e; j++) {
+                    if (j == i) continue;
+                    or_pp(xi, yi, zi, spos + 4 * j, e2, acc);
+                    cnt_pp++;
+                }
+            }
+            const int64_t o = perm[i];
+            for (int a = 0; a < 4; a++) out[4 * o + a] = acc[a];
+            if (margin) margin[o] = mmin;
+            if (n_pp) n_pp[o] = cnt_pp;
+            if (n_pc) n_pc[o] = npc;
+        }
+        free(stack);
+        free(pc);
+        free(pp);
+    }
+    return err;
+}
+
+/* Accepted-node and opened-leaf lists of one group (for invariant tests). */
+int64_t or_group_lists(int64_t nn, const float* spos, const int32_t* first, const int32_t* count,
+                       const int32_t* child_first, const int32_t* nchild, const double* com_m,
+                       const double* s_eff, int32_t gb, int32_t gc, int32_t* pc, int64_t* npc_out,
+                       int32_t* pp, int64_t* npp_out)
+{
+    (void)first; (void)count;
+    double lo[3], hi[3];
+    for (int a = 0; a < 3; a++) lo[a] = hi[a] = spos[4 * (int64_t)gb + a];
+    for (int64_t k = gb; k < (int64_t)gb + gc; k++)
+        for (int a = 0; a < 3; a++) {
+            const double v = spos[4 * k + a];
+            if (v < lo[a]) lo[a] = v;
+            if (v > hi[a]) hi[a] = v;
+        }
+    int32_t* stack = (int32_t*)malloc((size_t)nn * sizeof(int32_t));
+    if (!stack) return -1;
+    int64_t sp = 0, npc = 0, npp = 0;
+    stack[sp++] = 0;
+    while (sp > 0) {
+        const int32_t v = stack[--sp];
+        const double* c = com_m + 4 * v;
+        double d2 = 0;
+        for (int a = 0; a < 3; a++) {
+            double t = 0;
+            if (c[a] < lo[a]) t = lo[a] - c[a];
+            else if (c[a] > hi[a]) t = c[a] - hi[a];
+            d2 += t * t;
+        }
+        if (d2 > s_eff[v]) pc[npc++] = v;
+        else if (nchild[v] == 0) pp[npp++] = v;
+        else
+            for (int ch = nchild[v] - 1; ch >= 0; ch--) stack[sp++] = child_first[v] + ch;
+    }
+    free(stack);
+    *npc_out = npc;
+    *npp_out = npp;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------
+ * Per-particle walk of Fig. 3 / Fig. 5 (the paper's own form): for target i,
+ * a node holding a single particle is a particle-particle term; otherwise
+ * the node is accepted when d^2 > S_eff with d = |x_i - COM| (Eq. 2); a
+ * rejected leaf gives particle-particle terms with its members; a rejected
+ * internal node is opened.  The self term is skipped by index.  With
+ * unsoftened_pc the particle-cell term uses eps = 0 (the Appendix A kernel).
+ * Targets are the Morton positions [t0, t1); out etc. are in caller order.
+ * ---------------------------------------------------------------------- */
+int or_force_particles(int64_t n, const float* spos, const uint32_t* perm, int64_t nn,
+                       const int32_t* first, const int32_t* count, const int32_t* child_first,
+                       const int32_t* nchild, const double* com_m, const double* quad,
+                       const double* s_eff, int64_t t0, int64_t t1, double eps, int unsoftened_pc,
+                       double* out, int64_t* n_pp, int64_t* n_pc)
+{
+    const double e2 = eps * eps;
+    const double e2c = unsoftened_pc ? 0.0 : e2;
+    int err = 0;
+    (void)n;
+    int64_t i;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (i = t0; i < t1; i++) {
+        int32_t* stack = (int32_t*)malloc((size_t)nn * sizeof(int32_t));
+        if (!stack) {
+#pragma omp atomic write
+            err = -1;
+            continue;
+        }
+        const double xi = spos[4 * i], yi = spos[4 * i + 1], zi = spos[4 * i + 2];
+        double acc[4] = {0, 0, 0, 0};
+        int64_t cpp = 0, cpc = 0, sp = 0;
+        stack[sp++] = 0;
+        while (sp > 0) {
+            const int32_t v = stack[--sp];
+            if (count[v] == 1) {
+                if (first[v] != i) {
+                    or_pp(xi, yi, zi, spos + 4 * (int64_t)first[v], e2, acc);
+                    cpp++;
+                }
+                continue;
+            }
+            const double* c = com_m + 4 * v;
+            const double dx = c[0] - xi, dy = c[1] - yi, dz = c[2] - zi;
+            const double d2 = dx * dx + dy * dy + dz * dz;
+            if (d2 > s_eff[v]) {
+                or_pc(xi, yi, zi, c, quad ? quad + 6 * v : NULL, e2c, acc);
+                cpc++;
+            } else if (nchild[v] == 0) {
+                for (int64_t j = first[v]; j < (int64_t)first[v] + count[v]; j++) {
+                    if (j == i) continue;
+                    or_pp(xi, yi, zi, spos + 4 * j, e2, acc);
+                    cpp++;
+                }
+            } else {
+                for (int ch = nchild[v] - 1; ch >= 0; ch--) stack[sp++] = child_first[v] + ch;
+            }
+        }
+        const int64_t o = perm[i];
+        for (int a = 0; a < 4; a++) out[4 * o + a] = acc[a];
+        if (n_pp) n_pp[o] = cpp;
+        if (n_pc) n_pc[o] = cpc;
+        free(stack);
+    }
+    return err;
+}
+
+/* One particle-cell term at target x (for the quadrupole pins). */
+void or_pc_eval(const double* x, const double* com_m, const double* quad, double eps, double* out)
+{
+    double acc[4] = {0, 0, 0, 0};
+    or_pc(x[0], x[1], x[2], com_m, quad, eps * eps, acc);
+    for (int a = 0; a < 4; a++) out[a] = acc[a];
+}
