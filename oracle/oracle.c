@@ -20,6 +20,8 @@
  *   - the self term is excluded by index (Eq. 1, j != i);
  *   - particle-cell terms are softened with the same eps as particle-particle
  *     terms unless `unsoftened_pc` is set (the Appendix A kernel's form);
+ *   - a node holding the target (or, in the group walk, any group member) is
+ *     never accepted, it is opened;
  *   - tree: node = non-empty cell of the 2^l grid (l = 0..10) whose parent cell
  *     holds more than n_leaf particles; a node is a leaf when it holds at most
  *     n_leaf particles or l == 10; nodes are stored breadth first, i.e. sorted
@@ -439,7 +441,9 @@ static void or_pp(double xi, double yi, double zi, const float* pj, double e2, d
  * applied conservatively to the whole group): a node is accepted for the
  * group when the squared distance from its centre of mass to the group's
  * axis-aligned bounding box exceeds S_eff (strict, as the Appendix A kernel's
- * `s < r2`); an accepted node gives a particle-cell term to every member; a
+ * `s < r2`) and the node holds no member of the group (for theta above
+ * 1/sqrt(3) Eq. 2 alone could accept a cell holding the target itself); an
+ * accepted node gives a particle-cell term to every member; a
  * rejected leaf gives particle-particle terms with all its particles (the
  * target itself excluded by index); a rejected internal node is opened.
  *
@@ -497,9 +501,12 @@ int or_force_groups(int64_t n, const float* spos, const uint32_t* perm, int64_t 
                 d2 += t * t;
             }
             const double S = s_eff[v];
-            const double mg = fabs(d2 - S) / S;
-            if (mg < mmin) mmin = mg;
-            if (d2 > S) pc[npc++] = v;
+            const int holds_member = first[v] < ge && (int64_t)first[v] + count[v] > gb;
+            if (!holds_member) {
+                const double mg = fabs(d2 - S) / S;
+                if (mg < mmin) mmin = mg;
+            }
+            if (d2 > S && !holds_member) pc[npc++] = v;
             else if (nchild[v] == 0) pp[npp++] = v;
             else
                 for (int ch = nchild[v] - 1; ch >= 0; ch--) stack[sp++] = child_first[v] + ch;
@@ -537,7 +544,6 @@ int64_t or_group_lists(int64_t nn, const float* spos, const int32_t* first, cons
                        const double* s_eff, int32_t gb, int32_t gc, int32_t* pc, int64_t* npc_out,
                        int32_t* pp, int64_t* npp_out)
 {
-    (void)first; (void)count;
     double lo[3], hi[3];
     for (int a = 0; a < 3; a++) lo[a] = hi[a] = spos[4 * (int64_t)gb + a];
     for (int64_t k = gb; k < (int64_t)gb + gc; k++)
@@ -560,7 +566,8 @@ int64_t or_group_lists(int64_t nn, const float* spos, const int32_t* first, cons
             else if (c[a] > hi[a]) t = c[a] - hi[a];
             d2 += t * t;
         }
-        if (d2 > s_eff[v]) pc[npc++] = v;
+        const int holds_member = first[v] < gb + gc && first[v] + count[v] > gb;
+        if (d2 > s_eff[v] && !holds_member) pc[npc++] = v;
         else if (nchild[v] == 0) pp[npp++] = v;
         else
             for (int ch = nchild[v] - 1; ch >= 0; ch--) stack[sp++] = child_first[v] + ch;
@@ -574,7 +581,8 @@ int64_t or_group_lists(int64_t nn, const float* spos, const int32_t* first, cons
 /* ------------------------------------------------------------------------
  * Per-particle walk of Fig. 3 / Fig. 5 (the paper's own form): for target i,
  * a node holding a single particle is a particle-particle term; otherwise
- * the node is accepted when d^2 > S_eff with d = |x_i - COM| (Eq. 2); a
+ * the node is accepted when d^2 > S_eff with d = |x_i - COM| (Eq. 2) and
+ * it does not hold particle i itself; a
  * rejected leaf gives particle-particle terms with its members; a rejected
  * internal node is opened.  The self term is skipped by index.  With
  * unsoftened_pc the particle-cell term uses eps = 0 (the Appendix A kernel).
@@ -615,7 +623,8 @@ int or_force_particles(int64_t n, const float* spos, const uint32_t* perm, int64
             const double* c = com_m + 4 * v;
             const double dx = c[0] - xi, dy = c[1] - yi, dz = c[2] - zi;
             const double d2 = dx * dx + dy * dy + dz * dz;
-            if (d2 > s_eff[v]) {
+            const int holds_i = first[v] <= i && i < (int64_t)first[v] + count[v];
+            if (d2 > s_eff[v] && !holds_i) {
                 or_pc(xi, yi, zi, c, quad ? quad + 6 * v : NULL, e2c, acc);
                 cpc++;
             } else if (nchild[v] == 0) {

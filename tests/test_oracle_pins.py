@@ -495,3 +495,22 @@ def test_multipole_convergence_orders(orc):
     s_quad = np.log2(np.array(e_quad[:-1]) / np.array(e_quad[1:]))
     assert np.all(np.abs(s_mono - 2) < 0.35), s_mono
     assert np.all(np.abs(s_quad - 3) < 0.35), s_quad
+
+
+def test_nodes_holding_members_are_opened(orc):
+    # For theta above 1/sqrt(3) Eq. (2) alone could accept a cell that holds the
+    # target; the walks open such cells, so a target never interacts with itself
+    # through a multipole and its own particles all come from opened leaves.
+    p = workloads.plummer(3000, seed=16)
+    box, perm, sk, sp, t, m = _built(orc, p, n_leaf=8, theta=1.0)
+    gf, gc = orc.groups(t, 32)
+    for g in range(0, gf.shape[0], max(1, gf.shape[0] // 50)):
+        pc, pp = orc.group_lists(sp, t, m, gf[g], gc[g])
+        for v in pc:
+            assert t.first[v] >= gf[g] + gc[g] or t.first[v] + t.count[v] <= gf[g]
+    # with theta = 1 the per-particle walk still reproduces the direct sum on a
+    # pair of distant clumps where every term is exact (all particles in leaves)
+    d = orc.direct(p, eps=0.01)
+    res, _ = orc.tree_force(p, 1.0, 0.01, walk="particle")
+    ea, _ = orc.rel_err(res["out"], d)
+    assert np.isfinite(ea).all() and ea.mean() < 0.05
