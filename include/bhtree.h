@@ -1,0 +1,178 @@
+/*
+ * bhtree.h -- C ABI of the GB300 tree-code force evaluation
+ * (N. Nakasato, "Implementation of a Parallel Tree Method on a GPU").
+ *
+ * The library evaluates softened gravitational accelerations and potentials
+ * (Eq. 1) with the tree method of Sec. 4: a Morton ordering of the particles
+ * (Sec. 5), an octree with monopole (and optionally quadrupole) cell moments
+ * (Sec. 4.1, 4.4), a tree walk with the modified opening criterion of Eq. (2),
+ * and softened particle-cell / particle-particle interactions.  Every step
+ * runs in hand-written sm_103a kernels; there is no CPU fallback.
+ *
+ * Conventions for every entry point:
+ *   - pointers named d_* are DEVICE pointers on the context's device; h_* are
+ *     host pointers; nothing else is accepted.
+ *   - particles are float4 records (x, y, z, m), 16-byte aligned, n of them;
+ *     results are float4 records (ax, ay, az, phi) in the caller's order, with
+ *     attractive accelerations and phi = -sum m_j / sqrt(r^2 + eps^2) (the
+ *     paper's p_i is -phi_i).  Gravitational constant G = 1.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls are stream-ordered and asynchronous: they only enqueue
+ *     work.  Device-side failures (non-finite input, capacity, a wait that
+ *     timed out) are recorded in the context's status word and returned by the
+ *     next bh_status() / bh_stats() call, which synchronise the stream.
+ *   - the caller owns every pointer it passes; the context owns its workspace.
+ *   - return value: BH_OK (0) or a negative BH_ERR_* code; bh_strerror()
+ *     names it.  Argument errors are reported before anything is enqueued.
+ */
+#ifndef BHTREE_H
+#define BHTREE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    BH_OK = 0,
+    BH_ERR_INVALID = -1,        /* bad argument (null, misaligned, n < 0, bad theta/eps/config) */
+    BH_ERR_TOO_LARGE = -2,      /* n exceeds the context's max_n, or a size limit */
+    BH_ERR_NONFINITE = -3,      /* a particle coordinate or mass is NaN or infinite */
+    BH_ERR_CAPACITY = -4,       /* a device work list overflowed (walk stack); result invalid */
+    BH_ERR_DEVICE_TIMEOUT = -5, /* a bounded device wait gave up; result invalid */
+    BH_ERR_CUDA = -6,           /* a CUDA runtime call failed */
+    BH_ERR_STATE = -7,          /* call order violated (e.g. tree_force before tree_build) */
+    BH_ERR_NOMEM = -8           /* device allocation failed */
+};
+
+typedef struct bh_ctx bh_ctx;
+
+/* Tunable parameters of one context (bh_config_default fills the defaults). */
+typedef struct bh_config {
+    int leaf_size;           /* n_leaf: a cell with <= n_leaf particles is a leaf (Sec. 4.1
+                                splits down to one particle; n_leaf = 1 is the paper's tree) */
+    int group_size;          /* G: particles per walk group, 1..256 */
+    int order;               /* 1 = monopole (the paper), 2 = monopole + quadrupole */
+    int fp64_node_threshold; /* nodes holding >= this many particles combine moments in FP64 */
+    int block_threads;       /* threads per block of the walk kernel (multiple of 32, 64..1024) */
+    int blocks_per_sm;       /* resident walk blocks per SM for the persistent grid (0 = auto) */
+    int reserved[2];
+} bh_config;
+
+/* Counters of the last evaluation (bh_stats synchronises the stream). */
+typedef struct bh_stats_t {
+    int64_t n;               /* particles of the last tree_build */
+    int64_t n_nodes;         /* tree nodes */
+    int64_t n_leaves;        /* leaf nodes */
+    int64_t n_groups;        /* walk groups */
+    int64_t n_pp;            /* particle-particle interactions of the last tree_force (self excluded) */
+    int64_t n_pc;            /* particle-cell interactions of the last tree_force */
+    int64_t max_leaf_count;  /* largest leaf (only level-10 leaves may exceed leaf_size) */
+    int32_t status;          /* device status word as a BH_* code */
+    int32_t reserved;
+    float box[4];            /* root cube: xmin, ymin, zmin, side L (Sec. 4.1) */
+} bh_stats_t;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int bh_version(void);
+
+/* Human-readable name of a BH_* code (static string, never NULL). */
+const char* bh_strerror(int code);
+
+/* Fill *cfg with the defaults: leaf 8, group 64, order 1, FP64 threshold
+ * 4096, 128 walk threads per block, automatic blocks per SM. */
+void bh_config_default(bh_config* cfg);
+
+/* Create a context on `device` for up to max_n particles (1 <= max_n < 2^30).
+ * Allocates all device workspace up front (about 200 bytes per particle);
+ * later calls allocate nothing.  cfg may be NULL (defaults).
+ * Errors: BH_ERR_INVALID (bad cfg), BH_ERR_TOO_LARGE, BH_ERR_NOMEM, BH_ERR_CUDA. */
+int bh_create(bh_ctx** out, const bh_config* cfg, int64_t max_n, int device);
+
+/* Free a context and its workspace (NULL is ignored).  Synchronises its device. */
+void bh_destroy(bh_ctx* ctx);
+
+/* Steps 1-3 of the paper's flow (Sec. 4.4), on the device: the root cube
+ * (Sec. 4.1), 30-bit Morton keys and a stable radix sort of the particles
+ * into Morton order (Sec. 5), the octree (Sec. 4.1; leaf: <= leaf_size
+ * particles or level 10) and the walk groups.
+ * d_pos_mass: n float4 (x, y, z, m), read only by the work this call
+ * enqueues; the context keeps its own Morton-ordered copy, so the buffer may
+ * be reused once that work has run (stream order).
+ * n = 0 is allowed (tree_force then writes nothing).
+ * Errors: BH_ERR_INVALID, BH_ERR_TOO_LARGE (n > max_n); device status
+ * BH_ERR_NONFINITE for a NaN/Inf coordinate or mass. */
+int tree_build(bh_ctx* ctx, const float* d_pos_mass, int64_t n, void* stream);
+
+/* Step 2 of Sec. 4.4: per node the total mass and centre of mass, the
+ * quadrupole second moment when the context's order is 2, and Eq. (2)'s
+ * effective size S_eff = (l/theta + s)^2 (l = cube side, s = distance from
+ * the cube centre to the centre of mass).  theta > 0.
+ * Errors: BH_ERR_INVALID (theta <= 0 or not finite), BH_ERR_STATE (no tree). */
+int tree_moments(bh_ctx* ctx, float theta, void* stream);
+
+/* Step 5 of Sec. 4.4: the tree walk and force evaluation.  Each group of
+ * particles walks the tree once; a node is accepted when the squared
+ * distance from its centre of mass to the group's bounding box exceeds
+ * S_eff and it holds no group member (Eq. 2 applied to the whole group),
+ * giving a particle-cell term; a rejected leaf gives particle-particle
+ * terms (the target itself excluded); other rejected nodes are opened.
+ * Interactions are FP32 with Kahan-compensated accumulation.
+ * eps >= 0 is the Plummer softening of Eq. (1), applied to both kinds of term.
+ * d_acc_pot: n float4 (ax, ay, az, phi) written in the caller's order.
+ * Errors: BH_ERR_INVALID, BH_ERR_STATE (tree_moments not run after the last
+ * tree_build); device status BH_ERR_CAPACITY or BH_ERR_DEVICE_TIMEOUT. */
+int tree_force(bh_ctx* ctx, float eps, float* d_acc_pot, void* stream);
+
+/* Eq. (1) by direct summation (Sec. 3): for each target t,
+ * a_t = sum_j m_j (x_j - x_t) / (|x_j - x_t|^2 + eps^2)^1.5 and
+ * phi_t = -sum_j m_j / (|x_j - x_t|^2 + eps^2)^0.5 over all sources j except
+ * d_tgt_self[t] (an index into the sources, or -1; d_tgt_self may be NULL).
+ * d_src: n_src float4 (x, y, z, m); d_tgt: n_tgt float4 (x, y, z, ignored).
+ * precision 32: FP32 interactions, Kahan-compensated, d_out = n_tgt float4;
+ * precision 64: FP64 throughout, d_out = n_tgt double4 (the error judge).
+ * No context is needed; nothing is allocated.
+ * Errors: BH_ERR_INVALID (bad pointer/alignment/precision, eps < 0),
+ * BH_ERR_TOO_LARGE (n_src or n_tgt >= 2^31). */
+int direct_force(const float* d_src, int64_t n_src, const float* d_tgt, const int64_t* d_tgt_self,
+                 int64_t n_tgt, double eps, void* d_out, int precision, void* stream);
+
+/* Synchronise `stream` and return the context's device status as a BH_*
+ * code (BH_OK if no device-side error was recorded since the last call;
+ * the status is then cleared). */
+int bh_status(bh_ctx* ctx, void* stream);
+
+/* Synchronise `stream`, then report counters of the last build/evaluation
+ * and the status word (not cleared). */
+int bh_stats(bh_ctx* ctx, void* stream, bh_stats_t* out);
+
+/* Copy an internal array of the last build into caller memory (device or
+ * host: the copy direction is inferred), for inspection and tests.
+ * what: BH_EXPORT_* below; cap_bytes: capacity of dst.  *out_bytes receives
+ * the byte count of the array.  Stream-ordered; synchronises the stream to
+ * read the array's current length.
+ * Errors: BH_ERR_INVALID, BH_ERR_TOO_LARGE (cap_bytes too small), BH_ERR_STATE. */
+enum {
+    BH_EXPORT_KEYS = 1,        /* uint32[n]   Morton keys in Morton order */
+    BH_EXPORT_PERM = 2,        /* uint32[n]   caller index of each Morton-ordered particle */
+    BH_EXPORT_SPOS = 3,        /* float4[n]   particles in Morton order */
+    BH_EXPORT_NODE_FIRST = 4,  /* int32[nn]   first particle (Morton position) of each node */
+    BH_EXPORT_NODE_COUNT = 5,  /* int32[nn]   particle count of each node */
+    BH_EXPORT_NODE_CHILD = 6,  /* int32[nn]   index of the first child, -1 for leaves */
+    BH_EXPORT_NODE_NCHILD = 7, /* int32[nn]   number of children (0 for leaves) */
+    BH_EXPORT_NODE_LEVEL = 8,  /* int32[nn]   level (0 = root cube) */
+    BH_EXPORT_COM_M = 9,       /* float4[nn]  centre of mass and mass */
+    BH_EXPORT_SEFF = 10,       /* float[nn]   S_eff of Eq. (2) */
+    BH_EXPORT_QUAD = 11,       /* float[nn*6] second moments xx, yy, zz, xy, xz, yz (order 2) */
+    BH_EXPORT_GROUP_FIRST = 12,/* int32[ng]   first particle of each group */
+    BH_EXPORT_GROUP_COUNT = 13,/* int32[ng]   particles per group */
+    BH_EXPORT_BOX = 14         /* float[4]    xmin, ymin, zmin, L */
+};
+int bh_export(bh_ctx* ctx, int what, void* dst, int64_t cap_bytes, int64_t* out_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BHTREE_H */

@@ -1,0 +1,254 @@
+"""Python binding of libbhtree, the GB300 tree-code force evaluation.
+
+Argument marshalling only: every step of the evaluation runs in the CUDA
+library (include/bhtree.h).  PyTorch supplies device memory and streams.
+The binding raises if the compiled library is missing; there is no fallback.
+
+Functions keep the C names: bh_create / tree_build / tree_moments /
+tree_force / direct_force / bh_status / bh_stats / bh_export, and
+`Context` bundles them for one particle-set capacity.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libbhtree.so")
+
+BH_OK = 0
+BH_ERR_INVALID = -1
+BH_ERR_TOO_LARGE = -2
+BH_ERR_NONFINITE = -3
+BH_ERR_CAPACITY = -4
+BH_ERR_DEVICE_TIMEOUT = -5
+BH_ERR_CUDA = -6
+BH_ERR_STATE = -7
+BH_ERR_NOMEM = -8
+
+EXPORT = dict(keys=1, perm=2, spos=3, node_first=4, node_count=5, node_child=6, node_nchild=7,
+              node_level=8, com_m=9, seff=10, quad=11, group_first=12, group_count=13, box=14)
+
+# the symbols declared in include/bhtree.h
+SYMBOLS = ["bh_version", "bh_strerror", "bh_config_default", "bh_create", "bh_destroy", "tree_build",
+           "tree_moments", "tree_force", "direct_force", "bh_status", "bh_stats", "bh_export"]
+
+
+class BhConfig(ctypes.Structure):
+    _fields_ = [("leaf_size", ctypes.c_int), ("group_size", ctypes.c_int), ("order", ctypes.c_int),
+                ("fp64_node_threshold", ctypes.c_int), ("block_threads", ctypes.c_int),
+                ("blocks_per_sm", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+
+
+class BhStats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
+                ("n_groups", ctypes.c_int64), ("n_pp", ctypes.c_int64), ("n_pc", ctypes.c_int64),
+                ("max_leaf_count", ctypes.c_int64), ("status", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("box", ctypes.c_float * 4)]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "box")}
+        d["box"] = list(self.box)
+        return d
+
+
+class BhError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__("%s: %s (%d)" % (what, _lib_or_none_strerror(code), code))
+
+
+_lib = None
+
+
+def _lib_or_none_strerror(code):
+    try:
+        return lib().bh_strerror(code).decode()
+    except Exception:  # library missing while formatting an error
+        return "error"
+
+
+def lib():
+    """Load libbhtree.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libbhtree.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        L.bh_version.restype = i32
+        L.bh_strerror.argtypes = [i32]
+        L.bh_strerror.restype = ctypes.c_char_p
+        L.bh_config_default.argtypes = [ctypes.POINTER(BhConfig)]
+        L.bh_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(BhConfig), i64, i32]
+        L.bh_create.restype = i32
+        L.bh_destroy.argtypes = [vp]
+        L.tree_build.argtypes = [vp, vp, i64, vp]
+        L.tree_build.restype = i32
+        L.tree_moments.argtypes = [vp, ctypes.c_float, vp]
+        L.tree_moments.restype = i32
+        L.tree_force.argtypes = [vp, ctypes.c_float, vp, vp]
+        L.tree_force.restype = i32
+        L.direct_force.argtypes = [vp, i64, vp, vp, i64, ctypes.c_double, vp, i32, vp]
+        L.direct_force.restype = i32
+        L.bh_status.argtypes = [vp, vp]
+        L.bh_status.restype = i32
+        L.bh_stats.argtypes = [vp, vp, ctypes.POINTER(BhStats)]
+        L.bh_stats.restype = i32
+        L.bh_export.argtypes = [vp, i32, vp, i64, ctypes.POINTER(ctypes.c_int64), vp]
+        L.bh_export.restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(rc, what):
+    if rc != BH_OK:
+        raise BhError(rc, what)
+
+
+def _stream(stream):
+    """cudaStream_t of a torch stream (None = torch's current stream)."""
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def config(**kw):
+    c = BhConfig()
+    lib().bh_config_default(ctypes.byref(c))
+    for k, v in kw.items():
+        if not hasattr(c, k):
+            raise KeyError(k)
+        setattr(c, k, int(v))
+    return c
+
+
+def bh_create(cfg, max_n, device=0):
+    h = ctypes.c_void_p()
+    _check(lib().bh_create(ctypes.byref(h), ctypes.byref(cfg) if cfg is not None else None,
+                           int(max_n), int(device)), "bh_create")
+    return h
+
+
+def bh_destroy(h):
+    lib().bh_destroy(h)
+
+
+def tree_build(h, pos, n=None, stream=None):
+    n = pos.shape[0] if n is None else n
+    return lib().tree_build(h, _dptr(pos), int(n), _stream(stream))
+
+
+def tree_moments(h, theta, stream=None):
+    return lib().tree_moments(h, ctypes.c_float(theta), _stream(stream))
+
+
+def tree_force(h, eps, out, stream=None):
+    return lib().tree_force(h, ctypes.c_float(eps), _dptr(out), _stream(stream))
+
+
+def direct_force(src, tgt, tgt_self, eps, out, precision, stream=None):
+    """Eq. (1) by direct summation: src (n,4) f32, tgt (m,4) f32, tgt_self (m,) int64
+    or None, out (m,4) f32 (precision 32) or f64 (precision 64)."""
+    return lib().direct_force(_dptr(src), int(src.shape[0]), _dptr(tgt), _dptr(tgt_self),
+                              int(tgt.shape[0]), float(eps), _dptr(out), int(precision), _stream(stream))
+
+
+def bh_status(h, stream=None):
+    return lib().bh_status(h, _stream(stream))
+
+
+def bh_stats(h, stream=None):
+    st = BhStats()
+    _check(lib().bh_stats(h, _stream(stream), ctypes.byref(st)), "bh_stats")
+    return st
+
+
+def bh_export(h, what, dst, stream=None):
+    nb = ctypes.c_int64(0)
+    rc = lib().bh_export(h, EXPORT[what] if isinstance(what, str) else int(what), _dptr(dst),
+                         int(dst.numel() * dst.element_size()), ctypes.byref(nb), _stream(stream))
+    return rc, nb.value
+
+
+class Context:
+    """One tree context on a CUDA device (owns the library's workspace)."""
+
+    def __init__(self, max_n, device=0, **cfg):
+        self.cfg = config(**cfg)
+        self.device = int(device)
+        self.max_n = int(max_n)
+        self.h = bh_create(self.cfg, self.max_n, self.device)
+
+    def close(self):
+        if self.h:
+            bh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def build(self, pos, stream=None):
+        _check(tree_build(self.h, pos, stream=stream), "tree_build")
+
+    def moments(self, theta, stream=None):
+        _check(tree_moments(self.h, theta, stream), "tree_moments")
+
+    def force(self, eps, out, stream=None):
+        _check(tree_force(self.h, eps, out, stream), "tree_force")
+
+    def evaluate(self, pos, theta, eps, out=None, stream=None):
+        """Whole force evaluation (build, moments, walk); returns (n, 4) f32 on the device."""
+        import torch
+        if out is None:
+            out = torch.empty_like(pos)
+        self.build(pos, stream)
+        self.moments(theta, stream)
+        self.force(eps, out, stream)
+        return out
+
+    def status(self, stream=None):
+        return bh_status(self.h, stream)
+
+    def stats(self, stream=None):
+        return bh_stats(self.h, stream).as_dict()
+
+    def export(self, what, stream=None):
+        """Copy an internal array to a new host numpy array."""
+        import torch
+        dt = {"keys": torch.int32, "perm": torch.int32, "spos": torch.float32, "com_m": torch.float32,
+              "seff": torch.float32, "quad": torch.float32, "box": torch.float32}.get(what, torch.int32)
+        cap = max(self.max_n, 1) * 16 + 64
+        if what not in ("keys", "perm", "spos", "group_first", "group_count", "box"):
+            cap = (self.max_n + 10 * (self.max_n // (self.cfg.leaf_size + 1)) + 1) * 32
+        buf = torch.empty(cap // 4, dtype=dt, device="cuda:%d" % self.device)
+        rc, nb = bh_export(self.h, what, buf, stream)
+        _check(rc, "bh_export(%s)" % what)
+        a = buf[: nb // 4].cpu().numpy()
+        if what in ("keys", "perm"):
+            a = a.view(np.uint32)
+        if what in ("spos", "com_m"):
+            a = a.reshape(-1, 4)
+        if what == "quad":
+            a = a.reshape(-1, 6)
+        return a
+
+
+def direct(src, tgt=None, tgt_self=None, eps=0.0, precision=32, stream=None):
+    """Convenience: direct sum on torch CUDA tensors; with tgt=None every
+    particle is a target and skips itself."""
+    import torch
+    if tgt is None:
+        tgt = src
+        tgt_self = torch.arange(src.shape[0], device=src.device, dtype=torch.int64)
+    out = torch.empty((tgt.shape[0], 4), device=src.device,
+                      dtype=torch.float64 if precision == 64 else torch.float32)
+    _check(direct_force(src, tgt, tgt_self, eps, out, precision, stream), "direct_force")
+    return out

@@ -1,0 +1,423 @@
+// bh_api.cu -- the C ABI of libbhtree (declared in include/bhtree.h).
+//
+// A context owns one device slab holding every work array for up to max_n
+// particles, so tree_build / tree_moments / tree_force allocate nothing and
+// never synchronise: the whole evaluation is stream-ordered and can be
+// captured in a CUDA graph.  Device-side failures land in the control block's
+// status word, read back by bh_status / bh_stats.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "bh_internal.cuh"
+
+struct bh_ctx {
+    int device = 0;
+    int sm_count = 1;
+    bh_config cfg{};
+    int64_t max_n = 0;
+    int64_t node_cap = 0;
+    int64_t n = -1;  // particles of the last tree_build (-1: none)
+    bool have_moments = false;
+    float theta = 0.f;
+    unsigned int sort_epoch = 0;
+    void* slab = nullptr;
+    bh_dev_ctrl* ctrl = nullptr;
+    bh_dev_ctrl* host_ctrl = nullptr;  // pinned staging for read-back
+    float4* pos_s = nullptr;
+    uint32_t *keys = nullptr, *keys_alt = nullptr, *vals = nullptr, *vals_alt = nullptr;
+    unsigned long long* lookback = nullptr;
+    uint8_t* dl = nullptr;
+    uint32_t* blk = nullptr;
+    uint8_t* flags = nullptr;
+    int32_t *g_first = nullptr, *g_count = nullptr;
+    bh_nodes nd{};
+};
+
+namespace {
+
+int grid_for(const bh_ctx* c) { return c->sm_count * 8; }
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// true if p is a device pointer usable on `device` (device or managed memory)
+bool is_device_ptr(const void* p, int device)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int d)
+    {
+        cudaGetDevice(&prev);
+        if (prev != d) cudaSetDevice(d);
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" {
+
+int bh_version(void) { return 10000; }
+
+const char* bh_strerror(int code)
+{
+    switch (code) {
+        case BH_OK: return "ok";
+        case BH_ERR_INVALID: return "invalid argument";
+        case BH_ERR_TOO_LARGE: return "size exceeds a limit";
+        case BH_ERR_NONFINITE: return "non-finite particle coordinate or mass";
+        case BH_ERR_CAPACITY: return "device work list capacity exceeded";
+        case BH_ERR_DEVICE_TIMEOUT: return "bounded device wait timed out";
+        case BH_ERR_CUDA: return "CUDA runtime error";
+        case BH_ERR_STATE: return "call order violated";
+        case BH_ERR_NOMEM: return "device allocation failed";
+        default: return "unknown error";
+    }
+}
+
+void bh_config_default(bh_config* cfg)
+{
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->leaf_size = 8;
+    cfg->group_size = 64;
+    cfg->order = 1;
+    cfg->fp64_node_threshold = 4096;
+    cfg->block_threads = 128;
+    cfg->blocks_per_sm = 0;
+}
+
+static int validate_config(const bh_config* c)
+{
+    if (c->leaf_size < 1 || c->leaf_size > 64) return BH_ERR_INVALID;
+    if (c->group_size < 1 || c->group_size > 256) return BH_ERR_INVALID;
+    if (c->order != 1 && c->order != 2) return BH_ERR_INVALID;
+    if (c->fp64_node_threshold < 1) return BH_ERR_INVALID;
+    if (c->block_threads != 64 && c->block_threads != 128 && c->block_threads != 256) return BH_ERR_INVALID;
+    if (c->blocks_per_sm < 0 || c->blocks_per_sm > 32) return BH_ERR_INVALID;
+    return BH_OK;
+}
+
+int bh_create(bh_ctx** out, const bh_config* cfg, int64_t max_n, int device)
+{
+    if (!out) return BH_ERR_INVALID;
+    *out = nullptr;
+    bh_config c;
+    if (cfg) c = *cfg;
+    else bh_config_default(&c);
+    int rc = validate_config(&c);
+    if (rc) return rc;
+    if (max_n < 1) return BH_ERR_INVALID;
+    if (max_n >= (int64_t)1 << 30) return BH_ERR_TOO_LARGE;
+    const int64_t node_cap = max_n + 10 * (max_n / (c.leaf_size + 1)) + 1;
+    if (node_cap >= (int64_t)1 << 28) return BH_ERR_TOO_LARGE;  // walk stack packs node ids in 28 bits
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return BH_ERR_INVALID;
+    }
+    DeviceGuard guard(device);
+    bh_ctx* x = new (std::nothrow) bh_ctx();
+    if (!x) return BH_ERR_NOMEM;
+    x->device = device;
+    x->cfg = c;
+    x->max_n = max_n;
+    x->node_cap = node_cap;
+    cudaDeviceGetAttribute(&x->sm_count, cudaDevAttrMultiProcessorCount, device);
+
+    const size_t N = (size_t)max_n, NN = (size_t)node_cap;
+    const size_t sort_tiles = (N + bh::kSortTile - 1) / bh::kSortTile;
+    const size_t lvl_blocks = (N + bh::kLevelTile - 1) / bh::kLevelTile;
+    const size_t flag_blocks = (N + bh::kFlagTile - 1) / bh::kFlagTile;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    const size_t o_ctrl = take(sizeof(bh_dev_ctrl));
+    const size_t o_pos = take(N * sizeof(float4));
+    const size_t o_keys = take(N * 4), o_keys2 = take(N * 4), o_vals = take(N * 4), o_vals2 = take(N * 4);
+    const size_t o_look = take(sort_tiles * 256 * sizeof(unsigned long long));
+    const size_t o_dl = take(N);
+    const size_t o_blk = take(std::max(lvl_blocks * 11, flag_blocks) * 4);
+    const size_t o_flags = take(flag_blocks * bh::kFlagTile);
+    const size_t o_gf = take(N * 4), o_gc = take(N * 4);
+    const size_t o_first = take(NN * 4), o_count = take(NN * 4), o_child = take(NN * 4), o_nch = take(NN * 4);
+    const size_t o_level = take(NN);
+    const size_t o_rec = take(NN * sizeof(int4));
+    const size_t o_com = take(NN * sizeof(float4));
+    const size_t o_seff = take(NN * 4);
+    const size_t o_quad = c.order >= 2 ? take(NN * 2 * sizeof(float4)) : 0;
+    const size_t o_com64 = take(NN * sizeof(bh_double4));
+    const size_t o_quad64 = c.order >= 2 ? take(NN * 6 * sizeof(double)) : 0;
+    const size_t total = off;
+
+    if (cudaMalloc(&x->slab, total) != cudaSuccess) {
+        cudaGetLastError();
+        delete x;
+        return BH_ERR_NOMEM;
+    }
+    if (cudaMallocHost((void**)&x->host_ctrl, sizeof(bh_dev_ctrl)) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(x->slab);
+        delete x;
+        return BH_ERR_NOMEM;
+    }
+    char* b = (char*)x->slab;
+    x->ctrl = (bh_dev_ctrl*)(b + o_ctrl);
+    x->pos_s = (float4*)(b + o_pos);
+    x->keys = (uint32_t*)(b + o_keys);
+    x->keys_alt = (uint32_t*)(b + o_keys2);
+    x->vals = (uint32_t*)(b + o_vals);
+    x->vals_alt = (uint32_t*)(b + o_vals2);
+    x->lookback = (unsigned long long*)(b + o_look);
+    x->dl = (uint8_t*)(b + o_dl);
+    x->blk = (uint32_t*)(b + o_blk);
+    x->flags = (uint8_t*)(b + o_flags);
+    x->g_first = (int32_t*)(b + o_gf);
+    x->g_count = (int32_t*)(b + o_gc);
+    x->nd.first = (int32_t*)(b + o_first);
+    x->nd.count = (int32_t*)(b + o_count);
+    x->nd.child = (int32_t*)(b + o_child);
+    x->nd.nchild = (int32_t*)(b + o_nch);
+    x->nd.level = (uint8_t*)(b + o_level);
+    x->nd.rec = (int4*)(b + o_rec);
+    x->nd.com_m = (float4*)(b + o_com);
+    x->nd.seff = (float*)(b + o_seff);
+    x->nd.quad = c.order >= 2 ? (float4*)(b + o_quad) : nullptr;
+    x->nd.com64 = (bh_double4*)(b + o_com64);
+    x->nd.quad64 = c.order >= 2 ? (double*)(b + o_quad64) : nullptr;
+    // look-back words start at epoch 0, which no pass uses; control block zeroed
+    if (cudaMemset(x->lookback, 0, sort_tiles * 256 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(x->ctrl, 0, sizeof(bh_dev_ctrl)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(x->host_ctrl);
+        cudaFree(x->slab);
+        delete x;
+        return BH_ERR_CUDA;
+    }
+    *out = x;
+    return BH_OK;
+}
+
+void bh_destroy(bh_ctx* x)
+{
+    if (!x) return;
+    DeviceGuard guard(x->device);
+    cudaDeviceSynchronize();
+    cudaFreeHost(x->host_ctrl);
+    cudaFree(x->slab);
+    delete x;
+}
+
+int tree_build(bh_ctx* x, const float* d_pos_mass, int64_t n, void* stream)
+{
+    if (!x) return BH_ERR_INVALID;
+    if (n < 0) return BH_ERR_INVALID;
+    if (n > x->max_n) return BH_ERR_TOO_LARGE;
+    if (n > 0 && (!d_pos_mass || !aligned16(d_pos_mass) || !is_device_ptr(d_pos_mass, x->device)))
+        return BH_ERR_INVALID;
+    DeviceGuard guard(x->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int N = (int)n;
+    const float4* pos = (const float4*)d_pos_mass;
+    bh::launch_init(x->ctrl, s);
+    if (N > 0) {
+        bh::launch_bbox(pos, N, x->ctrl, grid_for(x), s);
+        bh::launch_keys(pos, N, x->ctrl, x->keys, grid_for(x), s);
+        bh::launch_sort(x->keys, x->keys_alt, x->vals, x->vals_alt, pos, x->pos_s, N, x->lookback,
+                        &x->sort_epoch, x->ctrl, s);
+        bh::launch_tree(x->keys, N, x->cfg.leaf_size, x->dl, x->blk, x->nd, x->node_cap, x->ctrl, grid_for(x), s);
+        bh::launch_groups(x->nd, N, x->cfg.group_size, x->flags, x->blk, x->g_first, x->g_count, x->ctrl,
+                          grid_for(x), s);
+    }
+    if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
+    x->n = n;
+    x->have_moments = false;
+    return BH_OK;
+}
+
+int tree_moments(bh_ctx* x, float theta, void* stream)
+{
+    if (!x) return BH_ERR_INVALID;
+    if (!(theta > 0.0f) || !std::isfinite(theta)) return BH_ERR_INVALID;
+    if (x->n < 0) return BH_ERR_STATE;
+    DeviceGuard guard(x->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (x->n > 0)
+        bh::launch_moments(x->pos_s, x->keys, x->nd, x->cfg.order, theta, x->cfg.fp64_node_threshold, x->ctrl,
+                           grid_for(x), s);
+    if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
+    x->theta = theta;
+    x->have_moments = true;
+    return BH_OK;
+}
+
+int tree_force(bh_ctx* x, float eps, float* d_acc_pot, void* stream)
+{
+    if (!x) return BH_ERR_INVALID;
+    if (!(eps >= 0.0f) || !std::isfinite(eps)) return BH_ERR_INVALID;
+    if (x->n < 0 || !x->have_moments) return BH_ERR_STATE;
+    if (x->n == 0) return BH_OK;
+    if (!d_acc_pot || !aligned16(d_acc_pot) || !is_device_ptr(d_acc_pot, x->device)) return BH_ERR_INVALID;
+    DeviceGuard guard(x->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = bh::launch_walk(x->pos_s, x->vals, x->g_first, x->g_count, x->nd, x->cfg.order, x->cfg.group_size,
+                             eps, (float4*)d_acc_pot, x->ctrl, x->sm_count, x->cfg.block_threads,
+                             x->cfg.blocks_per_sm, s);
+    if (rc) return rc;
+    if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
+    return BH_OK;
+}
+
+int direct_force(const float* d_src, int64_t n_src, const float* d_tgt, const int64_t* d_tgt_self, int64_t n_tgt,
+                 double eps, void* d_out, int precision, void* stream)
+{
+    if (n_src < 0 || n_tgt < 0) return BH_ERR_INVALID;
+    if (n_src >= ((int64_t)1 << 31) || n_tgt >= ((int64_t)1 << 31)) return BH_ERR_TOO_LARGE;
+    if (precision != 32 && precision != 64) return BH_ERR_INVALID;
+    if (!(eps >= 0.0) || !std::isfinite(eps)) return BH_ERR_INVALID;
+    if (n_tgt == 0) return BH_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BH_ERR_CUDA;
+    if (!d_tgt || !aligned16(d_tgt) || !is_device_ptr(d_tgt, dev)) return BH_ERR_INVALID;
+    if (!d_out || !aligned16(d_out) || !is_device_ptr(d_out, dev)) return BH_ERR_INVALID;
+    if (n_src > 0 && (!d_src || !aligned16(d_src) || !is_device_ptr(d_src, dev))) return BH_ERR_INVALID;
+    if (d_tgt_self && (((uintptr_t)d_tgt_self & 7u) || !is_device_ptr(d_tgt_self, dev))) return BH_ERR_INVALID;
+    return bh::launch_direct((const float4*)d_src, (int)n_src, (const float4*)d_tgt, d_tgt_self, (int)n_tgt, eps,
+                             d_out, precision, (cudaStream_t)stream);
+}
+
+static int read_ctrl(bh_ctx* x, cudaStream_t s)
+{
+    if (cudaMemcpyAsync(x->host_ctrl, x->ctrl, sizeof(bh_dev_ctrl), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return BH_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return BH_ERR_CUDA;
+    return BH_OK;
+}
+
+int bh_status(bh_ctx* x, void* stream)
+{
+    if (!x) return BH_ERR_INVALID;
+    DeviceGuard guard(x->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = read_ctrl(x, s);
+    if (rc) return rc;
+    const int st = -(int)x->host_ctrl->status;
+    if (st != 0) {
+        const unsigned int zero[2] = {0u, 0u};
+        cudaMemcpyAsync(&x->ctrl->status, zero, sizeof(zero), cudaMemcpyHostToDevice, s);
+        cudaStreamSynchronize(s);
+    }
+    return st;
+}
+
+int bh_stats(bh_ctx* x, void* stream, bh_stats_t* out)
+{
+    if (!x || !out) return BH_ERR_INVALID;
+    DeviceGuard guard(x->device);
+    int rc = read_ctrl(x, (cudaStream_t)stream);
+    if (rc) return rc;
+    const bh_dev_ctrl& h = *x->host_ctrl;
+    std::memset(out, 0, sizeof(*out));
+    out->n = x->n < 0 ? 0 : x->n;
+    out->n_nodes = h.level_offset[11];
+    out->n_leaves = h.n_leaves;
+    out->n_groups = h.n_groups;
+    out->n_pp = (int64_t)h.n_pp;
+    out->n_pc = (int64_t)h.n_pc;
+    out->max_leaf_count = h.max_leaf;
+    out->status = -(int)h.status;
+    for (int i = 0; i < 4; i++) out->box[i] = h.box[i];
+    return BH_OK;
+}
+
+int bh_export(bh_ctx* x, int what, void* dst, int64_t cap_bytes, int64_t* out_bytes, void* stream)
+{
+    if (!x || !dst) return BH_ERR_INVALID;
+    if (x->n < 0) return BH_ERR_STATE;
+    DeviceGuard guard(x->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = read_ctrl(x, s);
+    if (rc) return rc;
+    const int64_t n = x->n, nn = x->host_ctrl->level_offset[11], ng = x->host_ctrl->n_groups;
+    const void* src = nullptr;
+    int64_t bytes = 0;
+    switch (what) {
+        case BH_EXPORT_KEYS: src = x->keys; bytes = n * 4; break;
+        case BH_EXPORT_PERM: src = x->vals; bytes = n * 4; break;
+        case BH_EXPORT_SPOS: src = x->pos_s; bytes = n * 16; break;
+        case BH_EXPORT_NODE_FIRST: src = x->nd.first; bytes = nn * 4; break;
+        case BH_EXPORT_NODE_COUNT: src = x->nd.count; bytes = nn * 4; break;
+        case BH_EXPORT_NODE_CHILD: src = x->nd.child; bytes = nn * 4; break;
+        case BH_EXPORT_NODE_NCHILD: src = x->nd.nchild; bytes = nn * 4; break;
+        case BH_EXPORT_NODE_LEVEL: src = nullptr; bytes = nn * 4; break;
+        case BH_EXPORT_COM_M: src = x->nd.com_m; bytes = nn * 16; break;
+        case BH_EXPORT_SEFF: src = x->nd.seff; bytes = nn * 4; break;
+        case BH_EXPORT_QUAD:
+            if (x->cfg.order < 2) return BH_ERR_STATE;
+            src = nullptr;
+            bytes = nn * 24;
+            break;
+        case BH_EXPORT_GROUP_FIRST: src = x->g_first; bytes = ng * 4; break;
+        case BH_EXPORT_GROUP_COUNT: src = x->g_count; bytes = ng * 4; break;
+        case BH_EXPORT_BOX: src = x->ctrl->box; bytes = 16; break;
+        default: return BH_ERR_INVALID;
+    }
+    if (out_bytes) *out_bytes = bytes;
+    if (cap_bytes < bytes) return BH_ERR_TOO_LARGE;
+    if (bytes == 0) return BH_OK;
+    if (what == BH_EXPORT_NODE_LEVEL || what == BH_EXPORT_QUAD) {
+        // widen / unpack through a host copy
+        const bool lev = what == BH_EXPORT_NODE_LEVEL;
+        const size_t hb = lev ? (size_t)nn : (size_t)nn * 32;
+        void* h = std::malloc(hb ? hb : 1);
+        if (!h) return BH_ERR_NOMEM;
+        void* hout = std::malloc((size_t)bytes);
+        if (!hout) {
+            std::free(h);
+            return BH_ERR_NOMEM;
+        }
+        cudaMemcpyAsync(h, lev ? (const void*)x->nd.level : (const void*)x->nd.quad, hb, cudaMemcpyDeviceToHost, s);
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            std::free(h);
+            std::free(hout);
+            return BH_ERR_CUDA;
+        }
+        if (lev) {
+            for (int64_t i = 0; i < nn; i++) ((int32_t*)hout)[i] = ((const uint8_t*)h)[i];
+        } else {
+            const float* q = (const float*)h;
+            float* o = (float*)hout;
+            for (int64_t i = 0; i < nn; i++)
+                for (int k = 0; k < 6; k++) o[6 * i + k] = q[8 * i + k];
+        }
+        const cudaError_t e = cudaMemcpy(dst, hout, (size_t)bytes, cudaMemcpyDefault);
+        std::free(h);
+        std::free(hout);
+        return e == cudaSuccess ? BH_OK : BH_ERR_CUDA;
+    }
+    if (cudaMemcpyAsync(dst, src, (size_t)bytes, cudaMemcpyDefault, s) != cudaSuccess) return BH_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return BH_ERR_CUDA;
+    return BH_OK;
+}
+
+}  // extern "C"

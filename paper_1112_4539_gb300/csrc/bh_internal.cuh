@@ -1,0 +1,181 @@
+// bh_internal.cuh -- device-side layout shared by the kernels of libbhtree.
+//
+// Everything here belongs to the CUDA library; nothing is shared with the CPU
+// oracle.  Tree conventions (Sec. 4.1, Sec. 5 of the paper, with this
+// library's readings):
+//   * 30-bit Morton keys, 10 bits per axis, x in the high bit of each triple;
+//   * node = non-empty cell of the 2^l grid (l = 0..10) whose parent cell holds
+//     more than n_leaf particles; leaf = holds <= n_leaf particles or l == 10;
+//   * nodes are stored breadth first (sorted by level, then first particle),
+//     so the children of a node are contiguous.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/bhtree.h"
+
+#define BH_MAX_LEVEL 10
+#define BH_FULL_MASK 0xffffffffu
+
+// ------------------------------------------------------------------ control
+// One control block per context, in device memory.  Reset at every
+// tree_build by bh_init_kernel (tree_force resets its own counters).
+struct bh_dev_ctrl {
+    unsigned int minmax[6];      // ordered-uint encoded min x,y,z then max x,y,z
+    float box[4];                // xmin, ymin, zmin, L  (written by the keys kernel)
+    float inv;                   // 1024 / L
+    unsigned int status;         // first device-side error, as -BH_ERR_* (0 = ok)
+    unsigned int abort;          // set with status: waiting kernels give up early
+    unsigned int hist[4][256];   // upfront digit histograms of the 4 sort passes
+    unsigned int tile_ctr[4];    // onesweep tile tickets, one per pass
+    unsigned int level_total[12];
+    unsigned int level_offset[12];  // first node of each level; [11] = node count
+    unsigned int n_leaves;
+    unsigned int max_leaf;
+    unsigned int n_groups;
+    unsigned int group_ctr;      // walk work queue
+    unsigned long long n_pp;
+    unsigned long long n_pc;
+    unsigned int pad[8];
+};
+
+// Record a device-side error (first one wins) and raise the abort flag.
+__device__ __forceinline__ void bh_set_error(bh_dev_ctrl* c, int code)
+{
+    atomicCAS(&c->status, 0u, (unsigned int)(-code));
+    atomicExch(&c->abort, 1u);
+}
+
+// Order-preserving map float -> uint (for atomicMin/Max on floats).
+__device__ __forceinline__ unsigned int bh_f2ord(float f)
+{
+    const unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float bh_ord2f(unsigned int u)
+{
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+// Spread the low 10 bits of v to every third bit (bit k -> bit 3k).
+__device__ __forceinline__ unsigned int bh_spread3(unsigned int v)
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+// Inverse of bh_spread3.
+__device__ __forceinline__ unsigned int bh_compact3(unsigned int v)
+{
+    v &= 0x09249249u;
+    v = (v | (v >> 2)) & 0x030c30c3u;
+    v = (v | (v >> 4)) & 0x0300f00fu;
+    v = (v | (v >> 8)) & 0x030000ffu;
+    v = (v | (v >> 16)) & 0x000003ffu;
+    return v;
+}
+
+// Deepest level whose cell holds both keys (0..10); keys of one cell share
+// their top 3*l bits.
+__device__ __forceinline__ int bh_common_level(unsigned int a, unsigned int b)
+{
+    const unsigned int x = a ^ b;
+    if (x == 0u) return BH_MAX_LEVEL;
+    return (BH_MAX_LEVEL - 1) - (31 - __clz((int)x)) / 3;
+}
+
+// Root cube from the reduced bounds (same rule as the build's first kernel).
+__device__ __forceinline__ void bh_box_from_minmax(const unsigned int* mm, float* box, float* inv)
+{
+    const float lo0 = bh_ord2f(mm[0]), lo1 = bh_ord2f(mm[1]), lo2 = bh_ord2f(mm[2]);
+    const float hi0 = bh_ord2f(mm[3]), hi1 = bh_ord2f(mm[4]), hi2 = bh_ord2f(mm[5]);
+    float L = __fsub_rn(hi0, lo0);
+    const float L1 = __fsub_rn(hi1, lo1), L2 = __fsub_rn(hi2, lo2);
+    if (L1 > L) L = L1;
+    if (L2 > L) L = L2;
+    float iv = __fdiv_rn(1024.0f, L);
+    if (!(L > 0.0f) || !isfinite(iv)) {
+        L = 1.0f;
+        iv = 1024.0f;
+    }
+    box[0] = lo0;
+    box[1] = lo1;
+    box[2] = lo2;
+    box[3] = L;
+    *inv = iv;
+}
+
+// ---------------------------------------------------------- warp helpers
+__device__ __forceinline__ unsigned int bh_lanemask_lt()
+{
+    unsigned int m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ int bh_warp_incl_scan(int v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(BH_FULL_MASK, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// 32-byte FP64 vector (x, y, z, w)
+struct __align__(32) bh_double4 {
+    double x, y, z, w;
+};
+
+// ------------------------------------------------------------- node arrays
+// Node record read by the walk: first particle, count, first child (-1 for
+// leaves), number of children.
+struct bh_nodes {
+    int32_t* first;
+    int32_t* count;
+    int32_t* child;
+    int32_t* nchild;
+    uint8_t* level;
+    int4* rec;        // (first, count, child, nchild) packed for the walk
+    float4* com_m;    // centre of mass, mass
+    float* seff;      // S_eff of Eq. (2)
+    float4* quad;     // 2 per node: (xx, yy, zz, xy), (xz, yz, 1.5 T, 0.5 T)
+    bh_double4* com64;   // FP64 centre of mass + mass (nodes above the FP64 threshold)
+    double* quad64;   // 6 per node (FP64 nodes, order 2)
+};
+
+// --------------------------------------------------------------- launches
+// (bodies in the .cu files; all are stream-ordered and take device pointers)
+namespace bh {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per tile
+constexpr int kLevelTile = 2048;                       // positions per node-build block
+constexpr int kFlagTile = 4096;                        // positions per group-compaction block
+
+void launch_init(bh_dev_ctrl* ctrl, cudaStream_t s);
+void launch_bbox(const float4* pos, int n, bh_dev_ctrl* ctrl, int grid, cudaStream_t s);
+void launch_keys(const float4* pos, int n, bh_dev_ctrl* ctrl, uint32_t* keys, int grid, cudaStream_t s);
+void launch_sort(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
+                 const float4* pos, float4* pos_s, int n, unsigned long long* lookback,
+                 unsigned int* epoch, bh_dev_ctrl* ctrl, cudaStream_t s);
+void launch_tree(const uint32_t* keys, int n, int n_leaf, uint8_t* dl, uint32_t* blk_lvl,
+                 const bh_nodes& nd, int64_t node_cap, bh_dev_ctrl* ctrl, int grid, cudaStream_t s);
+void launch_groups(const bh_nodes& nd, int n, int G, uint8_t* flags, uint32_t* blk, int32_t* g_first,
+                   int32_t* g_count, bh_dev_ctrl* ctrl, int grid, cudaStream_t s);
+void launch_moments(const float4* pos_s, const uint32_t* keys, const bh_nodes& nd, int order,
+                    float theta, int fp64_threshold, bh_dev_ctrl* ctrl, int grid, cudaStream_t s);
+int launch_walk(const float4* pos_s, const uint32_t* perm, const int32_t* g_first, const int32_t* g_count,
+                const bh_nodes& nd, int order, int G, float eps, float4* out, bh_dev_ctrl* ctrl,
+                int sm_count, int block_threads, int blocks_per_sm, cudaStream_t s);
+int launch_direct(const float4* src, int n_src, const float4* tgt, const int64_t* self, int n_tgt,
+                  double eps, void* out, int precision, cudaStream_t s);
+
+}  // namespace bh

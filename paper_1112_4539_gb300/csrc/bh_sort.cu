@@ -1,0 +1,299 @@
+// bh_sort.cu -- root cube, Morton keys and the onesweep radix sort.
+//
+// Sec. 4.1: the root cell is a cube enclosing every particle (origin = the
+// per-axis minimum, side = the largest extent).  Sec. 5: particles are put in
+// Morton order, here by a stable least-significant-digit radix sort of 30-bit
+// keys in the single-pass "onesweep" form (Adinets & Merrill 2022): one
+// upfront histogram pass fused into key generation, then one kernel per 8-bit
+// digit that ranks a tile, resolves its global offsets by decoupled look-back
+// and scatters through shared memory.  The last pass also gathers the float4
+// particles into Morton order.
+#include "bh_internal.cuh"
+
+namespace bh {
+
+// ------------------------------------------------------------ init / bbox
+
+__global__ void bh_init_kernel(bh_dev_ctrl* c)
+{
+    const int t = threadIdx.x;
+    if (t < 3) {
+        c->minmax[t] = 0xffffffffu;
+        c->minmax[3 + t] = 0u;
+    }
+    for (int i = t; i < 4 * 256; i += blockDim.x) (&c->hist[0][0])[i] = 0u;
+    if (t < 4) c->tile_ctr[t] = 0u;
+    if (t < 12) {
+        c->level_total[t] = 0u;
+        c->level_offset[t] = 0u;
+    }
+    if (t == 0) {
+        c->status = 0u;
+        c->abort = 0u;
+        c->n_leaves = 0u;
+        c->max_leaf = 0u;
+        c->n_groups = 0u;
+        c->group_ctr = 0u;
+        c->n_pp = 0ull;
+        c->n_pc = 0ull;
+    }
+}
+
+void launch_init(bh_dev_ctrl* ctrl, cudaStream_t s) { bh_init_kernel<<<1, 256, 0, s>>>(ctrl); }
+
+// Per-axis min/max over all particles; flags NaN/Inf coordinates or masses.
+__global__ void __launch_bounds__(256) bh_bbox_kernel(const float4* __restrict__ pos, int n, bh_dev_ctrl* c)
+{
+    unsigned int lo0 = 0xffffffffu, lo1 = 0xffffffffu, lo2 = 0xffffffffu, hi0 = 0u, hi1 = 0u, hi2 = 0u;
+    bool bad = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 p = pos[i];
+        bad |= !(isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(p.w));
+        const unsigned int ox = bh_f2ord(p.x), oy = bh_f2ord(p.y), oz = bh_f2ord(p.z);
+        lo0 = min(lo0, ox); lo1 = min(lo1, oy); lo2 = min(lo2, oz);
+        hi0 = max(hi0, ox); hi1 = max(hi1, oy); hi2 = max(hi2, oz);
+    }
+    lo0 = __reduce_min_sync(BH_FULL_MASK, lo0);
+    lo1 = __reduce_min_sync(BH_FULL_MASK, lo1);
+    lo2 = __reduce_min_sync(BH_FULL_MASK, lo2);
+    hi0 = __reduce_max_sync(BH_FULL_MASK, hi0);
+    hi1 = __reduce_max_sync(BH_FULL_MASK, hi1);
+    hi2 = __reduce_max_sync(BH_FULL_MASK, hi2);
+    const bool anybad = __any_sync(BH_FULL_MASK, bad);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(&c->minmax[0], lo0);
+        atomicMin(&c->minmax[1], lo1);
+        atomicMin(&c->minmax[2], lo2);
+        atomicMax(&c->minmax[3], hi0);
+        atomicMax(&c->minmax[4], hi1);
+        atomicMax(&c->minmax[5], hi2);
+        if (anybad) atomicCAS(&c->status, 0u, (unsigned int)(-BH_ERR_NONFINITE));
+    }
+}
+
+void launch_bbox(const float4* pos, int n, bh_dev_ctrl* ctrl, int grid, cudaStream_t s)
+{
+    bh_bbox_kernel<<<grid, 256, 0, s>>>(pos, n, ctrl);
+}
+
+// ------------------------------------------------------------------ keys
+// q = (x - xmin) * (1024 / L) as two separately rounded FP32 operations,
+// c = min(trunc(q), 1023); bit k of cx, cy, cz -> key bit 3k+2, 3k+1, 3k.
+// The four digit histograms of the sort (bits 0-7, 8-15, 16-23, 24-29) are
+// accumulated on the way.
+__global__ void __launch_bounds__(256) bh_keys_kernel(const float4* __restrict__ pos, int n, bh_dev_ctrl* c,
+                                                      uint32_t* __restrict__ keys)
+{
+    __shared__ unsigned int sh[4][256];
+    __shared__ float sbox[4];
+    __shared__ float sinv;
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&sh[0][0])[i] = 0u;
+    if (threadIdx.x == 0) {
+        bh_box_from_minmax(c->minmax, sbox, &sinv);
+        if (blockIdx.x == 0) {
+            c->box[0] = sbox[0];
+            c->box[1] = sbox[1];
+            c->box[2] = sbox[2];
+            c->box[3] = sbox[3];
+            c->inv = sinv;
+        }
+    }
+    __syncthreads();
+    const float x0 = sbox[0], y0 = sbox[1], z0 = sbox[2], inv = sinv;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 p = pos[i];
+        const unsigned int cx = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.x, x0), inv)), 1023u);
+        const unsigned int cy = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.y, y0), inv)), 1023u);
+        const unsigned int cz = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.z, z0), inv)), 1023u);
+        const unsigned int k = (bh_spread3(cx) << 2) | (bh_spread3(cy) << 1) | bh_spread3(cz);
+        keys[i] = k;
+        atomicAdd(&sh[0][k & 255u], 1u);
+        atomicAdd(&sh[1][(k >> 8) & 255u], 1u);
+        atomicAdd(&sh[2][(k >> 16) & 255u], 1u);
+        atomicAdd(&sh[3][(k >> 24) & 255u], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
+        const unsigned int v = (&sh[0][0])[i];
+        if (v) atomicAdd(&(&c->hist[0][0])[i], v);
+    }
+}
+
+void launch_keys(const float4* pos, int n, bh_dev_ctrl* ctrl, uint32_t* keys, int grid, cudaStream_t s)
+{
+    bh_keys_kernel<<<grid, 256, 0, s>>>(pos, n, ctrl, keys);
+}
+
+// ------------------------------------------------------------- onesweep
+// Look-back status word: epoch (32 bits) | flag (2 bits) | value (30 bits).
+// flag 1 = tile aggregate only, 2 = inclusive prefix.  The epoch changes at
+// every pass, so stale words from earlier passes read as "not ready" and the
+// array never needs clearing.
+constexpr unsigned int kFlagAgg = 1u, kFlagPrefix = 2u;
+constexpr int kSpinLimit = 1 << 22;
+
+__device__ __forceinline__ unsigned long long bh_status_word(unsigned int epoch, unsigned int flag, unsigned int v)
+{
+    return ((unsigned long long)epoch << 32) | ((unsigned long long)flag << 30) | (unsigned long long)(v & 0x3fffffffu);
+}
+
+// Exclusive scan of one value per thread over a 256-thread block.
+__device__ __forceinline__ unsigned int bh_block_excl_scan256(unsigned int v, unsigned int* warp_tot)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int t = __shfl_up_sync(BH_FULL_MASK, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) warp_tot[w] = incl;
+    __syncthreads();
+    unsigned int base = 0;
+    for (int i = 0; i < w; i++) base += warp_tot[i];
+    __syncthreads();
+    return base + incl - v;
+}
+
+template <bool FIRST, bool LAST>
+__global__ void __launch_bounds__(kSortThreads)
+bh_onesweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+                   uint32_t* __restrict__ vout, const float4* __restrict__ pos, float4* __restrict__ pos_s, int n,
+                   int shift, int pass, unsigned int epoch, unsigned long long* lookback, bh_dev_ctrl* c)
+{
+    constexpr int W = kSortThreads / 32;
+    __shared__ uint32_t s_keys[kSortTile];
+    __shared__ uint32_t s_vals[kSortTile];
+    __shared__ unsigned int s_whist[W][256];
+    __shared__ unsigned int s_start[256];  // tile-local start of each digit
+    __shared__ int s_base[256];            // global position of a digit's first tile-local slot
+    __shared__ unsigned int s_wtot[W];
+    __shared__ int s_tile;
+
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    if (tid == 0) s_tile = (int)atomicAdd(&c->tile_ctr[pass], 1u);
+    for (int i = tid; i < W * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0u;
+    __syncthreads();
+    const int tile = s_tile;
+    const int base = tile * kSortTile;
+    if (base >= n) return;
+    const int tile_n = min(kSortTile, n - base);
+
+    // warp-striped load: item k of lane l of warp w is tile position w*512 + k*32 + l
+    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+#pragma unroll
+    for (int k = 0; k < kSortItems; k++) {
+        const int p = base + w * (32 * kSortItems) + k * 32 + lane;
+        const bool ok = p < n;
+        key[k] = ok ? kin[p] : 0xffffffffu;
+        val[k] = FIRST ? (uint32_t)p : (ok ? vin[p] : 0u);
+    }
+    // stable rank within the warp, item by item
+    const unsigned int lt = bh_lanemask_lt();
+#pragma unroll
+    for (int k = 0; k < kSortItems; k++) {
+        const int p = base + w * (32 * kSortItems) + k * 32 + lane;
+        const bool ok = p < n;
+        const unsigned int d = ok ? ((key[k] >> shift) & 255u) : 256u;
+        const unsigned int peers = __match_any_sync(BH_FULL_MASK, d);
+        unsigned int prior = 0u;
+        if (ok) prior = s_whist[w][d];
+        __syncwarp();
+        if (ok && lane == __ffs(peers) - 1) s_whist[w][d] = prior + __popc(peers);
+        __syncwarp();
+        rank[k] = prior + __popc(peers & lt);
+    }
+    __syncthreads();
+
+    // per digit (thread = digit): exclusive over warps, tile count
+    const int d = tid;
+    unsigned int run = 0u;
+#pragma unroll
+    for (int i = 0; i < W; i++) {
+        const unsigned int t = s_whist[i][d];
+        s_whist[i][d] = run;
+        run += t;
+    }
+    const unsigned int tile_cnt = run;
+    unsigned long long* my = lookback + (size_t)tile * 256 + d;
+    if (tile == 0) {
+        *(volatile unsigned long long*)my = bh_status_word(epoch, kFlagPrefix, tile_cnt);
+    } else {
+        *(volatile unsigned long long*)my = bh_status_word(epoch, kFlagAgg, tile_cnt);
+    }
+    const unsigned int tstart = bh_block_excl_scan256(tile_cnt, s_wtot);
+    const unsigned int goff = bh_block_excl_scan256(c->hist[pass][d], s_wtot);
+
+    // decoupled look-back over earlier tiles (bounded waits)
+    unsigned int prefix = 0u;
+    if (tile > 0) {
+        int j = tile - 1;
+        bool timed_out = false;
+        while (j >= 0) {
+            const volatile unsigned long long* q = lookback + (size_t)j * 256 + d;
+            unsigned long long st = *q;
+            int spins = 0;
+            while ((unsigned int)(st >> 32) != epoch || ((st >> 30) & 3ull) == 0ull) {
+                if (++spins > kSpinLimit || *(volatile unsigned int*)&c->abort) {
+                    timed_out = true;
+                    break;
+                }
+                __nanosleep(32);
+                st = *q;
+            }
+            if (timed_out) break;
+            prefix += (unsigned int)(st & 0x3fffffffull);
+            if (((st >> 30) & 3ull) == kFlagPrefix) break;
+            j--;
+        }
+        if (timed_out) bh_set_error(c, BH_ERR_DEVICE_TIMEOUT);
+        *(volatile unsigned long long*)my = bh_status_word(epoch, kFlagPrefix, prefix + tile_cnt);
+    }
+    s_start[d] = tstart;
+    s_base[d] = (int)(goff + prefix) - (int)tstart;
+    __syncthreads();
+
+    // scatter into shared memory in sorted order
+#pragma unroll
+    for (int k = 0; k < kSortItems; k++) {
+        const int p = base + w * (32 * kSortItems) + k * 32 + lane;
+        if (p < n) {
+            const unsigned int dg = (key[k] >> shift) & 255u;
+            const unsigned int sp = s_start[dg] + s_whist[w][dg] + rank[k];
+            s_keys[sp] = key[k];
+            s_vals[sp] = val[k];
+        }
+    }
+    __syncthreads();
+    // write out: runs of equal digits go to consecutive global positions
+    for (int i = tid; i < tile_n; i += kSortThreads) {
+        const uint32_t kk = s_keys[i];
+        const uint32_t vv = s_vals[i];
+        const int dest = s_base[(kk >> shift) & 255u] + i;
+        if (dest >= 0 && dest < n) {
+            kout[dest] = kk;
+            vout[dest] = vv;
+            if (LAST) pos_s[dest] = pos[vv < (uint32_t)n ? vv : 0u];
+        }
+    }
+}
+
+// Four passes: bits 0-7, 8-15, 16-23, 24-29.  keys/vals end in keys/vals;
+// vals[k] = caller index of the k-th particle in Morton order.
+void launch_sort(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals, uint32_t* vals_alt, const float4* pos,
+                 float4* pos_s, int n, unsigned long long* lookback, unsigned int* epoch, bh_dev_ctrl* ctrl,
+                 cudaStream_t s)
+{
+    if (n <= 0) return;
+    const int tiles = (n + kSortTile - 1) / kSortTile;
+    bh_onesweep_kernel<true, false><<<tiles, kSortThreads, 0, s>>>(keys, nullptr, keys_alt, vals_alt, pos, pos_s,
+                                                                     n, 0, 0, ++*epoch, lookback, ctrl);
+    bh_onesweep_kernel<false, false><<<tiles, kSortThreads, 0, s>>>(keys_alt, vals_alt, keys, vals, pos, pos_s, n,
+                                                                      8, 1, ++*epoch, lookback, ctrl);
+    bh_onesweep_kernel<false, false><<<tiles, kSortThreads, 0, s>>>(keys, vals, keys_alt, vals_alt, pos, pos_s, n,
+                                                                      16, 2, ++*epoch, lookback, ctrl);
+    bh_onesweep_kernel<false, true><<<tiles, kSortThreads, 0, s>>>(keys_alt, vals_alt, keys, vals, pos, pos_s, n,
+                                                                     24, 3, ++*epoch, lookback, ctrl);
+}
+
+}  // namespace bh

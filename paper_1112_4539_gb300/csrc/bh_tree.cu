@@ -1,0 +1,573 @@
+// bh_tree.cu -- octree over Morton-sorted keys, cell moments, walk groups.
+//
+// Sec. 4.1 builds the octree by recursive subdivision of the root cube; here
+// the same tree is read off the sorted keys in parallel.  For Morton position
+// k let d_k be the deepest level whose cell holds both particles k-1 and k
+// (-1 for k = 0): the cells starting at k are those of levels d_k+1 .. 10.
+// A level-l cell is a node iff its parent cell holds more than n_leaf
+// particles; a window of n_leaf+1 consecutive particles shares a level-l cell
+// iff its end keys share their top 3l bits, so with W_k = the largest such
+// shared level over the windows containing k, the nodes containing k are the
+// levels 0 .. lambda_k = min(10, W_k + 1), the deepest being k's leaf.  Node
+// (k, l) therefore exists for d_k < l <= lambda_k.  Breadth-first order
+// (level, then first particle) gives each node its index by a per-level rank.
+//
+// Sec. 4.4 (host steps 2-3 of the paper's flow) computes the cell mass,
+// centre of mass and effective size S_eff = (l/theta + s)^2 (Eq. 2); here a
+// bottom-up pass per level, leaves from their particles, internal nodes from
+// their (contiguous) children, FP64 for nodes above a particle-count
+// threshold.
+#include "bh_internal.cuh"
+
+namespace bh {
+
+constexpr int kLvlThreads = 256;
+constexpr int kLvlPer = kLevelTile / kLvlThreads;  // 8 positions per thread
+constexpr int kMaxLeaf = 64;
+
+// ------------------------------------------------------------ pass 1
+// dl[k] = (d_k + 1) | (lambda_k << 4); per-block node counts per level.
+__global__ void __launch_bounds__(kLvlThreads)
+bh_levels_kernel(const uint32_t* __restrict__ keys, int n, int n_leaf, uint8_t* __restrict__ dl,
+                 uint32_t* __restrict__ blk_lvl, int nblk)
+{
+    __shared__ uint32_t sk[kLevelTile + 2 * kMaxLeaf + 2];
+    __shared__ int8_t sw[kLevelTile + kMaxLeaf + 1];
+    __shared__ unsigned int scnt[kLvlThreads / 32][12];
+    const int tid = threadIdx.x;
+    const int base = blockIdx.x * kLevelTile;
+    const int lo = base - n_leaf - 1;
+    const int span = kLevelTile + 2 * n_leaf + 1;
+    for (int i = tid; i < span; i += kLvlThreads) {
+        const int p = lo + i;
+        sk[i] = (p >= 0 && p < n) ? keys[p] : 0u;
+    }
+    __syncthreads();
+    // w_j for j in [base - n_leaf, base + kLevelTile): common level of the window [j, j + n_leaf]
+    for (int i = tid; i < kLevelTile + n_leaf; i += kLvlThreads) {
+        const int j = base - n_leaf + i;
+        int wv = -1;
+        if (j >= 0 && j + n_leaf < n) wv = bh_common_level(sk[j - lo], sk[j + n_leaf - lo]);
+        sw[i] = (int8_t)wv;
+    }
+    __syncthreads();
+    unsigned int cnt[11];
+#pragma unroll
+    for (int l = 0; l < 11; l++) cnt[l] = 0u;
+    for (int r = 0; r < kLvlPer; r++) {
+        const int k = base + tid * kLvlPer + r;
+        if (k >= n) break;
+        const int d = (k == 0) ? -1 : bh_common_level(sk[k - 1 - lo], sk[k - lo]);
+        int W = -1;
+        const int j0 = max(0, k - n_leaf);
+        for (int j = j0; j <= k; j++) W = max(W, (int)sw[j - (base - n_leaf)]);
+        const int lam = min(BH_MAX_LEVEL, W + 1);
+        dl[k] = (uint8_t)((d + 1) | (lam << 4));
+#pragma unroll
+        for (int l = 0; l < 11; l++) cnt[l] += (l > d && l <= lam) ? 1u : 0u;
+    }
+    const int lane = tid & 31, w = tid >> 5;
+#pragma unroll
+    for (int l = 0; l < 11; l++) {
+        const unsigned int s = __reduce_add_sync(BH_FULL_MASK, cnt[l]);
+        if (lane == 0) scnt[w][l] = s;
+    }
+    __syncthreads();
+    if (tid < 11) {
+        unsigned int s = 0u;
+        for (int i = 0; i < kLvlThreads / 32; i++) s += scnt[i][tid];
+        blk_lvl[(size_t)tid * nblk + blockIdx.x] = s;
+    }
+}
+
+// 1024-thread block: exclusive scan of v (one per thread), returns the total.
+__device__ unsigned int bh_block_scan1024(unsigned int& v, unsigned int* wtot)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int t = __shfl_up_sync(BH_FULL_MASK, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wtot[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        unsigned int x = (lane < (int)(blockDim.x >> 5)) ? wtot[lane] : 0u;
+        unsigned int xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int t = __shfl_up_sync(BH_FULL_MASK, xi, o);
+            if (lane >= o) xi += t;
+        }
+        wtot[lane] = xi - x;
+        if (lane == 31) wtot[32] = xi;
+    }
+    __syncthreads();
+    const unsigned int total = wtot[32];
+    v = wtot[w] + incl - v;
+    __syncthreads();
+    return total;
+}
+
+// In-place exclusive scan of `len` values with one 1024-thread block.
+__device__ unsigned int bh_scan_segment(uint32_t* a, int len, unsigned int* wtot)
+{
+    const int per = (len + 1023) / 1024;
+    const int b0 = threadIdx.x * per;
+    unsigned int s = 0u;
+    for (int i = 0; i < per; i++)
+        if (b0 + i < len) s += a[b0 + i];
+    unsigned int ex = s;
+    const unsigned int total = bh_block_scan1024(ex, wtot);
+    unsigned int run = ex;
+    for (int i = 0; i < per; i++)
+        if (b0 + i < len) {
+            const unsigned int t = a[b0 + i];
+            a[b0 + i] = run;
+            run += t;
+        }
+    __syncthreads();
+    return total;
+}
+
+// ------------------------------------------------------------ pass 2
+__global__ void __launch_bounds__(1024) bh_level_scan_kernel(uint32_t* blk_lvl, int nblk, bh_dev_ctrl* c,
+                                                             long long node_cap)
+{
+    __shared__ unsigned int wtot[33];
+    __shared__ unsigned int tot[11];
+    for (int l = 0; l < 11; l++) {
+        const unsigned int t = bh_scan_segment(blk_lvl + (size_t)l * nblk, nblk, wtot);
+        if (threadIdx.x == 0) tot[l] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long run = 0ull;
+        for (int l = 0; l < 11; l++) {
+            c->level_total[l] = tot[l];
+            c->level_offset[l] = (unsigned int)run;
+            run += tot[l];
+        }
+        if ((long long)run > node_cap) {
+            bh_set_error(c, BH_ERR_CAPACITY);
+            run = 0ull;  // later kernels see an empty tree
+            for (int l = 0; l < 11; l++) c->level_offset[l] = 0u;
+        }
+        c->level_offset[11] = (unsigned int)run;
+    }
+}
+
+// ------------------------------------------------------------ pass 3
+// Write (first, level, child) of every node at its breadth-first index.
+__global__ void __launch_bounds__(kLvlThreads)
+bh_node_write_kernel(const uint8_t* __restrict__ dl, int n, const uint32_t* __restrict__ blk_lvl, int nblk,
+                     const bh_dev_ctrl* __restrict__ c, int32_t* __restrict__ nfirst, uint8_t* __restrict__ nlevel,
+                     int32_t* __restrict__ nchildidx)
+{
+    __shared__ unsigned int swt[kLvlThreads / 32][11];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int base = blockIdx.x * kLevelTile;
+    if (c->level_offset[11] == 0u) return;  // capacity error (or empty)
+    uint8_t my[kLvlPer];
+    unsigned int cnt[11];
+#pragma unroll
+    for (int l = 0; l < 11; l++) cnt[l] = 0u;
+#pragma unroll
+    for (int r = 0; r < kLvlPer; r++) {
+        const int k = base + tid * kLvlPer + r;
+        my[r] = (k < n) ? dl[k] : (uint8_t)(11 | (0 << 4));  // d+1 = 11 > lambda: no node
+        const int d = (int)(my[r] & 15) - 1, lam = my[r] >> 4;
+#pragma unroll
+        for (int l = 0; l < 11; l++) cnt[l] += (l > d && l <= lam) ? 1u : 0u;
+    }
+    // per-level exclusive scan over the block (thread order = position order)
+    unsigned int ex[11];
+#pragma unroll
+    for (int l = 0; l < 11; l++) {
+        unsigned int incl = cnt[l];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int t = __shfl_up_sync(BH_FULL_MASK, incl, o);
+            if (lane >= o) incl += t;
+        }
+        ex[l] = incl - cnt[l];
+        if (lane == 31) swt[w][l] = incl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int l = 0; l < 11; l++) {
+        unsigned int b = c->level_offset[l] + blk_lvl[(size_t)l * nblk + blockIdx.x];
+        for (int i = 0; i < w; i++) b += swt[i][l];
+        ex[l] += b;
+    }
+#pragma unroll
+    for (int r = 0; r < kLvlPer; r++) {
+        const int k = base + tid * kLvlPer + r;
+        const int d = (int)(my[r] & 15) - 1, lam = my[r] >> 4;
+        int below = -1;  // index of node (k, l+1)
+#pragma unroll
+        for (int l = 10; l >= 0; l--) {
+            if (l > d && l <= lam) {
+                const int idx = (int)ex[l]++;
+                nfirst[idx] = k;
+                nlevel[idx] = (uint8_t)l;
+                nchildidx[idx] = (l < lam) ? below : -1;
+                below = idx;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ pass 4
+// Particle count of each node (end of its key range by galloping search),
+// number of children, packed walk record, leaf statistics.
+__global__ void __launch_bounds__(256)
+bh_node_finalize_kernel(const uint32_t* __restrict__ keys, int n, bh_nodes nd, bh_dev_ctrl* c)
+{
+    const int nn = (int)c->level_offset[11];
+    unsigned int leaves = 0u, maxleaf = 0u;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
+        const int l = nd.level[v];
+        const int k = nd.first[v];
+        int end = n;
+        if (l > 0) {
+            const int sh = 3 * (BH_MAX_LEVEL - l);
+            const unsigned int target = ((keys[k] >> sh) + 1u) << sh;
+            int lo = k, hi = k + 1, step = 1;
+            while (hi < n && keys[hi] < target) {
+                lo = hi;
+                step <<= 1;
+                hi = k + step;
+            }
+            if (hi > n) hi = n;
+            while (hi - lo > 1) {
+                const int mid = lo + ((hi - lo) >> 1);
+                if (keys[mid] < target) lo = mid;
+                else hi = mid;
+            }
+            end = hi;
+        }
+        const int cnt = end - k;
+        const int ch = nd.child[v];
+        int nch = 0;
+        if (ch >= 0) {
+            const int lim = (int)c->level_offset[l + 2];
+            nch = 1;
+            while (nch < 8 && ch + nch < lim && nd.first[ch + nch] < end) nch++;
+        } else {
+            leaves++;
+            maxleaf = max(maxleaf, (unsigned int)cnt);
+        }
+        nd.count[v] = cnt;
+        nd.nchild[v] = nch;
+        nd.rec[v] = make_int4(k, cnt, ch, nch);
+    }
+    leaves = __reduce_add_sync(BH_FULL_MASK, leaves);
+    maxleaf = __reduce_max_sync(BH_FULL_MASK, maxleaf);
+    if ((threadIdx.x & 31) == 0) {
+        if (leaves) atomicAdd(&c->n_leaves, leaves);
+        if (maxleaf) atomicMax(&c->max_leaf, maxleaf);
+    }
+}
+
+void launch_tree(const uint32_t* keys, int n, int n_leaf, uint8_t* dl, uint32_t* blk_lvl, const bh_nodes& nd,
+                 int64_t node_cap, bh_dev_ctrl* ctrl, int grid, cudaStream_t s)
+{
+    if (n <= 0) return;
+    const int nblk = (n + kLevelTile - 1) / kLevelTile;
+    bh_levels_kernel<<<nblk, kLvlThreads, 0, s>>>(keys, n, n_leaf, dl, blk_lvl, nblk);
+    bh_level_scan_kernel<<<1, 1024, 0, s>>>(blk_lvl, nblk, ctrl, (long long)node_cap);
+    bh_node_write_kernel<<<nblk, kLvlThreads, 0, s>>>(dl, n, blk_lvl, nblk, ctrl, nd.first, nd.level, nd.child);
+    bh_node_finalize_kernel<<<grid, 256, 0, s>>>(keys, n, nd, ctrl);
+}
+
+// ------------------------------------------------------------ groups
+// Mark the first particle of every group (see the group rule in the walk
+// documentation): children of an internal node holding > G particles are
+// packed in octant order into runs of <= G particles; a leaf holding > G
+// particles is cut into chunks of G; a root holding <= G is one group.
+__global__ void __launch_bounds__(256) bh_group_mark_kernel(bh_nodes nd, int G, uint8_t* __restrict__ flags,
+                                                            const bh_dev_ctrl* __restrict__ c)
+{
+    const int nn = (int)c->level_offset[11];
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
+        const int4 r = nd.rec[v];
+        if (v == 0) {
+            if (r.y <= G) flags[r.x] = 1;
+            else if (r.z < 0)
+                for (int j = 0; j < r.y; j += G) flags[r.x + j] = 1;
+        }
+        if (r.z < 0 || r.y <= G) continue;
+        int run_first = -1, run = 0;
+        for (int ci = 0; ci < r.w; ci++) {
+            const int4 q = nd.rec[r.z + ci];
+            if (q.y <= G) {
+                if (run_first >= 0 && run + q.y <= G) {
+                    run += q.y;
+                } else {
+                    if (run_first >= 0) flags[run_first] = 1;
+                    run_first = q.x;
+                    run = q.y;
+                }
+            } else {
+                if (run_first >= 0) flags[run_first] = 1;
+                run_first = -1;
+                run = 0;
+                if (q.z < 0)
+                    for (int j = 0; j < q.y; j += G) flags[q.x + j] = 1;
+            }
+        }
+        if (run_first >= 0) flags[run_first] = 1;
+    }
+}
+
+constexpr int kFlagThreads = 256;
+constexpr int kFlagPer = kFlagTile / kFlagThreads;  // 16 bytes per thread
+
+__global__ void __launch_bounds__(kFlagThreads) bh_flag_count_kernel(const uint8_t* __restrict__ flags, int n,
+                                                                     uint32_t* __restrict__ blk)
+{
+    __shared__ unsigned int ws[kFlagThreads / 32];
+    const int base = blockIdx.x * kFlagTile + threadIdx.x * kFlagPer;
+    unsigned int s = 0u;
+    if (base + kFlagPer <= n) {
+        const uint4 q = *reinterpret_cast<const uint4*>(flags + base);
+        s = __popc(q.x) + __popc(q.y) + __popc(q.z) + __popc(q.w);  // flags are 0/1 bytes
+    } else {
+        for (int i = base; i < n && i < base + kFlagPer; i++) s += flags[i];
+    }
+    s = __reduce_add_sync(BH_FULL_MASK, s);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int t = 0u;
+        for (int i = 0; i < kFlagThreads / 32; i++) t += ws[i];
+        blk[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024) bh_flag_scan_kernel(uint32_t* blk, int nblk, bh_dev_ctrl* c)
+{
+    __shared__ unsigned int wtot[33];
+    const unsigned int t = bh_scan_segment(blk, nblk, wtot);
+    if (threadIdx.x == 0) c->n_groups = t;
+}
+
+__global__ void __launch_bounds__(kFlagThreads)
+bh_flag_write_kernel(const uint8_t* __restrict__ flags, int n, const uint32_t* __restrict__ blk,
+                     int32_t* __restrict__ g_first)
+{
+    __shared__ unsigned int ws[kFlagThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const int base = blockIdx.x * kFlagTile + tid * kFlagPer;
+    uint8_t f[kFlagPer];
+    unsigned int s = 0u;
+#pragma unroll
+    for (int i = 0; i < kFlagPer; i++) {
+        f[i] = (base + i < n) ? flags[base + i] : (uint8_t)0;
+        s += f[i];
+    }
+    unsigned int incl = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int t = __shfl_up_sync(BH_FULL_MASK, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) ws[w] = incl;
+    __syncthreads();
+    unsigned int idx = blk[blockIdx.x] + incl - s;
+    for (int i = 0; i < w; i++) idx += ws[i];
+#pragma unroll
+    for (int i = 0; i < kFlagPer; i++)
+        if (f[i]) g_first[idx++] = base + i;
+}
+
+__global__ void __launch_bounds__(256) bh_group_count_kernel(const int32_t* __restrict__ g_first,
+                                                             int32_t* __restrict__ g_count, int n,
+                                                             const bh_dev_ctrl* __restrict__ c)
+{
+    const int ng = (int)c->n_groups;
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < ng; g += gridDim.x * blockDim.x)
+        g_count[g] = ((g + 1 < ng) ? g_first[g + 1] : n) - g_first[g];
+}
+
+void launch_groups(const bh_nodes& nd, int n, int G, uint8_t* flags, uint32_t* blk, int32_t* g_first,
+                   int32_t* g_count, bh_dev_ctrl* ctrl, int grid, cudaStream_t s)
+{
+    if (n <= 0) return;
+    const int nblk = (n + kFlagTile - 1) / kFlagTile;
+    cudaMemsetAsync(flags, 0, (size_t)nblk * kFlagTile, s);
+    bh_group_mark_kernel<<<grid, 256, 0, s>>>(nd, G, flags, ctrl);
+    bh_flag_count_kernel<<<nblk, kFlagThreads, 0, s>>>(flags, n, blk);
+    bh_flag_scan_kernel<<<1, 1024, 0, s>>>(blk, nblk, ctrl);
+    bh_flag_write_kernel<<<nblk, kFlagThreads, 0, s>>>(flags, n, blk, g_first);
+    bh_group_count_kernel<<<grid, 256, 0, s>>>(g_first, g_count, n, ctrl);
+}
+
+// ------------------------------------------------------------ moments
+template <typename R>
+struct bh_mom {
+    R M, cx, cy, cz, q[6];
+};
+
+template <typename R, int ORDER>
+__device__ __forceinline__ void bh_leaf_moments(const float4* __restrict__ pos_s, int k, int cnt, bh_mom<R>& o,
+                                                bool& massless)
+{
+    const float4 p0 = pos_s[k];
+    const R x0 = p0.x, y0 = p0.y, z0 = p0.z;
+    R M = 0, sx = 0, sy = 0, sz = 0;
+    for (int j = k; j < k + cnt; j++) {
+        const float4 p = pos_s[j];
+        const R m = p.w;
+        M += m;
+        sx += m * ((R)p.x - x0);
+        sy += m * ((R)p.y - y0);
+        sz += m * ((R)p.z - z0);
+    }
+    massless = !(M != (R)0);
+    o.M = M;
+    o.cx = massless ? x0 : x0 + sx / M;
+    o.cy = massless ? y0 : y0 + sy / M;
+    o.cz = massless ? z0 : z0 + sz / M;
+    if (ORDER >= 2) {
+        R q0 = 0, q1 = 0, q2 = 0, q3 = 0, q4 = 0, q5 = 0;
+        for (int j = k; j < k + cnt; j++) {
+            const float4 p = pos_s[j];
+            const R m = p.w;
+            const R a = (R)p.x - o.cx, b = (R)p.y - o.cy, e = (R)p.z - o.cz;
+            q0 += m * a * a;
+            q1 += m * b * b;
+            q2 += m * e * e;
+            q3 += m * a * b;
+            q4 += m * a * e;
+            q5 += m * b * e;
+        }
+        o.q[0] = q0; o.q[1] = q1; o.q[2] = q2; o.q[3] = q3; o.q[4] = q4; o.q[5] = q5;
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ void bh_child_moments(const bh_nodes& nd, int cidx, int fp64_threshold, int order,
+                                                 bh_mom<R>& o)
+{
+    if (sizeof(R) == 8 && nd.count[cidx] >= fp64_threshold) {
+        const bh_double4 c = nd.com64[cidx];
+        o.cx = (R)c.x; o.cy = (R)c.y; o.cz = (R)c.z; o.M = (R)c.w;
+        if (order >= 2)
+            for (int i = 0; i < 6; i++) o.q[i] = (R)nd.quad64[(size_t)cidx * 6 + i];
+    } else {
+        const float4 c = nd.com_m[cidx];
+        o.cx = c.x; o.cy = c.y; o.cz = c.z; o.M = c.w;
+        if (order >= 2) {
+            const float4 a = nd.quad[2 * (size_t)cidx], b = nd.quad[2 * (size_t)cidx + 1];
+            o.q[0] = a.x; o.q[1] = a.y; o.q[2] = a.z; o.q[3] = a.w; o.q[4] = b.x; o.q[5] = b.y;
+        }
+    }
+}
+
+template <typename R, int ORDER>
+__device__ __forceinline__ void bh_internal_moments(const bh_nodes& nd, int ch, int nch, int fp64_threshold,
+                                                    bh_mom<R>& o, bool& massless)
+{
+    bh_mom<R> cm[8];
+    for (int i = 0; i < nch; i++) bh_child_moments<R>(nd, ch + i, fp64_threshold, ORDER, cm[i]);
+    const R x0 = cm[0].cx, y0 = cm[0].cy, z0 = cm[0].cz;
+    R M = 0, sx = 0, sy = 0, sz = 0;
+    for (int i = 0; i < nch; i++) {
+        M += cm[i].M;
+        sx += cm[i].M * (cm[i].cx - x0);
+        sy += cm[i].M * (cm[i].cy - y0);
+        sz += cm[i].M * (cm[i].cz - z0);
+    }
+    massless = !(M != (R)0);
+    o.M = M;
+    o.cx = massless ? x0 : x0 + sx / M;
+    o.cy = massless ? y0 : y0 + sy / M;
+    o.cz = massless ? z0 : z0 + sz / M;
+    if (ORDER >= 2) {
+        R q[6] = {0, 0, 0, 0, 0, 0};
+        for (int i = 0; i < nch; i++) {
+            const R a = cm[i].cx - o.cx, b = cm[i].cy - o.cy, e = cm[i].cz - o.cz, m = cm[i].M;
+            q[0] += cm[i].q[0] + m * a * a;
+            q[1] += cm[i].q[1] + m * b * b;
+            q[2] += cm[i].q[2] + m * e * e;
+            q[3] += cm[i].q[3] + m * a * b;
+            q[4] += cm[i].q[4] + m * a * e;
+            q[5] += cm[i].q[5] + m * b * e;
+        }
+        for (int i = 0; i < 6; i++) o.q[i] = q[i];
+    }
+}
+
+template <int ORDER>
+__global__ void __launch_bounds__(256)
+bh_moments_level_kernel(const float4* __restrict__ pos_s, const uint32_t* __restrict__ keys, bh_nodes nd, int lev,
+                        float theta, int fp64_threshold, const bh_dev_ctrl* __restrict__ c)
+{
+    const int v0 = (int)c->level_offset[lev], v1 = (int)c->level_offset[lev + 1];
+    if (c->level_offset[11] == 0u) return;
+    const float xmin = c->box[0], ymin = c->box[1], zmin = c->box[2], L = c->box[3];
+    const float side = ldexpf(L, -lev);  // exact: power-of-two scaling
+    const float opening = side / theta;
+    for (int v = v0 + blockIdx.x * blockDim.x + threadIdx.x; v < v1; v += gridDim.x * blockDim.x) {
+        const int4 r = nd.rec[v];
+        const bool f64 = r.y >= fp64_threshold;
+        // geometric centre of the node's level-lev cell
+        const unsigned int pref = (lev == 0) ? 0u : (keys[r.x] >> (3 * (BH_MAX_LEVEL - lev)));
+        const float gx = xmin + ((float)bh_compact3(pref >> 2) + 0.5f) * side;
+        const float gy = ymin + ((float)bh_compact3(pref >> 1) + 0.5f) * side;
+        const float gz = zmin + ((float)bh_compact3(pref) + 0.5f) * side;
+        float cx, cy, cz, M, q[6];
+        bool massless;
+        if (f64) {
+            bh_mom<double> o;
+            if (r.z < 0) bh_leaf_moments<double, ORDER>(pos_s, r.x, r.y, o, massless);
+            else bh_internal_moments<double, ORDER>(nd, r.z, r.w, fp64_threshold, o, massless);
+            if (massless) {
+                o.cx = gx; o.cy = gy; o.cz = gz;
+            }
+            nd.com64[v] = bh_double4{o.cx, o.cy, o.cz, o.M};
+            cx = (float)o.cx; cy = (float)o.cy; cz = (float)o.cz; M = (float)o.M;
+            if (ORDER >= 2)
+                for (int i = 0; i < 6; i++) {
+                    nd.quad64[(size_t)v * 6 + i] = o.q[i];
+                    q[i] = (float)o.q[i];
+                }
+        } else {
+            bh_mom<float> o;
+            if (r.z < 0) bh_leaf_moments<float, ORDER>(pos_s, r.x, r.y, o, massless);
+            else bh_internal_moments<float, ORDER>(nd, r.z, r.w, fp64_threshold, o, massless);
+            if (massless) {
+                o.cx = gx; o.cy = gy; o.cz = gz;
+            }
+            cx = o.cx; cy = o.cy; cz = o.cz; M = o.M;
+            if (ORDER >= 2)
+                for (int i = 0; i < 6; i++) q[i] = o.q[i];
+        }
+        nd.com_m[v] = make_float4(cx, cy, cz, M);
+        const float dx = gx - cx, dy = gy - cy, dz = gz - cz;
+        const float s = sqrtf(dx * dx + dy * dy + dz * dz);
+        const float t = opening + s;
+        nd.seff[v] = t * t;
+        if (ORDER >= 2) {
+            const float T = q[0] + q[1] + q[2];
+            nd.quad[2 * (size_t)v] = make_float4(q[0], q[1], q[2], q[3]);
+            nd.quad[2 * (size_t)v + 1] = make_float4(q[4], q[5], 1.5f * T, 0.5f * T);
+        }
+    }
+}
+
+void launch_moments(const float4* pos_s, const uint32_t* keys, const bh_nodes& nd, int order, float theta,
+                    int fp64_threshold, bh_dev_ctrl* ctrl, int grid, cudaStream_t s)
+{
+    for (int lev = BH_MAX_LEVEL; lev >= 0; lev--) {
+        if (order >= 2)
+            bh_moments_level_kernel<2><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, ctrl);
+        else
+            bh_moments_level_kernel<1><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, ctrl);
+    }
+}
+
+}  // namespace bh

@@ -1,0 +1,466 @@
+// bh_walk.cu -- group tree walk and force evaluation (step 5 of the paper's
+// flow, Sec. 4.4; Fig. 3 / Fig. 5 walk, Eq. 1 interactions, Eq. 2 criterion).
+//
+// The paper walks the tree once per particle with the next/more pointers of
+// Fig. 5.  Here one warp walks the tree once for a whole group of up to 32*T
+// Morton-contiguous particles (the GRAPE-style shared interaction list of
+// Sec. 4.2, built on the device): nodes are tested 32 at a time, one per lane,
+// against the group's bounding box.  A node is accepted when the squared
+// distance from its centre of mass to the box exceeds S_eff (Eq. 2 made
+// conservative for every member) and it holds no group member; accepted
+// nodes become particle-cell sources, rejected leaves contribute their
+// particles as particle-particle sources, other rejected nodes are opened.
+// Sources go through a 64-entry ring in shared memory and are evaluated in
+// tiles of 32: every lane applies each source to its T targets (FP32,
+// rsqrtf), each tile's partial sums are added to the running totals with
+// Kahan compensation.  The group's own particles are applied once, as a
+// masked "self" tile, so the target itself is excluded by index.
+//
+// Stack bound: entries are ranges of <= 8 sibling nodes.  A pop takes the top
+// 32 nodes; all entries above the deepest one touched are consumed, so after
+// a pop the stack holds only levels below those popped, and the pushes of one
+// pop (<= 32 ranges) are the only entries of their levels.  Hence at most 33
+// ranges per level 1..10 are ever stored: kStackCap = 352 cannot overflow
+// (overflow is still checked and reported as BH_ERR_CAPACITY).
+#include "bh_internal.cuh"
+
+namespace bh {
+
+constexpr int kStackCap = 352;
+constexpr int kRing = 64;
+
+struct WarpSmem {
+    uint32_t stack[kStackCap];  // (first node << 3) | (count - 1)
+    uint32_t staging[32];
+    int2 leafq[64];             // pending particle ranges (first, count)
+    float4 ring[kRing];         // point sources (x, y, z, m): particles and monopole cells
+};
+struct WarpQuad {
+    float4 a[kRing], b[kRing], c[kRing];  // cell (x, y, z, M), (xx, yy, zz, xy), (xz, yz, 1.5T, 0.5T)
+};
+
+struct WalkParams {
+    const float4* pos_s;
+    const uint32_t* perm;
+    const int32_t* g_first;
+    const int32_t* g_count;
+    const int4* rec;
+    const float4* com_m;
+    const float* seff;
+    const float4* quad;
+    float4* out;
+    bh_dev_ctrl* ctrl;
+    float eps2;
+};
+
+template <int T>
+struct Acc {
+    float x[T], y[T], z[T], p[T];
+    float cx[T], cy[T], cz[T], cp[T];
+};
+
+__device__ __forceinline__ void bh_kahan(float& s, float& c, float v)
+{
+    const float y = __fsub_rn(v, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+}
+
+template <int T>
+__device__ __forceinline__ void bh_add_tile(Acc<T>& A, const float (&tx)[T], const float (&ty)[T],
+                                            const float (&tz)[T], const float (&tp)[T])
+{
+#pragma unroll
+    for (int t = 0; t < T; t++) {
+        bh_kahan(A.x[t], A.cx[t], tx[t]);
+        bh_kahan(A.y[t], A.cy[t], ty[t]);
+        bh_kahan(A.z[t], A.cz[t], tz[t]);
+        bh_kahan(A.p[t], A.cp[t], tp[t]);
+    }
+}
+
+// 32 point sources (particles or monopole cells) on T targets per lane.
+template <int T>
+__device__ __forceinline__ void bh_eval_points(const float4* __restrict__ src, float eps2, const float (&xi)[T],
+                                               const float (&yi)[T], const float (&zi)[T], Acc<T>& A)
+{
+    float tx[T], ty[T], tz[T], tp[T];
+#pragma unroll
+    for (int t = 0; t < T; t++) tx[t] = ty[t] = tz[t] = tp[t] = 0.0f;
+#pragma unroll 8
+    for (int j = 0; j < 32; j++) {
+        const float4 s = src[j];
+#pragma unroll
+        for (int t = 0; t < T; t++) {
+            const float dx = s.x - xi[t], dy = s.y - yi[t], dz = s.z - zi[t];
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+            const float ri = rsqrtf(r2);
+            const float mr = s.w * ri;
+            const float mr3 = mr * ri * ri;
+            tx[t] = fmaf(mr3, dx, tx[t]);
+            ty[t] = fmaf(mr3, dy, ty[t]);
+            tz[t] = fmaf(mr3, dz, tz[t]);
+            tp[t] -= mr;
+        }
+    }
+    bh_add_tile<T>(A, tx, ty, tz, tp);
+}
+
+// 32 quadrupole cells on T targets per lane.  With r = x_i - c, h^2 = r^2 + eps^2,
+// g_n = h^-n, T = tr I, q = r.I.r:
+//   a += -M g3 r + 3 g5 I r + (1.5 T g5 - 7.5 q g7) r
+//   phi += -M g1 - 1.5 q g5 + 0.5 T g3
+template <int T>
+__device__ __forceinline__ void bh_eval_quads(const float4* __restrict__ ca, const float4* __restrict__ cb,
+                                              const float4* __restrict__ cc, float eps2, const float (&xi)[T],
+                                              const float (&yi)[T], const float (&zi)[T], Acc<T>& A)
+{
+    float tx[T], ty[T], tz[T], tp[T];
+#pragma unroll
+    for (int t = 0; t < T; t++) tx[t] = ty[t] = tz[t] = tp[t] = 0.0f;
+#pragma unroll 2
+    for (int j = 0; j < 32; j++) {
+        const float4 a = ca[j], b = cb[j], c = cc[j];
+#pragma unroll
+        for (int t = 0; t < T; t++) {
+            const float rx = xi[t] - a.x, ry = yi[t] - a.y, rz = zi[t] - a.z;
+            const float h2 = fmaf(rz, rz, fmaf(ry, ry, fmaf(rx, rx, eps2)));
+            const float g1 = rsqrtf(h2);
+            const float g2 = g1 * g1;
+            const float g3 = g1 * g2;
+            const float g5 = g3 * g2;
+            const float g7 = g5 * g2;
+            const float ir0 = fmaf(b.w, ry, fmaf(c.x, rz, b.x * rx));
+            const float ir1 = fmaf(b.w, rx, fmaf(c.y, rz, b.y * ry));
+            const float ir2 = fmaf(c.x, rx, fmaf(c.y, ry, b.z * rz));
+            const float q = fmaf(rx, ir0, fmaf(ry, ir1, rz * ir2));
+            const float k = fmaf(c.z, g5, -fmaf(7.5f * q, g7, a.w * g3));
+            const float g5x3 = 3.0f * g5;
+            tx[t] = fmaf(g5x3, ir0, fmaf(k, rx, tx[t]));
+            ty[t] = fmaf(g5x3, ir1, fmaf(k, ry, ty[t]));
+            tz[t] = fmaf(g5x3, ir2, fmaf(k, rz, tz[t]));
+            tp[t] -= fmaf(a.w, g1, fmaf(1.5f * q, g5, -c.w * g3));
+        }
+    }
+    bh_add_tile<T>(A, tx, ty, tz, tp);
+}
+
+// The group's own particles on its members, target itself masked.
+template <int T>
+__device__ __forceinline__ void bh_eval_self(int gc, float eps2, const float (&xi)[T], const float (&yi)[T],
+                                             const float (&zi)[T], const float (&mi)[T], Acc<T>& A)
+{
+    const int lane = threadIdx.x & 31;
+    float tx[T], ty[T], tz[T], tp[T];
+#pragma unroll
+    for (int t = 0; t < T; t++) tx[t] = ty[t] = tz[t] = tp[t] = 0.0f;
+#pragma unroll
+    for (int t2 = 0; t2 < T; t2++) {
+        for (int j = 0; j < 32; j++) {
+            if (t2 * 32 + j >= gc) break;
+            const float sx = __shfl_sync(BH_FULL_MASK, xi[t2], j);
+            const float sy = __shfl_sync(BH_FULL_MASK, yi[t2], j);
+            const float sz = __shfl_sync(BH_FULL_MASK, zi[t2], j);
+            const float sm = __shfl_sync(BH_FULL_MASK, mi[t2], j);
+#pragma unroll
+            for (int t = 0; t < T; t++) {
+                const bool self = (t == t2) && (lane == j);
+                const float dx = sx - xi[t], dy = sy - yi[t], dz = sz - zi[t];
+                float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+                r2 = self ? 1.0f : r2;
+                const float ri = rsqrtf(r2);
+                const float mr = (self ? 0.0f : sm) * ri;
+                const float mr3 = mr * ri * ri;
+                tx[t] = fmaf(mr3, dx, tx[t]);
+                ty[t] = fmaf(mr3, dy, ty[t]);
+                tz[t] = fmaf(mr3, dz, tz[t]);
+                tp[t] -= mr;
+            }
+        }
+    }
+    bh_add_tile<T>(A, tx, ty, tz, tp);
+}
+
+__device__ __forceinline__ float4 bh_pad_source() { return make_float4(1e18f, 1e18f, 1e18f, 0.0f); }
+
+template <int T, int ORDER>
+__global__ void __launch_bounds__(256) bh_walk_kernel(WalkParams P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    WarpSmem& S = reinterpret_cast<WarpSmem*>(smem_raw)[wib];
+    WarpQuad* Q = nullptr;
+    if (ORDER >= 2) Q = reinterpret_cast<WarpQuad*>(smem_raw + (size_t)nwarps * sizeof(WarpSmem)) + wib;
+    const unsigned int lt = bh_lanemask_lt();
+    const float eps2 = P.eps2;
+    bh_dev_ctrl* ctrl = P.ctrl;
+    const int ng = (int)ctrl->n_groups;
+    unsigned long long cnt_pp = 0ull, cnt_pc = 0ull;
+
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = (int)atomicAdd(&ctrl->group_ctr, 1u);
+        g = __shfl_sync(BH_FULL_MASK, g, 0);
+        if (g >= ng) break;
+        int ab = 0;
+        if (lane == 0) ab = (int)*(volatile unsigned int*)&ctrl->abort;
+        if (__shfl_sync(BH_FULL_MASK, ab, 0)) break;
+        const int gb = P.g_first[g], gc = P.g_count[g], ge = gb + gc;
+
+        float xi[T], yi[T], zi[T], mi[T];
+        unsigned int lo0 = 0xffffffffu, lo1 = 0xffffffffu, lo2 = 0xffffffffu, hi0 = 0u, hi1 = 0u, hi2 = 0u;
+#pragma unroll
+        for (int t = 0; t < T; t++) {
+            const int o = t * 32 + lane;
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (o < gc) {
+                q = P.pos_s[gb + o];
+                lo0 = min(lo0, bh_f2ord(q.x)); lo1 = min(lo1, bh_f2ord(q.y)); lo2 = min(lo2, bh_f2ord(q.z));
+                hi0 = max(hi0, bh_f2ord(q.x)); hi1 = max(hi1, bh_f2ord(q.y)); hi2 = max(hi2, bh_f2ord(q.z));
+            }
+            xi[t] = q.x; yi[t] = q.y; zi[t] = q.z; mi[t] = q.w;
+        }
+        const float bx0 = bh_ord2f(__reduce_min_sync(BH_FULL_MASK, lo0));
+        const float by0 = bh_ord2f(__reduce_min_sync(BH_FULL_MASK, lo1));
+        const float bz0 = bh_ord2f(__reduce_min_sync(BH_FULL_MASK, lo2));
+        const float bx1 = bh_ord2f(__reduce_max_sync(BH_FULL_MASK, hi0));
+        const float by1 = bh_ord2f(__reduce_max_sync(BH_FULL_MASK, hi1));
+        const float bz1 = bh_ord2f(__reduce_max_sync(BH_FULL_MASK, hi2));
+
+        Acc<T> A;
+#pragma unroll
+        for (int t = 0; t < T; t++) {
+            A.x[t] = A.y[t] = A.z[t] = A.p[t] = 0.0f;
+            A.cx[t] = A.cy[t] = A.cz[t] = A.cp[t] = 0.0f;
+        }
+        bh_eval_self<T>(gc, eps2, xi, yi, zi, mi, A);
+        cnt_pp += (unsigned long long)gc * (unsigned long long)(gc - 1);
+
+        int sp = 1, ring_head = 0, ring_cnt = 0, q_head = 0, q_cnt = 0;
+        if (lane == 0) S.stack[0] = 0u;  // root: node 0, one node
+        __syncwarp();
+        bool overflow = false;
+        while (sp > 0) {
+            // ---- pop the top 32 nodes (ranges of siblings)
+            int c = 0;
+            uint32_t e = 0u;
+            if (lane < sp) {
+                e = S.stack[sp - 1 - lane];
+                c = (int)(e & 7u) + 1;
+            }
+            const int incl = bh_warp_incl_scan(c);
+            const int excl = incl - c;
+            const int take = max(0, min(c, 32 - excl));
+            const int st = (int)(e >> 3);
+            for (int t = 0; t < take; t++) S.staging[excl + t] = (uint32_t)(st + t);
+            const bool full = (lane < sp) && (take == c);
+            const int nfull = __popc(__ballot_sync(BH_FULL_MASK, full));
+            const int npop = min(__shfl_sync(BH_FULL_MASK, incl, 31), 32);
+            __syncwarp();
+            if (lane == nfull && lane < sp && take > 0)
+                S.stack[sp - 1 - lane] = ((uint32_t)(st + take) << 3) | (uint32_t)(c - take - 1);
+            sp -= nfull;
+            const bool has = lane < npop;
+            const int v = has ? (int)S.staging[lane] : 0;
+            __syncwarp();
+
+            // ---- test the nodes
+            float4 cm = make_float4(0.f, 0.f, 0.f, 0.f);
+            float se = 0.f;
+            int4 r = make_int4(0, 0, -1, 0);
+            if (has) {
+                cm = P.com_m[v];
+                se = P.seff[v];
+                r = P.rec[v];
+            }
+            const float dx = fmaxf(fmaxf(bx0 - cm.x, cm.x - bx1), 0.0f);
+            const float dy = fmaxf(fmaxf(by0 - cm.y, cm.y - by1), 0.0f);
+            const float dz = fmaxf(fmaxf(bz0 - cm.z, cm.z - bz1), 0.0f);
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            const bool member = (r.x < ge) && (r.x + r.y > gb);
+            const bool acc = has && (d2 > se) && !member;
+            const bool leaf = has && !acc && (r.z < 0);
+            const bool opn = has && !acc && (r.z >= 0);
+
+            // ---- open: push child ranges
+            const unsigned int om = __ballot_sync(BH_FULL_MASK, opn);
+            const int npush = __popc(om);
+            if (sp + npush > kStackCap) {
+                overflow = true;
+                break;
+            }
+            if (opn) S.stack[sp + __popc(om & lt)] = ((uint32_t)r.z << 3) | (uint32_t)(r.w - 1);
+            sp += npush;
+
+            // ---- accept: cell sources
+            const unsigned int am = __ballot_sync(BH_FULL_MASK, acc);
+            const int nacc = __popc(am);
+            cnt_pc += (unsigned long long)nacc * (unsigned long long)gc;
+            if (ORDER >= 2) {
+                if (acc) {
+                    const int slot = (q_head + q_cnt + __popc(am & lt)) & (kRing - 1);
+                    Q->a[slot] = cm;
+                    Q->b[slot] = P.quad[2 * (size_t)v];
+                    Q->c[slot] = P.quad[2 * (size_t)v + 1];
+                }
+                q_cnt += nacc;
+            } else {
+                if (acc) S.ring[(ring_head + ring_cnt + __popc(am & lt)) & (kRing - 1)] = cm;
+                ring_cnt += nacc;
+            }
+
+            // ---- rejected leaves: particle ranges outside the group
+            const int a0 = r.x, a1 = r.x + r.y;
+            const bool pa = leaf && (a0 < gb);
+            const bool pb = leaf && (a1 > ge);
+            const int pa_n = pa ? (min(a1, gb) - a0) : 0;
+            const int pb_s = max(a0, ge);
+            const int pb_n = pb ? (a1 - pb_s) : 0;
+            const unsigned int ma = __ballot_sync(BH_FULL_MASK, pa), mb = __ballot_sync(BH_FULL_MASK, pb);
+            int lq_n = __popc(ma) + __popc(mb);
+            if (pa) S.leafq[__popc(ma & lt)] = make_int2(a0, pa_n);
+            if (pb) S.leafq[__popc(ma) + __popc(mb & lt)] = make_int2(pb_s, pb_n);
+            cnt_pp += (unsigned long long)__reduce_add_sync(BH_FULL_MASK, (unsigned int)(pa_n + pb_n)) *
+                      (unsigned long long)gc;
+            __syncwarp();
+
+            // ---- drain: quadrupole tiles, point tiles, particle fills
+            if (ORDER >= 2) {
+                while (q_cnt >= 32) {
+                    bh_eval_quads<T>(Q->a + q_head, Q->b + q_head, Q->c + q_head, eps2, xi, yi, zi, A);
+                    q_head ^= 32;
+                    q_cnt -= 32;
+                }
+            }
+            int lq_pos = 0;
+            for (;;) {
+                if (ring_cnt >= 32) {
+                    bh_eval_points<T>(S.ring + ring_head, eps2, xi, yi, zi, A);
+                    ring_head ^= 32;
+                    ring_cnt -= 32;
+                    continue;
+                }
+                if (lq_pos >= lq_n) break;
+                int c2 = 0;
+                int2 q = make_int2(0, 0);
+                if (lq_pos + lane < lq_n) {
+                    q = S.leafq[lq_pos + lane];
+                    c2 = q.y;
+                }
+                const int inc2 = bh_warp_incl_scan(c2);
+                const int ex2 = inc2 - c2;
+                const int take2 = max(0, min(c2, 32 - ex2));
+                for (int t = 0; t < take2; t++) S.staging[ex2 + t] = (uint32_t)(q.x + t);
+                const bool full2 = (lq_pos + lane < lq_n) && (take2 == c2);
+                const int nf2 = __popc(__ballot_sync(BH_FULL_MASK, full2));
+                const int nfill = min(__shfl_sync(BH_FULL_MASK, inc2, 31), 32);
+                __syncwarp();
+                if (lane == nf2 && lq_pos + lane < lq_n && take2 > 0)
+                    S.leafq[lq_pos + lane] = make_int2(q.x + take2, c2 - take2);
+                lq_pos += nf2;
+                if (lane < nfill)
+                    S.ring[(ring_head + ring_cnt + lane) & (kRing - 1)] = P.pos_s[S.staging[lane]];
+                ring_cnt += nfill;
+                __syncwarp();
+            }
+        }
+        if (overflow) {
+            if (lane == 0) bh_set_error(ctrl, BH_ERR_CAPACITY);
+            break;
+        }
+        // ---- flush the partial tiles (padded with far, massless sources)
+        if (ORDER >= 2 && q_cnt > 0) {
+            if (lane >= q_cnt) {
+                Q->a[q_head + lane] = bh_pad_source();
+                Q->b[q_head + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+                Q->c[q_head + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            __syncwarp();
+            bh_eval_quads<T>(Q->a + q_head, Q->b + q_head, Q->c + q_head, eps2, xi, yi, zi, A);
+        }
+        if (ring_cnt > 0) {
+            if (lane >= ring_cnt) S.ring[ring_head + lane] = bh_pad_source();
+            __syncwarp();
+            bh_eval_points<T>(S.ring + ring_head, eps2, xi, yi, zi, A);
+        }
+        __syncwarp();
+        // ---- write (ax, ay, az, phi) in the caller's order
+#pragma unroll
+        for (int t = 0; t < T; t++) {
+            const int o = t * 32 + lane;
+            if (o < gc) {
+                const uint32_t dst = P.perm[gb + o];
+                P.out[dst] = make_float4(A.x[t] - A.cx[t], A.y[t] - A.cy[t], A.z[t] - A.cz[t], A.p[t] - A.cp[t]);
+            }
+        }
+    }
+    if (lane == 0) {
+        atomicAdd(&ctrl->n_pp, cnt_pp);
+        atomicAdd(&ctrl->n_pc, cnt_pc);
+    }
+}
+
+__global__ void bh_walk_reset_kernel(bh_dev_ctrl* c)
+{
+    c->group_ctr = 0u;
+    c->n_pp = 0ull;
+    c->n_pc = 0ull;
+}
+
+template <int T, int ORDER>
+static int bh_walk_launch_t(const WalkParams& P, int sm_count, int block_threads, int blocks_per_sm,
+                            cudaStream_t s)
+{
+    const int nw = block_threads / 32;
+    const size_t smem = (size_t)nw * (sizeof(WarpSmem) + (ORDER >= 2 ? sizeof(WarpQuad) : 0));
+    auto kern = bh_walk_kernel<T, ORDER>;
+    if (smem > 48 * 1024) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+            return BH_ERR_CUDA;
+    }
+    int bps = blocks_per_sm;
+    if (bps <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, block_threads, smem) != cudaSuccess || bps < 1)
+            bps = 1;
+    }
+    kern<<<sm_count * bps, block_threads, smem, s>>>(P);
+    return BH_OK;
+}
+
+int launch_walk(const float4* pos_s, const uint32_t* perm, const int32_t* g_first, const int32_t* g_count,
+                const bh_nodes& nd, int order, int G, float eps, float4* out, bh_dev_ctrl* ctrl, int sm_count,
+                int block_threads, int blocks_per_sm, cudaStream_t s)
+{
+    bh_walk_reset_kernel<<<1, 1, 0, s>>>(ctrl);
+    WalkParams P;
+    P.pos_s = pos_s;
+    P.perm = perm;
+    P.g_first = g_first;
+    P.g_count = g_count;
+    P.rec = nd.rec;
+    P.com_m = nd.com_m;
+    P.seff = nd.seff;
+    P.quad = nd.quad;
+    P.out = out;
+    P.ctrl = ctrl;
+    P.eps2 = eps * eps;
+    const int T = G <= 32 ? 1 : G <= 64 ? 2 : G <= 128 ? 4 : 8;
+    if (order >= 2) {
+        switch (T) {
+            case 1: return bh_walk_launch_t<1, 2>(P, sm_count, block_threads, blocks_per_sm, s);
+            case 2: return bh_walk_launch_t<2, 2>(P, sm_count, block_threads, blocks_per_sm, s);
+            case 4: return bh_walk_launch_t<4, 2>(P, sm_count, block_threads, blocks_per_sm, s);
+            default: return bh_walk_launch_t<8, 2>(P, sm_count, block_threads, blocks_per_sm, s);
+        }
+    }
+    switch (T) {
+        case 1: return bh_walk_launch_t<1, 1>(P, sm_count, block_threads, blocks_per_sm, s);
+        case 2: return bh_walk_launch_t<2, 1>(P, sm_count, block_threads, blocks_per_sm, s);
+        case 4: return bh_walk_launch_t<4, 1>(P, sm_count, block_threads, blocks_per_sm, s);
+        default: return bh_walk_launch_t<8, 1>(P, sm_count, block_threads, blocks_per_sm, s);
+    }
+}
+
+}  // namespace bh
