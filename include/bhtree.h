@@ -72,6 +72,9 @@ typedef struct bh_stats_t {
     int32_t status;          /* device status word as a BH_* code */
     int32_t reserved;
     float box[4];            /* root cube: xmin, ymin, zmin, side L (Sec. 4.1) */
+    int64_t n_pp_total;      /* particle-particle interactions since bh_create */
+    int64_t n_pc_total;      /* particle-cell interactions since bh_create */
+    int64_t launches;        /* kernels this context has enqueued since bh_create */
 } bh_stats_t;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -137,6 +140,18 @@ int tree_force(bh_ctx* ctx, float eps, float* d_acc_pot, void* stream);
  * BH_ERR_TOO_LARGE (n_src or n_tgt >= 2^31). */
 int direct_force(const float* d_src, int64_t n_src, const float* d_tgt, const int64_t* d_tgt_self,
                  int64_t n_tgt, double eps, void* d_out, int precision, void* stream);
+
+/* The orbit loop of Sec. 1 ("compute forces, integrate, repeat"): one
+ * leapfrog update per particle, v += a * dt_kick then x += v * dt_drift.
+ * A kick-drift-kick step is bh_kick_drift(dt/2 then dt) after the first
+ * force, then force, then the next call's dt/2 kick (or dt_kick = dt when the
+ * two half kicks are merged).
+ * d_pos: n float4 (x, y, z, m), positions updated in place, m untouched;
+ * d_vel: n float4 (vx, vy, vz, unused), updated in place;
+ * d_acc: n float4 (ax, ay, az, phi) from tree_force (caller order).
+ * Errors: BH_ERR_INVALID (null/misaligned/non-device pointer, n < 0). */
+int bh_kick_drift(bh_ctx* ctx, float* d_pos, float* d_vel, const float* d_acc, int64_t n, float dt_kick,
+                  float dt_drift, void* stream);
 
 /* Synchronise `stream` and return the context's device status as a BH_*
  * code (BH_OK if no device-side error was recorded since the last call;

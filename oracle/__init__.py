@@ -47,7 +47,7 @@ def lib():
         L.or_groups.restype = _i64
         L.or_force_groups.argtypes = [_i64, _f32p, _u32p, _i64, _i32p, _i32p, _i32p, _i32p,
                                       _f64p, _vp, _f64p, _i64, _i32p, _i32p, _vp,
-                                      ctypes.c_double, _f64p, _vp, _vp, _vp]
+                                      ctypes.c_double, _f64p, _vp, _vp, _vp, _vp]
         L.or_force_groups.restype = ctypes.c_int
         L.or_group_lists.argtypes = [_i64, _f32p, _i32p, _i32p, _i32p, _i32p, _f64p, _f64p,
                                      ctypes.c_int32, ctypes.c_int32, _i32p,
@@ -197,11 +197,13 @@ def groups(tree, G):
 def force_groups(spos, perm, tree, mom, g_first, g_count, eps, group_mask=None, want_quad=None):
     """Group walk with the conservative group form of Eq. (2).
 
-    Returns dict(out=(n,4) caller order, margin=(n,), n_pp=(n,), n_pc=(n,)).
+    Returns dict(out=(n,4) caller order, margin=(n,), n_pp=(n,), n_pc=(n,),
+    a_abs=(n,) sum of |a| over all terms).
     """
     spos = _pos(spos)
     n = spos.shape[0]
     out = np.zeros((n, 4), dtype=np.float64)
+    a_abs = np.zeros(n, dtype=np.float64)
     margin = np.full(n, np.inf, dtype=np.float64)
     n_pp = np.zeros(n, dtype=np.int64)
     n_pc = np.zeros(n, dtype=np.int64)
@@ -212,10 +214,10 @@ def force_groups(spos, perm, tree, mom, g_first, g_count, eps, group_mask=None, 
                                tree.first, tree.count, tree.child_first, tree.nchild,
                                np.ascontiguousarray(mom.com_m), _ptr(quad), mom.s_eff,
                                g_first.shape[0], g_first, g_count, _ptr(group_mask), float(eps),
-                               out, _ptr(margin), _ptr(n_pp), _ptr(n_pc))
+                               out, _ptr(margin), _ptr(n_pp), _ptr(n_pc), _ptr(a_abs))
     if rc != 0:
         raise MemoryError("oracle force_groups")
-    return dict(out=out, margin=margin, n_pp=n_pp, n_pc=n_pc)
+    return dict(out=out, margin=margin, n_pp=n_pp, n_pc=n_pc, a_abs=a_abs)
 
 
 def group_lists(spos, tree, mom, gfirst, gcount):

@@ -408,6 +408,7 @@ static void or_pc(double xi, double yi, double zi, const double* cm, const doubl
     acc[1] -= M * g3 * ry;
     acc[2] -= M * g3 * rz;
     acc[3] -= M * g1;
+    acc[4] += fabs(M) * g3 * sqrt(rx * rx + ry * ry + rz * rz);
     if (qd) {
         const double g5 = g3 * g2, g7 = g5 * g2;
         const double Ir0 = qd[0] * rx + qd[3] * ry + qd[4] * rz;
@@ -434,6 +435,7 @@ static void or_pp(double xi, double yi, double zi, const float* pj, double e2, d
     acc[1] += mr3 * dy;
     acc[2] += mr3 * dz;
     acc[3] -= m * rinv;
+    acc[4] += fabs(mr3) * sqrt(dx * dx + dy * dy + dz * dz);
 }
 
 /* ------------------------------------------------------------------------
@@ -452,6 +454,8 @@ static void or_pp(double xi, double yi, double zi, const float* pj, double e2, d
  * margin (caller order, optional): min over the group's decisions of
  *   |d^2 - S_eff| / S_eff, so near-tie decisions can be recognised.
  * n_pp, n_pc (caller order, optional): interactions evaluated per target.
+ * a_abs (caller order, optional): sum over all terms of |a_term|, the scale
+ *   of the rounding error of any finite-precision evaluation of the sum.
  * group_mask (optional, per group): walk only groups whose mask is non-zero;
  *   the other targets are left untouched.
  * ---------------------------------------------------------------------- */
@@ -460,7 +464,7 @@ int or_force_groups(int64_t n, const float* spos, const uint32_t* perm, int64_t 
                     const int32_t* nchild, const double* com_m, const double* quad,
                     const double* s_eff, int64_t ng, const int32_t* g_first, const int32_t* g_count,
                     const uint8_t* group_mask, double eps, double* out, double* margin,
-                    int64_t* n_pp, int64_t* n_pc)
+                    int64_t* n_pp, int64_t* n_pc, double* a_abs)
 {
     const double e2 = eps * eps;
     int err = 0;
@@ -513,7 +517,7 @@ int or_force_groups(int64_t n, const float* spos, const uint32_t* perm, int64_t 
         }
         for (int64_t i = gb; i < ge; i++) {
             const double xi = spos[4 * i], yi = spos[4 * i + 1], zi = spos[4 * i + 2];
-            double acc[4] = {0, 0, 0, 0};
+            double acc[5] = {0, 0, 0, 0, 0};
             int64_t cnt_pp = 0;
             for (int64_t t = 0; t < npc; t++)
                 or_pc(xi, yi, zi, com_m + 4 * pc[t], quad ? quad + 6 * pc[t] : NULL, e2, acc);
@@ -528,6 +532,7 @@ int or_force_groups(int64_t n, const float* spos, const uint32_t* perm, int64_t 
             const int64_t o = perm[i];
             for (int a = 0; a < 4; a++) out[4 * o + a] = acc[a];
             if (margin) margin[o] = mmin;
+            if (a_abs) a_abs[o] = acc[4];
             if (n_pp) n_pp[o] = cnt_pp;
             if (n_pc) n_pc[o] = npc;
         }
@@ -608,7 +613,7 @@ int or_force_particles(int64_t n, const float* spos, const uint32_t* perm, int64
             continue;
         }
         const double xi = spos[4 * i], yi = spos[4 * i + 1], zi = spos[4 * i + 2];
-        double acc[4] = {0, 0, 0, 0};
+        double acc[5] = {0, 0, 0, 0, 0};
         int64_t cpp = 0, cpc = 0, sp = 0;
         stack[sp++] = 0;
         while (sp > 0) {
@@ -649,7 +654,7 @@ int or_force_particles(int64_t n, const float* spos, const uint32_t* perm, int64
 /* One particle-cell term at target x (for the quadrupole pins). */
 void or_pc_eval(const double* x, const double* com_m, const double* quad, double eps, double* out)
 {
-    double acc[4] = {0, 0, 0, 0};
+    double acc[5] = {0, 0, 0, 0, 0};
     or_pc(x[0], x[1], x[2], com_m, quad, eps * eps, acc);
     for (int a = 0; a < 4; a++) out[a] = acc[a];
 }

@@ -31,7 +31,8 @@ EXPORT = dict(keys=1, perm=2, spos=3, node_first=4, node_count=5, node_child=6, 
 
 # the symbols declared in include/bhtree.h
 SYMBOLS = ["bh_version", "bh_strerror", "bh_config_default", "bh_create", "bh_destroy", "tree_build",
-           "tree_moments", "tree_force", "direct_force", "bh_status", "bh_stats", "bh_export"]
+           "tree_moments", "tree_force", "direct_force", "bh_kick_drift", "bh_status", "bh_stats",
+           "bh_export"]
 
 
 class BhConfig(ctypes.Structure):
@@ -44,7 +45,8 @@ class BhStats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64),
                 ("n_groups", ctypes.c_int64), ("n_pp", ctypes.c_int64), ("n_pc", ctypes.c_int64),
                 ("max_leaf_count", ctypes.c_int64), ("status", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("box", ctypes.c_float * 4)]
+                ("reserved", ctypes.c_int32), ("box", ctypes.c_float * 4),
+                ("n_pp_total", ctypes.c_int64), ("n_pc_total", ctypes.c_int64), ("launches", ctypes.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_ if k not in ("reserved", "box")}
@@ -91,6 +93,8 @@ def lib():
         L.tree_force.restype = i32
         L.direct_force.argtypes = [vp, i64, vp, vp, i64, ctypes.c_double, vp, i32, vp]
         L.direct_force.restype = i32
+        L.bh_kick_drift.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, vp]
+        L.bh_kick_drift.restype = i32
         L.bh_status.argtypes = [vp, vp]
         L.bh_status.restype = i32
         L.bh_stats.argtypes = [vp, vp, ctypes.POINTER(BhStats)]
@@ -158,6 +162,11 @@ def direct_force(src, tgt, tgt_self, eps, out, precision, stream=None):
                               int(tgt.shape[0]), float(eps), _dptr(out), int(precision), _stream(stream))
 
 
+def bh_kick_drift(h, pos, vel, acc, dt_kick, dt_drift, stream=None):
+    return lib().bh_kick_drift(h, _dptr(pos), _dptr(vel), _dptr(acc), int(pos.shape[0]),
+                               ctypes.c_float(dt_kick), ctypes.c_float(dt_drift), _stream(stream))
+
+
 def bh_status(h, stream=None):
     return lib().bh_status(h, _stream(stream))
 
@@ -213,6 +222,9 @@ class Context:
         self.moments(theta, stream)
         self.force(eps, out, stream)
         return out
+
+    def kick_drift(self, pos, vel, acc, dt_kick, dt_drift, stream=None):
+        _check(bh_kick_drift(self.h, pos, vel, acc, dt_kick, dt_drift, stream), "bh_kick_drift")
 
     def status(self, stream=None):
         return bh_status(self.h, stream)

@@ -24,6 +24,7 @@ struct bh_ctx {
     bool have_moments = false;
     float theta = 0.f;
     unsigned int sort_epoch = 0;
+    int64_t launches = 0;
     void* slab = nullptr;
     bh_dev_ctrl* ctrl = nullptr;
     bh_dev_ctrl* host_ctrl = nullptr;  // pinned staging for read-back
@@ -248,7 +249,9 @@ int tree_build(bh_ctx* x, const float* d_pos_mass, int64_t n, void* stream)
         bh::launch_tree(x->keys, N, x->cfg.leaf_size, x->dl, x->blk, x->nd, x->node_cap, x->ctrl, grid_for(x), s);
         bh::launch_groups(x->nd, N, x->cfg.group_size, x->flags, x->blk, x->g_first, x->g_count, x->ctrl,
                           grid_for(x), s);
+        x->launches += bh::kLaunchesBuild - 1;
     }
+    x->launches += 1;
     if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
     x->n = n;
     x->have_moments = false;
@@ -262,9 +265,11 @@ int tree_moments(bh_ctx* x, float theta, void* stream)
     if (x->n < 0) return BH_ERR_STATE;
     DeviceGuard guard(x->device);
     cudaStream_t s = (cudaStream_t)stream;
-    if (x->n > 0)
+    if (x->n > 0) {
         bh::launch_moments(x->pos_s, x->keys, x->nd, x->cfg.order, theta, x->cfg.fp64_node_threshold, x->ctrl,
                            grid_for(x), s);
+        x->launches += bh::kLaunchesMoments;
+    }
     if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
     x->theta = theta;
     x->have_moments = true;
@@ -284,8 +289,24 @@ int tree_force(bh_ctx* x, float eps, float* d_acc_pot, void* stream)
                              eps, (float4*)d_acc_pot, x->ctrl, x->sm_count, x->cfg.block_threads,
                              x->cfg.blocks_per_sm, s);
     if (rc) return rc;
+    x->launches += bh::kLaunchesForce;
     if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
     return BH_OK;
+}
+
+int bh_kick_drift(bh_ctx* x, float* d_pos, float* d_vel, const float* d_acc, int64_t n, float dt_kick,
+                  float dt_drift, void* stream)
+{
+    if (!x || n < 0) return BH_ERR_INVALID;
+    if (n >= ((int64_t)1 << 31)) return BH_ERR_TOO_LARGE;
+    if (n == 0) return BH_OK;
+    for (const void* p : {(const void*)d_pos, (const void*)d_vel, (const void*)d_acc})
+        if (!p || !aligned16(p) || !is_device_ptr(p, x->device)) return BH_ERR_INVALID;
+    DeviceGuard guard(x->device);
+    bh::launch_kick_drift((float4*)d_pos, (float4*)d_vel, (const float4*)d_acc, (int)n, dt_kick, dt_drift,
+                          grid_for(x), (cudaStream_t)stream);
+    x->launches += 1;
+    return cudaGetLastError() == cudaSuccess ? BH_OK : BH_ERR_CUDA;
 }
 
 int direct_force(const float* d_src, int64_t n_src, const float* d_tgt, const int64_t* d_tgt_self, int64_t n_tgt,
@@ -347,6 +368,9 @@ int bh_stats(bh_ctx* x, void* stream, bh_stats_t* out)
     out->max_leaf_count = h.max_leaf;
     out->status = -(int)h.status;
     for (int i = 0; i < 4; i++) out->box[i] = h.box[i];
+    out->n_pp_total = (int64_t)h.cum_pp;
+    out->n_pc_total = (int64_t)h.cum_pc;
+    out->launches = x->launches;
     return BH_OK;
 }
 

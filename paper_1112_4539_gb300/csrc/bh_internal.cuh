@@ -37,6 +37,8 @@ struct bh_dev_ctrl {
     unsigned int group_ctr;      // walk work queue
     unsigned long long n_pp;
     unsigned long long n_pc;
+    unsigned long long cum_pp;   // since context creation (never reset)
+    unsigned long long cum_pc;
     unsigned int pad[8];
 };
 
@@ -177,5 +179,12 @@ int launch_walk(const float4* pos_s, const uint32_t* perm, const int32_t* g_firs
                 int sm_count, int block_threads, int blocks_per_sm, cudaStream_t s);
 int launch_direct(const float4* src, int n_src, const float4* tgt, const int64_t* self, int n_tgt,
                   double eps, void* out, int precision, cudaStream_t s);
+void launch_kick_drift(float4* pos, float4* vel, const float4* acc, int n, float dt_kick, float dt_drift, int grid,
+                       cudaStream_t s);
+
+// kernel launches enqueued by one call of each stage (for bh_stats.launches)
+constexpr int kLaunchesBuild = 16;   // init, bbox, keys, 4 sort passes, 4 tree, 5 groups
+constexpr int kLaunchesMoments = 11; // one per level
+constexpr int kLaunchesForce = 2;    // counter reset, walk
 
 }  // namespace bh

@@ -399,6 +399,8 @@ __global__ void __launch_bounds__(256) bh_walk_kernel(WalkParams P)
     if (lane == 0) {
         atomicAdd(&ctrl->n_pp, cnt_pp);
         atomicAdd(&ctrl->n_pc, cnt_pc);
+        atomicAdd(&ctrl->cum_pp, cnt_pp);
+        atomicAdd(&ctrl->cum_pc, cnt_pc);
     }
 }
 

@@ -4,7 +4,10 @@ Integer and index work (root cube, Morton keys, sort permutation, tree,
 groups) must be bit-exact.  Floating point: moments within FP32 rounding of
 the oracle's FP64 sums; tree forces within 1e-5 relative per particle (the
 acceleration's denominator floored at 1e-3 of the median |a|, which guards
-the Plummer centre where |a| -> 0), checked on every particle whose group's
+the Plummer centre where |a| -> 0, and at a tenth of the particle's sum of
+term magnitudes sum|a_term|: an FP32 sum cannot be more accurate than a few
+units of 6e-8 times sum|a_term|, so where terms cancel by more than tenfold
+the bar becomes 1e-6 sum|a_term|), checked on every particle whose group's
 opening decisions all have a relative margin |d^2 - S_eff| / S_eff >= 1e-5;
 the rest took a near-tie decision that FP32 may take the other way, and are
 only checked to be valid tree results (within a few per cent of the oracle).
@@ -44,11 +47,14 @@ def _run(bh, pos, theta, eps, **cfg):
     return ctx, out.cpu().numpy().astype(np.float64), rc
 
 
-def _check_force(got, ref, margin, tol=TOL, min_checked=0.85, mask=None):
+def _check_force(got, ref, margin, tol=TOL, min_checked=0.85, mask=None, a_abs=None):
     sel = np.ones(got.shape[0], bool) if mask is None else mask
     a_ref = np.linalg.norm(ref[:, :3], axis=1)
     floor = 1e-3 * np.median(a_ref[sel])
-    ea = np.linalg.norm(got[:, :3] - ref[:, :3], axis=1) / np.maximum(a_ref, floor)
+    den = np.maximum(a_ref, floor)
+    if a_abs is not None:
+        den = np.maximum(den, 0.1 * a_abs)
+    ea = np.linalg.norm(got[:, :3] - ref[:, :3], axis=1) / den
     ep = np.abs(got[:, 3] - ref[:, 3]) / np.abs(ref[:, 3])
     ok = sel & (margin >= MARGIN)
     assert ok.sum() >= min_checked * sel.sum(), (ok.sum(), sel.sum())
@@ -137,7 +143,13 @@ def test_moments(bh, orc, order, fp64_threshold):
     big = b.tree.count >= fp64_threshold
     if big.any():
         assert (err[big] <= 2e-7 * (np.abs(ref[big, :3]) + side[big, None])).all()
-    np.testing.assert_allclose(ctx.export("seff"), b.mom.s_eff, rtol=1e-5)
+    # S_eff = (l/theta + s)^2 with s = |geometric centre - COM|: the difference
+    # of two FP32 coordinates carries an absolute error ~1e-7 of the coordinate
+    # scale, so compare sqrt(S_eff) in those units
+    r_gpu = np.sqrt(ctx.export("seff").astype(np.float64))
+    r_ref = np.sqrt(b.mom.s_eff)
+    cscale = np.abs(ref[:, :3]).max(axis=1) + side
+    assert (np.abs(r_gpu - r_ref) <= 1e-6 * r_ref + 4e-7 * cscale).all()
     if order == 2:
         q = ctx.export("quad").astype(np.float64)
         qs = b.mom.com_m[:, 3:4] * side[:, None] ** 2  # natural scale M l^2
@@ -163,7 +175,7 @@ def test_tree_force_parity(bh, orc, kind, n, seed, theta, eps, leaf, G, order):
     ctx, got, rc = _run(bh, pos, theta, eps, leaf_size=leaf, group_size=G, order=order)
     assert rc == 0
     ref, b = orc.tree_force(pos, theta, eps, n_leaf=leaf, G=G, order=order, walk="group")
-    _check_force(got, ref["out"], ref["margin"])
+    _check_force(got, ref["out"], ref["margin"], a_abs=ref["a_abs"])
     st = ctx.stats()
     ok = ref["margin"] >= MARGIN
     # interaction counts equal the oracle's when no decision is a near tie
@@ -255,7 +267,7 @@ def test_coincident_and_clustered(bh, orc):
     st = ctx.stats()
     assert st["max_leaf_count"] > 64
     ref, b = orc.tree_force(pos, 0.5, 0.01, n_leaf=8, G=64, walk="group")
-    _check_force(got, ref["out"], ref["margin"])
+    _check_force(got, ref["out"], ref["margin"], a_abs=ref["a_abs"])
     ctx.close()
 
 
@@ -328,5 +340,5 @@ def test_full_size_clumpy_sampled(bh, orc):
     sel = np.zeros(n, bool)
     for g in np.nonzero(mask)[0]:
         sel[b.perm[b.g_first[g]:b.g_first[g] + b.g_count[g]]] = True
-    _check_force(got, res["out"], res["margin"], mask=sel)
+    _check_force(got, res["out"], res["margin"], mask=sel, a_abs=res["a_abs"])
     ctx.close()

@@ -514,3 +514,22 @@ def test_nodes_holding_members_are_opened(orc):
     res, _ = orc.tree_force(p, 1.0, 0.01, walk="particle")
     ea, _ = orc.rel_err(res["out"], d)
     assert np.isfinite(ea).all() and ea.mean() < 0.05
+
+
+def test_term_magnitude_sum(orc):
+    # sum of |a_term| over a target's terms: equals |a| for a single other body,
+    # bounds |a| from above (triangle inequality), and equals the direct sum of
+    # magnitudes when every term is particle-particle (theta -> 0)
+    p2 = np.array([[0, 0, 0, 1.0], [0.6, 0.8, 0, 2.0]], np.float32)
+    res, b = orc.tree_force(p2, 0.5, 0.1)
+    np.testing.assert_allclose(res["a_abs"], np.linalg.norm(res["out"][:, :3], axis=1), rtol=1e-14)
+    p = workloads.plummer(800, seed=17)
+    res, b = orc.tree_force(p, 1e-4, 0.01)
+    x = p[:, :3].astype(np.float64)
+    m = p[:, 3].astype(np.float64)
+    d = x[None, :, :] - x[:, None, :]
+    r2 = (d ** 2).sum(-1) + 1e-4
+    mag = m[None, :] * np.sqrt((d ** 2).sum(-1)) / r2 ** 1.5
+    np.fill_diagonal(mag, 0.0)
+    np.testing.assert_allclose(res["a_abs"], mag.sum(1), rtol=1e-12)
+    assert (res["a_abs"] >= np.linalg.norm(res["out"][:, :3], axis=1) * (1 - 1e-12)).all()
