@@ -46,8 +46,11 @@ SM_MAX_MHZ = 2070.0
 
 WORKLOADS = {
     "clumpy16m": dict(kind="clumpy", n=1 << 24, seed=2, eps=1e-3, leaf=8, G=64, order=1, dt=1e-4,
-                      theta=0.60, desc="clumpy N=16777216: 64 Hernquist clumps (a=0.05) + 20% uniform "
+                      theta=0.29375, desc="clumpy N=16777216: 64 Hernquist clumps (a=0.05) + 20% uniform "
                                        "background, eps=1e-3, leapfrog dt=1e-4"),
+    "clumpy2m": dict(kind="clumpy", n=1 << 21, seed=2, eps=1e-3, leaf=8, G=64, order=1, dt=1e-4,
+                     theta=0.30, desc="clumpy N=2097152 (profiling size): 64 Hernquist clumps (a=0.05) + 20% "
+                                      "uniform background, eps=1e-3"),
     "plummer1m": dict(kind="plummer", n=1 << 20, seed=1, eps=0.01, leaf=8, G=64, order=2, dt=1e-4,
                       theta=0.75, desc="Plummer N=1048576, eps=0.01, quadrupole"),
 }

@@ -24,6 +24,7 @@ namespace bh {
 constexpr int kLvlThreads = 256;
 constexpr int kLvlPer = kLevelTile / kLvlThreads;  // 8 positions per thread
 constexpr int kMaxLeaf = 64;
+constexpr int kLeafFp64 = 32;
 
 // ------------------------------------------------------------ pass 1
 // dl[k] = (d_k + 1) | (lambda_k << 4); per-block node counts per level.
@@ -452,7 +453,8 @@ template <typename R>
 __device__ __forceinline__ void bh_child_moments(const bh_nodes& nd, int cidx, int fp64_threshold, int order,
                                                  bh_mom<R>& o)
 {
-    if (sizeof(R) == 8 && nd.count[cidx] >= fp64_threshold) {
+    const int cc = nd.count[cidx];
+    if (sizeof(R) == 8 && (cc >= fp64_threshold || (nd.child[cidx] < 0 && cc > kLeafFp64))) {
         const bh_double4 c = nd.com64[cidx];
         o.cx = (R)c.x; o.cy = (R)c.y; o.cz = (R)c.z; o.M = (R)c.w;
         if (order >= 2)
@@ -513,7 +515,10 @@ bh_moments_level_kernel(const float4* __restrict__ pos_s, const uint32_t* __rest
     const float opening = side / theta;
     for (int v = v0 + blockIdx.x * blockDim.x + threadIdx.x; v < v1; v += gridDim.x * blockDim.x) {
         const int4 r = nd.rec[v];
-        const bool f64 = r.y >= fp64_threshold;
+        // FP64 above the threshold, and for leaves holding more than 32 particles
+        // (only level-10 leaves can): a sequential FP32 sum of k equal masses is
+        // off by up to ~k * 3e-9 relative (1e-5 at k = 3000)
+        const bool f64 = r.y >= fp64_threshold || (r.z < 0 && r.y > kLeafFp64);
         // geometric centre of the node's level-lev cell
         const unsigned int pref = (lev == 0) ? 0u : (keys[r.x] >> (3 * (BH_MAX_LEVEL - lev)));
         const float gx = xmin + ((float)bh_compact3(pref >> 2) + 0.5f) * side;

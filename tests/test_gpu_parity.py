@@ -54,8 +54,9 @@ def _check_force(got, ref, margin, tol=TOL, min_checked=0.85, mask=None, a_abs=N
     den = np.maximum(a_ref, floor)
     if a_abs is not None:
         den = np.maximum(den, 0.1 * a_abs)
-    ea = np.linalg.norm(got[:, :3] - ref[:, :3], axis=1) / den
-    ep = np.abs(got[:, 3] - ref[:, 3]) / np.abs(ref[:, 3])
+    with np.errstate(divide="ignore", invalid="ignore"):  # unselected targets may be empty
+        ea = np.linalg.norm(got[:, :3] - ref[:, :3], axis=1) / den
+        ep = np.abs(got[:, 3] - ref[:, 3]) / np.abs(ref[:, 3])
     ok = sel & (margin >= MARGIN)
     assert ok.sum() >= min_checked * sel.sum(), (ok.sum(), sel.sum())
     assert np.isfinite(got[sel]).all()
