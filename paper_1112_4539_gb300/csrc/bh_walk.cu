@@ -67,12 +67,12 @@ __device__ __forceinline__ void bh_kahan(float& s, float& c, float v)
     s = t;
 }
 
-template <int T>
+template <int T, int TN = T>
 __device__ __forceinline__ void bh_add_tile(Acc<T>& A, const float (&tx)[T], const float (&ty)[T],
                                             const float (&tz)[T], const float (&tp)[T])
 {
 #pragma unroll
-    for (int t = 0; t < T; t++) {
+    for (int t = 0; t < TN; t++) {
         bh_kahan(A.x[t], A.cx[t], tx[t]);
         bh_kahan(A.y[t], A.cy[t], ty[t]);
         bh_kahan(A.z[t], A.cz[t], tz[t]);
@@ -80,19 +80,20 @@ __device__ __forceinline__ void bh_add_tile(Acc<T>& A, const float (&tx)[T], con
     }
 }
 
-// 32 point sources (particles or monopole cells) on T targets per lane.
-template <int T>
+// 32 point sources (particles or monopole cells) on the first TN of the T
+// target slots of each lane.
+template <int T, int TN>
 __device__ __forceinline__ void bh_eval_points(const float4* __restrict__ src, float eps2, const float (&xi)[T],
                                                const float (&yi)[T], const float (&zi)[T], Acc<T>& A)
 {
     float tx[T], ty[T], tz[T], tp[T];
 #pragma unroll
-    for (int t = 0; t < T; t++) tx[t] = ty[t] = tz[t] = tp[t] = 0.0f;
+    for (int t = 0; t < TN; t++) tx[t] = ty[t] = tz[t] = tp[t] = 0.0f;
 #pragma unroll 8
     for (int j = 0; j < 32; j++) {
         const float4 s = src[j];
 #pragma unroll
-        for (int t = 0; t < T; t++) {
+        for (int t = 0; t < TN; t++) {
             const float dx = s.x - xi[t], dy = s.y - yi[t], dz = s.z - zi[t];
             const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
             const float ri = rsqrtf(r2);
@@ -104,26 +105,26 @@ __device__ __forceinline__ void bh_eval_points(const float4* __restrict__ src, f
             tp[t] -= mr;
         }
     }
-    bh_add_tile<T>(A, tx, ty, tz, tp);
+    bh_add_tile<T, TN>(A, tx, ty, tz, tp);
 }
 
 // 32 quadrupole cells on T targets per lane.  With r = x_i - c, h^2 = r^2 + eps^2,
 // g_n = h^-n, T = tr I, q = r.I.r:
 //   a += -M g3 r + 3 g5 I r + (1.5 T g5 - 7.5 q g7) r
 //   phi += -M g1 - 1.5 q g5 + 0.5 T g3
-template <int T>
+template <int T, int TN>
 __device__ __forceinline__ void bh_eval_quads(const float4* __restrict__ ca, const float4* __restrict__ cb,
                                               const float4* __restrict__ cc, float eps2, const float (&xi)[T],
                                               const float (&yi)[T], const float (&zi)[T], Acc<T>& A)
 {
     float tx[T], ty[T], tz[T], tp[T];
 #pragma unroll
-    for (int t = 0; t < T; t++) tx[t] = ty[t] = tz[t] = tp[t] = 0.0f;
+    for (int t = 0; t < TN; t++) tx[t] = ty[t] = tz[t] = tp[t] = 0.0f;
 #pragma unroll 2
     for (int j = 0; j < 32; j++) {
         const float4 a = ca[j], b = cb[j], c = cc[j];
 #pragma unroll
-        for (int t = 0; t < T; t++) {
+        for (int t = 0; t < TN; t++) {
             const float rx = xi[t] - a.x, ry = yi[t] - a.y, rz = zi[t] - a.z;
             const float h2 = fmaf(rz, rz, fmaf(ry, ry, fmaf(rx, rx, eps2)));
             const float g1 = rsqrtf(h2);
@@ -143,7 +144,31 @@ __device__ __forceinline__ void bh_eval_quads(const float4* __restrict__ ca, con
             tp[t] -= fmaf(a.w, g1, fmaf(1.5f * q, g5, -c.w * g3));
         }
     }
-    bh_add_tile<T>(A, tx, ty, tz, tp);
+    bh_add_tile<T, TN>(A, tx, ty, tz, tp);
+}
+
+// Evaluate with only as many target slots per lane as the group fills
+// (tn = ceil(group count / 32), warp-uniform).
+template <int T>
+__device__ __forceinline__ void bh_points(int tn, const float4* __restrict__ src, float eps2, const float (&xi)[T],
+                                          const float (&yi)[T], const float (&zi)[T], Acc<T>& A)
+{
+    if (T >= 4 && tn == 4) bh_eval_points<T, (T >= 4 ? 4 : T)>(src, eps2, xi, yi, zi, A);
+    else if (T >= 3 && tn == 3) bh_eval_points<T, (T >= 3 ? 3 : T)>(src, eps2, xi, yi, zi, A);
+    else if (T >= 2 && tn == 2) bh_eval_points<T, (T >= 2 ? 2 : T)>(src, eps2, xi, yi, zi, A);
+    else if (tn == 1) bh_eval_points<T, 1>(src, eps2, xi, yi, zi, A);
+    else bh_eval_points<T, T>(src, eps2, xi, yi, zi, A);
+}
+template <int T>
+__device__ __forceinline__ void bh_quads(int tn, const float4* __restrict__ ca, const float4* __restrict__ cb,
+                                         const float4* __restrict__ cc, float eps2, const float (&xi)[T],
+                                         const float (&yi)[T], const float (&zi)[T], Acc<T>& A)
+{
+    if (T >= 4 && tn == 4) bh_eval_quads<T, (T >= 4 ? 4 : T)>(ca, cb, cc, eps2, xi, yi, zi, A);
+    else if (T >= 3 && tn == 3) bh_eval_quads<T, (T >= 3 ? 3 : T)>(ca, cb, cc, eps2, xi, yi, zi, A);
+    else if (T >= 2 && tn == 2) bh_eval_quads<T, (T >= 2 ? 2 : T)>(ca, cb, cc, eps2, xi, yi, zi, A);
+    else if (tn == 1) bh_eval_quads<T, 1>(ca, cb, cc, eps2, xi, yi, zi, A);
+    else bh_eval_quads<T, T>(ca, cb, cc, eps2, xi, yi, zi, A);
 }
 
 // The group's own particles on its members, target itself masked.
@@ -208,6 +233,7 @@ __global__ void __launch_bounds__(256) bh_walk_kernel(WalkParams P)
         if (lane == 0) ab = (int)*(volatile unsigned int*)&ctrl->abort;
         if (__shfl_sync(BH_FULL_MASK, ab, 0)) break;
         const int gb = P.g_first[g], gc = P.g_count[g], ge = gb + gc;
+        const int tn = (gc + 31) >> 5;  // target slots in use (1..T)
 
         float xi[T], yi[T], zi[T], mi[T];
         unsigned int lo0 = 0xffffffffu, lo1 = 0xffffffffu, lo2 = 0xffffffffu, hi0 = 0u, hi1 = 0u, hi2 = 0u;
@@ -329,7 +355,7 @@ __global__ void __launch_bounds__(256) bh_walk_kernel(WalkParams P)
             // ---- drain: quadrupole tiles, point tiles, particle fills
             if (ORDER >= 2) {
                 while (q_cnt >= 32) {
-                    bh_eval_quads<T>(Q->a + q_head, Q->b + q_head, Q->c + q_head, eps2, xi, yi, zi, A);
+                    bh_quads<T>(tn, Q->a + q_head, Q->b + q_head, Q->c + q_head, eps2, xi, yi, zi, A);
                     q_head ^= 32;
                     q_cnt -= 32;
                 }
@@ -337,7 +363,7 @@ __global__ void __launch_bounds__(256) bh_walk_kernel(WalkParams P)
             int lq_pos = 0;
             for (;;) {
                 if (ring_cnt >= 32) {
-                    bh_eval_points<T>(S.ring + ring_head, eps2, xi, yi, zi, A);
+                    bh_points<T>(tn, S.ring + ring_head, eps2, xi, yi, zi, A);
                     ring_head ^= 32;
                     ring_cnt -= 32;
                     continue;
@@ -378,12 +404,12 @@ __global__ void __launch_bounds__(256) bh_walk_kernel(WalkParams P)
                 Q->c[q_head + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
             __syncwarp();
-            bh_eval_quads<T>(Q->a + q_head, Q->b + q_head, Q->c + q_head, eps2, xi, yi, zi, A);
+            bh_quads<T>(tn, Q->a + q_head, Q->b + q_head, Q->c + q_head, eps2, xi, yi, zi, A);
         }
         if (ring_cnt > 0) {
             if (lane >= ring_cnt) S.ring[ring_head + lane] = bh_pad_source();
             __syncwarp();
-            bh_eval_points<T>(S.ring + ring_head, eps2, xi, yi, zi, A);
+            bh_points<T>(tn, S.ring + ring_head, eps2, xi, yi, zi, A);
         }
         __syncwarp();
         // ---- write (ax, ay, az, phi) in the caller's order
@@ -448,11 +474,13 @@ int launch_walk(const float4* pos_s, const uint32_t* perm, const int32_t* g_firs
     P.out = out;
     P.ctrl = ctrl;
     P.eps2 = eps * eps;
-    const int T = G <= 32 ? 1 : G <= 64 ? 2 : G <= 128 ? 4 : 8;
+    // target slots per lane: ceil(G / 32), one instantiation per value up to 4
+    const int T = G <= 32 ? 1 : G <= 64 ? 2 : G <= 96 ? 3 : G <= 128 ? 4 : 8;
     if (order >= 2) {
         switch (T) {
             case 1: return bh_walk_launch_t<1, 2>(P, sm_count, block_threads, blocks_per_sm, s);
             case 2: return bh_walk_launch_t<2, 2>(P, sm_count, block_threads, blocks_per_sm, s);
+            case 3: return bh_walk_launch_t<3, 2>(P, sm_count, block_threads, blocks_per_sm, s);
             case 4: return bh_walk_launch_t<4, 2>(P, sm_count, block_threads, blocks_per_sm, s);
             default: return bh_walk_launch_t<8, 2>(P, sm_count, block_threads, blocks_per_sm, s);
         }
@@ -460,6 +488,7 @@ int launch_walk(const float4* pos_s, const uint32_t* perm, const int32_t* g_firs
     switch (T) {
         case 1: return bh_walk_launch_t<1, 1>(P, sm_count, block_threads, blocks_per_sm, s);
         case 2: return bh_walk_launch_t<2, 1>(P, sm_count, block_threads, blocks_per_sm, s);
+        case 3: return bh_walk_launch_t<3, 1>(P, sm_count, block_threads, blocks_per_sm, s);
         case 4: return bh_walk_launch_t<4, 1>(P, sm_count, block_threads, blocks_per_sm, s);
         default: return bh_walk_launch_t<8, 1>(P, sm_count, block_threads, blocks_per_sm, s);
     }
