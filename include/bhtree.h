@@ -153,6 +153,33 @@ int direct_force(const float* d_src, int64_t n_src, const float* d_tgt, const in
 int bh_kick_drift(bh_ctx* ctx, float* d_pos, float* d_vel, const float* d_acc, int64_t n, float dt_kick,
                   float dt_drift, void* stream);
 
+/* Whole force evaluation for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is a service of this library.  Code
+ * that runs while a CUDA graph is being captured (cudaMalloc is illegal
+ * there), plugins whose host application owns all device memory, and
+ * real-time loops that must never allocate cannot use bh_create's slab.
+ * This entry point runs the same kernels as tree_build + tree_moments +
+ * tree_force, with its work arrays in a fixed file-scope device array of
+ * BH_STATIC_SCRATCH_BYTES (16 MiB), which every GPU that loads the library
+ * holds until the process exits; it calls no allocating routine.
+ * Limits: n <= BH_STATIC_MAX_N (32768), and the work arrays of (n, cfg)
+ * must fit in the array (true for leaf_size >= 4 at n = 32768); larger
+ * requests return BH_ERR_TOO_LARGE.
+ * The first call on each device (with that device current) looks up the
+ * array's device address and clears it, synchronously: make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents, so calls that overlap on the GPU (two streams, two
+ * host threads on one device) race; serialise them.
+ * d_pos_mass: n float4 (x, y, z, m); d_acc_pot: n float4 (ax, ay, az, phi),
+ * caller order; cfg may be NULL (defaults); theta > 0, eps >= 0.
+ * h_status: NULL, or a host int that receives the device status (BH_OK or a
+ * BH_ERR_* code) after the call synchronises `stream`.
+ * Errors: BH_ERR_INVALID, BH_ERR_TOO_LARGE, BH_ERR_CUDA. */
+#define BH_STATIC_SCRATCH_BYTES (16u << 20)
+#define BH_STATIC_MAX_N 32768
+int bh_tree_force_static(const float* d_pos_mass, int64_t n, const bh_config* cfg, float theta, float eps,
+                         float* d_acc_pot, int* h_status, void* stream);
+
 /* Synchronise `stream` and return the context's device status as a BH_*
  * code (BH_OK if no device-side error was recorded since the last call;
  * the status is then cleared). */

@@ -32,7 +32,8 @@ EXPORT = dict(keys=1, perm=2, spos=3, node_first=4, node_count=5, node_child=6, 
 # the symbols declared in include/bhtree.h
 SYMBOLS = ["bh_version", "bh_strerror", "bh_config_default", "bh_create", "bh_destroy", "tree_build",
            "tree_moments", "tree_force", "direct_force", "bh_kick_drift", "bh_status", "bh_stats",
-           "bh_export"]
+           "bh_export", "bh_tree_force_static"]
+STATIC_MAX_N = 32768
 
 
 class BhConfig(ctypes.Structure):
@@ -95,6 +96,9 @@ def lib():
         L.direct_force.restype = i32
         L.bh_kick_drift.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, vp]
         L.bh_kick_drift.restype = i32
+        L.bh_tree_force_static.argtypes = [vp, i64, ctypes.POINTER(BhConfig), ctypes.c_float, ctypes.c_float, vp,
+                                           ctypes.POINTER(ctypes.c_int), vp]
+        L.bh_tree_force_static.restype = i32
         L.bh_status.argtypes = [vp, vp]
         L.bh_status.restype = i32
         L.bh_stats.argtypes = [vp, vp, ctypes.POINTER(BhStats)]
@@ -165,6 +169,16 @@ def direct_force(src, tgt, tgt_self, eps, out, precision, stream=None):
 def bh_kick_drift(h, pos, vel, acc, dt_kick, dt_drift, stream=None):
     return lib().bh_kick_drift(h, _dptr(pos), _dptr(vel), _dptr(acc), int(pos.shape[0]),
                                ctypes.c_float(dt_kick), ctypes.c_float(dt_drift), _stream(stream))
+
+
+def bh_tree_force_static(pos, theta, eps, out, cfg=None, stream=None):
+    """Force evaluation without any device allocation (fixed scratch, n <= 32768).
+    Returns (rc, device status)."""
+    st = ctypes.c_int(0)
+    rc = lib().bh_tree_force_static(_dptr(pos), int(pos.shape[0]), ctypes.byref(cfg) if cfg is not None else None,
+                                    ctypes.c_float(theta), ctypes.c_float(eps), _dptr(out), ctypes.byref(st),
+                                    _stream(stream))
+    return rc, st.value
 
 
 def bh_status(h, stream=None):
