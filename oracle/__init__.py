@@ -59,6 +59,21 @@ def lib():
                                          ctypes.c_int, _f64p, _vp, _vp]
         L.or_force_particles.restype = ctypes.c_int
         L.or_pc_eval.argtypes = [_f64p, _f64p, _vp, ctypes.c_double, _f64p]
+        L.or_mlp_nparams.restype = ctypes.c_int
+        L.or_mlp_forward.argtypes = [_f64p, _i64, _f64p, ctypes.c_int, _f64p]
+        L.or_mlp_loss_grad.argtypes = [_f64p, _i64, _f64p, _f64p, ctypes.c_double, _f64p]
+        L.or_mlp_loss_grad.restype = ctypes.c_double
+        L.or_adam_step.argtypes = [_i64, _f64p, _f64p, _f64p, _f64p, _i64, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double]
+        L.or_mac_training_pairs.argtypes = [_f32p, _i64, _i32p, _i32p, _i32p, _i32p, _i32p, _f64p, _vp, _f64p,
+                                            _f64p, _i64, _i32p, _i32p, _f64p, ctypes.c_double, ctypes.c_double,
+                                            _i64, _f64p, _f64p, _i32p, _i32p]
+        L.or_mac_training_pairs.restype = _i64
+        L.or_force_groups_learned.argtypes = [_i64, _f32p, _u32p, _i64, _i32p, _i32p, _i32p, _i32p, _i32p,
+                                              _f64p, _vp, _f64p, _f64p, ctypes.c_double, ctypes.c_double, _i64,
+                                              _i32p, _i32p, _vp, _f64p, _f64p, _f64p, ctypes.c_double,
+                                              ctypes.c_double, _f64p, _vp, _vp, _vp, _vp]
+        L.or_force_groups_learned.restype = ctypes.c_int
         L.or_num_threads.restype = ctypes.c_int
         L.or_set_threads.argtypes = [ctypes.c_int]
         _lib = L
@@ -303,3 +318,94 @@ def rel_err(a, ref):
     ea = np.linalg.norm(a[:, :3] - ref[:, :3], axis=1) / np.linalg.norm(ref[:, :3], axis=1)
     ep = np.abs(a[:, 3] - ref[:, 3]) / np.abs(ref[:, 3])
     return ea, ep
+
+
+# ---------------------------------------------------------------- learned MAC
+NF = 6
+
+
+def mlp_nparams():
+    return lib().or_mlp_nparams()
+
+
+def mlp_forward(params, X, bf16=False):
+    """Network prediction per sample (FP64; bf16=True emulates the in-walk inference)."""
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, NF)
+    y = np.zeros(X.shape[0])
+    lib().or_mlp_forward(P, X.shape[0], X, int(bool(bf16)), y)
+    return y
+
+
+def mlp_loss_grad(params, X, Y, under_weight=4.0):
+    P = np.ascontiguousarray(params, dtype=np.float64)
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, NF)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    g = np.zeros(P.shape[0])
+    loss = lib().or_mlp_loss_grad(P, X.shape[0], X, Y, float(under_weight), g)
+    return loss, g
+
+
+def adam_step(params, grad, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    """In place on params, m, v (float64 arrays)."""
+    lib().or_adam_step(params.shape[0], params, np.ascontiguousarray(grad, dtype=np.float64), m, v, int(t),
+                       lr, b1, b2, eps)
+
+
+def mac_training_pairs(b, group_idx, a_tot_sorted, eps, descend_above=1e-6, cap=None):
+    """(features, labels, group, node) of the guard-passing (group, node) pairs
+    of the listed groups; the guard is b's S_eff (b built with theta = theta_guard)."""
+    gl_first = np.ascontiguousarray(b.g_first[group_idx], dtype=np.int32)
+    gl_count = np.ascontiguousarray(b.g_count[group_idx], dtype=np.int32)
+    cap = cap or int(4000 * len(group_idx) + 1000)
+    X = np.zeros((cap, NF))
+    Y = np.zeros(cap)
+    pg = np.zeros(cap, np.int32)
+    pn = np.zeros(cap, np.int32)
+    t = b.tree
+    np_ = lib().or_mac_training_pairs(b.spos, t.n_nodes, t.level, t.first, t.count, t.child_first, t.nchild,
+                                      np.ascontiguousarray(b.mom.com_m), _ptr(b.mom.quad), b.mom.side,
+                                      b.mom.s_eff, len(group_idx), gl_first, gl_count,
+                                      np.ascontiguousarray(a_tot_sorted, dtype=np.float64), float(eps),
+                                      float(descend_above), cap, X, Y, pg, pn)
+    if np_ < 0:
+        raise RuntimeError("mac_training_pairs: capacity exceeded")
+    return X[:np_], Y[:np_], pg[:np_], pn[:np_]
+
+
+def force_groups_learned(b, params, fmin, fmax, tau, eps, theta_guard, theta_fb, group_mask=None):
+    """Group walk with the learned criterion (guard = b's S_eff, built with theta_guard)."""
+    n = b.spos.shape[0]
+    out = np.zeros((n, 4))
+    mnet = np.full(n, np.inf)
+    mgeo = np.full(n, np.inf)
+    n_pp = np.zeros(n, np.int64)
+    n_pc = np.zeros(n, np.int64)
+    t = b.tree
+    if group_mask is not None:
+        group_mask = np.ascontiguousarray(group_mask, dtype=np.uint8)
+    rc = lib().or_force_groups_learned(n, b.spos, np.ascontiguousarray(b.perm, dtype=np.uint32), t.n_nodes,
+                                       t.level, t.first, t.count, t.child_first, t.nchild,
+                                       np.ascontiguousarray(b.mom.com_m), _ptr(b.mom.quad), b.mom.side,
+                                       b.mom.s_eff, float(theta_guard), float(theta_fb), b.g_first.shape[0],
+                                       b.g_first, b.g_count, _ptr(group_mask),
+                                       np.ascontiguousarray(params, dtype=np.float64),
+                                       np.ascontiguousarray(fmin, dtype=np.float64),
+                                       np.ascontiguousarray(fmax, dtype=np.float64), float(tau), float(eps),
+                                       out, _ptr(mnet), _ptr(mgeo), _ptr(n_pp), _ptr(n_pc))
+    if rc != 0:
+        raise MemoryError("oracle force_groups_learned")
+    return dict(out=out, margin_net=mnet, margin_geo=mgeo, n_pp=n_pp, n_pc=n_pc)
+
+
+def mac_features_one(lo, hi, com_m, quad, side, level, count, mtot):
+    L = lib()
+    L.or_mac_features_one.argtypes = [_f64p, _f64p, _f64p, _vp, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, _f64p]
+    L.or_mac_features_one.restype = ctypes.c_int
+    f = np.zeros(NF)
+    q = None if quad is None else np.ascontiguousarray(quad, dtype=np.float64)
+    ok = L.or_mac_features_one(np.asarray(lo, np.float64), np.asarray(hi, np.float64),
+                               np.asarray(com_m, np.float64), _ptr(q), float(side), int(level), int(count),
+                               float(mtot), f)
+    return f if ok else None

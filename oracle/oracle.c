@@ -658,3 +658,358 @@ void or_pc_eval(const double* x, const double* com_m, const double* quad, double
     or_pc(x[0], x[1], x[2], com_m, quad, eps * eps, acc);
     for (int a = 0; a < 4; a++) out[a] = acc[a];
 }
+
+/* ========================================================================
+ * Learned opening criterion (an extension of Eq. 2's test, not in the paper).
+ *
+ * A small network predicts, for a (group, node) pair, log10 of the node's
+ * relative force-error contribution; the node is accepted when the
+ * prediction is below log10(tau) and a permissive geometric guard (Eq. 2 with
+ * theta_max, applied to the group's box, node holding no member) passes.
+ *
+ * Features (all FP64 here):
+ *   f1 = l / d            l = node cube side, d = |COM - group box centre|
+ *   f2 = log10(M / M_tot)
+ *   f3 = |I - (T/3) 1|_F / (M l^2)     (0 when no second moments)
+ *   f4 = r_g / d          r_g = half diagonal of the group box
+ *   f5 = level / 10
+ *   f6 = log2(count) / 24
+ * Network 6 -> 32 -> 32 -> 1, ReLU hidden layers; parameters packed as
+ * W1[32][6], b1[32], W2[32][32], b2[32], W3[32], b3 (1313 values).
+ * ====================================================================== */
+#define OR_NF 6
+#define OR_NH 32
+#define OR_NPARAM (OR_NH * OR_NF + OR_NH + OR_NH * OR_NH + OR_NH + OR_NH + 1)
+
+int or_mlp_nparams(void) { return OR_NPARAM; }
+
+/* float -> bf16 -> float, round to nearest even (inference emulation) */
+static double or_bf16(double x)
+{
+    float f = (float)x;
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    const uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    u &= 0xffff0000u;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+/* Forward pass of one sample; h1/h2 receive the hidden activations (after
+ * ReLU) when non-NULL.  bf16 != 0 rounds inputs, weights and hidden
+ * activations to bfloat16 as the in-walk inference does. */
+static double or_mlp_one(const double* P, const double* x, int bf16, double* h1o, double* h2o)
+{
+    const double *W1 = P, *b1 = W1 + OR_NH * OR_NF, *W2 = b1 + OR_NH, *b2 = W2 + OR_NH * OR_NH,
+                 *W3 = b2 + OR_NH, *b3 = W3 + OR_NH;
+    double xin[OR_NF], h1[OR_NH], h2[OR_NH];
+    for (int k = 0; k < OR_NF; k++) xin[k] = bf16 ? or_bf16(x[k]) : x[k];
+    for (int j = 0; j < OR_NH; j++) {
+        double s = b1[j];
+        for (int k = 0; k < OR_NF; k++) s += (bf16 ? or_bf16(W1[j * OR_NF + k]) : W1[j * OR_NF + k]) * xin[k];
+        h1[j] = s > 0 ? s : 0;
+        if (bf16) h1[j] = or_bf16(h1[j]);
+    }
+    for (int j = 0; j < OR_NH; j++) {
+        double s = b2[j];
+        for (int k = 0; k < OR_NH; k++) s += (bf16 ? or_bf16(W2[j * OR_NH + k]) : W2[j * OR_NH + k]) * h1[k];
+        h2[j] = s > 0 ? s : 0;
+        if (bf16) h2[j] = or_bf16(h2[j]);
+    }
+    double y = b3[0];
+    for (int k = 0; k < OR_NH; k++) y += (bf16 ? or_bf16(W3[k]) : W3[k]) * h2[k];
+    if (h1o) memcpy(h1o, h1, sizeof(h1));
+    if (h2o) memcpy(h2o, h2, sizeof(h2));
+    return y;
+}
+
+void or_mlp_forward(const double* P, int64_t ns, const double* X, int bf16, double* y)
+{
+    int64_t i;
+#pragma omp parallel for schedule(static)
+    for (i = 0; i < ns; i++) y[i] = or_mlp_one(P, X + OR_NF * i, bf16, NULL, NULL);
+}
+
+/* Weighted mean squared error on log10 errors: w = under_weight when the
+ * prediction is below the label (an under-predicted error is the unsafe
+ * side), else 1.  Returns the loss; grad (OR_NPARAM) = d loss / d params. */
+double or_mlp_loss_grad(const double* P, int64_t ns, const double* X, const double* Y, double under_weight,
+                        double* grad)
+{
+    const double *W2 = P + OR_NH * OR_NF + OR_NH, *W3 = W2 + OR_NH * OR_NH + OR_NH;
+    memset(grad, 0, sizeof(double) * OR_NPARAM);
+    double* gW1 = grad;
+    double* gb1 = gW1 + OR_NH * OR_NF;
+    double* gW2 = gb1 + OR_NH;
+    double* gb2 = gW2 + OR_NH * OR_NH;
+    double* gW3 = gb2 + OR_NH;
+    double* gb3 = gW3 + OR_NH;
+    double loss = 0;
+    for (int64_t i = 0; i < ns; i++) {
+        double h1[OR_NH], h2[OR_NH];
+        const double* x = X + OR_NF * i;
+        const double yh = or_mlp_one(P, x, 0, h1, h2);
+        const double r = yh - Y[i];
+        const double w = (yh < Y[i]) ? under_weight : 1.0;
+        loss += w * r * r;
+        const double dy = 2.0 * w * r / (double)ns;
+        gb3[0] += dy;
+        double dh2[OR_NH], dh1[OR_NH];
+        for (int k = 0; k < OR_NH; k++) {
+            gW3[k] += dy * h2[k];
+            dh2[k] = h2[k] > 0 ? dy * W3[k] : 0;
+        }
+        for (int k = 0; k < OR_NH; k++) dh1[k] = 0;
+        for (int j = 0; j < OR_NH; j++) {
+            gb2[j] += dh2[j];
+            for (int k = 0; k < OR_NH; k++) {
+                gW2[j * OR_NH + k] += dh2[j] * h1[k];
+                dh1[k] += dh2[j] * W2[j * OR_NH + k];
+            }
+        }
+        for (int j = 0; j < OR_NH; j++) {
+            const double d1 = h1[j] > 0 ? dh1[j] : 0;
+            gb1[j] += d1;
+            for (int k = 0; k < OR_NF; k++) gW1[j * OR_NF + k] += d1 * x[k];
+        }
+    }
+    return loss / (double)ns;
+}
+
+/* One Adam step (Kingma & Ba 2015) with bias correction; t counts from 1. */
+void or_adam_step(int64_t np, double* P, const double* g, double* m, double* v, int64_t t, double lr, double b1,
+                  double b2, double eps)
+{
+    const double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
+    for (int64_t k = 0; k < np; k++) {
+        m[k] = b1 * m[k] + (1 - b1) * g[k];
+        v[k] = b2 * v[k] + (1 - b2) * g[k] * g[k];
+        P[k] -= lr * (m[k] / c1) / (sqrt(v[k] / c2) + eps);
+    }
+}
+
+/* Features of (group box [lo, hi], node v); returns 0 when d == 0. */
+static int or_mac_feat(const double* lo, const double* hi, const double* cm, const double* qd, double side,
+                       int level, int count, double mtot, double* f)
+{
+    double c[3], r2 = 0, d2 = 0;
+    for (int a = 0; a < 3; a++) {
+        c[a] = 0.5 * (lo[a] + hi[a]);
+        r2 += 0.25 * (hi[a] - lo[a]) * (hi[a] - lo[a]);
+        d2 += (cm[a] - c[a]) * (cm[a] - c[a]);
+    }
+    const double d = sqrt(d2);
+    if (!(d > 0)) return 0;
+    double qn = 0;
+    if (qd && cm[3] > 0) {
+        const double T = qd[0] + qd[1] + qd[2];
+        const double a0 = qd[0] - T / 3, a1 = qd[1] - T / 3, a2 = qd[2] - T / 3;
+        qn = sqrt(a0 * a0 + a1 * a1 + a2 * a2 + 2 * (qd[3] * qd[3] + qd[4] * qd[4] + qd[5] * qd[5])) /
+             (cm[3] * side * side);
+    }
+    f[0] = side / d;
+    f[1] = (cm[3] > 0 && mtot > 0) ? log10(cm[3] / mtot) : -30.0;
+    f[2] = qn;
+    f[3] = sqrt(r2) / d;
+    f[4] = level / 10.0;
+    f[5] = log2((double)count) / 24.0;
+    return 1;
+}
+
+/* Training pairs: for each listed group, the nodes accepted by the guard
+ * alone (Eq. 2 with theta_guard via s_eff_guard, node holding no member),
+ * their features, and the label log10(max over members of
+ * |a_PC(node) - a_exact(node)| / |a_total,member|), a_PC with the given
+ * order (quad may be NULL), a_exact the direct sum over the node's
+ * particles.  a_tot: per Morton position, |a| of the member's total force.
+ * The walk also descends into a guard-passing internal node whose label
+ * exceeds descend_above (the network meets such nodes' children whenever it
+ * rejects them), so the pairs cover every depth the network is asked about.
+ * Returns the number of pairs written, or -1 if cap is exceeded. */
+int64_t or_mac_training_pairs(const float* spos, int64_t nn, const int32_t* level, const int32_t* first,
+                              const int32_t* count, const int32_t* child_first, const int32_t* nchild,
+                              const double* com_m, const double* quad, const double* side,
+                              const double* s_eff_guard, int64_t ng, const int32_t* gl_first,
+                              const int32_t* gl_count, const double* a_tot, double eps, double descend_above,
+                              int64_t cap, double* X, double* Y, int32_t* pair_group, int32_t* pair_node)
+{
+    const double e2 = eps * eps, mtot = com_m[3];
+    int64_t np = 0;
+    int32_t* stack = (int32_t*)malloc((size_t)nn * sizeof(int32_t));
+    if (!stack) return -1;
+    for (int64_t g = 0; g < ng; g++) {
+        const int64_t gb = gl_first[g], ge = gb + gl_count[g];
+        double lo[3], hi[3];
+        for (int a = 0; a < 3; a++) lo[a] = hi[a] = spos[4 * gb + a];
+        for (int64_t k = gb; k < ge; k++)
+            for (int a = 0; a < 3; a++) {
+                const double v = spos[4 * k + a];
+                if (v < lo[a]) lo[a] = v;
+                if (v > hi[a]) hi[a] = v;
+            }
+        int64_t sp = 0;
+        stack[sp++] = 0;
+        while (sp > 0) {
+            const int32_t v = stack[--sp];
+            const double* c = com_m + 4 * v;
+            double d2 = 0;
+            for (int a = 0; a < 3; a++) {
+                double t = 0;
+                if (c[a] < lo[a]) t = lo[a] - c[a];
+                else if (c[a] > hi[a]) t = c[a] - hi[a];
+                d2 += t * t;
+            }
+            const int member = first[v] < ge && (int64_t)first[v] + count[v] > gb;
+            if (d2 > s_eff_guard[v] && !member) {
+                double f[OR_NF];
+                if (!or_mac_feat(lo, hi, c, quad ? quad + 6 * v : NULL, side[v], level[v], count[v], mtot, f))
+                    continue;
+                double worst = 0;
+                for (int64_t i = gb; i < ge; i++) {
+                    const double xi = spos[4 * i], yi = spos[4 * i + 1], zi = spos[4 * i + 2];
+                    double apc[5] = {0, 0, 0, 0, 0}, aex[5] = {0, 0, 0, 0, 0};
+                    or_pc(xi, yi, zi, c, quad ? quad + 6 * v : NULL, e2, apc);
+                    for (int64_t j = first[v]; j < (int64_t)first[v] + count[v]; j++)
+                        or_pp(xi, yi, zi, spos + 4 * j, e2, aex);
+                    const double dx = apc[0] - aex[0], dy = apc[1] - aex[1], dz = apc[2] - aex[2];
+                    const double e = sqrt(dx * dx + dy * dy + dz * dz) / a_tot[i];
+                    if (e > worst) worst = e;
+                }
+                if (np >= cap) {
+                    free(stack);
+                    return -1;
+                }
+                for (int k = 0; k < OR_NF; k++) X[OR_NF * np + k] = f[k];
+                Y[np] = log10(worst > 1e-12 ? worst : 1e-12);
+                pair_group[np] = (int32_t)g;
+                pair_node[np] = v;
+                np++;
+                if (worst > descend_above && nchild[v] > 0)
+                    for (int ch = nchild[v] - 1; ch >= 0; ch--) stack[sp++] = child_first[v] + ch;
+            } else if (nchild[v] > 0) {
+                for (int ch = nchild[v] - 1; ch >= 0; ch--) stack[sp++] = child_first[v] + ch;
+            }
+        }
+    }
+    free(stack);
+    return np;
+}
+
+/* Group walk with the learned criterion.  A node passing the guard
+ * (s_eff_guard, no member held) is accepted when the network's prediction
+ * (bf16 inference emulation) is below log10(tau); when a feature lies outside
+ * [fmin, fmax] the plain Eq. (2) test with theta_fb decides instead
+ * (S_fb = (l/theta_fb + s)^2, s recovered from the guard's S_eff).
+ * margin: per target, min over its group's network decisions of
+ * |prediction - log10 tau| (infinity if none), and the guard margins. */
+int or_force_groups_learned(int64_t n, const float* spos, const uint32_t* perm, int64_t nn, const int32_t* level,
+                            const int32_t* first, const int32_t* count, const int32_t* child_first,
+                            const int32_t* nchild, const double* com_m, const double* quad, const double* side,
+                            const double* s_eff_guard, double theta_guard, double theta_fb, int64_t ng,
+                            const int32_t* g_first, const int32_t* g_count, const uint8_t* group_mask,
+                            const double* P, const double* fmin, const double* fmax, double tau, double eps,
+                            double* out, double* margin_net, double* margin_geo, int64_t* n_pp, int64_t* n_pc)
+{
+    const double e2 = eps * eps, mtot = com_m[3], ltau = log10(tau);
+    int err = 0;
+    (void)n;
+    int64_t g;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (g = 0; g < ng; g++) {
+        if (group_mask && !group_mask[g]) continue;
+        const int64_t gb = g_first[g], ge = gb + g_count[g];
+        double lo[3], hi[3];
+        for (int a = 0; a < 3; a++) lo[a] = hi[a] = spos[4 * gb + a];
+        for (int64_t k = gb; k < ge; k++)
+            for (int a = 0; a < 3; a++) {
+                const double v = spos[4 * k + a];
+                if (v < lo[a]) lo[a] = v;
+                if (v > hi[a]) hi[a] = v;
+            }
+        int32_t* stack = (int32_t*)malloc((size_t)nn * sizeof(int32_t));
+        int32_t* pc = (int32_t*)malloc((size_t)nn * sizeof(int32_t));
+        int32_t* pp = (int32_t*)malloc((size_t)nn * sizeof(int32_t));
+        if (!stack || !pc || !pp) {
+            free(stack); free(pc); free(pp);
+#pragma omp atomic write
+            err = -1;
+            continue;
+        }
+        int64_t sp = 0, npc = 0, npp = 0;
+        double mnet = INFINITY, mgeo = INFINITY;
+        stack[sp++] = 0;
+        while (sp > 0) {
+            const int32_t v = stack[--sp];
+            const double* c = com_m + 4 * v;
+            double d2 = 0;
+            for (int a = 0; a < 3; a++) {
+                double t = 0;
+                if (c[a] < lo[a]) t = lo[a] - c[a];
+                else if (c[a] > hi[a]) t = c[a] - hi[a];
+                d2 += t * t;
+            }
+            const int member = first[v] < ge && (int64_t)first[v] + count[v] > gb;
+            int accept = 0;
+            if (!member) {
+                const double S = s_eff_guard[v];
+                const double mg = fabs(d2 - S) / S;
+                if (mg < mgeo) mgeo = mg;
+                if (d2 > S) {
+                    double f[OR_NF];
+                    int inrange = or_mac_feat(lo, hi, c, quad ? quad + 6 * v : NULL, side[v], level[v], count[v],
+                                              mtot, f);
+                    for (int k = 0; inrange && k < OR_NF; k++)
+                        if (f[k] < fmin[k] || f[k] > fmax[k]) inrange = 0;
+                    if (inrange) {
+                        const double yh = or_mlp_one(P, f, 1, NULL, NULL);
+                        const double mn = fabs(yh - ltau);
+                        if (mn < mnet) mnet = mn;
+                        accept = yh < ltau;
+                    } else {
+                        const double s = sqrt(S) - side[v] / theta_guard;
+                        const double t = side[v] / theta_fb + (s > 0 ? s : 0);
+                        const double Sf = t * t;
+                        const double mf = fabs(d2 - Sf) / Sf;
+                        if (mf < mgeo) mgeo = mf;
+                        accept = d2 > Sf;
+                    }
+                }
+            }
+            if (accept) pc[npc++] = v;
+            else if (nchild[v] == 0) pp[npp++] = v;
+            else
+                for (int ch = nchild[v] - 1; ch >= 0; ch--) stack[sp++] = child_first[v] + ch;
+        }
+        for (int64_t i = gb; i < ge; i++) {
+            const double xi = spos[4 * i], yi = spos[4 * i + 1], zi = spos[4 * i + 2];
+            double acc[5] = {0, 0, 0, 0, 0};
+            int64_t cnt_pp = 0;
+            for (int64_t t = 0; t < npc; t++)
+                or_pc(xi, yi, zi, com_m + 4 * pc[t], quad ? quad + 6 * pc[t] : NULL, e2, acc);
+            for (int64_t t = 0; t < npp; t++)
+                for (int64_t j = first[pp[t]]; j < (int64_t)first[pp[t]] + count[pp[t]]; j++) {
+                    if (j == i) continue;
+                    or_pp(xi, yi, zi, spos + 4 * j, e2, acc);
+                    cnt_pp++;
+                }
+            const int64_t o = perm[i];
+            for (int a = 0; a < 4; a++) out[4 * o + a] = acc[a];
+            if (margin_net) margin_net[o] = mnet;
+            if (margin_geo) margin_geo[o] = mgeo;
+            if (n_pp) n_pp[o] = cnt_pp;
+            if (n_pc) n_pc[o] = npc;
+        }
+        free(stack);
+        free(pc);
+        free(pp);
+    }
+    return err;
+}
+
+/* Features of one (group box, node) pair (for the feature pins). */
+int or_mac_features_one(const double* lo, const double* hi, const double* cm, const double* qd, double side,
+                        int level, int count, double mtot, double* f)
+{
+    return or_mac_feat(lo, hi, cm, qd, side, level, count, mtot, f);
+}
