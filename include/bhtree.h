@@ -55,7 +55,7 @@ typedef struct bh_config {
     int group_size;          /* G: particles per walk group, 1..256 */
     int order;               /* 1 = monopole (the paper), 2 = monopole + quadrupole */
     int fp64_node_threshold; /* nodes holding >= this many particles combine moments in FP64 */
-    int block_threads;       /* threads per block of the walk kernel (multiple of 32, 64..1024) */
+    int block_threads;       /* threads per block of the walk kernel: 64 or 128 */
     int blocks_per_sm;       /* resident walk blocks per SM for the persistent grid (0 = auto) */
     int reserved[2];
 } bh_config;
@@ -152,6 +152,73 @@ int direct_force(const float* d_src, int64_t n_src, const float* d_tgt, const in
  * Errors: BH_ERR_INVALID (null/misaligned/non-device pointer, n < 0). */
 int bh_kick_drift(bh_ctx* ctx, float* d_pos, float* d_vel, const float* d_acc, int64_t n, float dt_kick,
                   float dt_drift, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned opening criterion.  An extension of Eq. (2)'s test (the paper's
+ * criterion is purely geometric): a 6 -> 32 -> 32 -> 1 ReLU network predicts
+ * log10 of a node's relative force-error contribution to a group from the
+ * features f1 = l/d (l cube side, d = |COM - group box centre|),
+ * f2 = log10(M/M_total), f3 = |I - (T/3)1|_F / (M l^2) (0 for order 1),
+ * f4 = r_g/d (r_g = half diagonal of the group box), f5 = level/10,
+ * f6 = log2(count)/24.  Parameters: 1313 floats packed W1[32][6], b1[32],
+ * W2[32][32], b2[32], W3[32], b3.  In the walk the network runs as BF16
+ * tensor-core MMAs with FP32 accumulation.
+ * ------------------------------------------------------------------------- */
+
+/* Switch ctx to the learned criterion (h_params: host, 1313 FP32) or back to
+ * the plain criterion (h_params NULL).  With the learned criterion a node is
+ * accepted when Eq. (2) with the theta given to tree_moments (the guard)
+ * passes, it holds no group member, and the prediction is below log10(tau);
+ * if a feature lies outside [h_fmin[k], h_fmax[k]] (host, 6 floats each) the
+ * plain criterion at theta_fb decides instead.  Synchronises the device;
+ * tree_moments must run again before tree_force.
+ * Errors: BH_ERR_INVALID (tau or theta_fb <= 0, non-finite parameters). */
+int bh_mac_set(bh_ctx* ctx, const float* h_params, const float* h_fmin, const float* h_fmax, float tau,
+               float theta_fb);
+
+/* Training data for the criterion, measured by the method itself: for each
+ * group index in d_groups (n_groups int32) the kernel walks the tree with the
+ * guard (Eq. 2 at tree_moments' theta, no member held) and, for every node
+ * passing it, writes the six features to d_X (float[cap][6]) and the label
+ * log10(max over members of |a_PC(node) - a_direct(node)| / |a_ref|) to d_Y
+ * (float[cap]); a_direct sums the node's particles, d_acc_ref (n float4,
+ * caller order) gives each member's reference total acceleration.  It also
+ * descends into such nodes while their label exceeds log10_floor.
+ * *d_count (device u64, caller-zeroed) receives the number of pairs found;
+ * only the first cap are written, in no particular order; d_pairs (int32
+ * [cap][2], or NULL) receives each pair's (node index, group index).
+ * Needs tree_build + tree_moments.
+ * Errors: BH_ERR_INVALID, BH_ERR_STATE. */
+int bh_mac_label(bh_ctx* ctx, const int32_t* d_groups, int64_t n_groups, const float* d_acc_ref, float eps,
+                 float log10_floor, float* d_X, float* d_Y, int32_t* d_pairs, int64_t cap,
+                 unsigned long long* d_count, void* stream);
+
+/* `steps` Adam steps (lr, beta 0.9 / 0.999, eps 1e-8; step t0+1 onwards) of
+ * the network on (d_X float[n][6], d_Y float[n]) with the weighted squared
+ * loss w (y_hat - y)^2, w = under_weight when y_hat < y (an under-estimated
+ * error is the unsafe side) else 1.  Mini-batches of `batch` samples are
+ * taken in the order d_order (int32[n], a permutation drawn by the caller;
+ * NULL = 0..n-1), continuing from sample t0*batch.  d_params (1313 FP32
+ * master weights), d_adam_m / d_adam_v (1313 each) are updated in place;
+ * d_loss (float[steps], caller-zeroed, or NULL) receives each step's loss.
+ * d_work: at least batch*135 + 1313 floats of scratch.
+ * Errors: BH_ERR_INVALID, BH_ERR_TOO_LARGE (work too small). */
+int bh_mlp_train(const float* d_X, const float* d_Y, const int32_t* d_order, int64_t n, float* d_params,
+                 float* d_adam_m, float* d_adam_v, float* d_work, int64_t work_floats, int64_t steps, int batch,
+                 float lr, float under_weight, float* d_loss, int64_t t0, void* stream);
+
+/* Gradient (d_grad, 1313) and loss (*d_loss, caller-zeroed, or NULL) of the
+ * mean weighted loss over n samples, FP32.  d_work: n*135 floats.
+ * Errors: BH_ERR_INVALID, BH_ERR_TOO_LARGE. */
+int bh_mlp_grad(const float* d_params, const float* d_X, const float* d_Y, int64_t n, float under_weight,
+                float* d_work, int64_t work_floats, float* d_grad, float* d_loss, void* stream);
+
+/* Network predictions d_y[n] for d_X[n][6]: precision 32 = FP32 with the
+ * device parameters d_params (training path); precision 16 = the walk's BF16
+ * tensor-core path with the network loaded into ctx by bh_mac_set.
+ * Errors: BH_ERR_INVALID, BH_ERR_STATE (precision 16 without a network). */
+int bh_mlp_forward(bh_ctx* ctx, const float* d_params, const float* d_X, int64_t n, float* d_y, int precision,
+                   void* stream);
 
 /* Whole force evaluation for callers that cannot allocate device memory.
  * The paper has no counterpart: this is a service of this library.  Code

@@ -32,7 +32,10 @@ EXPORT = dict(keys=1, perm=2, spos=3, node_first=4, node_count=5, node_child=6, 
 # the symbols declared in include/bhtree.h
 SYMBOLS = ["bh_version", "bh_strerror", "bh_config_default", "bh_create", "bh_destroy", "tree_build",
            "tree_moments", "tree_force", "direct_force", "bh_kick_drift", "bh_status", "bh_stats",
-           "bh_export", "bh_tree_force_static"]
+           "bh_export", "bh_tree_force_static", "bh_mac_set", "bh_mac_label", "bh_mlp_train", "bh_mlp_grad",
+           "bh_mlp_forward"]
+MLP_NPARAM = 1313
+MLP_ACT = 135  # floats of training scratch per sample
 STATIC_MAX_N = 32768
 
 
@@ -99,6 +102,18 @@ def lib():
         L.bh_tree_force_static.argtypes = [vp, i64, ctypes.POINTER(BhConfig), ctypes.c_float, ctypes.c_float, vp,
                                            ctypes.POINTER(ctypes.c_int), vp]
         L.bh_tree_force_static.restype = i32
+        f32p = ctypes.POINTER(ctypes.c_float)
+        L.bh_mac_set.argtypes = [vp, f32p, f32p, f32p, ctypes.c_float, ctypes.c_float]
+        L.bh_mac_set.restype = i32
+        L.bh_mac_label.argtypes = [vp, vp, i64, vp, ctypes.c_float, ctypes.c_float, vp, vp, vp, i64, vp, vp]
+        L.bh_mac_label.restype = i32
+        L.bh_mlp_train.argtypes = [vp, vp, vp, i64, vp, vp, vp, vp, i64, i64, i32, ctypes.c_float,
+                                   ctypes.c_float, vp, i64, vp]
+        L.bh_mlp_train.restype = i32
+        L.bh_mlp_grad.argtypes = [vp, vp, vp, i64, ctypes.c_float, vp, i64, vp, vp, vp]
+        L.bh_mlp_grad.restype = i32
+        L.bh_mlp_forward.argtypes = [vp, vp, vp, i64, vp, i32, vp]
+        L.bh_mlp_forward.restype = i32
         L.bh_status.argtypes = [vp, vp]
         L.bh_status.restype = i32
         L.bh_stats.argtypes = [vp, vp, ctypes.POINTER(BhStats)]
@@ -179,6 +194,45 @@ def bh_tree_force_static(pos, theta, eps, out, cfg=None, stream=None):
                                     ctypes.c_float(theta), ctypes.c_float(eps), _dptr(out), ctypes.byref(st),
                                     _stream(stream))
     return rc, st.value
+
+
+def _f32host(a):
+    a = np.ascontiguousarray(a, dtype=np.float32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def bh_mac_set(h, params=None, fmin=None, fmax=None, tau=1e-3, theta_fb=0.5):
+    """Learned criterion on (params: 1313 host floats) or off (params None)."""
+    if params is None:
+        return lib().bh_mac_set(h, None, None, None, ctypes.c_float(1.0), ctypes.c_float(1.0))
+    p, pp = _f32host(params)
+    lo, plo = _f32host(fmin)
+    hi, phi = _f32host(fmax)
+    return lib().bh_mac_set(h, pp, plo, phi, ctypes.c_float(tau), ctypes.c_float(theta_fb))
+
+
+def bh_mac_label(h, groups, acc_ref, eps, log10_floor, X, Y, count, pairs=None, stream=None):
+    return lib().bh_mac_label(h, _dptr(groups), int(groups.numel()), _dptr(acc_ref), ctypes.c_float(eps),
+                              ctypes.c_float(log10_floor), _dptr(X), _dptr(Y), _dptr(pairs), int(Y.numel()),
+                              _dptr(count), _stream(stream))
+
+
+def bh_mlp_train(X, Y, order, params, adam_m, adam_v, work, steps, batch, lr, under_weight, loss, t0,
+                 stream=None):
+    return lib().bh_mlp_train(_dptr(X), _dptr(Y), _dptr(order), int(Y.numel()), _dptr(params), _dptr(adam_m),
+                              _dptr(adam_v), _dptr(work), int(work.numel()), int(steps), int(batch),
+                              ctypes.c_float(lr), ctypes.c_float(under_weight), _dptr(loss), int(t0),
+                              _stream(stream))
+
+
+def bh_mlp_grad(params, X, Y, under_weight, work, grad, loss, stream=None):
+    return lib().bh_mlp_grad(_dptr(params), _dptr(X), _dptr(Y), int(Y.numel()), ctypes.c_float(under_weight),
+                             _dptr(work), int(work.numel()), _dptr(grad), _dptr(loss), _stream(stream))
+
+
+def bh_mlp_forward(h, params, X, y, precision, stream=None):
+    return lib().bh_mlp_forward(h, _dptr(params), _dptr(X), int(y.numel()), _dptr(y), int(precision),
+                                _stream(stream))
 
 
 def bh_status(h, stream=None):

@@ -12,7 +12,7 @@
 #include <cstring>
 #include <new>
 
-#include "bh_internal.cuh"
+#include "bh_mlp.cuh"
 
 struct bh_ctx {
     int device = 0;
@@ -36,6 +36,10 @@ struct bh_ctx {
     uint8_t* flags = nullptr;
     int32_t *g_first = nullptr, *g_count = nullptr;
     bh_nodes nd{};
+    // learned opening criterion
+    bool mac_learned = false;
+    float4* mfeat = nullptr;        // node-constant features
+    bh_mlp_dev* mlp = nullptr;      // packed network (device)
 };
 
 namespace {
@@ -111,7 +115,7 @@ static int validate_config(const bh_config* c)
     if (c->group_size < 1 || c->group_size > 256) return BH_ERR_INVALID;
     if (c->order != 1 && c->order != 2) return BH_ERR_INVALID;
     if (c->fp64_node_threshold < 1) return BH_ERR_INVALID;
-    if (c->block_threads != 64 && c->block_threads != 128 && c->block_threads != 256) return BH_ERR_INVALID;
+    if (c->block_threads != 64 && c->block_threads != 128) return BH_ERR_INVALID;
     if (c->blocks_per_sm < 0 || c->blocks_per_sm > 32) return BH_ERR_INVALID;
     return BH_OK;
 }
@@ -169,6 +173,8 @@ int bh_create(bh_ctx** out, const bh_config* cfg, int64_t max_n, int device)
     const size_t o_quad = c.order >= 2 ? take(NN * 2 * sizeof(float4)) : 0;
     const size_t o_com64 = take(NN * sizeof(bh_double4));
     const size_t o_quad64 = c.order >= 2 ? take(NN * 6 * sizeof(double)) : 0;
+    const size_t o_mfeat = take(NN * sizeof(float4));
+    const size_t o_mlp = take(sizeof(bh_mlp_dev));
     const size_t total = off;
 
     if (cudaMalloc(&x->slab, total) != cudaSuccess) {
@@ -206,6 +212,8 @@ int bh_create(bh_ctx** out, const bh_config* cfg, int64_t max_n, int device)
     x->nd.quad = c.order >= 2 ? (float4*)(b + o_quad) : nullptr;
     x->nd.com64 = (bh_double4*)(b + o_com64);
     x->nd.quad64 = c.order >= 2 ? (double*)(b + o_quad64) : nullptr;
+    x->mfeat = (float4*)(b + o_mfeat);
+    x->mlp = (bh_mlp_dev*)(b + o_mlp);
     // look-back words start at epoch 0, which no pass uses; control block zeroed
     if (cudaMemset(x->lookback, 0, sort_tiles * 256 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMemset(x->ctrl, 0, sizeof(bh_dev_ctrl)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
@@ -269,6 +277,10 @@ int tree_moments(bh_ctx* x, float theta, void* stream)
         bh::launch_moments(x->pos_s, x->keys, x->nd, x->cfg.order, theta, x->cfg.fp64_node_threshold, x->ctrl,
                            grid_for(x), s);
         x->launches += bh::kLaunchesMoments;
+        if (x->mac_learned) {
+            bh::launch_mac_nodefeat(x->nd, x->cfg.order, x->mfeat, x->ctrl, grid_for(x), s);
+            x->launches += 1;
+        }
     }
     if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
     x->theta = theta;
@@ -285,9 +297,10 @@ int tree_force(bh_ctx* x, float eps, float* d_acc_pot, void* stream)
     if (!d_acc_pot || !aligned16(d_acc_pot) || !is_device_ptr(d_acc_pot, x->device)) return BH_ERR_INVALID;
     DeviceGuard guard(x->device);
     cudaStream_t s = (cudaStream_t)stream;
+    bh::WalkLearned wl{x->mfeat, x->mlp, x->theta};
     int rc = bh::launch_walk(x->pos_s, x->vals, x->g_first, x->g_count, x->nd, x->cfg.order, x->cfg.group_size,
                              eps, (float4*)d_acc_pot, x->ctrl, x->sm_count, x->cfg.block_threads,
-                             x->cfg.blocks_per_sm, s);
+                             x->cfg.blocks_per_sm, s, x->mac_learned ? &wl : nullptr);
     if (rc) return rc;
     x->launches += bh::kLaunchesForce;
     if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
@@ -442,6 +455,99 @@ int bh_export(bh_ctx* x, int what, void* dst, int64_t cap_bytes, int64_t* out_by
     if (cudaMemcpyAsync(dst, src, (size_t)bytes, cudaMemcpyDefault, s) != cudaSuccess) return BH_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return BH_ERR_CUDA;
     return BH_OK;
+}
+
+// ------------------------------------------------------------------ learned criterion
+int bh_mac_set(bh_ctx* x, const float* h_params, const float* h_fmin, const float* h_fmax, float tau,
+               float theta_fb)
+{
+    if (!x) return BH_ERR_INVALID;
+    if (!h_params) {
+        x->mac_learned = false;
+        x->have_moments = false;
+        return BH_OK;
+    }
+    if (!h_fmin || !h_fmax || !(tau > 0.0f) || !std::isfinite(tau) || !(theta_fb > 0.0f) || !std::isfinite(theta_fb))
+        return BH_ERR_INVALID;
+    for (int k = 0; k < BH_MLP_NPARAM; k++)
+        if (!std::isfinite(h_params[k])) return BH_ERR_INVALID;
+    bh_mlp_dev host;
+    bh::mlp_pack(h_params, h_fmin, h_fmax, std::log10(tau), theta_fb, &host);
+    DeviceGuard guard(x->device);
+    // the packed copy may be read by enqueued walks: wait for them first
+    if (cudaDeviceSynchronize() != cudaSuccess || cudaMemcpy(x->mlp, &host, sizeof(host), cudaMemcpyHostToDevice) !=
+                                                      cudaSuccess)
+        return BH_ERR_CUDA;
+    x->mac_learned = true;
+    x->have_moments = false;  // node features are computed by the next tree_moments
+    return BH_OK;
+}
+
+int bh_mac_label(bh_ctx* x, const int32_t* d_groups, int64_t n_groups, const float* d_acc_ref, float eps,
+                 float log10_floor, float* d_X, float* d_Y, int32_t* d_pairs, int64_t cap,
+                 unsigned long long* d_count, void* stream)
+{
+    if (d_pairs && x && !is_device_ptr(d_pairs, x->device)) return BH_ERR_INVALID;
+    if (!x || n_groups < 0 || cap < 0 || !(eps >= 0.0f) || !std::isfinite(eps)) return BH_ERR_INVALID;
+    if (x->n < 0 || !x->have_moments) return BH_ERR_STATE;
+    if (n_groups >= ((int64_t)1 << 31)) return BH_ERR_TOO_LARGE;
+    if (n_groups == 0 || x->n == 0) return BH_OK;
+    for (const void* p : {(const void*)d_groups, (const void*)d_X, (const void*)d_Y, (const void*)d_count})
+        if (!p || !is_device_ptr(p, x->device)) return BH_ERR_INVALID;
+    if (!d_acc_ref || !aligned16(d_acc_ref) || !is_device_ptr(d_acc_ref, x->device)) return BH_ERR_INVALID;
+    DeviceGuard guard(x->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    bh::launch_mac_nodefeat(x->nd, x->cfg.order, x->mfeat, x->ctrl, grid_for(x), s);
+    x->launches += 2;
+    return bh::mac_label(x->pos_s, x->vals, x->g_first, x->g_count, d_groups, (int)n_groups, x->nd, x->mfeat,
+                         (const float4*)d_acc_ref, eps, log10_floor, x->cfg.order, d_X, d_Y, d_pairs, (long long)cap,
+                         d_count, x->ctrl, s);
+}
+
+int bh_mlp_train(const float* d_X, const float* d_Y, const int32_t* d_order, int64_t n, float* d_params,
+                 float* d_adam_m, float* d_adam_v, float* d_work, int64_t work_floats, int64_t steps, int batch,
+                 float lr, float under_weight, float* d_loss, int64_t t0, void* stream)
+{
+    if (n < 1 || steps < 0 || batch < 1 || t0 < 0 || !(lr > 0.0f) || !(under_weight > 0.0f)) return BH_ERR_INVALID;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BH_ERR_CUDA;
+    for (const void* p : {(const void*)d_X, (const void*)d_Y, (const void*)d_params, (const void*)d_adam_m,
+                          (const void*)d_adam_v, (const void*)d_work})
+        if (!p || !is_device_ptr(p, dev)) return BH_ERR_INVALID;
+    if (d_order && !is_device_ptr(d_order, dev)) return BH_ERR_INVALID;
+    if (d_loss && !is_device_ptr(d_loss, dev)) return BH_ERR_INVALID;
+    return bh::mlp_train(d_X, d_Y, d_order, (long long)n, d_params, d_adam_m, d_adam_v, d_work, (long long)work_floats,
+                         (long long)steps, batch, lr, under_weight, d_loss, (long long)t0, (cudaStream_t)stream);
+}
+
+int bh_mlp_grad(const float* d_params, const float* d_X, const float* d_Y, int64_t n, float under_weight,
+                float* d_work, int64_t work_floats, float* d_grad, float* d_loss, void* stream)
+{
+    if (n < 1 || !(under_weight > 0.0f)) return BH_ERR_INVALID;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BH_ERR_CUDA;
+    for (const void* p : {(const void*)d_params, (const void*)d_X, (const void*)d_Y, (const void*)d_work,
+                          (const void*)d_grad})
+        if (!p || !is_device_ptr(p, dev)) return BH_ERR_INVALID;
+    if (d_loss && !is_device_ptr(d_loss, dev)) return BH_ERR_INVALID;
+    return bh::mlp_grad(d_params, d_X, d_Y, (long long)n, under_weight, d_work, (long long)work_floats, d_grad,
+                        d_loss, (cudaStream_t)stream);
+}
+
+int bh_mlp_forward(bh_ctx* x, const float* d_params, const float* d_X, int64_t n, float* d_y, int precision,
+                   void* stream)
+{
+    if (n < 0 || (precision != 16 && precision != 32)) return BH_ERR_INVALID;
+    if (n == 0) return BH_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BH_ERR_CUDA;
+    if (!d_X || !d_y || !is_device_ptr(d_X, dev) || !is_device_ptr(d_y, dev)) return BH_ERR_INVALID;
+    if (precision == 16) {
+        if (!x || !x->mac_learned) return BH_ERR_STATE;
+        return bh::mlp_forward(nullptr, x->mlp, d_X, (long long)n, d_y, 16, (cudaStream_t)stream);
+    }
+    if (!d_params || !is_device_ptr(d_params, dev)) return BH_ERR_INVALID;
+    return bh::mlp_forward(d_params, nullptr, d_X, (long long)n, d_y, 32, (cudaStream_t)stream);
 }
 
 }  // extern "C"

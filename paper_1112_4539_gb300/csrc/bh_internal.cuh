@@ -174,9 +174,19 @@ void launch_groups(const bh_nodes& nd, int n, int G, uint8_t* flags, uint32_t* b
                    int32_t* g_count, bh_dev_ctrl* ctrl, int grid, cudaStream_t s);
 void launch_moments(const float4* pos_s, const uint32_t* keys, const bh_nodes& nd, int order,
                     float theta, int fp64_threshold, bh_dev_ctrl* ctrl, int grid, cudaStream_t s);
+}  // namespace bh
+struct bh_mlp_dev;
+namespace bh {
+// learned-criterion inputs of the walk (null pointer: plain Eq. 2 criterion)
+struct WalkLearned {
+    const float4* mfeat;
+    const bh_mlp_dev* mlp;
+    float theta_guard;
+};
 int launch_walk(const float4* pos_s, const uint32_t* perm, const int32_t* g_first, const int32_t* g_count,
                 const bh_nodes& nd, int order, int G, float eps, float4* out, bh_dev_ctrl* ctrl,
-                int sm_count, int block_threads, int blocks_per_sm, cudaStream_t s);
+                int sm_count, int block_threads, int blocks_per_sm, cudaStream_t s,
+                const WalkLearned* learned = nullptr);
 int launch_direct(const float4* src, int n_src, const float4* tgt, const int64_t* self, int n_tgt,
                   double eps, void* out, int precision, cudaStream_t s);
 void launch_kick_drift(float4* pos, float4* vel, const float4* acc, int n, float dt_kick, float dt_drift, int grid,

@@ -68,7 +68,7 @@ extern "C" int bh_tree_force_static(const float* d_pos_mass, int64_t n, const bh
     }
     if (c.leaf_size < 1 || c.leaf_size > 64 || c.group_size < 1 || c.group_size > 256 ||
         (c.order != 1 && c.order != 2) || c.fp64_node_threshold < 1 ||
-        (c.block_threads != 64 && c.block_threads != 128 && c.block_threads != 256) || c.blocks_per_sm < 0 ||
+        (c.block_threads != 64 && c.block_threads != 128) || c.blocks_per_sm < 0 ||
         c.blocks_per_sm > 32)
         return BH_ERR_INVALID;
     if (n < 0 || !(theta > 0.0f) || !std::isfinite(theta) || !(eps >= 0.0f) || !std::isfinite(eps))

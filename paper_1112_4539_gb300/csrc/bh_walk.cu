@@ -22,7 +22,7 @@
 // pop (<= 32 ranges) are the only entries of their levels.  Hence at most 33
 // ranges per level 1..10 are ever stored: kStackCap = 352 cannot overflow
 // (overflow is still checked and reported as BH_ERR_CAPACITY).
-#include "bh_internal.cuh"
+#include "bh_mlp.cuh"
 
 namespace bh {
 
@@ -51,6 +51,10 @@ struct WalkParams {
     float4* out;
     bh_dev_ctrl* ctrl;
     float eps2;
+    // learned criterion
+    const float4* mfeat;     // node-constant features
+    const bh_mlp_dev* mlp;   // network (global copy)
+    float theta_guard;       // theta of the S_eff in use (the guard)
 };
 
 template <int T>
@@ -209,8 +213,10 @@ __device__ __forceinline__ void bh_eval_self(int gc, float eps2, const float (&x
 
 __device__ __forceinline__ float4 bh_pad_source() { return make_float4(1e18f, 1e18f, 1e18f, 0.0f); }
 
-template <int T, int ORDER>
-__global__ void __launch_bounds__(256) bh_walk_kernel(WalkParams P)
+template <int T, int ORDER, bool LEARNED>
+__global__ void __launch_bounds__(128, LEARNED ? (T <= 2 ? 4 : T <= 4 ? 3 : 2)
+                                             : (T <= 1 ? 8 : T <= 2 ? 6 : T <= 4 ? 4 : 2))
+    bh_walk_kernel(WalkParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -218,10 +224,20 @@ __global__ void __launch_bounds__(256) bh_walk_kernel(WalkParams P)
     WarpSmem& S = reinterpret_cast<WarpSmem*>(smem_raw)[wib];
     WarpQuad* Q = nullptr;
     if (ORDER >= 2) Q = reinterpret_cast<WarpQuad*>(smem_raw + (size_t)nwarps * sizeof(WarpSmem)) + wib;
+    // learned criterion: the network (per block) and a feature staging area (per warp)
+    unsigned char* lbase = smem_raw + (size_t)nwarps * (sizeof(WarpSmem) + (ORDER >= 2 ? sizeof(WarpQuad) : 0));
+    bh_mlp_dev* MW = reinterpret_cast<bh_mlp_dev*>(lbase);
+    uint32_t* xs = reinterpret_cast<uint32_t*>(lbase + sizeof(bh_mlp_dev)) + wib * (32 * 8);
+    if (LEARNED) {
+        for (int i = threadIdx.x; i < (int)(sizeof(bh_mlp_dev) / 4); i += blockDim.x)
+            reinterpret_cast<uint32_t*>(MW)[i] = reinterpret_cast<const uint32_t*>(P.mlp)[i];
+        __syncthreads();
+    }
     const unsigned int lt = bh_lanemask_lt();
     const float eps2 = P.eps2;
     bh_dev_ctrl* ctrl = P.ctrl;
     const int ng = (int)ctrl->n_groups;
+    const float boxL = LEARNED ? ctrl->box[3] : 1.0f;
     unsigned long long cnt_pp = 0ull, cnt_pc = 0ull;
 
     for (;;) {
@@ -254,6 +270,9 @@ __global__ void __launch_bounds__(256) bh_walk_kernel(WalkParams P)
         const float bx1 = bh_ord2f(__reduce_max_sync(BH_FULL_MASK, hi0));
         const float by1 = bh_ord2f(__reduce_max_sync(BH_FULL_MASK, hi1));
         const float bz1 = bh_ord2f(__reduce_max_sync(BH_FULL_MASK, hi2));
+        // group centre and radius (features of the learned criterion)
+        const float gcx = 0.5f * (bx0 + bx1), gcy = 0.5f * (by0 + by1), gcz = 0.5f * (bz0 + bz1);
+        const float grg = 0.5f * sqrtf((bx1 - bx0) * (bx1 - bx0) + (by1 - by0) * (by1 - by0) + (bz1 - bz0) * (bz1 - bz0));
 
         Acc<T> A;
 #pragma unroll
@@ -306,7 +325,19 @@ __global__ void __launch_bounds__(256) bh_walk_kernel(WalkParams P)
             const float dz = fmaxf(fmaxf(bz0 - cm.z, cm.z - bz1), 0.0f);
             const float d2 = dx * dx + dy * dy + dz * dz;
             const bool member = (r.x < ge) && (r.x + r.y > gb);
-            const bool acc = has && (d2 > se) && !member;
+            bool acc = has && (d2 > se) && !member;
+            if (LEARNED && __ballot_sync(BH_FULL_MASK, acc)) {
+                // the guard passed: the network decides (the plain criterion at
+                // theta_fb when a feature lies outside the training range)
+                const float4 nf = has ? P.mfeat[v] : make_float4(0.f, 0.f, 0.f, 0.f);
+                float f[BH_MLP_NF], side;
+                bool inr = bh_mac_features(cm, nf, gcx, gcy, gcz, grg, boxL, f, side);
+#pragma unroll
+                for (int k = 0; k < BH_MLP_NF; k++) inr = inr && f[k] >= MW->fmin[k] && f[k] <= MW->fmax[k];
+                const float yh = bh_mlp_warp(*MW, xs, f);
+                const float sfb = fmaxf(sqrtf(se) - side / P.theta_guard, 0.0f) + side / MW->theta_fb;
+                acc = acc && (inr ? (yh < MW->ltau) : (d2 > sfb * sfb));
+            }
             const bool leaf = has && !acc && (r.z < 0);
             const bool opn = has && !acc && (r.z >= 0);
 
@@ -437,13 +468,14 @@ __global__ void bh_walk_reset_kernel(bh_dev_ctrl* c)
     c->n_pc = 0ull;
 }
 
-template <int T, int ORDER>
+template <int T, int ORDER, bool LEARNED>
 static int bh_walk_launch_t(const WalkParams& P, int sm_count, int block_threads, int blocks_per_sm,
                             cudaStream_t s)
 {
     const int nw = block_threads / 32;
-    const size_t smem = (size_t)nw * (sizeof(WarpSmem) + (ORDER >= 2 ? sizeof(WarpQuad) : 0));
-    auto kern = bh_walk_kernel<T, ORDER>;
+    size_t smem = (size_t)nw * (sizeof(WarpSmem) + (ORDER >= 2 ? sizeof(WarpQuad) : 0));
+    if (LEARNED) smem += sizeof(bh_mlp_dev) + (size_t)nw * 32 * 8 * sizeof(uint32_t);
+    auto kern = bh_walk_kernel<T, ORDER, LEARNED>;
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return BH_ERR_CUDA;
@@ -457,9 +489,33 @@ static int bh_walk_launch_t(const WalkParams& P, int sm_count, int block_threads
     return BH_OK;
 }
 
+template <bool LEARNED>
+static int bh_walk_dispatch(const WalkParams& P, int order, int G, int sm_count, int block_threads,
+                            int blocks_per_sm, cudaStream_t s)
+{
+    // target slots per lane: ceil(G / 32), one instantiation per value up to 4
+    const int T = G <= 32 ? 1 : G <= 64 ? 2 : G <= 96 ? 3 : G <= 128 ? 4 : 8;
+    if (order >= 2) {
+        switch (T) {
+            case 1: return bh_walk_launch_t<1, 2, LEARNED>(P, sm_count, block_threads, blocks_per_sm, s);
+            case 2: return bh_walk_launch_t<2, 2, LEARNED>(P, sm_count, block_threads, blocks_per_sm, s);
+            case 3: return bh_walk_launch_t<3, 2, LEARNED>(P, sm_count, block_threads, blocks_per_sm, s);
+            case 4: return bh_walk_launch_t<4, 2, LEARNED>(P, sm_count, block_threads, blocks_per_sm, s);
+            default: return bh_walk_launch_t<8, 2, LEARNED>(P, sm_count, block_threads, blocks_per_sm, s);
+        }
+    }
+    switch (T) {
+        case 1: return bh_walk_launch_t<1, 1, LEARNED>(P, sm_count, block_threads, blocks_per_sm, s);
+        case 2: return bh_walk_launch_t<2, 1, LEARNED>(P, sm_count, block_threads, blocks_per_sm, s);
+        case 3: return bh_walk_launch_t<3, 1, LEARNED>(P, sm_count, block_threads, blocks_per_sm, s);
+        case 4: return bh_walk_launch_t<4, 1, LEARNED>(P, sm_count, block_threads, blocks_per_sm, s);
+        default: return bh_walk_launch_t<8, 1, LEARNED>(P, sm_count, block_threads, blocks_per_sm, s);
+    }
+}
+
 int launch_walk(const float4* pos_s, const uint32_t* perm, const int32_t* g_first, const int32_t* g_count,
                 const bh_nodes& nd, int order, int G, float eps, float4* out, bh_dev_ctrl* ctrl, int sm_count,
-                int block_threads, int blocks_per_sm, cudaStream_t s)
+                int block_threads, int blocks_per_sm, cudaStream_t s, const WalkLearned* learned)
 {
     bh_walk_reset_kernel<<<1, 1, 0, s>>>(ctrl);
     WalkParams P;
@@ -474,24 +530,16 @@ int launch_walk(const float4* pos_s, const uint32_t* perm, const int32_t* g_firs
     P.out = out;
     P.ctrl = ctrl;
     P.eps2 = eps * eps;
-    // target slots per lane: ceil(G / 32), one instantiation per value up to 4
-    const int T = G <= 32 ? 1 : G <= 64 ? 2 : G <= 96 ? 3 : G <= 128 ? 4 : 8;
-    if (order >= 2) {
-        switch (T) {
-            case 1: return bh_walk_launch_t<1, 2>(P, sm_count, block_threads, blocks_per_sm, s);
-            case 2: return bh_walk_launch_t<2, 2>(P, sm_count, block_threads, blocks_per_sm, s);
-            case 3: return bh_walk_launch_t<3, 2>(P, sm_count, block_threads, blocks_per_sm, s);
-            case 4: return bh_walk_launch_t<4, 2>(P, sm_count, block_threads, blocks_per_sm, s);
-            default: return bh_walk_launch_t<8, 2>(P, sm_count, block_threads, blocks_per_sm, s);
-        }
+    P.mfeat = nullptr;
+    P.mlp = nullptr;
+    P.theta_guard = 1.0f;
+    if (learned) {
+        P.mfeat = learned->mfeat;
+        P.mlp = learned->mlp;
+        P.theta_guard = learned->theta_guard;
+        return bh_walk_dispatch<true>(P, order, G, sm_count, block_threads, blocks_per_sm, s);
     }
-    switch (T) {
-        case 1: return bh_walk_launch_t<1, 1>(P, sm_count, block_threads, blocks_per_sm, s);
-        case 2: return bh_walk_launch_t<2, 1>(P, sm_count, block_threads, blocks_per_sm, s);
-        case 3: return bh_walk_launch_t<3, 1>(P, sm_count, block_threads, blocks_per_sm, s);
-        case 4: return bh_walk_launch_t<4, 1>(P, sm_count, block_threads, blocks_per_sm, s);
-        default: return bh_walk_launch_t<8, 1>(P, sm_count, block_threads, blocks_per_sm, s);
-    }
+    return bh_walk_dispatch<false>(P, order, G, sm_count, block_threads, blocks_per_sm, s);
 }
 
 }  // namespace bh
