@@ -44,16 +44,19 @@ FLOPS_PC_QUAD = 59  # FP32 flops per quadrupole particle-cell term (FMA = 2), + 
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 
+# Operating points: the largest theta with p99 <= 1e-3 found by --calibrate on
+# a GB300 (re-verified at every run; recalibrated if the check fails).
 WORKLOADS = {
-    "clumpy16m": dict(kind="clumpy", n=1 << 24, seed=2, eps=1e-3, leaf=8, G=64, order=1, dt=1e-4,
-                      theta=0.29375, desc="clumpy N=16777216: 64 Hernquist clumps (a=0.05) + 20% uniform "
-                                       "background, eps=1e-3, leapfrog dt=1e-4"),
-    "clumpy2m": dict(kind="clumpy", n=1 << 21, seed=2, eps=1e-3, leaf=8, G=64, order=1, dt=1e-4,
-                     theta=0.30, desc="clumpy N=2097152 (profiling size): 64 Hernquist clumps (a=0.05) + 20% "
-                                      "uniform background, eps=1e-3"),
-    "plummer1m": dict(kind="plummer", n=1 << 20, seed=1, eps=0.01, leaf=8, G=64, order=2, dt=1e-4,
-                      theta=0.75, desc="Plummer N=1048576, eps=0.01, quadrupole"),
+    "clumpy16m": dict(kind="clumpy", n=1 << 24, seed=2, eps=1e-3, leaf=16, G=96, order=2, dt=1e-4,
+                      theta=0.525, desc="clumpy N=16777216: 64 Hernquist clumps (a=0.05) + 20% uniform "
+                                        "background, eps=1e-3, leapfrog dt=1e-4, quadrupole"),
+    "clumpy2m": dict(kind="clumpy", n=1 << 21, seed=2, eps=1e-3, leaf=16, G=96, order=2, dt=1e-4,
+                     theta=0.525, desc="clumpy N=2097152 (profiling size): 64 Hernquist clumps (a=0.05) + 20% "
+                                       "uniform background, eps=1e-3, quadrupole"),
+    "plummer1m": dict(kind="plummer", n=1 << 20, seed=1, eps=0.01, leaf=16, G=96, order=2, dt=1e-4,
+                      theta=0.6, desc="Plummer N=1048576, eps=0.01, quadrupole"),
 }
+WEIGHTS = os.path.join(ROOT, "paper_1112_4539_gb300", "weights", "mac_G96_l16_o2.npz")
 
 
 def parse():
@@ -69,6 +72,7 @@ def parse():
     ap.add_argument("--group", type=int, default=None)
     ap.add_argument("--leaf", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-criterion comparison")
     ap.add_argument("--cpu-sample-groups", type=int, default=6000)
     return ap.parse_args()
 
@@ -189,6 +193,52 @@ def oracle_throughput(pos, theta, eps, leaf, G, order, n_groups_sample, seed=0):
     t_eval = t_build + t_walk * scale
     return dict(value=I * scale / t_eval / 1e9, t_build=t_build, t_walk=t_walk, groups=S, ng=ng,
                 interactions=I, s_per_eval=t_eval, cores=oracle.num_threads())
+
+
+def learned_comparison(bh, ctx, x, idx_t, ref, eps, theta, G, leaf, order, reps=3):
+    """The learned criterion against the plain one on the same particles, each
+    at its own p99 = 1e-3 operating point: whole force evaluations (build,
+    moments, walk) timed with CUDA events."""
+    import torch
+
+    from paper_1112_4539_gb300 import learned
+    P, fmin, fmax, meta = learned.load(WEIGHTS)
+    if (meta.get("G"), meta.get("leaf"), meta.get("order")) != (G, leaf, order):
+        return {"skipped": "weights were trained for another configuration"}
+    tg = float(meta.get("theta_guard", 1.0))
+    tau = learned.calibrate_tau(ctx, x, idx_t, ref, eps, P, fmin, fmax, theta_guard=tg)
+    if tau is None:
+        bh.bh_mac_set(ctx.h, None)
+        return {"skipped": "no tau reaches p99 <= 1e-3"}
+    acc = torch.empty_like(x)
+
+    def timed(learned_on, th):
+        if learned_on:
+            bh.bh_mac_set(ctx.h, P, fmin, fmax, tau, 0.5)
+        else:
+            bh.bh_mac_set(ctx.h, None)
+        ctx.evaluate(x, th, eps, acc)
+        errs = learned.p99_error(acc, idx_t, ref)
+        torch.cuda.synchronize()
+        s0 = ctx.stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            ctx.evaluate(x, th, eps, acc)
+        e1.record()
+        torch.cuda.synchronize()
+        s1 = ctx.stats()
+        inter = (s1["n_pp_total"] - s0["n_pp_total"] + s1["n_pc_total"] - s0["n_pc_total"]) / reps
+        return {"ms_per_eval": e0.elapsed_time(e1) / reps, "interactions": inter, "p99": errs}
+
+    plain = timed(False, theta)
+    lrn = timed(True, tg)
+    bh.bh_mac_set(ctx.h, None)
+    return {"weights": os.path.relpath(WEIGHTS, ROOT), "tau": tau, "theta_guard": tg, "theta_fb": 0.5,
+            "theta_criterion": dict(plain, theta=theta), "learned_criterion": lrn,
+            "speedup": plain["ms_per_eval"] / lrn["ms_per_eval"],
+            "interaction_ratio": lrn["interactions"] / plain["interactions"],
+            "trained_on": "%d samples, %s" % (meta.get("samples", 0), meta.get("sets"))}
 
 
 def source_hash():
@@ -425,6 +475,9 @@ def run_ours(args, W):
                     "d2h_bytes_per_step": int(h_acc.numel() * 4), "steps": e2e_steps,
                     "ms_per_step": e2e_max / e2e_steps},
             "gpu_launches": launches, "roofline": roofline, "clocks": clk}
+
+    if not args.no_learned and os.path.exists(WEIGHTS):
+        line["learned_mac"] = learned_comparison(bh, ctx, x0, idx_t, ref, eps, theta, G, leaf, order)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_throughput(pos_np, theta, eps, leaf, G, order, args.cpu_sample_groups)
