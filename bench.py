@@ -243,7 +243,7 @@ def learned_comparison(bh, ctx, x, idx_t, ref, eps, theta, G, leaf, order, reps=
 
 def source_hash():
     h = hashlib.sha256()
-    for f in ("bh_walk.cu", "bh_internal.cuh"):
+    for f in ("bh_walk.cu", "bh_internal.cuh", "bh_mlp.cuh"):
         with open(os.path.join(ROOT, "paper_1112_4539_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
