@@ -57,7 +57,8 @@ typedef struct bh_config {
     int fp64_node_threshold; /* nodes holding >= this many particles combine moments in FP64 */
     int block_threads;       /* threads per block of the walk kernel: 64 or 128 */
     int blocks_per_sm;       /* resident walk blocks per SM for the persistent grid (0 = auto) */
-    int reserved[2];
+    int max_systems;         /* independent systems one bh_force_batched call may hold (>= 1) */
+    int reserved;
 } bh_config;
 
 /* Counters of the last evaluation (bh_stats synchronises the stream). */
@@ -152,6 +153,40 @@ int direct_force(const float* d_src, int64_t n_src, const float* d_tgt, const in
  * Errors: BH_ERR_INVALID (null/misaligned/non-device pointer, n < 0). */
 int bh_kick_drift(bh_ctx* ctx, float* d_pos, float* d_vel, const float* d_acc, int64_t n, float dt_kick,
                   float dt_drift, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Many independent systems in one evaluation (the paper evaluates one system;
+ * this batches the same method).  Each system gets its own root cube, Morton
+ * order and tree; all systems are built by the same few launches and walked
+ * by one persistent walk launch whose work queue holds every system's groups.
+ * ------------------------------------------------------------------------- */
+
+/* Fix the layout of the next bh_force_batched calls: h_offsets (host, nsys+1
+ * int64) = first particle of each system, h_offsets[0] = 0, nondecreasing;
+ * each system holds at most 65536 particles; the total at most max_n;
+ * 1 <= nsys <= cfg.max_systems.  Synchronous (copies the layout to the
+ * device); call it outside any stream capture.
+ * Errors: BH_ERR_INVALID, BH_ERR_TOO_LARGE. */
+int bh_batch_layout(bh_ctx* ctx, const int64_t* h_offsets, int nsys);
+
+/* Forces of every system of the layout: d_pos_mass holds the systems'
+ * particles back to back (float4 x, y, z, m), d_acc_pot receives
+ * (ax, ay, az, phi) in the same order; systems never interact.  Same method
+ * as tree_build + tree_moments(theta) + tree_force(eps) per system (plain
+ * Eq. 2 criterion).  Stream-ordered, allocates nothing, syncs nothing: it can
+ * be captured in a CUDA graph (see bh_graph_capture_batched).
+ * Errors: BH_ERR_INVALID, BH_ERR_STATE (no layout, or the learned criterion is on). */
+int bh_force_batched(bh_ctx* ctx, const float* d_pos_mass, float theta, float eps, float* d_acc_pot, void* stream);
+
+/* Capture one bh_force_batched call into an executable CUDA graph
+ * (*graph_exec, a cudaGraphExec_t passed as void*); replay it with
+ * bh_graph_launch on any stream, free it with bh_graph_destroy.  The graph
+ * keeps the pointers and parameters given here.
+ * Errors: those of bh_force_batched, BH_ERR_CUDA. */
+int bh_graph_capture_batched(bh_ctx* ctx, const float* d_pos_mass, float theta, float eps, float* d_acc_pot,
+                             void** graph_exec);
+int bh_graph_launch(void* graph_exec, void* stream);
+void bh_graph_destroy(void* graph_exec);
 
 /* ---------------------------------------------------------------------------
  * Learned opening criterion.  An extension of Eq. (2)'s test (the paper's

@@ -33,7 +33,9 @@ EXPORT = dict(keys=1, perm=2, spos=3, node_first=4, node_count=5, node_child=6, 
 SYMBOLS = ["bh_version", "bh_strerror", "bh_config_default", "bh_create", "bh_destroy", "tree_build",
            "tree_moments", "tree_force", "direct_force", "bh_kick_drift", "bh_status", "bh_stats",
            "bh_export", "bh_tree_force_static", "bh_mac_set", "bh_mac_label", "bh_mlp_train", "bh_mlp_grad",
-           "bh_mlp_forward"]
+           "bh_mlp_forward", "bh_batch_layout", "bh_force_batched", "bh_graph_capture_batched",
+           "bh_graph_launch", "bh_graph_destroy"]
+BATCH_MAX_N = 65536
 MLP_NPARAM = 1313
 MLP_ACT = 135  # floats of training scratch per sample
 STATIC_MAX_N = 32768
@@ -42,7 +44,7 @@ STATIC_MAX_N = 32768
 class BhConfig(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int), ("group_size", ctypes.c_int), ("order", ctypes.c_int),
                 ("fp64_node_threshold", ctypes.c_int), ("block_threads", ctypes.c_int),
-                ("blocks_per_sm", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("blocks_per_sm", ctypes.c_int), ("max_systems", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class BhStats(ctypes.Structure):
@@ -114,6 +116,15 @@ def lib():
         L.bh_mlp_grad.restype = i32
         L.bh_mlp_forward.argtypes = [vp, vp, vp, i64, vp, i32, vp]
         L.bh_mlp_forward.restype = i32
+        L.bh_batch_layout.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), i32]
+        L.bh_batch_layout.restype = i32
+        L.bh_force_batched.argtypes = [vp, vp, ctypes.c_float, ctypes.c_float, vp, vp]
+        L.bh_force_batched.restype = i32
+        L.bh_graph_capture_batched.argtypes = [vp, vp, ctypes.c_float, ctypes.c_float, vp, ctypes.POINTER(vp)]
+        L.bh_graph_capture_batched.restype = i32
+        L.bh_graph_launch.argtypes = [vp, vp]
+        L.bh_graph_launch.restype = i32
+        L.bh_graph_destroy.argtypes = [vp]
         L.bh_status.argtypes = [vp, vp]
         L.bh_status.restype = i32
         L.bh_stats.argtypes = [vp, vp, ctypes.POINTER(BhStats)]
@@ -233,6 +244,40 @@ def bh_mlp_grad(params, X, Y, under_weight, work, grad, loss, stream=None):
 def bh_mlp_forward(h, params, X, y, precision, stream=None):
     return lib().bh_mlp_forward(h, _dptr(params), _dptr(X), int(y.numel()), _dptr(y), int(precision),
                                 _stream(stream))
+
+
+def bh_batch_layout(h, offsets):
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    return lib().bh_batch_layout(h, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), int(off.size - 1))
+
+
+def bh_force_batched(h, pos, theta, eps, out, stream=None):
+    return lib().bh_force_batched(h, _dptr(pos), ctypes.c_float(theta), ctypes.c_float(eps), _dptr(out),
+                                  _stream(stream))
+
+
+class BatchedGraph:
+    """bh_force_batched captured once into a CUDA graph, replayed on demand."""
+
+    def __init__(self, ctx, pos, theta, eps, out):
+        self.exe = ctypes.c_void_p()
+        _check(lib().bh_graph_capture_batched(ctx.h, _dptr(pos), ctypes.c_float(theta), ctypes.c_float(eps),
+                                              _dptr(out), ctypes.byref(self.exe)), "bh_graph_capture_batched")
+        self.keep = (pos, out)
+
+    def launch(self, stream=None):
+        _check(lib().bh_graph_launch(self.exe, _stream(stream)), "bh_graph_launch")
+
+    def close(self):
+        if self.exe:
+            lib().bh_graph_destroy(self.exe)
+            self.exe = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def bh_status(h, stream=None):

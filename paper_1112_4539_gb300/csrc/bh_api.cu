@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "bh_mlp.cuh"
 
@@ -40,6 +41,12 @@ struct bh_ctx {
     bool mac_learned = false;
     float4* mfeat = nullptr;        // node-constant features
     bh_mlp_dev* mlp = nullptr;      // packed network (device)
+    // several independent systems
+    int nsys = 0;                   // systems of the current layout (0: none)
+    int64_t batch_n = 0;            // their total particle count
+    uint32_t* sys_of = nullptr;     // system of each Morton position
+    int32_t* sys_off = nullptr;     // first particle of each system (+ total)
+    float4* sys_box = nullptr;      // root cube of each system
 };
 
 namespace {
@@ -107,6 +114,7 @@ void bh_config_default(bh_config* cfg)
     cfg->fp64_node_threshold = 4096;
     cfg->block_threads = 128;
     cfg->blocks_per_sm = 0;
+    cfg->max_systems = 1;
 }
 
 static int validate_config(const bh_config* c)
@@ -117,6 +125,7 @@ static int validate_config(const bh_config* c)
     if (c->fp64_node_threshold < 1) return BH_ERR_INVALID;
     if (c->block_threads != 64 && c->block_threads != 128) return BH_ERR_INVALID;
     if (c->blocks_per_sm < 0 || c->blocks_per_sm > 32) return BH_ERR_INVALID;
+    if (c->max_systems < 0 || c->max_systems > (1 << 20)) return BH_ERR_INVALID;
     return BH_OK;
 }
 
@@ -175,6 +184,8 @@ int bh_create(bh_ctx** out, const bh_config* cfg, int64_t max_n, int device)
     const size_t o_quad64 = c.order >= 2 ? take(NN * 6 * sizeof(double)) : 0;
     const size_t o_mfeat = take(NN * sizeof(float4));
     const size_t o_mlp = take(sizeof(bh_mlp_dev));
+    const size_t S = (size_t)std::max(1, c.max_systems);
+    const size_t o_sys = take(N * 4), o_soff = take((S + 1) * 4), o_sbox = take(S * sizeof(float4));
     const size_t total = off;
 
     if (cudaMalloc(&x->slab, total) != cudaSuccess) {
@@ -214,6 +225,10 @@ int bh_create(bh_ctx** out, const bh_config* cfg, int64_t max_n, int device)
     x->nd.quad64 = c.order >= 2 ? (double*)(b + o_quad64) : nullptr;
     x->mfeat = (float4*)(b + o_mfeat);
     x->mlp = (bh_mlp_dev*)(b + o_mlp);
+    x->sys_of = (uint32_t*)(b + o_sys);
+    x->sys_off = (int32_t*)(b + o_soff);
+    x->sys_box = (float4*)(b + o_sbox);
+    if (x->cfg.max_systems < 1) x->cfg.max_systems = 1;
     // look-back words start at epoch 0, which no pass uses; control block zeroed
     if (cudaMemset(x->lookback, 0, sort_tiles * 256 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMemset(x->ctrl, 0, sizeof(bh_dev_ctrl)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
@@ -548,6 +563,105 @@ int bh_mlp_forward(bh_ctx* x, const float* d_params, const float* d_X, int64_t n
     }
     if (!d_params || !is_device_ptr(d_params, dev)) return BH_ERR_INVALID;
     return bh::mlp_forward(d_params, nullptr, d_X, (long long)n, d_y, 32, (cudaStream_t)stream);
+}
+
+// ------------------------------------------------------------------ many systems
+int bh_batch_layout(bh_ctx* x, const int64_t* h_offsets, int nsys)
+{
+    if (!x || !h_offsets || nsys < 1) return BH_ERR_INVALID;
+    if (nsys > x->cfg.max_systems) return BH_ERR_TOO_LARGE;
+    if (h_offsets[0] != 0) return BH_ERR_INVALID;
+    std::vector<int32_t> off32((size_t)nsys + 1);
+    for (int s = 0; s < nsys; s++) {
+        const int64_t c = h_offsets[s + 1] - h_offsets[s];
+        if (c < 0) return BH_ERR_INVALID;
+        if (c > bh::kBatchMaxN) return BH_ERR_TOO_LARGE;
+        off32[(size_t)s] = (int32_t)h_offsets[s];
+    }
+    if (h_offsets[nsys] > x->max_n) return BH_ERR_TOO_LARGE;
+    off32[(size_t)nsys] = (int32_t)h_offsets[nsys];
+    DeviceGuard guard(x->device);
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(x->sys_off, off32.data(), off32.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess)
+        return BH_ERR_CUDA;
+    x->nsys = nsys;
+    x->batch_n = h_offsets[nsys];
+    return BH_OK;
+}
+
+int bh_force_batched(bh_ctx* x, const float* d_pos_mass, float theta, float eps, float* d_acc_pot, void* stream)
+{
+    if (!x) return BH_ERR_INVALID;
+    if (x->nsys < 1 || x->mac_learned) return BH_ERR_STATE;
+    if (!(theta > 0.0f) || !std::isfinite(theta) || !(eps >= 0.0f) || !std::isfinite(eps)) return BH_ERR_INVALID;
+    const int64_t n = x->batch_n;
+    if (n == 0) return BH_OK;
+    if (!d_pos_mass || !aligned16(d_pos_mass) || !is_device_ptr(d_pos_mass, x->device)) return BH_ERR_INVALID;
+    if (!d_acc_pot || !aligned16(d_acc_pot) || !is_device_ptr(d_acc_pot, x->device)) return BH_ERR_INVALID;
+    DeviceGuard guard(x->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int N = (int)n;
+    bh::launch_init(x->ctrl, s);
+    bh::launch_batch_sort((const float4*)d_pos_mass, x->sys_off, x->nsys, x->keys, x->keys_alt, x->vals, x->vals_alt,
+                          x->pos_s, x->sys_of, x->sys_box, x->ctrl, s);
+    bh::launch_tree(x->keys, N, x->cfg.leaf_size, x->dl, x->blk, x->nd, x->node_cap, x->ctrl, grid_for(x), s,
+                    x->sys_of, x->sys_off);
+    bh::launch_groups(x->nd, N, x->cfg.group_size, x->flags, x->blk, x->g_first, x->g_count, x->ctrl, grid_for(x), s);
+    bh::launch_moments(x->pos_s, x->keys, x->nd, x->cfg.order, theta, x->cfg.fp64_node_threshold, x->ctrl,
+                       grid_for(x), s, x->sys_of, x->sys_box);
+    int rc = bh::launch_walk(x->pos_s, x->vals, x->g_first, x->g_count, x->nd, x->cfg.order, x->cfg.group_size, eps,
+                             (float4*)d_acc_pot, x->ctrl, x->sm_count, x->cfg.block_threads, x->cfg.blocks_per_sm, s);
+    if (rc) return rc;
+    // init, batch sort, 4 tree, 5 groups, 11 moments, 2 walk
+    x->launches += 2 + 4 + 5 + bh::kLaunchesMoments + bh::kLaunchesForce;
+    if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
+    x->n = n;
+    x->theta = theta;
+    x->have_moments = false;  // the tree of several systems is not for tree_force
+    return BH_OK;
+}
+
+int bh_graph_capture_batched(bh_ctx* x, const float* d_pos_mass, float theta, float eps, float* d_acc_pot,
+                             void** graph_exec)
+{
+    if (!x || !graph_exec) return BH_ERR_INVALID;
+    *graph_exec = nullptr;
+    DeviceGuard guard(x->device);
+    cudaStream_t cs;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return BH_ERR_CUDA;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return BH_ERR_CUDA;
+    }
+    const int rc = bh_force_batched(x, d_pos_mass, theta, eps, d_acc_pot, cs);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+    cudaStreamDestroy(cs);
+    if (rc != BH_OK || ec != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc != BH_OK ? rc : BH_ERR_CUDA;
+    }
+    cudaGraphExec_t ge = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        return BH_ERR_CUDA;
+    }
+    *graph_exec = (void*)ge;
+    return BH_OK;
+}
+
+int bh_graph_launch(void* graph_exec, void* stream)
+{
+    if (!graph_exec) return BH_ERR_INVALID;
+    return cudaGraphLaunch((cudaGraphExec_t)graph_exec, (cudaStream_t)stream) == cudaSuccess ? BH_OK : BH_ERR_CUDA;
+}
+
+void bh_graph_destroy(void* graph_exec)
+{
+    if (graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)graph_exec);
 }
 
 }  // extern "C"

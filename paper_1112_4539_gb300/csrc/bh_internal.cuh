@@ -168,12 +168,23 @@ void launch_keys(const float4* pos, int n, bh_dev_ctrl* ctrl, uint32_t* keys, in
 void launch_sort(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
                  const float4* pos, float4* pos_s, int n, unsigned long long* lookback,
                  unsigned int* epoch, bh_dev_ctrl* ctrl, cudaStream_t s);
+// sys / sys_off / sys_box: several independent systems (system of each
+// Morton position, first particle of each system + total, root cube of each);
+// null for a single system.
 void launch_tree(const uint32_t* keys, int n, int n_leaf, uint8_t* dl, uint32_t* blk_lvl,
-                 const bh_nodes& nd, int64_t node_cap, bh_dev_ctrl* ctrl, int grid, cudaStream_t s);
+                 const bh_nodes& nd, int64_t node_cap, bh_dev_ctrl* ctrl, int grid, cudaStream_t s,
+                 const uint32_t* sys = nullptr, const int32_t* sys_off = nullptr);
 void launch_groups(const bh_nodes& nd, int n, int G, uint8_t* flags, uint32_t* blk, int32_t* g_first,
                    int32_t* g_count, bh_dev_ctrl* ctrl, int grid, cudaStream_t s);
 void launch_moments(const float4* pos_s, const uint32_t* keys, const bh_nodes& nd, int order,
-                    float theta, int fp64_threshold, bh_dev_ctrl* ctrl, int grid, cudaStream_t s);
+                    float theta, int fp64_threshold, bh_dev_ctrl* ctrl, int grid, cudaStream_t s,
+                    const uint32_t* sys = nullptr, const float4* sys_box = nullptr);
+// One CTA per system: root cube, keys, stable radix sort and gather of each
+// system's particles (systems contiguous, each <= kBatchMaxN particles).
+constexpr int kBatchMaxN = 65536;
+void launch_batch_sort(const float4* pos, const int32_t* sys_off, int nsys, uint32_t* keys, uint32_t* keys_alt,
+                       uint32_t* vals, uint32_t* vals_alt, float4* pos_s, uint32_t* sys, float4* sys_box,
+                       bh_dev_ctrl* ctrl, cudaStream_t s);
 }  // namespace bh
 struct bh_mlp_dev;
 namespace bh {

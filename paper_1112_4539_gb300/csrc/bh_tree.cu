@@ -28,11 +28,15 @@ constexpr int kLeafFp64 = 32;
 
 // ------------------------------------------------------------ pass 1
 // dl[k] = (d_k + 1) | (lambda_k << 4); per-block node counts per level.
+// With several independent systems (sys = system of each Morton position,
+// systems contiguous), particles of different systems share no cell: a
+// system's first particle starts a root, and windows never span systems.
 __global__ void __launch_bounds__(kLvlThreads)
-bh_levels_kernel(const uint32_t* __restrict__ keys, int n, int n_leaf, uint8_t* __restrict__ dl,
-                 uint32_t* __restrict__ blk_lvl, int nblk)
+bh_levels_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ sys, int n, int n_leaf,
+                 uint8_t* __restrict__ dl, uint32_t* __restrict__ blk_lvl, int nblk)
 {
     __shared__ uint32_t sk[kLevelTile + 2 * kMaxLeaf + 2];
+    __shared__ uint32_t ss[kLevelTile + 2 * kMaxLeaf + 2];
     __shared__ int8_t sw[kLevelTile + kMaxLeaf + 1];
     __shared__ unsigned int scnt[kLvlThreads / 32][12];
     const int tid = threadIdx.x;
@@ -41,14 +45,17 @@ bh_levels_kernel(const uint32_t* __restrict__ keys, int n, int n_leaf, uint8_t* 
     const int span = kLevelTile + 2 * n_leaf + 1;
     for (int i = tid; i < span; i += kLvlThreads) {
         const int p = lo + i;
-        sk[i] = (p >= 0 && p < n) ? keys[p] : 0u;
+        const bool in = p >= 0 && p < n;
+        sk[i] = in ? keys[p] : 0u;
+        ss[i] = (in && sys) ? sys[p] : 0u;
     }
     __syncthreads();
     // w_j for j in [base - n_leaf, base + kLevelTile): common level of the window [j, j + n_leaf]
     for (int i = tid; i < kLevelTile + n_leaf; i += kLvlThreads) {
         const int j = base - n_leaf + i;
         int wv = -1;
-        if (j >= 0 && j + n_leaf < n) wv = bh_common_level(sk[j - lo], sk[j + n_leaf - lo]);
+        if (j >= 0 && j + n_leaf < n && ss[j - lo] == ss[j + n_leaf - lo])
+            wv = bh_common_level(sk[j - lo], sk[j + n_leaf - lo]);
         sw[i] = (int8_t)wv;
     }
     __syncthreads();
@@ -58,7 +65,7 @@ bh_levels_kernel(const uint32_t* __restrict__ keys, int n, int n_leaf, uint8_t* 
     for (int r = 0; r < kLvlPer; r++) {
         const int k = base + tid * kLvlPer + r;
         if (k >= n) break;
-        const int d = (k == 0) ? -1 : bh_common_level(sk[k - 1 - lo], sk[k - lo]);
+        const int d = (k == 0 || ss[k - 1 - lo] != ss[k - lo]) ? -1 : bh_common_level(sk[k - 1 - lo], sk[k - lo]);
         int W = -1;
         const int j0 = max(0, k - n_leaf);
         for (int j = j0; j <= k; j++) W = max(W, (int)sw[j - (base - n_leaf)]);
@@ -224,24 +231,27 @@ bh_node_write_kernel(const uint8_t* __restrict__ dl, int n, const uint32_t* __re
 // Particle count of each node (end of its key range by galloping search),
 // number of children, packed walk record, leaf statistics.
 __global__ void __launch_bounds__(256)
-bh_node_finalize_kernel(const uint32_t* __restrict__ keys, int n, bh_nodes nd, bh_dev_ctrl* c)
+bh_node_finalize_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ sys,
+                        const int32_t* __restrict__ sys_off, int n, bh_nodes nd, bh_dev_ctrl* c)
 {
     const int nn = (int)c->level_offset[11];
     unsigned int leaves = 0u, maxleaf = 0u;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
         const int l = nd.level[v];
         const int k = nd.first[v];
-        int end = n;
+        // a node never extends past its system's last particle
+        const int seg_end = sys ? sys_off[sys[k] + 1] : n;
+        int end = seg_end;
         if (l > 0) {
             const int sh = 3 * (BH_MAX_LEVEL - l);
             const unsigned int target = ((keys[k] >> sh) + 1u) << sh;
             int lo = k, hi = k + 1, step = 1;
-            while (hi < n && keys[hi] < target) {
+            while (hi < seg_end && keys[hi] < target) {
                 lo = hi;
                 step <<= 1;
                 hi = k + step;
             }
-            if (hi > n) hi = n;
+            if (hi > seg_end) hi = seg_end;
             while (hi - lo > 1) {
                 const int mid = lo + ((hi - lo) >> 1);
                 if (keys[mid] < target) lo = mid;
@@ -273,14 +283,15 @@ bh_node_finalize_kernel(const uint32_t* __restrict__ keys, int n, bh_nodes nd, b
 }
 
 void launch_tree(const uint32_t* keys, int n, int n_leaf, uint8_t* dl, uint32_t* blk_lvl, const bh_nodes& nd,
-                 int64_t node_cap, bh_dev_ctrl* ctrl, int grid, cudaStream_t s)
+                 int64_t node_cap, bh_dev_ctrl* ctrl, int grid, cudaStream_t s, const uint32_t* sys,
+                 const int32_t* sys_off)
 {
     if (n <= 0) return;
     const int nblk = (n + kLevelTile - 1) / kLevelTile;
-    bh_levels_kernel<<<nblk, kLvlThreads, 0, s>>>(keys, n, n_leaf, dl, blk_lvl, nblk);
+    bh_levels_kernel<<<nblk, kLvlThreads, 0, s>>>(keys, sys, n, n_leaf, dl, blk_lvl, nblk);
     bh_level_scan_kernel<<<1, 1024, 0, s>>>(blk_lvl, nblk, ctrl, (long long)node_cap);
     bh_node_write_kernel<<<nblk, kLvlThreads, 0, s>>>(dl, n, blk_lvl, nblk, ctrl, nd.first, nd.level, nd.child);
-    bh_node_finalize_kernel<<<grid, 256, 0, s>>>(keys, n, nd, ctrl);
+    bh_node_finalize_kernel<<<grid, 256, 0, s>>>(keys, sys, sys_off, n, nd, ctrl);
 }
 
 // ------------------------------------------------------------ groups
@@ -294,7 +305,7 @@ __global__ void __launch_bounds__(256) bh_group_mark_kernel(bh_nodes nd, int G, 
     const int nn = (int)c->level_offset[11];
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
         const int4 r = nd.rec[v];
-        if (v == 0) {
+        if (v < (int)c->level_offset[1]) {  // a root (one per system)
             if (r.y <= G) flags[r.x] = 1;
             else if (r.z < 0)
                 for (int j = 0; j < r.y; j += G) flags[r.x + j] = 1;
@@ -506,15 +517,19 @@ __device__ __forceinline__ void bh_internal_moments(const bh_nodes& nd, int ch, 
 template <int ORDER>
 __global__ void __launch_bounds__(256)
 bh_moments_level_kernel(const float4* __restrict__ pos_s, const uint32_t* __restrict__ keys, bh_nodes nd, int lev,
-                        float theta, int fp64_threshold, const bh_dev_ctrl* __restrict__ c)
+                        float theta, int fp64_threshold, const bh_dev_ctrl* __restrict__ c,
+                        const uint32_t* __restrict__ sys, const float4* __restrict__ sys_box)
 {
     const int v0 = (int)c->level_offset[lev], v1 = (int)c->level_offset[lev + 1];
     if (c->level_offset[11] == 0u) return;
-    const float xmin = c->box[0], ymin = c->box[1], zmin = c->box[2], L = c->box[3];
-    const float side = ldexpf(L, -lev);  // exact: power-of-two scaling
-    const float opening = side / theta;
+    const float4 gbox = make_float4(c->box[0], c->box[1], c->box[2], c->box[3]);
     for (int v = v0 + blockIdx.x * blockDim.x + threadIdx.x; v < v1; v += gridDim.x * blockDim.x) {
         const int4 r = nd.rec[v];
+        // root cube of the node's system (several systems: one cube each)
+        const float4 bx = sys ? sys_box[sys[r.x]] : gbox;
+        const float xmin = bx.x, ymin = bx.y, zmin = bx.z;
+        const float side = ldexpf(bx.w, -lev);  // exact: power-of-two scaling
+        const float opening = side / theta;
         // FP64 above the threshold, and for leaves holding more than 32 particles
         // (only level-10 leaves can): a sequential FP32 sum of k equal masses is
         // off by up to ~k * 3e-9 relative (1e-5 at k = 3000)
@@ -565,13 +580,16 @@ bh_moments_level_kernel(const float4* __restrict__ pos_s, const uint32_t* __rest
 }
 
 void launch_moments(const float4* pos_s, const uint32_t* keys, const bh_nodes& nd, int order, float theta,
-                    int fp64_threshold, bh_dev_ctrl* ctrl, int grid, cudaStream_t s)
+                    int fp64_threshold, bh_dev_ctrl* ctrl, int grid, cudaStream_t s, const uint32_t* sys,
+                    const float4* sys_box)
 {
     for (int lev = BH_MAX_LEVEL; lev >= 0; lev--) {
         if (order >= 2)
-            bh_moments_level_kernel<2><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, ctrl);
+            bh_moments_level_kernel<2><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, ctrl, sys,
+                                                            sys_box);
         else
-            bh_moments_level_kernel<1><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, ctrl);
+            bh_moments_level_kernel<1><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, ctrl, sys,
+                                                            sys_box);
     }
 }
 

@@ -237,6 +237,7 @@ __global__ void __launch_bounds__(128, LEARNED ? (T <= 2 ? 4 : T <= 4 ? 3 : 2)
     const float eps2 = P.eps2;
     bh_dev_ctrl* ctrl = P.ctrl;
     const int ng = (int)ctrl->n_groups;
+    const int n_roots = (int)ctrl->level_offset[1];
     const float boxL = LEARNED ? ctrl->box[3] : 1.0f;
     unsigned long long cnt_pp = 0ull, cnt_pc = 0ull;
 
@@ -284,7 +285,15 @@ __global__ void __launch_bounds__(128, LEARNED ? (T <= 2 ? 4 : T <= 4 ? 3 : 2)
         cnt_pp += (unsigned long long)gc * (unsigned long long)(gc - 1);
 
         int sp = 1, ring_head = 0, ring_cnt = 0, q_head = 0, q_cnt = 0;
-        if (lane == 0) S.stack[0] = 0u;  // root: node 0, one node
+        // root of the group's system: the last level-0 node starting at or before gb
+        // (one root per system; a single system has just node 0)
+        int root = 0;
+        for (int hi = n_roots; hi - root > 1;) {
+            const int mid = (root + hi) >> 1;
+            if (P.rec[mid].x <= gb) root = mid;
+            else hi = mid;
+        }
+        if (lane == 0) S.stack[0] = (uint32_t)root << 3;
         __syncwarp();
         bool overflow = false;
         while (sp > 0) {
