@@ -28,6 +28,17 @@ namespace bh {
 
 constexpr int kStackCap = 352;
 constexpr int kRing = 64;
+// unroll factors of the per-tile source loops (tuning constants: larger
+// factors overflow the instruction cache, as every T-slot variant of the
+// loops is live at once across the SM's warps)
+#ifndef BH_POINT_UNROLL
+#define BH_POINT_UNROLL 4
+#endif
+#ifndef BH_QUAD_UNROLL
+#define BH_QUAD_UNROLL 1
+#endif
+constexpr int kPointUnroll = BH_POINT_UNROLL;
+constexpr int kQuadUnroll = BH_QUAD_UNROLL;
 
 struct WarpSmem {
     uint32_t stack[kStackCap];  // (first node << 3) | (count - 1)
@@ -63,6 +74,23 @@ struct Acc {
     float cx[T], cy[T], cz[T], cp[T];
 };
 
+// Target layout of a group of gc particles on the warp's T slots per lane
+// (warp-uniform).  Slots 0..nf-1 hold targets t*32 + lane.  When the last
+// slot would hold at most kSplitMax targets (k = gc - 32*nf) it is "split":
+// lane l holds target nf*32 + (l mod m), m = 2^lg >= k, and evaluates only
+// the m sources of each tile in its phase (l / m); the phases' partial sums
+// are added across lanes once, when the group ends.  A slot with 4 targets
+// then costs 4 evaluations per tile instead of 32.
+#ifndef BH_SPLIT_MAX
+#define BH_SPLIT_MAX 16
+#endif
+constexpr int kSplitMax = BH_SPLIT_MAX;
+struct Layout {
+    int nf;      // full slots
+    bool split;  // slot nf is split
+    int lg;      // log2 of the targets per phase in the split slot
+};
+
 __device__ __forceinline__ void bh_kahan(float& s, float& c, float v)
 {
     const float y = __fsub_rn(v, c);
@@ -84,101 +112,172 @@ __device__ __forceinline__ void bh_add_tile(Acc<T>& A, const float (&tx)[T], con
     }
 }
 
-// 32 point sources (particles or monopole cells) on the first TN of the T
-// target slots of each lane.
-template <int T, int TN>
+// One point source s = (x, y, z, m) on one target (Eq. 1).
+__device__ __forceinline__ void bh_pp(const float4& s, float eps2, float xi, float yi, float zi, float& ax,
+                                      float& ay, float& az, float& ap)
+{
+    const float dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
+    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+    const float ri = rsqrtf(r2);
+    const float mr = s.w * ri;
+    const float mr3 = mr * ri * ri;
+    ax = fmaf(mr3, dx, ax);
+    ay = fmaf(mr3, dy, ay);
+    az = fmaf(mr3, dz, az);
+    ap -= mr;
+}
+
+// One quadrupole cell on one target.  The cell is staged as a = (c, M),
+// b = 3 (Ixx, Iyy, Izz, Ixy), e = (3 Ixz, 3 Iyz, 1.5 T, 0.5 T) with T = tr I.
+// With r = x_i - c, h^2 = r^2 + eps^2, g_n = h^-n, u = 3 I r, q3 = r.u
+// (three times the quadratic form):
+//   a   += g5 u + k r,   k = g5 (1.5 T - 2.5 q3 g2) - M g3
+//   phi += -M g1 + 0.5 T g3 - 0.5 q3 g5
+// the last term accumulated apart (aq) and scaled once per tile.
+__device__ __forceinline__ void bh_pq(const float4& a, const float4& b, const float4& e, float eps2, float xi,
+                                      float yi, float zi, float& ax, float& ay, float& az, float& ap, float& aq)
+{
+    const float rx = xi - a.x, ry = yi - a.y, rz = zi - a.z;
+    const float h2 = fmaf(rz, rz, fmaf(ry, ry, fmaf(rx, rx, eps2)));
+    const float g1 = rsqrtf(h2);
+    const float g2 = g1 * g1;
+    const float g3 = g1 * g2;
+    const float g5 = g3 * g2;
+    const float u0 = fmaf(b.w, ry, fmaf(e.x, rz, b.x * rx));
+    const float u1 = fmaf(b.w, rx, fmaf(e.y, rz, b.y * ry));
+    const float u2 = fmaf(e.x, rx, fmaf(e.y, ry, b.z * rz));
+    const float q3 = fmaf(rx, u0, fmaf(ry, u1, rz * u2));
+    const float w = fmaf(-2.5f * q3, g2, e.z);
+    const float k = fmaf(g5, w, -(a.w * g3));
+    ax = fmaf(g5, u0, fmaf(k, rx, ax));
+    ay = fmaf(g5, u1, fmaf(k, ry, ay));
+    az = fmaf(g5, u2, fmaf(k, rz, az));
+    ap = fmaf(e.w, g3, fmaf(-a.w, g1, ap));
+    aq = fmaf(q3, g5, aq);
+}
+
+// 32 point sources (particles or monopole cells) on the first NF slots of
+// every lane.
+template <int T, int NF>
 __device__ __forceinline__ void bh_eval_points(const float4* __restrict__ src, float eps2, const float (&xi)[T],
                                                const float (&yi)[T], const float (&zi)[T], Acc<T>& A)
 {
     float tx[T], ty[T], tz[T], tp[T];
 #pragma unroll
-    for (int t = 0; t < TN; t++) tx[t] = ty[t] = tz[t] = tp[t] = 0.0f;
-#pragma unroll 8
+    for (int t = 0; t < NF; t++) tx[t] = ty[t] = tz[t] = tp[t] = 0.0f;
+#pragma unroll kPointUnroll
     for (int j = 0; j < 32; j++) {
         const float4 s = src[j];
 #pragma unroll
-        for (int t = 0; t < TN; t++) {
-            const float dx = s.x - xi[t], dy = s.y - yi[t], dz = s.z - zi[t];
-            const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-            const float ri = rsqrtf(r2);
-            const float mr = s.w * ri;
-            const float mr3 = mr * ri * ri;
-            tx[t] = fmaf(mr3, dx, tx[t]);
-            ty[t] = fmaf(mr3, dy, ty[t]);
-            tz[t] = fmaf(mr3, dz, tz[t]);
-            tp[t] -= mr;
-        }
+        for (int t = 0; t < NF; t++) bh_pp(s, eps2, xi[t], yi[t], zi[t], tx[t], ty[t], tz[t], tp[t]);
     }
-    bh_add_tile<T, TN>(A, tx, ty, tz, tp);
+    bh_add_tile<T, NF>(A, tx, ty, tz, tp);
 }
 
-// 32 quadrupole cells on T targets per lane.  With r = x_i - c, h^2 = r^2 + eps^2,
-// g_n = h^-n, T = tr I, q = r.I.r:
-//   a += -M g3 r + 3 g5 I r + (1.5 T g5 - 7.5 q g7) r
-//   phi += -M g1 - 1.5 q g5 + 0.5 T g3
-template <int T, int TN>
+// 32 quadrupole cells on the first NF slots of every lane.
+template <int T, int NF>
 __device__ __forceinline__ void bh_eval_quads(const float4* __restrict__ ca, const float4* __restrict__ cb,
                                               const float4* __restrict__ cc, float eps2, const float (&xi)[T],
                                               const float (&yi)[T], const float (&zi)[T], Acc<T>& A)
 {
-    float tx[T], ty[T], tz[T], tp[T];
+    float tx[T], ty[T], tz[T], tp[T], tq[T];
 #pragma unroll
-    for (int t = 0; t < TN; t++) tx[t] = ty[t] = tz[t] = tp[t] = 0.0f;
-#pragma unroll 2
+    for (int t = 0; t < NF; t++) tx[t] = ty[t] = tz[t] = tp[t] = tq[t] = 0.0f;
+#pragma unroll kQuadUnroll
     for (int j = 0; j < 32; j++) {
         const float4 a = ca[j], b = cb[j], c = cc[j];
 #pragma unroll
-        for (int t = 0; t < TN; t++) {
-            const float rx = xi[t] - a.x, ry = yi[t] - a.y, rz = zi[t] - a.z;
-            const float h2 = fmaf(rz, rz, fmaf(ry, ry, fmaf(rx, rx, eps2)));
-            const float g1 = rsqrtf(h2);
-            const float g2 = g1 * g1;
-            const float g3 = g1 * g2;
-            const float g5 = g3 * g2;
-            const float g7 = g5 * g2;
-            const float ir0 = fmaf(b.w, ry, fmaf(c.x, rz, b.x * rx));
-            const float ir1 = fmaf(b.w, rx, fmaf(c.y, rz, b.y * ry));
-            const float ir2 = fmaf(c.x, rx, fmaf(c.y, ry, b.z * rz));
-            const float q = fmaf(rx, ir0, fmaf(ry, ir1, rz * ir2));
-            const float k = fmaf(c.z, g5, -fmaf(7.5f * q, g7, a.w * g3));
-            const float g5x3 = 3.0f * g5;
-            tx[t] = fmaf(g5x3, ir0, fmaf(k, rx, tx[t]));
-            ty[t] = fmaf(g5x3, ir1, fmaf(k, ry, ty[t]));
-            tz[t] = fmaf(g5x3, ir2, fmaf(k, rz, tz[t]));
-            tp[t] -= fmaf(a.w, g1, fmaf(1.5f * q, g5, -c.w * g3));
-        }
+        for (int t = 0; t < NF; t++) bh_pq(a, b, c, eps2, xi[t], yi[t], zi[t], tx[t], ty[t], tz[t], tp[t], tq[t]);
     }
-    bh_add_tile<T, TN>(A, tx, ty, tz, tp);
+#pragma unroll
+    for (int t = 0; t < NF; t++) tp[t] = fmaf(-0.5f, tq[t], tp[t]);
+    bh_add_tile<T, NF>(A, tx, ty, tz, tp);
 }
 
-// Evaluate with only as many target slots per lane as the group fills
-// (tn = ceil(group count / 32), warp-uniform).
+// The split slot: target of slot L.nf, the m = 2^lg sources of the lane's phase.
 template <int T>
-__device__ __forceinline__ void bh_points(int tn, const float4* __restrict__ src, float eps2, const float (&xi)[T],
-                                          const float (&yi)[T], const float (&zi)[T], Acc<T>& A)
+__device__ __forceinline__ void bh_split_target(const Layout& L, const float (&xi)[T], const float (&yi)[T],
+                                                const float (&zi)[T], float& x, float& y, float& z)
 {
-    if (T >= 4 && tn == 4) bh_eval_points<T, (T >= 4 ? 4 : T)>(src, eps2, xi, yi, zi, A);
-    else if (T >= 3 && tn == 3) bh_eval_points<T, (T >= 3 ? 3 : T)>(src, eps2, xi, yi, zi, A);
-    else if (T >= 2 && tn == 2) bh_eval_points<T, (T >= 2 ? 2 : T)>(src, eps2, xi, yi, zi, A);
-    else if (tn == 1) bh_eval_points<T, 1>(src, eps2, xi, yi, zi, A);
-    else bh_eval_points<T, T>(src, eps2, xi, yi, zi, A);
+    x = xi[0]; y = yi[0]; z = zi[0];
+#pragma unroll
+    for (int t = 1; t < T; t++)
+        if (t == L.nf) { x = xi[t]; y = yi[t]; z = zi[t]; }
 }
 template <int T>
-__device__ __forceinline__ void bh_quads(int tn, const float4* __restrict__ ca, const float4* __restrict__ cb,
-                                         const float4* __restrict__ cc, float eps2, const float (&xi)[T],
-                                         const float (&yi)[T], const float (&zi)[T], Acc<T>& A)
+__device__ __forceinline__ void bh_split_add(const Layout& L, Acc<T>& A, float ax, float ay, float az, float ap)
 {
-    if (T >= 4 && tn == 4) bh_eval_quads<T, (T >= 4 ? 4 : T)>(ca, cb, cc, eps2, xi, yi, zi, A);
-    else if (T >= 3 && tn == 3) bh_eval_quads<T, (T >= 3 ? 3 : T)>(ca, cb, cc, eps2, xi, yi, zi, A);
-    else if (T >= 2 && tn == 2) bh_eval_quads<T, (T >= 2 ? 2 : T)>(ca, cb, cc, eps2, xi, yi, zi, A);
-    else if (tn == 1) bh_eval_quads<T, 1>(ca, cb, cc, eps2, xi, yi, zi, A);
-    else bh_eval_quads<T, T>(ca, cb, cc, eps2, xi, yi, zi, A);
+#pragma unroll
+    for (int t = 0; t < T; t++)
+        if (t == L.nf) {
+            bh_kahan(A.x[t], A.cx[t], ax);
+            bh_kahan(A.y[t], A.cy[t], ay);
+            bh_kahan(A.z[t], A.cz[t], az);
+            bh_kahan(A.p[t], A.cp[t], ap);
+        }
+}
+template <int T>
+__device__ __forceinline__ void bh_split_points(const Layout& L, const float4* __restrict__ src, float eps2,
+                                                const float (&xi)[T], const float (&yi)[T], const float (&zi)[T],
+                                                Acc<T>& A)
+{
+    float x, y, z, ax = 0.f, ay = 0.f, az = 0.f, ap = 0.f;
+    bh_split_target<T>(L, xi, yi, zi, x, y, z);
+    const float4* ph = src + (((threadIdx.x & 31) >> L.lg) << L.lg);
+    const int m = 1 << L.lg;
+#pragma unroll 2
+    for (int i = 0; i < m; i++) bh_pp(ph[i], eps2, x, y, z, ax, ay, az, ap);
+    bh_split_add<T>(L, A, ax, ay, az, ap);
+}
+template <int T>
+__device__ __forceinline__ void bh_split_quads(const Layout& L, const float4* __restrict__ ca,
+                                               const float4* __restrict__ cb, const float4* __restrict__ cc,
+                                               float eps2, const float (&xi)[T], const float (&yi)[T],
+                                               const float (&zi)[T], Acc<T>& A)
+{
+    float x, y, z, ax = 0.f, ay = 0.f, az = 0.f, ap = 0.f, aq = 0.f;
+    bh_split_target<T>(L, xi, yi, zi, x, y, z);
+    const int o = ((threadIdx.x & 31) >> L.lg) << L.lg, m = 1 << L.lg;
+    for (int i = 0; i < m; i++) bh_pq(ca[o + i], cb[o + i], cc[o + i], eps2, x, y, z, ax, ay, az, ap, aq);
+    bh_split_add<T>(L, A, ax, ay, az, fmaf(-0.5f, aq, ap));
+}
+
+// Dispatch on the warp-uniform layout.  Every bh_eval_* instance is reached
+// from one call site only (they are inlined: a second site would double the
+// code of the hottest loop).
+template <int T>
+__device__ __forceinline__ void bh_points(const Layout& L, const float4* __restrict__ src, float eps2,
+                                          const float (&xi)[T], const float (&yi)[T], const float (&zi)[T],
+                                          Acc<T>& A)
+{
+    if (T > 1 && L.nf == 1) bh_eval_points<T, 1>(src, eps2, xi, yi, zi, A);
+    else if (T > 2 && L.nf == 2) bh_eval_points<T, (T > 2 ? 2 : T)>(src, eps2, xi, yi, zi, A);
+    else if (T > 3 && L.nf == 3) bh_eval_points<T, (T > 3 ? 3 : T)>(src, eps2, xi, yi, zi, A);
+    else if (T > 4 && L.nf == 4) bh_eval_points<T, (T > 4 ? 4 : T)>(src, eps2, xi, yi, zi, A);
+    else if (L.nf > 0) bh_eval_points<T, T>(src, eps2, xi, yi, zi, A);
+    if (L.split) bh_split_points<T>(L, src, eps2, xi, yi, zi, A);
+}
+template <int T>
+__device__ __forceinline__ void bh_quads(const Layout& L, const float4* __restrict__ ca,
+                                         const float4* __restrict__ cb, const float4* __restrict__ cc, float eps2,
+                                         const float (&xi)[T], const float (&yi)[T], const float (&zi)[T],
+                                         Acc<T>& A)
+{
+    if (T > 1 && L.nf == 1) bh_eval_quads<T, 1>(ca, cb, cc, eps2, xi, yi, zi, A);
+    else if (T > 2 && L.nf == 2) bh_eval_quads<T, (T > 2 ? 2 : T)>(ca, cb, cc, eps2, xi, yi, zi, A);
+    else if (T > 3 && L.nf == 3) bh_eval_quads<T, (T > 3 ? 3 : T)>(ca, cb, cc, eps2, xi, yi, zi, A);
+    else if (T > 4 && L.nf == 4) bh_eval_quads<T, (T > 4 ? 4 : T)>(ca, cb, cc, eps2, xi, yi, zi, A);
+    else if (L.nf > 0) bh_eval_quads<T, T>(ca, cb, cc, eps2, xi, yi, zi, A);
+    if (L.split) bh_split_quads<T>(L, ca, cb, cc, eps2, xi, yi, zi, A);
 }
 
 // The group's own particles on its members, target itself masked.
+// With a split slot, only its phase-0 lanes (lane < m) keep their sums: the
+// other phases hold copies of the same targets.
 template <int T>
-__device__ __forceinline__ void bh_eval_self(int gc, float eps2, const float (&xi)[T], const float (&yi)[T],
-                                             const float (&zi)[T], const float (&mi)[T], Acc<T>& A)
+__device__ __forceinline__ void bh_eval_self(int gc, const Layout& L, float eps2, const float (&xi)[T],
+                                             const float (&yi)[T], const float (&zi)[T], const float (&mi)[T],
+                                             Acc<T>& A)
 {
     const int lane = threadIdx.x & 31;
     float tx[T], ty[T], tz[T], tp[T];
@@ -208,14 +307,26 @@ __device__ __forceinline__ void bh_eval_self(int gc, float eps2, const float (&x
             }
         }
     }
+#pragma unroll
+    for (int t = 0; t < T; t++)
+        if (L.split && t == L.nf && (lane >> L.lg) != 0) tx[t] = ty[t] = tz[t] = tp[t] = 0.0f;
     bh_add_tile<T>(A, tx, ty, tz, tp);
 }
 
 __device__ __forceinline__ float4 bh_pad_source() { return make_float4(1e18f, 1e18f, 1e18f, 0.0f); }
 
+// resident blocks of 128 threads per SM (register budget 65536 / (128 * b))
+#ifndef BH_WALK_MINB3
+#define BH_WALK_MINB3 4
+#endif
+template <int T, bool LEARNED>
+constexpr int bh_walk_min_blocks()
+{
+    return LEARNED ? (T <= 4 ? 3 : 2) : (T <= 1 ? 8 : T <= 2 ? 6 : T <= 3 ? BH_WALK_MINB3 : T <= 4 ? 4 : 2);
+}
+
 template <int T, int ORDER, bool LEARNED>
-__global__ void __launch_bounds__(128, LEARNED ? (T <= 2 ? 4 : T <= 4 ? 3 : 2)
-                                             : (T <= 1 ? 8 : T <= 2 ? 6 : T <= 4 ? 4 : 2))
+__global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
     bh_walk_kernel(WalkParams P)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -251,12 +362,20 @@ __global__ void __launch_bounds__(128, LEARNED ? (T <= 2 ? 4 : T <= 4 ? 3 : 2)
         if (__shfl_sync(BH_FULL_MASK, ab, 0)) break;
         const int gb = P.g_first[g], gc = P.g_count[g], ge = gb + gc;
         const int tn = (gc + 31) >> 5;  // target slots in use (1..T)
+        Layout L;
+        {
+            const int kl = gc - 32 * (tn - 1);  // targets of the last slot
+            L.split = (T <= 4) && (kl <= kSplitMax);
+            L.nf = L.split ? tn - 1 : tn;
+            L.lg = L.split ? (kl > 1 ? 32 - __clz(kl - 1) : 0) : 5;
+        }
+        const int lmask = (1 << L.lg) - 1;
 
         float xi[T], yi[T], zi[T], mi[T];
         unsigned int lo0 = 0xffffffffu, lo1 = 0xffffffffu, lo2 = 0xffffffffu, hi0 = 0u, hi1 = 0u, hi2 = 0u;
 #pragma unroll
         for (int t = 0; t < T; t++) {
-            const int o = t * 32 + lane;
+            const int o = t * 32 + ((L.split && t == L.nf) ? (lane & lmask) : lane);
             float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
             if (o < gc) {
                 q = P.pos_s[gb + o];
@@ -281,7 +400,7 @@ __global__ void __launch_bounds__(128, LEARNED ? (T <= 2 ? 4 : T <= 4 ? 3 : 2)
             A.x[t] = A.y[t] = A.z[t] = A.p[t] = 0.0f;
             A.cx[t] = A.cy[t] = A.cz[t] = A.cp[t] = 0.0f;
         }
-        bh_eval_self<T>(gc, eps2, xi, yi, zi, mi, A);
+        bh_eval_self<T>(gc, L, eps2, xi, yi, zi, mi, A);
         cnt_pp += (unsigned long long)gc * (unsigned long long)(gc - 1);
 
         int sp = 1, ring_head = 0, ring_cnt = 0, q_head = 0, q_cnt = 0;
@@ -367,9 +486,10 @@ __global__ void __launch_bounds__(128, LEARNED ? (T <= 2 ? 4 : T <= 4 ? 3 : 2)
             if (ORDER >= 2) {
                 if (acc) {
                     const int slot = (q_head + q_cnt + __popc(am & lt)) & (kRing - 1);
+                    const float4 qb = P.quad[2 * (size_t)v], qc = P.quad[2 * (size_t)v + 1];
                     Q->a[slot] = cm;
-                    Q->b[slot] = P.quad[2 * (size_t)v];
-                    Q->c[slot] = P.quad[2 * (size_t)v + 1];
+                    Q->b[slot] = make_float4(3.0f * qb.x, 3.0f * qb.y, 3.0f * qb.z, 3.0f * qb.w);
+                    Q->c[slot] = make_float4(3.0f * qc.x, 3.0f * qc.y, qc.z, qc.w);
                 }
                 q_cnt += nacc;
             } else {
@@ -395,7 +515,7 @@ __global__ void __launch_bounds__(128, LEARNED ? (T <= 2 ? 4 : T <= 4 ? 3 : 2)
             // ---- drain: quadrupole tiles, point tiles, particle fills
             if (ORDER >= 2) {
                 while (q_cnt >= 32) {
-                    bh_quads<T>(tn, Q->a + q_head, Q->b + q_head, Q->c + q_head, eps2, xi, yi, zi, A);
+                    bh_quads<T>(L, Q->a + q_head, Q->b + q_head, Q->c + q_head, eps2, xi, yi, zi, A);
                     q_head ^= 32;
                     q_cnt -= 32;
                 }
@@ -403,7 +523,7 @@ __global__ void __launch_bounds__(128, LEARNED ? (T <= 2 ? 4 : T <= 4 ? 3 : 2)
             int lq_pos = 0;
             for (;;) {
                 if (ring_cnt >= 32) {
-                    bh_points<T>(tn, S.ring + ring_head, eps2, xi, yi, zi, A);
+                    bh_points<T>(L, S.ring + ring_head, eps2, xi, yi, zi, A);
                     ring_head ^= 32;
                     ring_cnt -= 32;
                     continue;
@@ -444,22 +564,29 @@ __global__ void __launch_bounds__(128, LEARNED ? (T <= 2 ? 4 : T <= 4 ? 3 : 2)
                 Q->c[q_head + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
             __syncwarp();
-            bh_quads<T>(tn, Q->a + q_head, Q->b + q_head, Q->c + q_head, eps2, xi, yi, zi, A);
+            bh_quads<T>(L, Q->a + q_head, Q->b + q_head, Q->c + q_head, eps2, xi, yi, zi, A);
         }
         if (ring_cnt > 0) {
             if (lane >= ring_cnt) S.ring[ring_head + lane] = bh_pad_source();
             __syncwarp();
-            bh_points<T>(tn, S.ring + ring_head, eps2, xi, yi, zi, A);
+            bh_points<T>(L, S.ring + ring_head, eps2, xi, yi, zi, A);
         }
         __syncwarp();
-        // ---- write (ax, ay, az, phi) in the caller's order
+        // ---- write (ax, ay, az, phi) in the caller's order; a split slot first
+        // adds its phases' sums (lanes l, l + m, l + 2m, ... hold target l)
 #pragma unroll
         for (int t = 0; t < T; t++) {
-            const int o = t * 32 + lane;
-            if (o < gc) {
-                const uint32_t dst = P.perm[gb + o];
-                P.out[dst] = make_float4(A.x[t] - A.cx[t], A.y[t] - A.cy[t], A.z[t] - A.cz[t], A.p[t] - A.cp[t]);
+            float4 f = make_float4(A.x[t] - A.cx[t], A.y[t] - A.cy[t], A.z[t] - A.cz[t], A.p[t] - A.cp[t]);
+            if (L.split && t == L.nf) {
+                for (int off = 1 << L.lg; off < 32; off <<= 1) {
+                    f.x += __shfl_xor_sync(BH_FULL_MASK, f.x, off);
+                    f.y += __shfl_xor_sync(BH_FULL_MASK, f.y, off);
+                    f.z += __shfl_xor_sync(BH_FULL_MASK, f.z, off);
+                    f.w += __shfl_xor_sync(BH_FULL_MASK, f.w, off);
+                }
             }
+            const int o = t * 32 + lane;
+            if (o < gc) P.out[P.perm[gb + o]] = f;
         }
     }
     if (lane == 0) {
