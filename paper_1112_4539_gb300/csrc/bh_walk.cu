@@ -27,12 +27,12 @@
 namespace bh {
 
 constexpr int kStackCap = 352;
-constexpr int kRing = 64;
-// unroll factors of the per-tile source loops (tuning constants: larger
-// factors overflow the instruction cache, as every T-slot variant of the
-// loops is live at once across the SM's warps)
+constexpr int kRing = 64;   // sources per ring (two tiles of 32), stored as 32 even/odd pairs
+// unroll factors of the per-tile pair loops (tuning constants: larger factors
+// overflow the instruction cache, as every T-slot variant of the loops is
+// live at once across the SM's warps)
 #ifndef BH_POINT_UNROLL
-#define BH_POINT_UNROLL 4
+#define BH_POINT_UNROLL 2
 #endif
 #ifndef BH_QUAD_UNROLL
 #define BH_QUAD_UNROLL 1
@@ -40,15 +40,50 @@ constexpr int kRing = 64;
 constexpr int kPointUnroll = BH_POINT_UNROLL;
 constexpr int kQuadUnroll = BH_QUAD_UNROLL;
 
+// Sources are staged negated and as pairs (ring positions 2p, 2p+1 side by
+// side) so that the interaction arithmetic runs on packed f32x2 operations:
+// one instruction computes the same step for two sources.
 struct WarpSmem {
     uint32_t stack[kStackCap];  // (first node << 3) | (count - 1)
     uint32_t staging[32];
     int2 leafq[64];             // pending particle ranges (first, count)
-    float4 ring[kRing];         // point sources (x, y, z, m): particles and monopole cells
+    float4 ra[kRing / 2];       // point sources: (-x, -x', -y, -y')
+    float4 rb[kRing / 2];       //                (-z, -z', -m, -m')
 };
-struct WarpQuad {
-    float4 a[kRing], b[kRing], c[kRing];  // cell (x, y, z, M), (xx, yy, zz, xy), (xz, yz, 1.5T, 0.5T)
+struct WarpQuad {               // quadrupole cells, pairs as above
+    float4 a[kRing / 2];        // (-x, -x', -y, -y')      centre of mass
+    float4 b[kRing / 2];        // (-z, -z', -M, -M')
+    float4 c[kRing / 2];        // 3 (Ixx, Ixx', Iyy, Iyy')
+    float4 d[kRing / 2];        // 3 (Izz, Izz', Ixy, Ixy')
+    float4 e[kRing / 2];        // 3 (Ixz, Ixz', Iyz, Iyz')
+    float4 f[kRing / 2];        // (1.5 T, 1.5 T', 0.5 T, 0.5 T'),  T = tr I
 };
+
+__device__ __forceinline__ void bh_put_point(WarpSmem& S, int r, float4 v)
+{
+    float* a = reinterpret_cast<float*>(&S.ra[r >> 1]) + (r & 1);
+    float* b = reinterpret_cast<float*>(&S.rb[r >> 1]) + (r & 1);
+    a[0] = -v.x; a[2] = -v.y;
+    b[0] = -v.z; b[2] = -v.w;
+}
+// cell with centre/mass cm and stored moments qb = (Ixx, Iyy, Izz, Ixy),
+// qc = (Ixz, Iyz, 1.5 T, 0.5 T)
+__device__ __forceinline__ void bh_put_quad(WarpQuad& Q, int r, float4 cm, float4 qb, float4 qc)
+{
+    const int p = r >> 1, h = r & 1;
+    float* a = reinterpret_cast<float*>(&Q.a[p]) + h;
+    float* b = reinterpret_cast<float*>(&Q.b[p]) + h;
+    float* c = reinterpret_cast<float*>(&Q.c[p]) + h;
+    float* d = reinterpret_cast<float*>(&Q.d[p]) + h;
+    float* e = reinterpret_cast<float*>(&Q.e[p]) + h;
+    float* f = reinterpret_cast<float*>(&Q.f[p]) + h;
+    a[0] = -cm.x; a[2] = -cm.y;
+    b[0] = -cm.z; b[2] = -cm.w;
+    c[0] = 3.0f * qb.x; c[2] = 3.0f * qb.y;
+    d[0] = 3.0f * qb.z; d[2] = 3.0f * qb.w;
+    e[0] = 3.0f * qc.x; e[2] = 3.0f * qc.y;
+    f[0] = qc.z; f[2] = qc.w;
+}
 
 struct WalkParams {
     const float4* pos_s;
@@ -68,11 +103,28 @@ struct WalkParams {
     float theta_guard;       // theta of the S_eff in use (the guard)
 };
 
+// Running totals of a lane's T targets with their Kahan compensations, the
+// latter either in registers or in shared memory (this lane's column of a
+// per-warp [4T][32] array: touched once per tile, they need no register).
+#ifndef BH_KAHAN_SMEM
+#define BH_KAHAN_SMEM 1
+#endif
 template <int T>
 struct Acc {
     float x[T], y[T], z[T], p[T];
-    float cx[T], cy[T], cz[T], cp[T];
+#if BH_KAHAN_SMEM
+    float* kc;
+    __device__ __forceinline__ float& c(int t, int k) { return kc[(4 * t + k) * 32]; }
+#else
+    float cc[4][T];
+    __device__ __forceinline__ float& c(int t, int k) { return cc[k][t]; }
+#endif
 };
+template <int T>
+__host__ __device__ constexpr size_t bh_kahan_smem_bytes()
+{
+    return BH_KAHAN_SMEM ? (size_t)T * 4 * 32 * sizeof(float) : 0;
+}
 
 // Target layout of a group of gc particles on the warp's T slots per lane
 // (warp-uniform).  Slots 0..nf-1 hold targets t*32 + lane.  When the last
@@ -99,110 +151,132 @@ __device__ __forceinline__ void bh_kahan(float& s, float& c, float v)
     s = t;
 }
 
-template <int T, int TN = T>
-__device__ __forceinline__ void bh_add_tile(Acc<T>& A, const float (&tx)[T], const float (&ty)[T],
-                                            const float (&tz)[T], const float (&tp)[T])
+typedef float2 f2;
+__device__ __forceinline__ f2 bh_add2(f2 a, f2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2 bh_mul2(f2 a, f2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2 bh_fma2(f2 a, f2 b, f2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2 bh_rsqrt2(f2 a) { return make_float2(rsqrtf(a.x), rsqrtf(a.y)); }
+__device__ __forceinline__ f2 bh_lo(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ f2 bh_hi(float4 v) { return make_float2(v.z, v.w); }
+
+// Per-slot partial sums of one tile, two lanes of a pair each.
+template <int T>
+struct Part {
+    f2 x[T], y[T], z[T], p[T], q[T];
+};
+
+// Adds the tile's pair sums of slots 0..TN-1 to the running totals.
+template <int T, int TN>
+__device__ __forceinline__ void bh_add_tile(Acc<T>& A, const Part<T>& P, bool with_q)
 {
 #pragma unroll
     for (int t = 0; t < TN; t++) {
-        bh_kahan(A.x[t], A.cx[t], tx[t]);
-        bh_kahan(A.y[t], A.cy[t], ty[t]);
-        bh_kahan(A.z[t], A.cz[t], tz[t]);
-        bh_kahan(A.p[t], A.cp[t], tp[t]);
+        float pt = P.p[t].x + P.p[t].y;
+        if (with_q) pt = fmaf(-0.5f, P.q[t].x + P.q[t].y, pt);
+        bh_kahan(A.x[t], A.c(t, 0), P.x[t].x + P.x[t].y);
+        bh_kahan(A.y[t], A.c(t, 1), P.y[t].x + P.y[t].y);
+        bh_kahan(A.z[t], A.c(t, 2), P.z[t].x + P.z[t].y);
+        bh_kahan(A.p[t], A.c(t, 3), pt);
     }
 }
 
-// One point source s = (x, y, z, m) on one target (Eq. 1).
-__device__ __forceinline__ void bh_pp(const float4& s, float eps2, float xi, float yi, float zi, float& ax,
-                                      float& ay, float& az, float& ap)
+// A pair of point sources (negated, as staged) on one target held twice in
+// (x, y, z); Eq. 1:  a += m (s - x_i) / r^3,  phi -= m / r.
+__device__ __forceinline__ void bh_pp2(float4 sa, float4 sb, f2 eps2, f2 x, f2 y, f2 z, f2& ax, f2& ay, f2& az,
+                                       f2& ap)
 {
-    const float dx = s.x - xi, dy = s.y - yi, dz = s.z - zi;
-    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
-    const float ri = rsqrtf(r2);
-    const float mr = s.w * ri;
-    const float mr3 = mr * ri * ri;
-    ax = fmaf(mr3, dx, ax);
-    ay = fmaf(mr3, dy, ay);
-    az = fmaf(mr3, dz, az);
-    ap -= mr;
+    const f2 dx = bh_add2(x, bh_lo(sa)), dy = bh_add2(y, bh_hi(sa)), dz = bh_add2(z, bh_lo(sb));  // x_i - s
+    const f2 r2 = bh_fma2(dz, dz, bh_fma2(dy, dy, bh_fma2(dx, dx, eps2)));
+    const f2 ri = bh_rsqrt2(r2);
+    const f2 mr = bh_mul2(bh_hi(sb), ri);          // -m / r
+    const f2 mr3 = bh_mul2(mr, bh_mul2(ri, ri));   // -m / r^3
+    ax = bh_fma2(mr3, dx, ax);
+    ay = bh_fma2(mr3, dy, ay);
+    az = bh_fma2(mr3, dz, az);
+    ap = bh_add2(ap, mr);
 }
 
-// One quadrupole cell on one target.  The cell is staged as a = (c, M),
-// b = 3 (Ixx, Iyy, Izz, Ixy), e = (3 Ixz, 3 Iyz, 1.5 T, 0.5 T) with T = tr I.
-// With r = x_i - c, h^2 = r^2 + eps^2, g_n = h^-n, u = 3 I r, q3 = r.u
-// (three times the quadratic form):
+// A pair of quadrupole cells on one target.  With r = x_i - c, h^2 = r^2 +
+// eps^2, g_n = h^-n, u = 3 I r, q3 = r.u (three times the quadratic form):
 //   a   += g5 u + k r,   k = g5 (1.5 T - 2.5 q3 g2) - M g3
 //   phi += -M g1 + 0.5 T g3 - 0.5 q3 g5
 // the last term accumulated apart (aq) and scaled once per tile.
-__device__ __forceinline__ void bh_pq(const float4& a, const float4& b, const float4& e, float eps2, float xi,
-                                      float yi, float zi, float& ax, float& ay, float& az, float& ap, float& aq)
+__device__ __forceinline__ void bh_pq2(float4 ca, float4 cb, float4 cc, float4 cd, float4 ce, float4 cf, f2 eps2,
+                                       f2 x, f2 y, f2 z, f2& ax, f2& ay, f2& az, f2& ap, f2& aq)
 {
-    const float rx = xi - a.x, ry = yi - a.y, rz = zi - a.z;
-    const float h2 = fmaf(rz, rz, fmaf(ry, ry, fmaf(rx, rx, eps2)));
-    const float g1 = rsqrtf(h2);
-    const float g2 = g1 * g1;
-    const float g3 = g1 * g2;
-    const float g5 = g3 * g2;
-    const float u0 = fmaf(b.w, ry, fmaf(e.x, rz, b.x * rx));
-    const float u1 = fmaf(b.w, rx, fmaf(e.y, rz, b.y * ry));
-    const float u2 = fmaf(e.x, rx, fmaf(e.y, ry, b.z * rz));
-    const float q3 = fmaf(rx, u0, fmaf(ry, u1, rz * u2));
-    const float w = fmaf(-2.5f * q3, g2, e.z);
-    const float k = fmaf(g5, w, -(a.w * g3));
-    ax = fmaf(g5, u0, fmaf(k, rx, ax));
-    ay = fmaf(g5, u1, fmaf(k, ry, ay));
-    az = fmaf(g5, u2, fmaf(k, rz, az));
-    ap = fmaf(e.w, g3, fmaf(-a.w, g1, ap));
-    aq = fmaf(q3, g5, aq);
+    const f2 rx = bh_add2(x, bh_lo(ca)), ry = bh_add2(y, bh_hi(ca)), rz = bh_add2(z, bh_lo(cb));
+    const f2 h2 = bh_fma2(rz, rz, bh_fma2(ry, ry, bh_fma2(rx, rx, eps2)));
+    const f2 g1 = bh_rsqrt2(h2);
+    const f2 g2 = bh_mul2(g1, g1);
+    const f2 g3 = bh_mul2(g1, g2);
+    const f2 g5 = bh_mul2(g3, g2);
+    const f2 mneg = bh_hi(cb);
+    const f2 u0 = bh_fma2(bh_hi(cd), ry, bh_fma2(bh_lo(ce), rz, bh_mul2(bh_lo(cc), rx)));
+    const f2 u1 = bh_fma2(bh_hi(cd), rx, bh_fma2(bh_hi(ce), rz, bh_mul2(bh_hi(cc), ry)));
+    const f2 u2 = bh_fma2(bh_lo(ce), rx, bh_fma2(bh_hi(ce), ry, bh_mul2(bh_lo(cd), rz)));
+    const f2 q3 = bh_fma2(rx, u0, bh_fma2(ry, u1, bh_mul2(rz, u2)));
+    const f2 w = bh_fma2(bh_mul2(q3, make_float2(-2.5f, -2.5f)), g2, bh_lo(cf));
+    const f2 k = bh_fma2(g5, w, bh_mul2(mneg, g3));
+    ax = bh_fma2(g5, u0, bh_fma2(k, rx, ax));
+    ay = bh_fma2(g5, u1, bh_fma2(k, ry, ay));
+    az = bh_fma2(g5, u2, bh_fma2(k, rz, az));
+    ap = bh_fma2(bh_hi(cf), g3, bh_fma2(mneg, g1, ap));
+    aq = bh_fma2(q3, g5, aq);
 }
 
-// 32 point sources (particles or monopole cells) on the first NF slots of
-// every lane.
-template <int T, int NF>
-__device__ __forceinline__ void bh_eval_points(const float4* __restrict__ src, float eps2, const float (&xi)[T],
-                                               const float (&yi)[T], const float (&zi)[T], Acc<T>& A)
-{
-    float tx[T], ty[T], tz[T], tp[T];
-#pragma unroll
-    for (int t = 0; t < NF; t++) tx[t] = ty[t] = tz[t] = tp[t] = 0.0f;
-#pragma unroll kPointUnroll
-    for (int j = 0; j < 32; j++) {
-        const float4 s = src[j];
-#pragma unroll
-        for (int t = 0; t < NF; t++) bh_pp(s, eps2, xi[t], yi[t], zi[t], tx[t], ty[t], tz[t], tp[t]);
-    }
-    bh_add_tile<T, NF>(A, tx, ty, tz, tp);
-}
-
-// 32 quadrupole cells on the first NF slots of every lane.
-template <int T, int NF>
-__device__ __forceinline__ void bh_eval_quads(const float4* __restrict__ ca, const float4* __restrict__ cb,
-                                              const float4* __restrict__ cc, float eps2, const float (&xi)[T],
-                                              const float (&yi)[T], const float (&zi)[T], Acc<T>& A)
-{
-    float tx[T], ty[T], tz[T], tp[T], tq[T];
-#pragma unroll
-    for (int t = 0; t < NF; t++) tx[t] = ty[t] = tz[t] = tp[t] = tq[t] = 0.0f;
-#pragma unroll kQuadUnroll
-    for (int j = 0; j < 32; j++) {
-        const float4 a = ca[j], b = cb[j], c = cc[j];
-#pragma unroll
-        for (int t = 0; t < NF; t++) bh_pq(a, b, c, eps2, xi[t], yi[t], zi[t], tx[t], ty[t], tz[t], tp[t], tq[t]);
-    }
-#pragma unroll
-    for (int t = 0; t < NF; t++) tp[t] = fmaf(-0.5f, tq[t], tp[t]);
-    bh_add_tile<T, NF>(A, tx, ty, tz, tp);
-}
-
-// The split slot: target of slot L.nf, the m = 2^lg sources of the lane's phase.
+// Targets of a lane: slot t holds (x, x), (y, y), (z, z).
 template <int T>
-__device__ __forceinline__ void bh_split_target(const Layout& L, const float (&xi)[T], const float (&yi)[T],
-                                                const float (&zi)[T], float& x, float& y, float& z)
+struct Tgt {
+    f2 x[T], y[T], z[T];
+};
+
+// One tile (16 pairs) of point sources on the first NF slots of every lane.
+template <int T, int NF>
+__device__ __forceinline__ void bh_eval_points(const float4* __restrict__ ra, const float4* __restrict__ rb,
+                                               f2 eps2, const Tgt<T>& X, Acc<T>& A)
 {
-    x = xi[0]; y = yi[0]; z = zi[0];
+    Part<T> P;
+#pragma unroll
+    for (int t = 0; t < NF; t++) P.x[t] = P.y[t] = P.z[t] = P.p[t] = make_float2(0.f, 0.f);
+#pragma unroll kPointUnroll
+    for (int j = 0; j < 16; j++) {
+        const float4 sa = ra[j], sb = rb[j];
+#pragma unroll
+        for (int t = 0; t < NF; t++) bh_pp2(sa, sb, eps2, X.x[t], X.y[t], X.z[t], P.x[t], P.y[t], P.z[t], P.p[t]);
+    }
+    bh_add_tile<T, NF>(A, P, false);
+}
+
+// One tile (16 pairs) of quadrupole cells on the first NF slots of every lane.
+template <int T, int NF>
+__device__ __forceinline__ void bh_eval_quads(const WarpQuad& Q, int p0, f2 eps2, const Tgt<T>& X, Acc<T>& A)
+{
+    Part<T> P;
+#pragma unroll
+    for (int t = 0; t < NF; t++) P.x[t] = P.y[t] = P.z[t] = P.p[t] = P.q[t] = make_float2(0.f, 0.f);
+#pragma unroll kQuadUnroll
+    for (int j = p0; j < p0 + 16; j++) {
+        const float4 ca = Q.a[j], cb = Q.b[j], cc = Q.c[j], cd = Q.d[j], ce = Q.e[j], cf = Q.f[j];
+#pragma unroll
+        for (int t = 0; t < NF; t++)
+            bh_pq2(ca, cb, cc, cd, ce, cf, eps2, X.x[t], X.y[t], X.z[t], P.x[t], P.y[t], P.z[t], P.p[t], P.q[t]);
+    }
+    bh_add_tile<T, NF>(A, P, true);
+}
+
+// The split slot: its target, and the m = 2^lg sources of the lane's phase
+// (pairs from p; with m = 1 the pair holding the lane's source, one half kept).
+template <int T>
+__device__ __forceinline__ void bh_split_target(const Layout& L, const Tgt<T>& X, f2& x, f2& y, f2& z)
+{
+    x = X.x[0]; y = X.y[0]; z = X.z[0];
 #pragma unroll
     for (int t = 1; t < T; t++)
-        if (t == L.nf) { x = xi[t]; y = yi[t]; z = zi[t]; }
+        if (t == L.nf) { x = X.x[t]; y = X.y[t]; z = X.z[t]; }
+}
+__device__ __forceinline__ float bh_split_sum(const Layout& L, f2 v)
+{
+    return L.lg ? v.x + v.y : ((threadIdx.x & 1) ? v.y : v.x);
 }
 template <int T>
 __device__ __forceinline__ void bh_split_add(const Layout& L, Acc<T>& A, float ax, float ay, float az, float ap)
@@ -210,65 +284,59 @@ __device__ __forceinline__ void bh_split_add(const Layout& L, Acc<T>& A, float a
 #pragma unroll
     for (int t = 0; t < T; t++)
         if (t == L.nf) {
-            bh_kahan(A.x[t], A.cx[t], ax);
-            bh_kahan(A.y[t], A.cy[t], ay);
-            bh_kahan(A.z[t], A.cz[t], az);
-            bh_kahan(A.p[t], A.cp[t], ap);
+            bh_kahan(A.x[t], A.c(t, 0), ax);
+            bh_kahan(A.y[t], A.c(t, 1), ay);
+            bh_kahan(A.z[t], A.c(t, 2), az);
+            bh_kahan(A.p[t], A.c(t, 3), ap);
         }
 }
 template <int T>
-__device__ __forceinline__ void bh_split_points(const Layout& L, const float4* __restrict__ src, float eps2,
-                                                const float (&xi)[T], const float (&yi)[T], const float (&zi)[T],
-                                                Acc<T>& A)
+__device__ __forceinline__ void bh_split_points(const Layout& L, const float4* __restrict__ ra,
+                                                const float4* __restrict__ rb, f2 eps2, const Tgt<T>& X, Acc<T>& A)
 {
-    float x, y, z, ax = 0.f, ay = 0.f, az = 0.f, ap = 0.f;
-    bh_split_target<T>(L, xi, yi, zi, x, y, z);
-    const float4* ph = src + (((threadIdx.x & 31) >> L.lg) << L.lg);
-    const int m = 1 << L.lg;
-#pragma unroll 2
-    for (int i = 0; i < m; i++) bh_pp(ph[i], eps2, x, y, z, ax, ay, az, ap);
-    bh_split_add<T>(L, A, ax, ay, az, ap);
+    f2 x, y, z, ax = make_float2(0.f, 0.f), ay = ax, az = ax, ap = ax;
+    bh_split_target<T>(L, X, x, y, z);
+    const int p = ((threadIdx.x & 31) >> L.lg) << L.lg >> 1, np = L.lg ? 1 << (L.lg - 1) : 1;
+    for (int i = p; i < p + np; i++) bh_pp2(ra[i], rb[i], eps2, x, y, z, ax, ay, az, ap);
+    bh_split_add<T>(L, A, bh_split_sum(L, ax), bh_split_sum(L, ay), bh_split_sum(L, az), bh_split_sum(L, ap));
 }
 template <int T>
-__device__ __forceinline__ void bh_split_quads(const Layout& L, const float4* __restrict__ ca,
-                                               const float4* __restrict__ cb, const float4* __restrict__ cc,
-                                               float eps2, const float (&xi)[T], const float (&yi)[T],
-                                               const float (&zi)[T], Acc<T>& A)
+__device__ __forceinline__ void bh_split_quads(const Layout& L, const WarpQuad& Q, int p0, f2 eps2, const Tgt<T>& X,
+                                               Acc<T>& A)
 {
-    float x, y, z, ax = 0.f, ay = 0.f, az = 0.f, ap = 0.f, aq = 0.f;
-    bh_split_target<T>(L, xi, yi, zi, x, y, z);
-    const int o = ((threadIdx.x & 31) >> L.lg) << L.lg, m = 1 << L.lg;
-    for (int i = 0; i < m; i++) bh_pq(ca[o + i], cb[o + i], cc[o + i], eps2, x, y, z, ax, ay, az, ap, aq);
-    bh_split_add<T>(L, A, ax, ay, az, fmaf(-0.5f, aq, ap));
+    f2 x, y, z, ax = make_float2(0.f, 0.f), ay = ax, az = ax, ap = ax, aq = ax;
+    bh_split_target<T>(L, X, x, y, z);
+    const int p = p0 + (((threadIdx.x & 31) >> L.lg) << L.lg >> 1), np = L.lg ? 1 << (L.lg - 1) : 1;
+    for (int i = p; i < p + np; i++)
+        bh_pq2(Q.a[i], Q.b[i], Q.c[i], Q.d[i], Q.e[i], Q.f[i], eps2, x, y, z, ax, ay, az, ap, aq);
+    bh_split_add<T>(L, A, bh_split_sum(L, ax), bh_split_sum(L, ay), bh_split_sum(L, az),
+                    fmaf(-0.5f, bh_split_sum(L, aq), bh_split_sum(L, ap)));
 }
 
 // Dispatch on the warp-uniform layout.  Every bh_eval_* instance is reached
 // from one call site only (they are inlined: a second site would double the
 // code of the hottest loop).
 template <int T>
-__device__ __forceinline__ void bh_points(const Layout& L, const float4* __restrict__ src, float eps2,
-                                          const float (&xi)[T], const float (&yi)[T], const float (&zi)[T],
-                                          Acc<T>& A)
+__device__ __forceinline__ void bh_points(const Layout& L, const float4* __restrict__ ra,
+                                          const float4* __restrict__ rb, f2 eps2, const Tgt<T>& X, Acc<T>& A)
 {
-    if (T > 1 && L.nf == 1) bh_eval_points<T, 1>(src, eps2, xi, yi, zi, A);
-    else if (T > 2 && L.nf == 2) bh_eval_points<T, (T > 2 ? 2 : T)>(src, eps2, xi, yi, zi, A);
-    else if (T > 3 && L.nf == 3) bh_eval_points<T, (T > 3 ? 3 : T)>(src, eps2, xi, yi, zi, A);
-    else if (T > 4 && L.nf == 4) bh_eval_points<T, (T > 4 ? 4 : T)>(src, eps2, xi, yi, zi, A);
-    else if (L.nf > 0) bh_eval_points<T, T>(src, eps2, xi, yi, zi, A);
-    if (L.split) bh_split_points<T>(L, src, eps2, xi, yi, zi, A);
+    if (T > 1 && L.nf == 1) bh_eval_points<T, 1>(ra, rb, eps2, X, A);
+    else if (T > 2 && L.nf == 2) bh_eval_points<T, (T > 2 ? 2 : T)>(ra, rb, eps2, X, A);
+    else if (T > 3 && L.nf == 3) bh_eval_points<T, (T > 3 ? 3 : T)>(ra, rb, eps2, X, A);
+    else if (T > 4 && L.nf == 4) bh_eval_points<T, (T > 4 ? 4 : T)>(ra, rb, eps2, X, A);
+    else if (L.nf > 0) bh_eval_points<T, T>(ra, rb, eps2, X, A);
+    if (L.split) bh_split_points<T>(L, ra, rb, eps2, X, A);
 }
 template <int T>
-__device__ __forceinline__ void bh_quads(const Layout& L, const float4* __restrict__ ca,
-                                         const float4* __restrict__ cb, const float4* __restrict__ cc, float eps2,
-                                         const float (&xi)[T], const float (&yi)[T], const float (&zi)[T],
+__device__ __forceinline__ void bh_quads(const Layout& L, const WarpQuad& Q, int p0, f2 eps2, const Tgt<T>& X,
                                          Acc<T>& A)
 {
-    if (T > 1 && L.nf == 1) bh_eval_quads<T, 1>(ca, cb, cc, eps2, xi, yi, zi, A);
-    else if (T > 2 && L.nf == 2) bh_eval_quads<T, (T > 2 ? 2 : T)>(ca, cb, cc, eps2, xi, yi, zi, A);
-    else if (T > 3 && L.nf == 3) bh_eval_quads<T, (T > 3 ? 3 : T)>(ca, cb, cc, eps2, xi, yi, zi, A);
-    else if (T > 4 && L.nf == 4) bh_eval_quads<T, (T > 4 ? 4 : T)>(ca, cb, cc, eps2, xi, yi, zi, A);
-    else if (L.nf > 0) bh_eval_quads<T, T>(ca, cb, cc, eps2, xi, yi, zi, A);
-    if (L.split) bh_split_quads<T>(L, ca, cb, cc, eps2, xi, yi, zi, A);
+    if (T > 1 && L.nf == 1) bh_eval_quads<T, 1>(Q, p0, eps2, X, A);
+    else if (T > 2 && L.nf == 2) bh_eval_quads<T, (T > 2 ? 2 : T)>(Q, p0, eps2, X, A);
+    else if (T > 3 && L.nf == 3) bh_eval_quads<T, (T > 3 ? 3 : T)>(Q, p0, eps2, X, A);
+    else if (T > 4 && L.nf == 4) bh_eval_quads<T, (T > 4 ? 4 : T)>(Q, p0, eps2, X, A);
+    else if (L.nf > 0) bh_eval_quads<T, T>(Q, p0, eps2, X, A);
+    if (L.split) bh_split_quads<T>(L, Q, p0, eps2, X, A);
 }
 
 // The group's own particles on its members, target itself masked.
@@ -310,7 +378,13 @@ __device__ __forceinline__ void bh_eval_self(int gc, const Layout& L, float eps2
 #pragma unroll
     for (int t = 0; t < T; t++)
         if (L.split && t == L.nf && (lane >> L.lg) != 0) tx[t] = ty[t] = tz[t] = tp[t] = 0.0f;
-    bh_add_tile<T>(A, tx, ty, tz, tp);
+#pragma unroll
+    for (int t = 0; t < T; t++) {
+        bh_kahan(A.x[t], A.c(t, 0), tx[t]);
+        bh_kahan(A.y[t], A.c(t, 1), ty[t]);
+        bh_kahan(A.z[t], A.c(t, 2), tz[t]);
+        bh_kahan(A.p[t], A.c(t, 3), tp[t]);
+    }
 }
 
 __device__ __forceinline__ float4 bh_pad_source() { return make_float4(1e18f, 1e18f, 1e18f, 0.0f); }
@@ -322,7 +396,7 @@ __device__ __forceinline__ float4 bh_pad_source() { return make_float4(1e18f, 1e
 template <int T, bool LEARNED>
 constexpr int bh_walk_min_blocks()
 {
-    return LEARNED ? (T <= 4 ? 3 : 2) : (T <= 1 ? 8 : T <= 2 ? 6 : T <= 3 ? BH_WALK_MINB3 : T <= 4 ? 4 : 2);
+    return LEARNED ? (T <= 4 ? 3 : 2) : (T <= 1 ? 6 : T <= 2 ? 4 : T <= 3 ? BH_WALK_MINB3 : T <= 4 ? 3 : 2);
 }
 
 template <int T, int ORDER, bool LEARNED>
@@ -339,6 +413,9 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
     unsigned char* lbase = smem_raw + (size_t)nwarps * (sizeof(WarpSmem) + (ORDER >= 2 ? sizeof(WarpQuad) : 0));
     bh_mlp_dev* MW = reinterpret_cast<bh_mlp_dev*>(lbase);
     uint32_t* xs = reinterpret_cast<uint32_t*>(lbase + sizeof(bh_mlp_dev)) + wib * (32 * 8);
+    // Kahan compensations (per warp, after the learned-criterion area)
+    unsigned char* kbase = lbase + (LEARNED ? sizeof(bh_mlp_dev) + (size_t)nwarps * 32 * 8 * sizeof(uint32_t) : 0);
+    float* kcol = reinterpret_cast<float*>(kbase + (size_t)wib * bh_kahan_smem_bytes<T>()) + lane;
     if (LEARNED) {
         for (int i = threadIdx.x; i < (int)(sizeof(bh_mlp_dev) / 4); i += blockDim.x)
             reinterpret_cast<uint32_t*>(MW)[i] = reinterpret_cast<const uint32_t*>(P.mlp)[i];
@@ -395,12 +472,23 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
         const float grg = 0.5f * sqrtf((bx1 - bx0) * (bx1 - bx0) + (by1 - by0) * (by1 - by0) + (bz1 - bz0) * (bz1 - bz0));
 
         Acc<T> A;
+#if BH_KAHAN_SMEM
+        A.kc = kcol;
+#endif
 #pragma unroll
         for (int t = 0; t < T; t++) {
             A.x[t] = A.y[t] = A.z[t] = A.p[t] = 0.0f;
-            A.cx[t] = A.cy[t] = A.cz[t] = A.cp[t] = 0.0f;
+            A.c(t, 0) = A.c(t, 1) = A.c(t, 2) = A.c(t, 3) = 0.0f;
         }
         bh_eval_self<T>(gc, L, eps2, xi, yi, zi, mi, A);
+        Tgt<T> X;
+#pragma unroll
+        for (int t = 0; t < T; t++) {
+            X.x[t] = make_float2(xi[t], xi[t]);
+            X.y[t] = make_float2(yi[t], yi[t]);
+            X.z[t] = make_float2(zi[t], zi[t]);
+        }
+        const f2 eps2v = make_float2(eps2, eps2);
         cnt_pp += (unsigned long long)gc * (unsigned long long)(gc - 1);
 
         int sp = 1, ring_head = 0, ring_cnt = 0, q_head = 0, q_cnt = 0;
@@ -486,14 +574,11 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
             if (ORDER >= 2) {
                 if (acc) {
                     const int slot = (q_head + q_cnt + __popc(am & lt)) & (kRing - 1);
-                    const float4 qb = P.quad[2 * (size_t)v], qc = P.quad[2 * (size_t)v + 1];
-                    Q->a[slot] = cm;
-                    Q->b[slot] = make_float4(3.0f * qb.x, 3.0f * qb.y, 3.0f * qb.z, 3.0f * qb.w);
-                    Q->c[slot] = make_float4(3.0f * qc.x, 3.0f * qc.y, qc.z, qc.w);
+                    bh_put_quad(*Q, slot, cm, P.quad[2 * (size_t)v], P.quad[2 * (size_t)v + 1]);
                 }
                 q_cnt += nacc;
             } else {
-                if (acc) S.ring[(ring_head + ring_cnt + __popc(am & lt)) & (kRing - 1)] = cm;
+                if (acc) bh_put_point(S, (ring_head + ring_cnt + __popc(am & lt)) & (kRing - 1), cm);
                 ring_cnt += nacc;
             }
 
@@ -515,7 +600,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
             // ---- drain: quadrupole tiles, point tiles, particle fills
             if (ORDER >= 2) {
                 while (q_cnt >= 32) {
-                    bh_quads<T>(L, Q->a + q_head, Q->b + q_head, Q->c + q_head, eps2, xi, yi, zi, A);
+                    bh_quads<T>(L, *Q, q_head >> 1, eps2v, X, A);
                     q_head ^= 32;
                     q_cnt -= 32;
                 }
@@ -523,7 +608,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
             int lq_pos = 0;
             for (;;) {
                 if (ring_cnt >= 32) {
-                    bh_points<T>(L, S.ring + ring_head, eps2, xi, yi, zi, A);
+                    bh_points<T>(L, S.ra + (ring_head >> 1), S.rb + (ring_head >> 1), eps2v, X, A);
                     ring_head ^= 32;
                     ring_cnt -= 32;
                     continue;
@@ -547,7 +632,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
                     S.leafq[lq_pos + lane] = make_int2(q.x + take2, c2 - take2);
                 lq_pos += nf2;
                 if (lane < nfill)
-                    S.ring[(ring_head + ring_cnt + lane) & (kRing - 1)] = P.pos_s[S.staging[lane]];
+                    bh_put_point(S, (ring_head + ring_cnt + lane) & (kRing - 1), P.pos_s[S.staging[lane]]);
                 ring_cnt += nfill;
                 __syncwarp();
             }
@@ -558,25 +643,23 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
         }
         // ---- flush the partial tiles (padded with far, massless sources)
         if (ORDER >= 2 && q_cnt > 0) {
-            if (lane >= q_cnt) {
-                Q->a[q_head + lane] = bh_pad_source();
-                Q->b[q_head + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-                Q->c[q_head + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
+            if (lane >= q_cnt)
+                bh_put_quad(*Q, q_head + lane, bh_pad_source(), make_float4(0.f, 0.f, 0.f, 0.f),
+                            make_float4(0.f, 0.f, 0.f, 0.f));
             __syncwarp();
-            bh_quads<T>(L, Q->a + q_head, Q->b + q_head, Q->c + q_head, eps2, xi, yi, zi, A);
+            bh_quads<T>(L, *Q, q_head >> 1, eps2v, X, A);
         }
         if (ring_cnt > 0) {
-            if (lane >= ring_cnt) S.ring[ring_head + lane] = bh_pad_source();
+            if (lane >= ring_cnt) bh_put_point(S, ring_head + lane, bh_pad_source());
             __syncwarp();
-            bh_points<T>(L, S.ring + ring_head, eps2, xi, yi, zi, A);
+            bh_points<T>(L, S.ra + (ring_head >> 1), S.rb + (ring_head >> 1), eps2v, X, A);
         }
         __syncwarp();
         // ---- write (ax, ay, az, phi) in the caller's order; a split slot first
         // adds its phases' sums (lanes l, l + m, l + 2m, ... hold target l)
 #pragma unroll
         for (int t = 0; t < T; t++) {
-            float4 f = make_float4(A.x[t] - A.cx[t], A.y[t] - A.cy[t], A.z[t] - A.cz[t], A.p[t] - A.cp[t]);
+            float4 f = make_float4(A.x[t] - A.c(t, 0), A.y[t] - A.c(t, 1), A.z[t] - A.c(t, 2), A.p[t] - A.c(t, 3));
             if (L.split && t == L.nf) {
                 for (int off = 1 << L.lg; off < 32; off <<= 1) {
                     f.x += __shfl_xor_sync(BH_FULL_MASK, f.x, off);
@@ -611,6 +694,7 @@ static int bh_walk_launch_t(const WalkParams& P, int sm_count, int block_threads
     const int nw = block_threads / 32;
     size_t smem = (size_t)nw * (sizeof(WarpSmem) + (ORDER >= 2 ? sizeof(WarpQuad) : 0));
     if (LEARNED) smem += sizeof(bh_mlp_dev) + (size_t)nw * 32 * 8 * sizeof(uint32_t);
+    smem += (size_t)nw * bh_kahan_smem_bytes<T>();
     auto kern = bh_walk_kernel<T, ORDER, LEARNED>;
     if (smem > 48 * 1024) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
