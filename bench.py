@@ -55,6 +55,16 @@ WORKLOADS = {
                                        "uniform background, eps=1e-3, quadrupole"),
     "plummer1m": dict(kind="plummer", n=1 << 20, seed=1, eps=0.01, leaf=16, G=96, order=2, dt=1e-4,
                       theta=0.6, desc="Plummer N=1048576, eps=0.01, quadrupole"),
+    # the learned criterion against theta on fresh sets (seed 4, not in its training data),
+    # each at its own p99 = 1e-3 point (theta searched every run)
+    "clumpy4m": dict(kind="clumpy", n=1 << 22, seed=4, eps=1e-3, leaf=16, G=96, order=2, dt=1e-4,
+                     theta=0.55, calibrate=True,
+                     desc="clumpy N=4194304 (seed 4): 64 Hernquist clumps (a=0.05) + 20% uniform background, "
+                          "eps=1e-3, quadrupole; learned criterion vs theta at matched p99"),
+    "plummer4m": dict(kind="plummer", n=1 << 22, seed=4, eps=0.01, leaf=16, G=96, order=2, dt=1e-4,
+                      theta=0.6, calibrate=True,
+                      desc="Plummer N=4194304 (seed 4), eps=0.01, quadrupole; learned criterion vs theta "
+                           "at matched p99"),
     "batched512": dict(kind="batched", nsys=512, nmin=1024, nmax=65536, seed=3, eps=0.01, theta=0.5, order=1,
                        desc="512 independent Plummer spheres, N log-uniform in [1024, 65536] (seed 3), "
                             "eps=0.01, theta=0.5, monopole; one evaluation of all systems per step"),
@@ -77,6 +87,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-criterion comparison")
     ap.add_argument("--cpu-sample-groups", type=int, default=6000)
+    ap.add_argument("--accuracy-sweep", action="store_true",
+                    help="Plummer N=2^20: errors and time over theta x group size x order (no bench line)")
     return ap.parse_args()
 
 
@@ -359,7 +371,7 @@ def run_ours(args, W):
     theta = args.theta if args.theta is not None else W["theta"]
     errs = measure_errors(ctx, x, idx_t, ref, theta, eps, acc)
     calibrated = False
-    if args.theta is None and (args.calibrate or errs["p99"] > TARGET_P99):
+    if args.theta is None and (args.calibrate or W.get("calibrate") or errs["p99"] > TARGET_P99):
         theta = calibrate(ctx, x, idx_t, ref, eps, acc)
         errs = measure_errors(ctx, x, idx_t, ref, theta, eps, acc)
         calibrated = True
@@ -610,8 +622,52 @@ def run_batched(args, W):
     return 0
 
 
+def run_accuracy_sweep(args):
+    """Force errors against the FP64 direct sum (4096 seeded targets) and the
+    evaluation time over theta in {0.3, 0.5, 0.75} x group size in {32, 64,
+    128, 256} x {monopole, quadrupole} on a Plummer sphere of 2^20 particles
+    (seed 1, eps = 0.01, leaf 16).  Prints one JSON object."""
+    import torch
+
+    import paper_1112_4539_gb300 as bh
+    bh.lib()
+    n, eps, leaf = 1 << 20, 0.01, 16
+    x = torch.from_numpy(workloads.make("plummer", n, 1)).cuda()
+    idx = workloads.sample_targets(n, 4096, seed=101)
+    idx_t = torch.from_numpy(idx).cuda()
+    ref = torch.empty((idx.size, 4), dtype=torch.float64, device=x.device)
+    assert bh.direct_force(x, x[idx_t].contiguous(), idx_t, eps, ref, 64) == 0
+    acc = torch.empty_like(x)
+    rows = []
+    for order in (1, 2):
+        for G in (32, 64, 128, 256):
+            ctx = bh.Context(n, leaf_size=leaf, group_size=G, order=order)
+            for theta in (0.3, 0.5, 0.75):
+                errs = measure_errors(ctx, x, idx_t, ref, theta, eps, acc)
+                s0 = ctx.stats()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(3):
+                    ctx.evaluate(x, theta, eps, acc)
+                e1.record()
+                torch.cuda.synchronize()
+                s1 = ctx.stats()
+                assert s1["status"] == 0, s1["status"]
+                inter = (s1["n_pp_total"] - s0["n_pp_total"] + s1["n_pc_total"] - s0["n_pc_total"]) / 3
+                rows.append(dict(order=order, G=G, theta=theta, p50=errs["p50"], p99=errs["p99"],
+                                 mean=errs["mean"], max=errs["max"], phi_p99=errs["phi_p99"],
+                                 ms_per_eval=e0.elapsed_time(e1) / 3, interactions=inter))
+            ctx.close()
+    print(json.dumps({"sweep": "Plummer N=1048576 (seed 1), eps=0.01, leaf 16; errors vs FP64 direct on "
+                               "4096 targets (seed 101); time = whole evaluation (build, moments, walk)",
+                      "gpu": torch.cuda.get_device_name(), "rows": rows}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.accuracy_sweep:
+        return run_accuracy_sweep(args)
     W = WORKLOADS[args.workload]
     if args.impl == "reference":
         if W["kind"] == "batched":
