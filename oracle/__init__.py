@@ -56,7 +56,7 @@ def lib():
         L.or_group_lists.restype = _i64
         L.or_force_particles.argtypes = [_i64, _f32p, _u32p, _i64, _i32p, _i32p, _i32p, _i32p,
                                          _f64p, _vp, _f64p, _i64, _i64, ctypes.c_double,
-                                         ctypes.c_int, _f64p, _vp, _vp]
+                                         ctypes.c_int, _f64p, _vp, _vp, _vp, _vp]
         L.or_force_particles.restype = ctypes.c_int
         L.or_pc_eval.argtypes = [_f64p, _f64p, _vp, ctypes.c_double, _f64p]
         L.or_mlp_nparams.restype = ctypes.c_int
@@ -258,15 +258,17 @@ def force_particles(spos, perm, tree, mom, eps, t0=0, t1=None, unsoftened_pc=Fal
     out = np.zeros((n, 4), dtype=np.float64)
     n_pp = np.zeros(n, dtype=np.int64)
     n_pc = np.zeros(n, dtype=np.int64)
+    margin = np.full(n, np.inf)
+    a_abs = np.zeros(n)
     quad = mom.quad if want_quad is None or want_quad else None
     rc = lib().or_force_particles(n, spos, np.ascontiguousarray(perm, dtype=np.uint32),
                                   tree.n_nodes, tree.first, tree.count, tree.child_first,
                                   tree.nchild, np.ascontiguousarray(mom.com_m), _ptr(quad),
                                   mom.s_eff, int(t0), int(t1), float(eps), int(bool(unsoftened_pc)),
-                                  out, _ptr(n_pp), _ptr(n_pc))
+                                  out, _ptr(n_pp), _ptr(n_pc), _ptr(margin), _ptr(a_abs))
     if rc != 0:
         raise MemoryError("oracle force_particles")
-    return dict(out=out, n_pp=n_pp, n_pc=n_pc)
+    return dict(out=out, n_pp=n_pp, n_pc=n_pc, margin=margin, a_abs=a_abs)
 
 
 class Built:

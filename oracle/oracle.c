@@ -592,12 +592,14 @@ int64_t or_group_lists(int64_t nn, const float* spos, const int32_t* first, cons
  * internal node is opened.  The self term is skipped by index.  With
  * unsoftened_pc the particle-cell term uses eps = 0 (the Appendix A kernel).
  * Targets are the Morton positions [t0, t1); out etc. are in caller order.
+ * margin (optional): min over the target's criterion decisions (nodes not
+ *   holding it) of |d^2 - S_eff| / S_eff; a_abs (optional): sum of |a_term|.
  * ---------------------------------------------------------------------- */
 int or_force_particles(int64_t n, const float* spos, const uint32_t* perm, int64_t nn,
                        const int32_t* first, const int32_t* count, const int32_t* child_first,
                        const int32_t* nchild, const double* com_m, const double* quad,
                        const double* s_eff, int64_t t0, int64_t t1, double eps, int unsoftened_pc,
-                       double* out, int64_t* n_pp, int64_t* n_pc)
+                       double* out, int64_t* n_pp, int64_t* n_pc, double* margin, double* a_abs)
 {
     const double e2 = eps * eps;
     const double e2c = unsoftened_pc ? 0.0 : e2;
@@ -614,6 +616,7 @@ int or_force_particles(int64_t n, const float* spos, const uint32_t* perm, int64
         }
         const double xi = spos[4 * i], yi = spos[4 * i + 1], zi = spos[4 * i + 2];
         double acc[5] = {0, 0, 0, 0, 0};
+        double mmin = INFINITY;
         int64_t cpp = 0, cpc = 0, sp = 0;
         stack[sp++] = 0;
         while (sp > 0) {
@@ -629,6 +632,10 @@ int or_force_particles(int64_t n, const float* spos, const uint32_t* perm, int64
             const double dx = c[0] - xi, dy = c[1] - yi, dz = c[2] - zi;
             const double d2 = dx * dx + dy * dy + dz * dz;
             const int holds_i = first[v] <= i && i < (int64_t)first[v] + count[v];
+            if (!holds_i && s_eff[v] > 0.0) {
+                const double mg = fabs(d2 - s_eff[v]) / s_eff[v];
+                if (mg < mmin) mmin = mg;
+            }
             if (d2 > s_eff[v] && !holds_i) {
                 or_pc(xi, yi, zi, c, quad ? quad + 6 * v : NULL, e2c, acc);
                 cpc++;
@@ -646,6 +653,8 @@ int or_force_particles(int64_t n, const float* spos, const uint32_t* perm, int64
         for (int a = 0; a < 4; a++) out[4 * o + a] = acc[a];
         if (n_pp) n_pp[o] = cpp;
         if (n_pc) n_pc[o] = cpc;
+        if (margin) margin[o] = mmin;
+        if (a_abs) a_abs[o] = acc[4];
         free(stack);
     }
     return err;

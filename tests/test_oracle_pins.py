@@ -533,3 +533,36 @@ def test_term_magnitude_sum(orc):
     np.fill_diagonal(mag, 0.0)
     np.testing.assert_allclose(res["a_abs"], mag.sum(1), rtol=1e-12)
     assert (res["a_abs"] >= np.linalg.norm(res["out"][:, :3], axis=1) * (1 - 1e-12)).all()
+
+
+def test_particle_walk_unsoftened_cells(orc):
+    # Appendix A's kernel applies cells without softening.  A light target at
+    # the origin and a tight cluster near (1, 1, 1): with theta = 1 the cluster's
+    # level-1 octant is accepted as one cell.  Unsoftened, the cell term must
+    # match the exact eps = 0 sum over the cluster's particles to the
+    # quadrupole truncation error ((a/D)^3 ~ 1e-9); softened, it must match the
+    # eps = 0.1 sum instead (the two differ by ~1.5 eps^2 / D^2 = 5e-3).
+    rng = np.random.default_rng(5)
+    k = 50
+    cl = np.concatenate([1.0 + 1e-3 * rng.random((k, 3)), np.full((k, 1), 1.0 / k)], axis=1)
+    p = np.concatenate([np.array([[0.0, 0.0, 0.0, 1e-6]]), cl]).astype(np.float32)
+    b = orc.Built(p, 8, 32, 1.0, 2)
+    x = p[1:, :3].astype(np.float64) - p[0, :3].astype(np.float64)
+    m = p[1:, 3].astype(np.float64)
+
+    def exact(eps):
+        r2 = (x * x).sum(1) + eps * eps
+        return (m[:, None] * x / r2[:, None] ** 1.5).sum(0)
+
+    eps = 0.1
+    hard = orc.force_particles(b.spos, b.perm, b.tree, b.mom, eps, unsoftened_pc=True)
+    soft = orc.force_particles(b.spos, b.perm, b.tree, b.mom, eps)
+    assert hard["n_pc"][0] == 1 and hard["n_pp"][0] == 0
+    e0, e1 = exact(0.0), exact(eps)
+    rel = lambda a, r: np.linalg.norm(a - r) / np.linalg.norm(r)
+    assert rel(hard["out"][0, :3], e0) < 1e-7
+    assert rel(soft["out"][0, :3], e1) < 1e-7
+    assert rel(e1, e0) > 1e-3
+    # margins and term magnitudes (monopole parts) are reported per target
+    assert np.isfinite(hard["margin"][0]) and hard["margin"][0] > 0
+    assert abs(hard["a_abs"][0] / np.linalg.norm(e0) - 1) < 1e-5
