@@ -87,6 +87,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-criterion comparison")
     ap.add_argument("--cpu-sample-groups", type=int, default=6000)
+    ap.add_argument("--walk", default="group", choices=["group", "particle"],
+                    help="group: one warp per particle group; particle: the paper's per-particle walk (Fig. 5)")
+    ap.add_argument("--unsoftened-cells", action="store_true",
+                    help="particle walk: cells without softening (the Appendix A kernel)")
     ap.add_argument("--accuracy-sweep", action="store_true",
                     help="Plummer N=2^20: errors and time over theta x group size x order (no bench line)")
     return ap.parse_args()
@@ -164,22 +168,22 @@ def rel_errors(got, ref):
     return da, dp
 
 
-def measure_errors(ctx, x, idx_t, ref, theta, eps, acc):
+def measure_errors(ctx, x, idx_t, ref, theta, eps, acc, walk="group", unsoftened=False):
     import torch
-    ctx.evaluate(x, theta, eps, acc)
+    ctx.evaluate(x, theta, eps, acc, walk=walk, unsoftened_cells=unsoftened)
     da, dp = rel_errors(acc[idx_t], ref)
     q = torch.quantile(da, torch.tensor([0.5, 0.99], dtype=torch.float64, device=da.device))
     return dict(p50=float(q[0]), p99=float(q[1]), mean=float(da.mean()), max=float(da.max()),
                 phi_mean=float(dp.mean()), phi_p99=float(torch.quantile(dp, 0.99)))
 
 
-def calibrate(ctx, x, idx_t, ref, eps, acc, lo=0.2, hi=1.2, iters=9):
+def calibrate(ctx, x, idx_t, ref, eps, acc, lo=0.2, hi=1.2, iters=9, walk="group", unsoftened=False):
     """Largest theta (bisection) with p99 relative acceleration error <= 1e-3."""
-    if measure_errors(ctx, x, idx_t, ref, hi, eps, acc)["p99"] <= TARGET_P99:
+    if measure_errors(ctx, x, idx_t, ref, hi, eps, acc, walk, unsoftened)["p99"] <= TARGET_P99:
         return hi
     for _ in range(iters):
         mid = 0.5 * (lo + hi)
-        if measure_errors(ctx, x, idx_t, ref, mid, eps, acc)["p99"] <= TARGET_P99:
+        if measure_errors(ctx, x, idx_t, ref, mid, eps, acc, walk, unsoftened)["p99"] <= TARGET_P99:
             lo = mid
         else:
             hi = mid
@@ -187,14 +191,32 @@ def calibrate(ctx, x, idx_t, ref, eps, acc, lo=0.2, hi=1.2, iters=9):
 
 
 # ------------------------------------------------------------ CPU oracle
-def oracle_throughput(pos, theta, eps, leaf, G, order, n_groups_sample, seed=0):
-    """FP64 CPU oracle (group walk, same criterion) on a bounded sample:
-    full build, then the walk of a random sample of groups; the evaluation
-    rate is extrapolated as (sample interactions * ng/S) / (build + walk * ng/S)."""
+def oracle_throughput(pos, theta, eps, leaf, G, order, n_groups_sample, seed=0, walk="group",
+                      unsoftened=False):
+    """FP64 CPU oracle (same walk and criterion) on a bounded sample:
+    full build, then the walk of a random sample of groups (group walk) or of
+    n_groups_sample * G / 4 targets in 8 Morton-contiguous chunks (particle
+    walk); the evaluation rate is extrapolated as (sample interactions *
+    scale) / (build + walk * scale)."""
     import oracle
     t0 = time.perf_counter()
     b = oracle.Built(pos, leaf, G, theta, order)
     t_build = time.perf_counter() - t0
+    if walk == "particle":
+        n = pos.shape[0]
+        chunk = max(1, min(n // 8, n_groups_sample * G // 32))
+        starts = np.linspace(0, n - chunk, 8).astype(np.int64)
+        I, t_walk = 0, 0.0
+        for s0 in starts:
+            t0 = time.perf_counter()
+            res = oracle.force_particles(b.spos, b.perm, b.tree, b.mom, eps, t0=int(s0), t1=int(s0 + chunk),
+                                         unsoftened_pc=unsoftened)
+            t_walk += time.perf_counter() - t0
+            I += int(res["n_pp"].sum() + res["n_pc"].sum())
+        scale = n / (8 * chunk)
+        t_eval = t_build + t_walk * scale
+        return dict(value=I * scale / t_eval / 1e9, t_build=t_build, t_walk=t_walk, groups=8 * chunk, ng=n,
+                    interactions=I, s_per_eval=t_eval, cores=oracle.num_threads())
     ng = b.g_first.shape[0]
     S = min(n_groups_sample, ng)
     rng = np.random.default_rng(seed)
@@ -369,11 +391,12 @@ def run_ours(args, W):
     assert rc == 0, rc
 
     theta = args.theta if args.theta is not None else W["theta"]
-    errs = measure_errors(ctx, x, idx_t, ref, theta, eps, acc)
+    walk, uns = args.walk, args.unsoftened_cells
+    errs = measure_errors(ctx, x, idx_t, ref, theta, eps, acc, walk, uns)
     calibrated = False
     if args.theta is None and (args.calibrate or W.get("calibrate") or errs["p99"] > TARGET_P99):
-        theta = calibrate(ctx, x, idx_t, ref, eps, acc)
-        errs = measure_errors(ctx, x, idx_t, ref, theta, eps, acc)
+        theta = calibrate(ctx, x, idx_t, ref, eps, acc, walk=walk, unsoftened=uns)
+        errs = measure_errors(ctx, x, idx_t, ref, theta, eps, acc, walk, uns)
         calibrated = True
     st = ctx.status()
     assert st == 0, st
@@ -383,7 +406,10 @@ def run_ours(args, W):
         ctx.moments(theta)
         if walk_ev is not None:
             walk_ev[0].record(stream)
-        ctx.force(eps, acc)
+        if walk == "group":
+            ctx.force(eps, acc)
+        else:
+            ctx.force_particles(eps, acc, uns)
         if walk_ev is not None:
             walk_ev[1].record(stream)
         ctx.kick_drift(x, vel, acc, dt, dt)
@@ -435,7 +461,7 @@ def run_ours(args, W):
     d_pos = torch.empty_like(x)
     for _ in range(2):
         d_pos.copy_(h_pos, non_blocking=True)
-        ctx.evaluate(d_pos, theta, eps, acc)
+        ctx.evaluate(d_pos, theta, eps, acc, walk=walk, unsoftened_cells=uns)
         h_acc.copy_(acc, non_blocking=True)
     torch.cuda.synchronize()
     if world > 1:
@@ -445,7 +471,7 @@ def run_ours(args, W):
     f0.record(stream)
     for _ in range(e2e_steps):
         d_pos.copy_(h_pos, non_blocking=True)
-        ctx.evaluate(d_pos, theta, eps, acc)
+        ctx.evaluate(d_pos, theta, eps, acc, walk=walk, unsoftened_cells=uns)
         h_acc.copy_(acc, non_blocking=True)
     f1.record(stream)
     torch.cuda.synchronize()
@@ -470,8 +496,9 @@ def run_ours(args, W):
     achieved = flops_per_launch / (walk_ms * 1e-3) / 1e12
     peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": stored_traffic(args.workload),
-                "kernel": "bh_walk_kernel", "walk_ms": walk_ms, "walk_share": walk_ms * steps / t_ms,
+                "traffic": stored_traffic(args.workload) if walk == "group" else None,
+                "kernel": "bh_walk_kernel" if walk == "group" else "bh_pwalk_kernel",
+                "walk_ms": walk_ms, "walk_share": walk_ms * steps / t_ms,
                 "peak_basis": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (max SM clock)" % (sms, SM_MAX_MHZ),
                 "frac_at_measured_clock": (achieved / (peak * clk["sm_mhz"] / SM_MAX_MHZ)) if clk.get("sm_mhz")
                 else None,
@@ -481,7 +508,8 @@ def run_ours(args, W):
             "warmup": args.warmup, "ms_per_step": max_ms / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": W["desc"], "n": n, "theta": theta, "theta_calibrated": calibrated,
-                       "leaf": leaf, "group": G, "order": order,
+                       "leaf": leaf, "group": G, "order": order, "walk": walk,
+                       "unsoftened_cells": uns if walk == "particle" else None,
                        "errors_vs_fp64_direct_4096": errs, "judge_s": t_judge,
                        "interactions_per_step": inter / steps, "pp_per_step": n_pp / steps,
                        "pc_per_step": n_pc / steps, "l2": "inputs larger than L2 (no flush)",
@@ -491,16 +519,18 @@ def run_ours(args, W):
                     "ms_per_step": e2e_max / e2e_steps},
             "gpu_launches": launches, "roofline": roofline, "clocks": clk}
 
-    if not args.no_learned and os.path.exists(WEIGHTS):
+    if not args.no_learned and walk == "group" and os.path.exists(WEIGHTS):
         line["learned_mac"] = learned_comparison(bh, ctx, x0, idx_t, ref, eps, theta, G, leaf, order)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = oracle_throughput(pos_np, theta, eps, leaf, G, order, args.cpu_sample_groups)
+        cb = oracle_throughput(pos_np, theta, eps, leaf, G, order, args.cpu_sample_groups, walk=walk,
+                               unsoftened=uns)
+        unit_s = "groups" if walk == "group" else "targets"
         line["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
-                                "sample": "FP64 oracle group walk on the same particles and theta: full build "
-                                          "(%.2f s) + %d of %d groups walked (%.2f s); rate extrapolated to a "
-                                          "whole evaluation (%.1f s)" % (cb["t_build"], cb["groups"], cb["ng"],
-                                                                         cb["t_walk"], cb["s_per_eval"])}
+                                "sample": "FP64 oracle %s walk on the same particles and theta: full build "
+                                          "(%.2f s) + %d of %d %s walked (%.2f s); rate extrapolated to a "
+                                          "whole evaluation (%.1f s)" % (walk, cb["t_build"], cb["groups"], cb["ng"],
+                                                                         unit_s, cb["t_walk"], cb["s_per_eval"])}
     ctx.close()
     if rank == 0:
         print(json.dumps(line))

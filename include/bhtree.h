@@ -129,6 +129,24 @@ int tree_moments(bh_ctx* ctx, float theta, void* stream);
  * tree_build); device status BH_ERR_CAPACITY or BH_ERR_DEVICE_TIMEOUT. */
 int tree_force(bh_ctx* ctx, float eps, float* d_acc_pot, void* stream);
 
+/* The paper's own walk (Sec. 4.4, Fig. 5, Appendix A): one thread per
+ * particle follows the depth-first "more" (first child) and "next" (node
+ * after the subtree) links from the root, with no stack.  For particle i a
+ * node holding a single particle is a particle-particle term (skipped if it
+ * is i); otherwise the node is accepted when |x_i - COM|^2 > S_eff (Eq. 2) and
+ * it does not hold i, giving a particle-cell term (quadrupole when the
+ * context's order is 2); a rejected leaf gives particle-particle terms with
+ * its other members; a rejected internal node is entered.  The links are
+ * derived from the current tree on each call.  FP32 terms, Kahan-compensated
+ * runs of 32.  bh_stats then counts this walk's interactions.
+ * eps >= 0: softening of Eq. (1).  flags: BH_PWALK_UNSOFTENED_CELLS applies
+ * particle-cell terms with eps = 0, as the Appendix A kernel does.
+ * d_acc_pot: n float4 (ax, ay, az, phi) in the caller's order.
+ * Errors: BH_ERR_INVALID, BH_ERR_STATE (tree_moments not run after the last
+ * tree_build); device status BH_ERR_CAPACITY for a malformed tree. */
+#define BH_PWALK_UNSOFTENED_CELLS 1
+int tree_force_particles(bh_ctx* ctx, float eps, int flags, float* d_acc_pot, void* stream);
+
 /* Eq. (1) by direct summation (Sec. 3): for each target t,
  * a_t = sum_j m_j (x_j - x_t) / (|x_j - x_t|^2 + eps^2)^1.5 and
  * phi_t = -sum_j m_j / (|x_j - x_t|^2 + eps^2)^0.5 over all sources j except
@@ -311,7 +329,9 @@ enum {
     BH_EXPORT_QUAD = 11,       /* float[nn*6] second moments xx, yy, zz, xy, xz, yz (order 2) */
     BH_EXPORT_GROUP_FIRST = 12,/* int32[ng]   first particle of each group */
     BH_EXPORT_GROUP_COUNT = 13,/* int32[ng]   particles per group */
-    BH_EXPORT_BOX = 14         /* float[4]    xmin, ymin, zmin, L */
+    BH_EXPORT_BOX = 14,        /* float[4]    xmin, ymin, zmin, L */
+    BH_EXPORT_NEXT = 15        /* int32[nn]   depth-first "next" link of each node, -1 after the last
+                                  (derived by tree_force_particles; Fig. 5) */
 };
 int bh_export(bh_ctx* ctx, int what, void* dst, int64_t cap_bytes, int64_t* out_bytes, void* stream);
 

@@ -27,11 +27,12 @@ BH_ERR_STATE = -7
 BH_ERR_NOMEM = -8
 
 EXPORT = dict(keys=1, perm=2, spos=3, node_first=4, node_count=5, node_child=6, node_nchild=7,
-              node_level=8, com_m=9, seff=10, quad=11, group_first=12, group_count=13, box=14)
+              node_level=8, com_m=9, seff=10, quad=11, group_first=12, group_count=13, box=14, next=15)
 
 # the symbols declared in include/bhtree.h
 SYMBOLS = ["bh_version", "bh_strerror", "bh_config_default", "bh_create", "bh_destroy", "tree_build",
-           "tree_moments", "tree_force", "direct_force", "bh_kick_drift", "bh_status", "bh_stats",
+           "tree_moments", "tree_force", "tree_force_particles", "direct_force", "bh_kick_drift", "bh_status",
+           "bh_stats",
            "bh_export", "bh_tree_force_static", "bh_mac_set", "bh_mac_label", "bh_mlp_train", "bh_mlp_grad",
            "bh_mlp_forward", "bh_batch_layout", "bh_force_batched", "bh_graph_capture_batched",
            "bh_graph_launch", "bh_graph_destroy"]
@@ -39,6 +40,7 @@ BATCH_MAX_N = 65536
 MLP_NPARAM = 1313
 MLP_ACT = 135  # floats of training scratch per sample
 STATIC_MAX_N = 32768
+PWALK_UNSOFTENED_CELLS = 1
 
 
 class BhConfig(ctypes.Structure):
@@ -97,6 +99,8 @@ def lib():
         L.tree_moments.restype = i32
         L.tree_force.argtypes = [vp, ctypes.c_float, vp, vp]
         L.tree_force.restype = i32
+        L.tree_force_particles.argtypes = [vp, ctypes.c_float, i32, vp, vp]
+        L.tree_force_particles.restype = i32
         L.direct_force.argtypes = [vp, i64, vp, vp, i64, ctypes.c_double, vp, i32, vp]
         L.direct_force.restype = i32
         L.bh_kick_drift.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, vp]
@@ -183,6 +187,12 @@ def tree_moments(h, theta, stream=None):
 
 def tree_force(h, eps, out, stream=None):
     return lib().tree_force(h, ctypes.c_float(eps), _dptr(out), _stream(stream))
+
+
+def tree_force_particles(h, eps, out, unsoftened_cells=False, stream=None):
+    """The paper's per-particle next/more walk (Fig. 5)."""
+    flags = PWALK_UNSOFTENED_CELLS if unsoftened_cells else 0
+    return lib().tree_force_particles(h, ctypes.c_float(eps), int(flags), _dptr(out), _stream(stream))
 
 
 def direct_force(src, tgt, tgt_self, eps, out, precision, stream=None):
@@ -326,14 +336,23 @@ class Context:
     def force(self, eps, out, stream=None):
         _check(tree_force(self.h, eps, out, stream), "tree_force")
 
-    def evaluate(self, pos, theta, eps, out=None, stream=None):
-        """Whole force evaluation (build, moments, walk); returns (n, 4) f32 on the device."""
+    def force_particles(self, eps, out, unsoftened_cells=False, stream=None):
+        _check(tree_force_particles(self.h, eps, out, unsoftened_cells, stream), "tree_force_particles")
+
+    def evaluate(self, pos, theta, eps, out=None, stream=None, walk="group", unsoftened_cells=False):
+        """Whole force evaluation (build, moments, walk); returns (n, 4) f32 on the device.
+        walk="group" (warp per group) or "particle" (the paper's per-particle walk)."""
         import torch
         if out is None:
             out = torch.empty_like(pos)
         self.build(pos, stream)
         self.moments(theta, stream)
-        self.force(eps, out, stream)
+        if walk == "group":
+            self.force(eps, out, stream)
+        elif walk == "particle":
+            self.force_particles(eps, out, unsoftened_cells, stream)
+        else:
+            raise ValueError(walk)
         return out
 
     def kick_drift(self, pos, vel, acc, dt_kick, dt_drift, stream=None):

@@ -47,6 +47,9 @@ struct bh_ctx {
     uint32_t* sys_of = nullptr;     // system of each Morton position
     int32_t* sys_off = nullptr;     // first particle of each system (+ total)
     float4* sys_box = nullptr;      // root cube of each system
+    // links of the per-particle walk
+    int32_t* parent = nullptr;
+    int32_t* next = nullptr;
 };
 
 namespace {
@@ -186,6 +189,7 @@ int bh_create(bh_ctx** out, const bh_config* cfg, int64_t max_n, int device)
     const size_t o_mlp = take(sizeof(bh_mlp_dev));
     const size_t S = (size_t)std::max(1, c.max_systems);
     const size_t o_sys = take(N * 4), o_soff = take((S + 1) * 4), o_sbox = take(S * sizeof(float4));
+    const size_t o_parent = take(NN * 4), o_next = take(NN * 4);
     const size_t total = off;
 
     if (cudaMalloc(&x->slab, total) != cudaSuccess) {
@@ -228,6 +232,8 @@ int bh_create(bh_ctx** out, const bh_config* cfg, int64_t max_n, int device)
     x->sys_of = (uint32_t*)(b + o_sys);
     x->sys_off = (int32_t*)(b + o_soff);
     x->sys_box = (float4*)(b + o_sbox);
+    x->parent = (int32_t*)(b + o_parent);
+    x->next = (int32_t*)(b + o_next);
     if (x->cfg.max_systems < 1) x->cfg.max_systems = 1;
     // look-back words start at epoch 0, which no pass uses; control block zeroed
     if (cudaMemset(x->lookback, 0, sort_tiles * 256 * sizeof(unsigned long long)) != cudaSuccess ||
@@ -318,6 +324,24 @@ int tree_force(bh_ctx* x, float eps, float* d_acc_pot, void* stream)
                              x->cfg.blocks_per_sm, s, x->mac_learned ? &wl : nullptr);
     if (rc) return rc;
     x->launches += bh::kLaunchesForce;
+    if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
+    return BH_OK;
+}
+
+int tree_force_particles(bh_ctx* x, float eps, int flags, float* d_acc_pot, void* stream)
+{
+    if (!x) return BH_ERR_INVALID;
+    if (!(eps >= 0.0f) || !std::isfinite(eps)) return BH_ERR_INVALID;
+    if (flags & ~BH_PWALK_UNSOFTENED_CELLS) return BH_ERR_INVALID;
+    if (x->n < 0 || !x->have_moments) return BH_ERR_STATE;
+    if (x->n == 0) return BH_OK;
+    if (!d_acc_pot || !aligned16(d_acc_pot) || !is_device_ptr(d_acc_pot, x->device)) return BH_ERR_INVALID;
+    DeviceGuard guard(x->device);
+    int rc = bh::launch_pwalk(x->pos_s, x->vals, x->nd, x->parent, x->next, x->cfg.order, (int)x->n,
+                              (int)x->node_cap, eps, (flags & BH_PWALK_UNSOFTENED_CELLS) != 0, (float4*)d_acc_pot,
+                              x->ctrl, x->sm_count, (cudaStream_t)stream);
+    if (rc) return rc;
+    x->launches += bh::kLaunchesPWalk;
     if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
     return BH_OK;
 }
@@ -432,6 +456,7 @@ int bh_export(bh_ctx* x, int what, void* dst, int64_t cap_bytes, int64_t* out_by
         case BH_EXPORT_GROUP_FIRST: src = x->g_first; bytes = ng * 4; break;
         case BH_EXPORT_GROUP_COUNT: src = x->g_count; bytes = ng * 4; break;
         case BH_EXPORT_BOX: src = x->ctrl->box; bytes = 16; break;
+        case BH_EXPORT_NEXT: src = x->next; bytes = nn * 4; break;
         default: return BH_ERR_INVALID;
     }
     if (out_bytes) *out_bytes = bytes;

@@ -204,8 +204,13 @@ void launch_kick_drift(float4* pos, float4* vel, const float4* acc, int n, float
                        cudaStream_t s);
 
 // kernel launches enqueued by one call of each stage (for bh_stats.launches)
+int launch_pwalk(const float4* pos_s, const uint32_t* perm, const bh_nodes& nd, int32_t* parent, int32_t* next,
+                 int order, int n, int node_cap, float eps, bool unsoftened_cells, float4* out, bh_dev_ctrl* ctrl,
+                 int sm_count, cudaStream_t s);
+
 constexpr int kLaunchesBuild = 16;   // init, bbox, keys, 4 sort passes, 4 tree, 5 groups
 constexpr int kLaunchesMoments = 11; // one per level
 constexpr int kLaunchesForce = 2;    // counter reset, walk
+constexpr int kLaunchesPWalk = 4;    // parent links, next links, counter reset, walk
 
 }  // namespace bh
