@@ -36,13 +36,16 @@ def lib():
         L = ctypes.CDLL(path)
         L.or_direct.argtypes = [_i64, _f32p, _i64, _f32p, _vp, ctypes.c_double, _f64p]
         L.or_bbox.argtypes = [_i64, _f32p, _f32p]
-        L.or_keys.argtypes = [_i64, _f32p, _f32p, _u32p]
+        L.or_keys.argtypes = [_i64, _f32p, _f32p, _u32p, ctypes.c_int]
+        L.or_key_of_cell.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int]
+        L.or_key_of_cell.restype = ctypes.c_uint32
+        L.or_cell_of_key.argtypes = [ctypes.c_uint32, ctypes.c_int, _u32p]
         L.or_sort.argtypes = [_i64, _u32p, _u32p]
         L.or_sort.restype = ctypes.c_int
         L.or_tree_build.argtypes = [_i64, _u32p, ctypes.c_int, _i64] + [_i32p] * 5
         L.or_tree_build.restype = _i64
         L.or_moments.argtypes = [_i64, _f32p, _u32p, _i32p, _i32p, _i32p, _f32p,
-                                 ctypes.c_double, _f64p, _vp, _f64p, _f64p]
+                                 ctypes.c_double, _f64p, _vp, _f64p, _f64p, ctypes.c_int]
         L.or_groups.argtypes = [_i64, _i32p, _i32p, _i32p, _i32p, ctypes.c_int, _i64, _i32p, _i32p]
         L.or_groups.restype = _i64
         L.or_force_groups.argtypes = [_i64, _f32p, _u32p, _i64, _i32p, _i32p, _i32p, _i32p,
@@ -124,12 +127,28 @@ def bbox(pos):
     return box
 
 
-def keys(pos, box):
-    """Sec. 5 Morton ordering: 30-bit keys (10 bits per axis)."""
+CURVE_MORTON = 0
+CURVE_HILBERT = 1
+
+
+def keys(pos, box, curve=CURVE_MORTON):
+    """Sec. 5 ordering: 30-bit keys (10 bits per axis), Morton or Peano-Hilbert."""
     pos = _pos(pos)
     k = np.zeros(pos.shape[0], dtype=np.uint32)
-    lib().or_keys(pos.shape[0], pos, np.ascontiguousarray(box, dtype=np.float32), k)
+    lib().or_keys(pos.shape[0], pos, np.ascontiguousarray(box, dtype=np.float32), k, int(curve))
     return k
+
+
+def key_of_cell(x, y, z, curve):
+    """Key of one integer cell (10 bits per axis)."""
+    return int(lib().or_key_of_cell(int(x), int(y), int(z), int(curve)))
+
+
+def cell_of_key(key, curve):
+    """Integer cell (x, y, z) of one key."""
+    c = np.zeros(3, dtype=np.uint32)
+    lib().or_cell_of_key(int(key), int(curve), c)
+    return tuple(int(v) for v in c)
 
 
 def sort(k):
@@ -180,7 +199,7 @@ class Moments:
         self.com_m, self.quad, self.s_eff, self.side = com_m, quad, s_eff, side
 
 
-def moments(spos, skeys, tree, box, theta, order=1):
+def moments(spos, skeys, tree, box, theta, order=1, curve=CURVE_MORTON):
     """Sec. 4.4 cell data: mass, centre of mass, Eq. (2) S_eff; quadrupole if order 2."""
     spos = _pos(spos)
     nn = tree.n_nodes
@@ -190,7 +209,7 @@ def moments(spos, skeys, tree, box, theta, order=1):
     side = np.zeros(nn, dtype=np.float64)
     lib().or_moments(nn, spos, np.ascontiguousarray(skeys, dtype=np.uint32), tree.level,
                      tree.first, tree.count, np.ascontiguousarray(box, dtype=np.float32),
-                     float(theta), com_m, _ptr(quad), s_eff, side)
+                     float(theta), com_m, _ptr(quad), s_eff, side, int(curve))
     return Moments(com_m, quad, s_eff, side)
 
 
@@ -274,26 +293,27 @@ def force_particles(spos, perm, tree, mom, eps, t0=0, t1=None, unsoftened_pc=Fal
 class Built:
     """Everything the oracle derives from one particle set before the walk."""
 
-    def __init__(self, pos, n_leaf, G, theta, order):
+    def __init__(self, pos, n_leaf, G, theta, order, curve=CURVE_MORTON):
         self.pos = _pos(pos)
         self.box = bbox(self.pos)
-        self.keys = keys(self.pos, self.box)
+        self.curve = curve
+        self.keys = keys(self.pos, self.box, curve)
         self.perm = sort(self.keys)
         self.skeys = self.keys[self.perm]
         self.spos = self.pos[self.perm]
         self.tree = tree_build(self.skeys, n_leaf)
-        self.mom = moments(self.spos, self.skeys, self.tree, self.box, theta, order)
+        self.mom = moments(self.spos, self.skeys, self.tree, self.box, theta, order, curve)
         self.g_first, self.g_count = groups(self.tree, G)
         self.order = order
 
 
-def tree_force(pos, theta, eps, n_leaf=8, G=32, order=1, walk="group", group_mask=None):
+def tree_force(pos, theta, eps, n_leaf=8, G=32, order=1, walk="group", group_mask=None, curve=CURVE_MORTON):
     """Whole force evaluation: box, keys, sort, tree, moments, groups, walk.
 
     walk="group" (the GPU path's criterion) or "particle" (the paper's).
     Returns (result dict, Built).
     """
-    b = Built(pos, n_leaf, G, theta, order)
+    b = Built(pos, n_leaf, G, theta, order, curve)
     if walk == "group":
         res = force_groups(b.spos, b.perm, b.tree, b.mom, b.g_first, b.g_count, eps,
                            group_mask=group_mask)

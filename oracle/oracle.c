@@ -36,6 +36,8 @@
 #endif
 
 #define OR_MAX_LEVEL 10
+#define OR_CURVE_MORTON 0
+#define OR_CURVE_HILBERT 1
 
 int or_version(void) { return 3; }
 
@@ -139,11 +141,92 @@ static uint32_t or_compact3(uint32_t v, int nbits)
 }
 
 /* ------------------------------------------------------------------------
+ * Peano-Hilbert order (the ordering Sec. 5 names as better than Morton's),
+ * after J. Skilling, "Programming the Hilbert curve", AIP Conf. Proc. 707
+ * (2004): the cell's coordinates are turned into the "transposed" index by
+ * undoing, from the top level down, the reflections and axis exchanges of
+ * the curve's sub-cubes, and are then Gray-coded; the 30-bit index
+ * interleaves the three transposed words as the Morton key does (first word
+ * in the high bit of each triple).  Level by level, each octree cell is one
+ * contiguous index range, so the tree is read off the sorted keys exactly as
+ * with Morton keys, only the children's order differs.
+ * ---------------------------------------------------------------------- */
+static uint32_t or_hilbert3(uint32_t x, uint32_t y, uint32_t z)
+{
+    uint32_t w[3] = {x, y, z};
+    for (uint32_t q = 1u << 9; q > 1u; q >>= 1) {
+        const uint32_t low = q - 1u;
+        for (int a = 0; a < 3; a++) {
+            if (w[a] & q) {
+                w[0] ^= low;                              /* reflect */
+            } else {
+                const uint32_t d = (w[0] ^ w[a]) & low;   /* exchange axes 0 and a */
+                w[0] ^= d;
+                w[a] ^= d;
+            }
+        }
+    }
+    w[1] ^= w[0];
+    w[2] ^= w[1];
+    uint32_t g = 0;
+    for (uint32_t q = 1u << 9; q > 1u; q >>= 1)
+        if (w[2] & q) g ^= q - 1u;
+    for (int a = 0; a < 3; a++) w[a] ^= g;
+    return (or_spread3(w[0]) << 2) | (or_spread3(w[1]) << 1) | or_spread3(w[2]);
+}
+
+/* Inverse of or_hilbert3: cell coordinates of a 30-bit index. */
+static void or_hilbert3_inv(uint32_t h, uint32_t* c)
+{
+    uint32_t w[3] = {or_compact3(h >> 2, 10), or_compact3(h >> 1, 10), or_compact3(h, 10)};
+    const uint32_t g = w[2] >> 1;                          /* Gray decode */
+    w[2] ^= w[1];
+    w[1] ^= w[0];
+    w[0] ^= g;
+    for (uint32_t q = 2u; q != (1u << 10); q <<= 1) {
+        const uint32_t low = q - 1u;
+        for (int a = 2; a >= 0; a--) {
+            if (w[a] & q) {
+                w[0] ^= low;
+            } else {
+                const uint32_t d = (w[0] ^ w[a]) & low;
+                w[0] ^= d;
+                w[a] ^= d;
+            }
+        }
+    }
+    c[0] = w[0];
+    c[1] = w[1];
+    c[2] = w[2];
+}
+
+/* Integer cell (10 bits per axis) of a key of either order. */
+static void or_key_cell(uint32_t key, int curve, uint32_t* c)
+{
+    if (curve == OR_CURVE_HILBERT) {
+        or_hilbert3_inv(key, c);
+    } else {
+        c[0] = or_compact3(key >> 2, 10);
+        c[1] = or_compact3(key >> 1, 10);
+        c[2] = or_compact3(key, 10);
+    }
+}
+
+/* Exported for the pins: key of a cell, and cell of a key. */
+uint32_t or_key_of_cell(uint32_t x, uint32_t y, uint32_t z, int curve)
+{
+    return curve == OR_CURVE_HILBERT ? or_hilbert3(x, y, z)
+                                     : (or_spread3(x) << 2) | (or_spread3(y) << 1) | or_spread3(z);
+}
+void or_cell_of_key(uint32_t key, int curve, uint32_t* c) { or_key_cell(key, curve, c); }
+
+/* ------------------------------------------------------------------------
  * Sec. 5 (Morton ordering): 30-bit Morton key, 10 bits per axis.
  * q = (x - xmin) * (1024/L) in FP32 (two rounded ops), integer cell
  * c = min(trunc(q), 1023); bit k of cx, cy, cz goes to key bit 3k+2, 3k+1, 3k.
+ * curve = OR_CURVE_HILBERT gives the Peano-Hilbert index of the same cell.
  * ---------------------------------------------------------------------- */
-void or_keys(int64_t n, const float* pos, const float* box, uint32_t* keys)
+void or_keys(int64_t n, const float* pos, const float* box, uint32_t* keys, int curve)
 {
     const float inv = 1024.0f / box[3];
     for (int64_t i = 0; i < n; i++) {
@@ -155,7 +238,7 @@ void or_keys(int64_t n, const float* pos, const float* box, uint32_t* keys)
             if (ci > 1023u) ci = 1023u;
             c[a] = ci;
         }
-        keys[i] = (or_spread3(c[0]) << 2) | (or_spread3(c[1]) << 1) | or_spread3(c[2]);
+        keys[i] = or_key_of_cell(c[0], c[1], c[2], curve);
     }
 }
 
@@ -254,7 +337,7 @@ int64_t or_tree_build(int64_t n, const uint32_t* skeys, int n_leaf, int64_t cap,
 void or_moments(int64_t nn, const float* spos, const uint32_t* skeys,
                 const int32_t* level, const int32_t* first, const int32_t* count,
                 const float* box, double theta, double* com_m, double* quad,
-                double* s_eff, double* side)
+                double* s_eff, double* side, int curve)
 {
     int64_t v;
 #pragma omp parallel for schedule(dynamic, 64)
@@ -271,9 +354,10 @@ void or_moments(int64_t nn, const float* spos, const uint32_t* skeys,
         }
         /* geometric centre of the level-l cell containing the node */
         const double lside = (double)box[3] / (double)(1u << l);
-        const uint32_t prefix = (l == 0) ? 0u : (skeys[b] >> (3 * (OR_MAX_LEVEL - l)));
-        const double px = or_compact3(prefix >> 2, l), py = or_compact3(prefix >> 1, l),
-                     pz = or_compact3(prefix, l);
+        uint32_t cell[3];
+        or_key_cell(skeys[b], curve, cell);  /* the first particle's cell, then its level-l ancestor */
+        const double px = cell[0] >> (OR_MAX_LEVEL - l), py = cell[1] >> (OR_MAX_LEVEL - l),
+                     pz = cell[2] >> (OR_MAX_LEVEL - l);
         const double gx = (double)box[0] + (px + 0.5) * lside;
         const double gy = (double)box[1] + (py + 0.5) * lside;
         const double gz = (double)box[2] + (pz + 0.5) * lside;
