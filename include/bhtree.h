@@ -58,8 +58,13 @@ typedef struct bh_config {
     int block_threads;       /* threads per block of the walk kernel: 64 or 128 */
     int blocks_per_sm;       /* resident walk blocks per SM for the persistent grid (0 = auto) */
     int max_systems;         /* independent systems one bh_force_batched call may hold (>= 1) */
-    int reserved;
+    int curve;               /* particle order (Sec. 5): BH_CURVE_MORTON (default) or
+                                BH_CURVE_HILBERT (Peano-Hilbert); the octree is the same,
+                                only the order of children and particles differs */
 } bh_config;
+
+#define BH_CURVE_MORTON 0
+#define BH_CURVE_HILBERT 1
 
 /* Counters of the last evaluation (bh_stats synchronises the stream). */
 typedef struct bh_stats_t {

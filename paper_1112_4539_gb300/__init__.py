@@ -41,12 +41,14 @@ MLP_NPARAM = 1313
 MLP_ACT = 135  # floats of training scratch per sample
 STATIC_MAX_N = 32768
 PWALK_UNSOFTENED_CELLS = 1
+CURVE_MORTON = 0
+CURVE_HILBERT = 1
 
 
 class BhConfig(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int), ("group_size", ctypes.c_int), ("order", ctypes.c_int),
                 ("fp64_node_threshold", ctypes.c_int), ("block_threads", ctypes.c_int),
-                ("blocks_per_sm", ctypes.c_int), ("max_systems", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("blocks_per_sm", ctypes.c_int), ("max_systems", ctypes.c_int), ("curve", ctypes.c_int)]
 
 
 class BhStats(ctypes.Structure):

@@ -118,6 +118,7 @@ void bh_config_default(bh_config* cfg)
     cfg->block_threads = 128;
     cfg->blocks_per_sm = 0;
     cfg->max_systems = 1;
+    cfg->curve = BH_CURVE_MORTON;
 }
 
 static int validate_config(const bh_config* c)
@@ -129,6 +130,7 @@ static int validate_config(const bh_config* c)
     if (c->block_threads != 64 && c->block_threads != 128) return BH_ERR_INVALID;
     if (c->blocks_per_sm < 0 || c->blocks_per_sm > 32) return BH_ERR_INVALID;
     if (c->max_systems < 0 || c->max_systems > (1 << 20)) return BH_ERR_INVALID;
+    if (c->curve != BH_CURVE_MORTON && c->curve != BH_CURVE_HILBERT) return BH_ERR_INVALID;
     return BH_OK;
 }
 
@@ -272,7 +274,7 @@ int tree_build(bh_ctx* x, const float* d_pos_mass, int64_t n, void* stream)
     bh::launch_init(x->ctrl, s);
     if (N > 0) {
         bh::launch_bbox(pos, N, x->ctrl, grid_for(x), s);
-        bh::launch_keys(pos, N, x->ctrl, x->keys, grid_for(x), s);
+        bh::launch_keys(pos, N, x->ctrl, x->keys, x->cfg.curve, grid_for(x), s);
         bh::launch_sort(x->keys, x->keys_alt, x->vals, x->vals_alt, pos, x->pos_s, N, x->lookback,
                         &x->sort_epoch, x->ctrl, s);
         bh::launch_tree(x->keys, N, x->cfg.leaf_size, x->dl, x->blk, x->nd, x->node_cap, x->ctrl, grid_for(x), s);
@@ -295,8 +297,8 @@ int tree_moments(bh_ctx* x, float theta, void* stream)
     DeviceGuard guard(x->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (x->n > 0) {
-        bh::launch_moments(x->pos_s, x->keys, x->nd, x->cfg.order, theta, x->cfg.fp64_node_threshold, x->ctrl,
-                           grid_for(x), s);
+        bh::launch_moments(x->pos_s, x->keys, x->nd, x->cfg.order, theta, x->cfg.fp64_node_threshold, x->cfg.curve,
+                           x->ctrl, grid_for(x), s);
         x->launches += bh::kLaunchesMoments;
         if (x->mac_learned) {
             bh::launch_mac_nodefeat(x->nd, x->cfg.order, x->mfeat, x->ctrl, grid_for(x), s);
@@ -628,12 +630,12 @@ int bh_force_batched(bh_ctx* x, const float* d_pos_mass, float theta, float eps,
     const int N = (int)n;
     bh::launch_init(x->ctrl, s);
     bh::launch_batch_sort((const float4*)d_pos_mass, x->sys_off, x->nsys, x->keys, x->keys_alt, x->vals, x->vals_alt,
-                          x->pos_s, x->sys_of, x->sys_box, x->ctrl, s);
+                          x->pos_s, x->sys_of, x->sys_box, x->cfg.curve, x->ctrl, s);
     bh::launch_tree(x->keys, N, x->cfg.leaf_size, x->dl, x->blk, x->nd, x->node_cap, x->ctrl, grid_for(x), s,
                     x->sys_of, x->sys_off);
     bh::launch_groups(x->nd, N, x->cfg.group_size, x->flags, x->blk, x->g_first, x->g_count, x->ctrl, grid_for(x), s);
-    bh::launch_moments(x->pos_s, x->keys, x->nd, x->cfg.order, theta, x->cfg.fp64_node_threshold, x->ctrl,
-                       grid_for(x), s, x->sys_of, x->sys_box);
+    bh::launch_moments(x->pos_s, x->keys, x->nd, x->cfg.order, theta, x->cfg.fp64_node_threshold, x->cfg.curve,
+                       x->ctrl, grid_for(x), s, x->sys_of, x->sys_box);
     int rc = bh::launch_walk(x->pos_s, x->vals, x->g_first, x->g_count, x->nd, x->cfg.order, x->cfg.group_size, eps,
                              (float4*)d_acc_pot, x->ctrl, x->sm_count, x->cfg.block_threads, x->cfg.blocks_per_sm, s);
     if (rc) return rc;

@@ -18,7 +18,7 @@ constexpr int kBItems = 8;
 constexpr int kBTile = kBT * kBItems;  // 4096 keys per tile
 
 __global__ void __launch_bounds__(kBT)
-bh_batch_sort_kernel(const float4* __restrict__ pos, const int32_t* __restrict__ off, uint32_t* keys,
+bh_batch_sort_kernel(const float4* __restrict__ pos, const int32_t* __restrict__ off, int curve, uint32_t* keys,
                      uint32_t* keys_alt, uint32_t* vals, uint32_t* vals_alt, float4* __restrict__ pos_s,
                      uint32_t* __restrict__ sys, float4* __restrict__ sys_box, bh_dev_ctrl* c)
 {
@@ -74,7 +74,8 @@ bh_batch_sort_kernel(const float4* __restrict__ pos, const int32_t* __restrict__
             const unsigned int cx = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.x, x0), inv)), 1023u);
             const unsigned int cy = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.y, y0), inv)), 1023u);
             const unsigned int cz = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.z, z0), inv)), 1023u);
-            keys[i] = (bh_spread3(cx) << 2) | (bh_spread3(cy) << 1) | bh_spread3(cz);
+            keys[i] = curve == BH_CURVE_HILBERT ? bh_key_of<BH_CURVE_HILBERT>(cx, cy, cz)
+                                                : bh_key_of<BH_CURVE_MORTON>(cx, cy, cz);
             vals[i] = (uint32_t)i;
         }
     }
@@ -172,11 +173,11 @@ bh_batch_sort_kernel(const float4* __restrict__ pos, const int32_t* __restrict__
 
 void launch_batch_sort(const float4* pos, const int32_t* sys_off, int nsys, uint32_t* keys, uint32_t* keys_alt,
                        uint32_t* vals, uint32_t* vals_alt, float4* pos_s, uint32_t* sys, float4* sys_box,
-                       bh_dev_ctrl* ctrl, cudaStream_t s)
+                       int curve, bh_dev_ctrl* ctrl, cudaStream_t s)
 {
     if (nsys <= 0) return;
-    bh_batch_sort_kernel<<<nsys, kBT, 0, s>>>(pos, sys_off, keys, keys_alt, vals, vals_alt, pos_s, sys, sys_box,
-                                              ctrl);
+    bh_batch_sort_kernel<<<nsys, kBT, 0, s>>>(pos, sys_off, curve, keys, keys_alt, vals, vals_alt, pos_s, sys,
+                                              sys_box, ctrl);
 }
 
 }  // namespace bh

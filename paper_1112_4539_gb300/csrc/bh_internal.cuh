@@ -81,6 +81,93 @@ __device__ __forceinline__ unsigned int bh_compact3(unsigned int v)
     return v;
 }
 
+// 30-bit Peano-Hilbert index of a cell (10 bits per axis), the ordering Sec. 5
+// names as better than Morton's.  Skilling's construction ("Programming the
+// Hilbert curve", 2004): from the top level down, the bits below the level
+// are reflected in x when an axis has the level's bit set, else exchanged
+// between x and that axis; the three words are then Gray-coded and
+// interleaved as a Morton key (x in the high bit of each triple).
+__device__ __forceinline__ unsigned int bh_hilbert3(unsigned int x, unsigned int y, unsigned int z)
+{
+#pragma unroll
+    for (int lv = 9; lv >= 1; lv--) {
+        const unsigned int bit = 1u << lv, below = bit - 1u;
+        if (x & bit) x ^= below;
+        if (y & bit) {
+            x ^= below;
+        } else {
+            const unsigned int d = (x ^ y) & below;
+            x ^= d;
+            y ^= d;
+        }
+        if (z & bit) {
+            x ^= below;
+        } else {
+            const unsigned int d = (x ^ z) & below;
+            x ^= d;
+            z ^= d;
+        }
+    }
+    y ^= x;
+    z ^= y;
+    unsigned int g = 0u;
+#pragma unroll
+    for (int lv = 9; lv >= 1; lv--)
+        if (z & (1u << lv)) g ^= (1u << lv) - 1u;
+    x ^= g;
+    y ^= g;
+    z ^= g;
+    return (bh_spread3(x) << 2) | (bh_spread3(y) << 1) | bh_spread3(z);
+}
+// Cell of a Peano-Hilbert index (inverse of bh_hilbert3).
+__device__ __forceinline__ void bh_hilbert3_cell(unsigned int h, unsigned int& x, unsigned int& y, unsigned int& z)
+{
+    x = bh_compact3(h >> 2);
+    y = bh_compact3(h >> 1);
+    z = bh_compact3(h);
+    const unsigned int g = z >> 1;
+    z ^= y;
+    y ^= x;
+    x ^= g;
+#pragma unroll
+    for (int lv = 1; lv <= 9; lv++) {
+        const unsigned int bit = 1u << lv, below = bit - 1u;
+        if (z & bit) {
+            x ^= below;
+        } else {
+            const unsigned int d = (x ^ z) & below;
+            x ^= d;
+            z ^= d;
+        }
+        if (y & bit) {
+            x ^= below;
+        } else {
+            const unsigned int d = (x ^ y) & below;
+            x ^= d;
+            y ^= d;
+        }
+        if (x & bit) x ^= below;
+    }
+}
+// Key of a cell, and cell of a key, for the context's order.
+template <int CURVE>
+__device__ __forceinline__ unsigned int bh_key_of(unsigned int x, unsigned int y, unsigned int z)
+{
+    return CURVE == BH_CURVE_HILBERT ? bh_hilbert3(x, y, z)
+                                     : (bh_spread3(x) << 2) | (bh_spread3(y) << 1) | bh_spread3(z);
+}
+__device__ __forceinline__ void bh_cell_of(unsigned int key, int curve, unsigned int& x, unsigned int& y,
+                                           unsigned int& z)
+{
+    if (curve == BH_CURVE_HILBERT) {
+        bh_hilbert3_cell(key, x, y, z);
+    } else {
+        x = bh_compact3(key >> 2);
+        y = bh_compact3(key >> 1);
+        z = bh_compact3(key);
+    }
+}
+
 // Deepest level whose cell holds both keys (0..10); keys of one cell share
 // their top 3*l bits.
 __device__ __forceinline__ int bh_common_level(unsigned int a, unsigned int b)
@@ -164,7 +251,8 @@ constexpr int kFlagTile = 4096;                        // positions per group-co
 
 void launch_init(bh_dev_ctrl* ctrl, cudaStream_t s);
 void launch_bbox(const float4* pos, int n, bh_dev_ctrl* ctrl, int grid, cudaStream_t s);
-void launch_keys(const float4* pos, int n, bh_dev_ctrl* ctrl, uint32_t* keys, int grid, cudaStream_t s);
+void launch_keys(const float4* pos, int n, bh_dev_ctrl* ctrl, uint32_t* keys, int curve, int grid,
+                 cudaStream_t s);
 void launch_sort(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
                  const float4* pos, float4* pos_s, int n, unsigned long long* lookback,
                  unsigned int* epoch, bh_dev_ctrl* ctrl, cudaStream_t s);
@@ -177,14 +265,14 @@ void launch_tree(const uint32_t* keys, int n, int n_leaf, uint8_t* dl, uint32_t*
 void launch_groups(const bh_nodes& nd, int n, int G, uint8_t* flags, uint32_t* blk, int32_t* g_first,
                    int32_t* g_count, bh_dev_ctrl* ctrl, int grid, cudaStream_t s);
 void launch_moments(const float4* pos_s, const uint32_t* keys, const bh_nodes& nd, int order,
-                    float theta, int fp64_threshold, bh_dev_ctrl* ctrl, int grid, cudaStream_t s,
+                    float theta, int fp64_threshold, int curve, bh_dev_ctrl* ctrl, int grid, cudaStream_t s,
                     const uint32_t* sys = nullptr, const float4* sys_box = nullptr);
 // One CTA per system: root cube, keys, stable radix sort and gather of each
 // system's particles (systems contiguous, each <= kBatchMaxN particles).
 constexpr int kBatchMaxN = 65536;
 void launch_batch_sort(const float4* pos, const int32_t* sys_off, int nsys, uint32_t* keys, uint32_t* keys_alt,
                        uint32_t* vals, uint32_t* vals_alt, float4* pos_s, uint32_t* sys, float4* sys_box,
-                       bh_dev_ctrl* ctrl, cudaStream_t s);
+                       int curve, bh_dev_ctrl* ctrl, cudaStream_t s);
 }  // namespace bh
 struct bh_mlp_dev;
 namespace bh {

@@ -81,6 +81,7 @@ void launch_bbox(const float4* pos, int n, bh_dev_ctrl* ctrl, int grid, cudaStre
 // c = min(trunc(q), 1023); bit k of cx, cy, cz -> key bit 3k+2, 3k+1, 3k.
 // The four digit histograms of the sort (bits 0-7, 8-15, 16-23, 24-29) are
 // accumulated on the way.
+template <int CURVE>
 __global__ void __launch_bounds__(256) bh_keys_kernel(const float4* __restrict__ pos, int n, bh_dev_ctrl* c,
                                                       uint32_t* __restrict__ keys)
 {
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(256) bh_keys_kernel(const float4* __restrict__
         const unsigned int cx = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.x, x0), inv)), 1023u);
         const unsigned int cy = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.y, y0), inv)), 1023u);
         const unsigned int cz = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.z, z0), inv)), 1023u);
-        const unsigned int k = (bh_spread3(cx) << 2) | (bh_spread3(cy) << 1) | bh_spread3(cz);
+        const unsigned int k = bh_key_of<CURVE>(cx, cy, cz);
         keys[i] = k;
         atomicAdd(&sh[0][k & 255u], 1u);
         atomicAdd(&sh[1][(k >> 8) & 255u], 1u);
@@ -119,9 +120,10 @@ __global__ void __launch_bounds__(256) bh_keys_kernel(const float4* __restrict__
     }
 }
 
-void launch_keys(const float4* pos, int n, bh_dev_ctrl* ctrl, uint32_t* keys, int grid, cudaStream_t s)
+void launch_keys(const float4* pos, int n, bh_dev_ctrl* ctrl, uint32_t* keys, int curve, int grid, cudaStream_t s)
 {
-    bh_keys_kernel<<<grid, 256, 0, s>>>(pos, n, ctrl, keys);
+    if (curve == BH_CURVE_HILBERT) bh_keys_kernel<BH_CURVE_HILBERT><<<grid, 256, 0, s>>>(pos, n, ctrl, keys);
+    else bh_keys_kernel<BH_CURVE_MORTON><<<grid, 256, 0, s>>>(pos, n, ctrl, keys);
 }
 
 // ------------------------------------------------------------- onesweep

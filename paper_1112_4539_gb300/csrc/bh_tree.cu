@@ -517,7 +517,7 @@ __device__ __forceinline__ void bh_internal_moments(const bh_nodes& nd, int ch, 
 template <int ORDER>
 __global__ void __launch_bounds__(256)
 bh_moments_level_kernel(const float4* __restrict__ pos_s, const uint32_t* __restrict__ keys, bh_nodes nd, int lev,
-                        float theta, int fp64_threshold, const bh_dev_ctrl* __restrict__ c,
+                        float theta, int fp64_threshold, int curve, const bh_dev_ctrl* __restrict__ c,
                         const uint32_t* __restrict__ sys, const float4* __restrict__ sys_box)
 {
     const int v0 = (int)c->level_offset[lev], v1 = (int)c->level_offset[lev + 1];
@@ -534,11 +534,14 @@ bh_moments_level_kernel(const float4* __restrict__ pos_s, const uint32_t* __rest
         // (only level-10 leaves can): a sequential FP32 sum of k equal masses is
         // off by up to ~k * 3e-9 relative (1e-5 at k = 3000)
         const bool f64 = r.y >= fp64_threshold || (r.z < 0 && r.y > kLeafFp64);
-        // geometric centre of the node's level-lev cell
-        const unsigned int pref = (lev == 0) ? 0u : (keys[r.x] >> (3 * (BH_MAX_LEVEL - lev)));
-        const float gx = xmin + ((float)bh_compact3(pref >> 2) + 0.5f) * side;
-        const float gy = ymin + ((float)bh_compact3(pref >> 1) + 0.5f) * side;
-        const float gz = zmin + ((float)bh_compact3(pref) + 0.5f) * side;
+        // geometric centre of the node's level-lev cell: the ancestor of the
+        // first particle's cell, decoded from its key
+        unsigned int ix, iy, iz;
+        bh_cell_of(keys[r.x], curve, ix, iy, iz);
+        const int sh = BH_MAX_LEVEL - lev;
+        const float gx = xmin + ((float)(ix >> sh) + 0.5f) * side;
+        const float gy = ymin + ((float)(iy >> sh) + 0.5f) * side;
+        const float gz = zmin + ((float)(iz >> sh) + 0.5f) * side;
         float cx, cy, cz, M, q[6];
         bool massless;
         if (f64) {
@@ -580,16 +583,16 @@ bh_moments_level_kernel(const float4* __restrict__ pos_s, const uint32_t* __rest
 }
 
 void launch_moments(const float4* pos_s, const uint32_t* keys, const bh_nodes& nd, int order, float theta,
-                    int fp64_threshold, bh_dev_ctrl* ctrl, int grid, cudaStream_t s, const uint32_t* sys,
+                    int fp64_threshold, int curve, bh_dev_ctrl* ctrl, int grid, cudaStream_t s, const uint32_t* sys,
                     const float4* sys_box)
 {
     for (int lev = BH_MAX_LEVEL; lev >= 0; lev--) {
         if (order >= 2)
-            bh_moments_level_kernel<2><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, ctrl, sys,
-                                                            sys_box);
+            bh_moments_level_kernel<2><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, curve,
+                                                            ctrl, sys, sys_box);
         else
-            bh_moments_level_kernel<1><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, ctrl, sys,
-                                                            sys_box);
+            bh_moments_level_kernel<1><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, curve,
+                                                            ctrl, sys, sys_box);
     }
 }
 
