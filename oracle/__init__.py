@@ -37,6 +37,9 @@ def lib():
         L.or_direct.argtypes = [_i64, _f32p, _i64, _f32p, _vp, ctypes.c_double, _f64p]
         L.or_bbox.argtypes = [_i64, _f32p, _f32p]
         L.or_keys.argtypes = [_i64, _f32p, _f32p, _u32p, ctypes.c_int]
+        L.or_sph_kernel.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.or_sph_kernel.restype = ctypes.c_double
+        L.or_sph_density.argtypes = [_i64, _f32p, _f32p, _i32p, _f64p]
         L.or_key_of_cell.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int]
         L.or_key_of_cell.restype = ctypes.c_uint32
         L.or_cell_of_key.argtypes = [ctypes.c_uint32, ctypes.c_int, _u32p]
@@ -431,3 +434,20 @@ def mac_features_one(lo, hi, com_m, quad, side, level, count, mtot):
                                np.asarray(com_m, np.float64), _ptr(q), float(side), int(level), int(count),
                                float(mtot), f)
     return f if ok else None
+
+
+def sph_kernel(r, h):
+    """Cubic spline W(r, h) with support h (Monaghan & Lattanzio 1985)."""
+    return float(lib().or_sph_kernel(float(r), float(h)))
+
+
+def sph_density(pos, h):
+    """Neighbour counts (|x_j - x_i| < h_i, j != i, decided in FP32) and SPH
+    densities (FP64) by the all-pairs definition.  h: per particle (n,) or a scalar."""
+    pos = _pos(pos)
+    n = pos.shape[0]
+    hh = np.ascontiguousarray(np.broadcast_to(np.asarray(h, dtype=np.float32), (n,)), dtype=np.float32)
+    count = np.zeros(n, dtype=np.int32)
+    rho = np.zeros(n, dtype=np.float64)
+    lib().or_sph_density(n, pos, hh, count, rho)
+    return count, rho

@@ -1106,3 +1106,51 @@ int or_mac_features_one(const double* lo, const double* hi, const double* cm, co
 {
     return or_mac_feat(lo, hi, cm, qd, side, level, count, mtot, f);
 }
+
+/* ========================================================================
+ * Neighbour search, the short-range application of the general tree walk
+ * (Sec. 4.3, Fig. 4), here by its plain definition (all pairs).
+ *
+ * For particle i with search radius h_i, particle j != i is a neighbour when
+ * |x_j - x_i| < h_i, the decision taken in FP32 as the device takes it:
+ * d = x_j - x_i per axis (FP32), r2 = fma(dz, dz, fma(dy, dy, dx * dx)),
+ * neighbour iff r2 < h_i * h_i (FP32 product).  The SPH density
+ *   rho_i = sum over i itself and its neighbours of m_j W(r_ij, h_i)
+ * uses the cubic spline of Monaghan & Lattanzio (1985) with support h:
+ *   W(r, h) = 8 / (pi h^3) * { 1 - 6 q^2 + 6 q^3,  0 <= q <= 1/2
+ *                              2 (1 - q)^3,        1/2 < q <= 1 },  q = r / h
+ * (normalised: its integral over space is 1), in FP64 with r = sqrt(r2) from
+ * the FP32 r2 above.  count[i] excludes i itself.
+ * ---------------------------------------------------------------------- */
+double or_sph_kernel(double r, double h)
+{
+    const double q = r / h;
+    const double c = 8.0 / (M_PI * h * h * h);
+    if (q <= 0.5) return c * (1.0 - 6.0 * q * q + 6.0 * q * q * q);
+    if (q <= 1.0) return c * 2.0 * (1.0 - q) * (1.0 - q) * (1.0 - q);
+    return 0.0;
+}
+
+void or_sph_density(int64_t n, const float* pos, const float* h, int32_t* count, double* rho)
+{
+    int64_t i;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (i = 0; i < n; i++) {
+        const float xi = pos[4 * i], yi = pos[4 * i + 1], zi = pos[4 * i + 2];
+        const float hi = h[i];
+        const float h2 = hi * hi;
+        double r = (double)pos[4 * i + 3] * or_sph_kernel(0.0, hi);
+        int32_t c = 0;
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            const float dx = pos[4 * j] - xi, dy = pos[4 * j + 1] - yi, dz = pos[4 * j + 2] - zi;
+            const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+            if (r2 < h2) {
+                c++;
+                r += (double)pos[4 * j + 3] * or_sph_kernel(sqrt((double)r2), hi);
+            }
+        }
+        count[i] = c;
+        rho[i] = r;
+    }
+}
