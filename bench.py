@@ -93,6 +93,8 @@ def parse():
                     help="particle order (Sec. 5): Morton or Peano-Hilbert keys")
     ap.add_argument("--unsoftened-cells", action="store_true",
                     help="particle walk: cells without softening (the Appendix A kernel)")
+    ap.add_argument("--neighbors", action="store_true",
+                    help="neighbour search + SPH density on Plummer spheres (no bench line)")
     ap.add_argument("--accuracy-sweep", action="store_true",
                     help="Plummer N=2^20: errors and time over theta x group size x order (no bench line)")
     return ap.parse_args()
@@ -697,10 +699,57 @@ def run_accuracy_sweep(args):
     return 0
 
 
+def run_neighbors(args):
+    """Neighbour search and SPH density (the general tree walk of Sec. 4.3)
+    on Plummer spheres of 2^20 and 2^24 particles, radii for ~64 neighbours:
+    time of tree_build + tree_neighbors per evaluation (CUDA events), pairs
+    tested and neighbours found.  Prints one JSON object."""
+    import torch
+
+    import paper_1112_4539_gb300 as bh
+    bh.lib()
+    rows = []
+    for n, G, leaf in ((1 << 20, 64, 16), (1 << 20, 32, 16), (1 << 24, 64, 16)):
+        pos = workloads.make("plummer", n, 1)
+        x = torch.from_numpy(pos).cuda()
+        h = torch.from_numpy(workloads.plummer_search_radii(pos, 64).astype(np.float32)).cuda()
+        ctx = bh.Context(n, leaf_size=leaf, group_size=G)
+        cnt = torch.empty(n, dtype=torch.int32, device="cuda")
+        rho = torch.empty(n, dtype=torch.float32, device="cuda")
+        for _ in range(3):
+            ctx.build(x)
+            bh._check(bh.tree_neighbors(ctx.h, h, cnt, rho), "tree_neighbors")
+        torch.cuda.synchronize()
+        s0 = ctx.stats()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        reps = 5
+        for _ in range(reps):
+            ctx.build(x)
+            bh.tree_neighbors(ctx.h, h, cnt, rho)
+        e1.record()
+        torch.cuda.synchronize()
+        s1 = ctx.stats()
+        assert s1["status"] == 0, s1["status"]
+        ms = e0.elapsed_time(e1) / reps
+        tested = (s1["n_pp_total"] - s0["n_pp_total"]) / reps
+        found = float(cnt.sum().item())
+        rows.append(dict(n=n, G=G, leaf=leaf, ms_per_eval=ms, pairs_tested=tested, neighbours=found,
+                         mean_neighbours=found / n, pairs_tested_per_s=tested / (ms * 1e-3),
+                         particles_per_s=n / (ms * 1e-3), median_neighbours=float(cnt.median().item())))
+        ctx.close()
+    print(json.dumps({"neighbors": "Plummer spheres (seed 1), radii from the analytic density for ~64 "
+                                   "neighbours; time = tree_build + tree_neighbors", "gpu": torch.cuda.get_device_name(),
+                      "rows": rows}))
+    return 0
+
+
 def main():
     args = parse()
     if args.accuracy_sweep:
         return run_accuracy_sweep(args)
+    if args.neighbors:
+        return run_neighbors(args)
     W = WORKLOADS[args.workload]
     if args.impl == "reference":
         if W["kind"] == "batched":

@@ -152,6 +152,25 @@ int tree_force(bh_ctx* ctx, float eps, float* d_acc_pot, void* stream);
 #define BH_PWALK_UNSOFTENED_CELLS 1
 int tree_force_particles(bh_ctx* ctx, float eps, int flags, float* d_acc_pot, void* stream);
 
+/* Neighbour search and SPH density, the short-range application of the
+ * general tree walk (Sec. 4.3, Fig. 4), on the tree of the last tree_build
+ * (tree_moments is not needed).  For particle i with search radius h_i,
+ * j != i is a neighbour when |x_j - x_i| < h_i, decided in FP32 as
+ * d = x_j - x_i per axis, r2 = fma(dz, dz, fma(dy, dy, dx * dx)), r2 < h_i * h_i.
+ * rho_i = sum over i itself and its neighbours of m_j W(sqrt(r2), h_i), with
+ * the cubic spline of Monaghan & Lattanzio (1985) of support h (unit
+ * integral), FP32.  One warp walks the tree per particle group; a node is
+ * skipped when its particles' bounding box is farther than the group's
+ * largest radius from the group's box, so no neighbour is ever missed.
+ * d_h: n radii in the caller's order, or NULL to use h for every particle.
+ * d_count: n int32 neighbour counts (caller order, self excluded), or NULL.
+ * d_rho: n float densities (caller order), or NULL.
+ * bh_stats afterwards: n_pp = candidate pairs tested, n_pc = 0.
+ * Errors: BH_ERR_INVALID (bad pointer, h <= 0 or not finite with d_h NULL),
+ * BH_ERR_STATE (no tree); device status BH_ERR_NONFINITE for a radius that
+ * is not positive and finite, BH_ERR_CAPACITY. */
+int tree_neighbors(bh_ctx* ctx, const float* d_h, float h, int32_t* d_count, float* d_rho, void* stream);
+
 /* Eq. (1) by direct summation (Sec. 3): for each target t,
  * a_t = sum_j m_j (x_j - x_t) / (|x_j - x_t|^2 + eps^2)^1.5 and
  * phi_t = -sum_j m_j / (|x_j - x_t|^2 + eps^2)^0.5 over all sources j except

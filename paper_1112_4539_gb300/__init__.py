@@ -31,10 +31,9 @@ EXPORT = dict(keys=1, perm=2, spos=3, node_first=4, node_count=5, node_child=6, 
 
 # the symbols declared in include/bhtree.h
 SYMBOLS = ["bh_version", "bh_strerror", "bh_config_default", "bh_create", "bh_destroy", "tree_build",
-           "tree_moments", "tree_force", "tree_force_particles", "direct_force", "bh_kick_drift", "bh_status",
-           "bh_stats",
-           "bh_export", "bh_tree_force_static", "bh_mac_set", "bh_mac_label", "bh_mlp_train", "bh_mlp_grad",
-           "bh_mlp_forward", "bh_batch_layout", "bh_force_batched", "bh_graph_capture_batched",
+           "tree_moments", "tree_force", "tree_force_particles", "tree_neighbors", "direct_force", "bh_kick_drift",
+           "bh_status", "bh_stats", "bh_export", "bh_tree_force_static", "bh_mac_set", "bh_mac_label",
+           "bh_mlp_train", "bh_mlp_grad", "bh_mlp_forward", "bh_batch_layout", "bh_force_batched", "bh_graph_capture_batched",
            "bh_graph_launch", "bh_graph_destroy"]
 BATCH_MAX_N = 65536
 MLP_NPARAM = 1313
@@ -103,6 +102,8 @@ def lib():
         L.tree_force.restype = i32
         L.tree_force_particles.argtypes = [vp, ctypes.c_float, i32, vp, vp]
         L.tree_force_particles.restype = i32
+        L.tree_neighbors.argtypes = [vp, vp, ctypes.c_float, vp, vp, vp]
+        L.tree_neighbors.restype = i32
         L.direct_force.argtypes = [vp, i64, vp, vp, i64, ctypes.c_double, vp, i32, vp]
         L.direct_force.restype = i32
         L.bh_kick_drift.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, vp]
@@ -195,6 +196,15 @@ def tree_force_particles(h, eps, out, unsoftened_cells=False, stream=None):
     """The paper's per-particle next/more walk (Fig. 5)."""
     flags = PWALK_UNSOFTENED_CELLS if unsoftened_cells else 0
     return lib().tree_force_particles(h, ctypes.c_float(eps), int(flags), _dptr(out), _stream(stream))
+
+
+def tree_neighbors(h_ctx, h, count=None, rho=None, stream=None):
+    """Neighbour counts and SPH densities (Sec. 4.3 general walk): h is a float
+    tensor of n radii (caller order) or a positive number."""
+    import torch
+    if isinstance(h, torch.Tensor):
+        return lib().tree_neighbors(h_ctx, _dptr(h), ctypes.c_float(0.0), _dptr(count), _dptr(rho), _stream(stream))
+    return lib().tree_neighbors(h_ctx, None, ctypes.c_float(h), _dptr(count), _dptr(rho), _stream(stream))
 
 
 def direct_force(src, tgt, tgt_self, eps, out, precision, stream=None):
@@ -356,6 +366,16 @@ class Context:
         else:
             raise ValueError(walk)
         return out
+
+    def neighbors(self, pos, h, stream=None):
+        """Build the tree of pos and return (counts int32, densities f32), caller order."""
+        import torch
+        n = pos.shape[0]
+        count = torch.empty(n, dtype=torch.int32, device=pos.device)
+        rho = torch.empty(n, dtype=torch.float32, device=pos.device)
+        self.build(pos, stream)
+        _check(tree_neighbors(self.h, h, count, rho, stream), "tree_neighbors")
+        return count, rho
 
     def kick_drift(self, pos, vel, acc, dt_kick, dt_drift, stream=None):
         _check(bh_kick_drift(self.h, pos, vel, acc, dt_kick, dt_drift, stream), "bh_kick_drift")

@@ -50,6 +50,9 @@ struct bh_ctx {
     // links of the per-particle walk
     int32_t* parent = nullptr;
     int32_t* next = nullptr;
+    // node bounding boxes of the neighbour search
+    float4* blo = nullptr;
+    float4* bhi = nullptr;
 };
 
 namespace {
@@ -192,6 +195,7 @@ int bh_create(bh_ctx** out, const bh_config* cfg, int64_t max_n, int device)
     const size_t S = (size_t)std::max(1, c.max_systems);
     const size_t o_sys = take(N * 4), o_soff = take((S + 1) * 4), o_sbox = take(S * sizeof(float4));
     const size_t o_parent = take(NN * 4), o_next = take(NN * 4);
+    const size_t o_blo = take(NN * sizeof(float4)), o_bhi = take(NN * sizeof(float4));
     const size_t total = off;
 
     if (cudaMalloc(&x->slab, total) != cudaSuccess) {
@@ -236,6 +240,8 @@ int bh_create(bh_ctx** out, const bh_config* cfg, int64_t max_n, int device)
     x->sys_box = (float4*)(b + o_sbox);
     x->parent = (int32_t*)(b + o_parent);
     x->next = (int32_t*)(b + o_next);
+    x->blo = (float4*)(b + o_blo);
+    x->bhi = (float4*)(b + o_bhi);
     if (x->cfg.max_systems < 1) x->cfg.max_systems = 1;
     // look-back words start at epoch 0, which no pass uses; control block zeroed
     if (cudaMemset(x->lookback, 0, sort_tiles * 256 * sizeof(unsigned long long)) != cudaSuccess ||
@@ -344,6 +350,24 @@ int tree_force_particles(bh_ctx* x, float eps, int flags, float* d_acc_pot, void
                               x->ctrl, x->sm_count, (cudaStream_t)stream);
     if (rc) return rc;
     x->launches += bh::kLaunchesPWalk;
+    if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
+    return BH_OK;
+}
+
+int tree_neighbors(bh_ctx* x, const float* d_h, float h, int32_t* d_count, float* d_rho, void* stream)
+{
+    if (!x) return BH_ERR_INVALID;
+    if (!d_h && !(h > 0.0f && std::isfinite(h))) return BH_ERR_INVALID;
+    if (x->n < 0) return BH_ERR_STATE;
+    if (x->n == 0) return BH_OK;
+    if (d_h && (((uintptr_t)d_h & 3u) || !is_device_ptr(d_h, x->device))) return BH_ERR_INVALID;
+    if (d_count && (((uintptr_t)d_count & 3u) || !is_device_ptr(d_count, x->device))) return BH_ERR_INVALID;
+    if (d_rho && (((uintptr_t)d_rho & 3u) || !is_device_ptr(d_rho, x->device))) return BH_ERR_INVALID;
+    DeviceGuard guard(x->device);
+    int rc = bh::launch_sph(x->pos_s, x->vals, x->g_first, x->g_count, x->nd, x->blo, x->bhi, x->cfg.group_size, d_h,
+                            h, d_count, d_rho, x->ctrl, x->sm_count, grid_for(x), (cudaStream_t)stream);
+    if (rc) return rc;
+    x->launches += bh::kLaunchesSph;
     if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
     return BH_OK;
 }

@@ -296,9 +296,14 @@ int launch_pwalk(const float4* pos_s, const uint32_t* perm, const bh_nodes& nd, 
                  int order, int n, int node_cap, float eps, bool unsoftened_cells, float4* out, bh_dev_ctrl* ctrl,
                  int sm_count, cudaStream_t s);
 
+int launch_sph(const float4* pos_s, const uint32_t* perm, const int32_t* g_first, const int32_t* g_count,
+               const bh_nodes& nd, float4* blo, float4* bhi, int G, const float* h, float h_const, int32_t* count,
+               float* rho, bh_dev_ctrl* ctrl, int sm_count, int grid, cudaStream_t s);
+
 constexpr int kLaunchesBuild = 16;   // init, bbox, keys, 4 sort passes, 4 tree, 5 groups
 constexpr int kLaunchesMoments = 11; // one per level
 constexpr int kLaunchesForce = 2;    // counter reset, walk
 constexpr int kLaunchesPWalk = 4;    // parent links, next links, counter reset, walk
+constexpr int kLaunchesSph = 13;     // 11 node-box levels, counter reset, walk
 
 }  // namespace bh

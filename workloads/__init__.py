@@ -132,6 +132,16 @@ def batched_plummer(n_sys=512, nmin=1024, nmax=65536, seed=3):
     return pos, offs
 
 
+def plummer_search_radii(pos, n_ngb=64):
+    """Search radii for a unit Plummer sphere (unit mass) that enclose about
+    n_ngb neighbours: (4/3) pi h^3 rho(r) N = n_ngb with the analytic density
+    rho(r) = 3 / (4 pi) (1 + r^2)^(-5/2)."""
+    n = pos.shape[0]
+    r2 = (pos[:, :3].astype(np.float64) ** 2).sum(1)
+    rho = 3.0 / (4.0 * np.pi) * (1.0 + r2) ** -2.5
+    return ((3.0 * n_ngb) / (4.0 * np.pi * rho * n)) ** (1.0 / 3.0)
+
+
 def sample_targets(n, n_sample=4096, seed=101):
     """Seeded, sorted, distinct sample of target indices for the FP64 error check."""
     rng = _rng(seed)
