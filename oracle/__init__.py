@@ -21,6 +21,7 @@ _lib = None
 _f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
 _f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
 _u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+_u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
 _i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
 _i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
 _u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
@@ -36,19 +37,19 @@ def lib():
         L = ctypes.CDLL(path)
         L.or_direct.argtypes = [_i64, _f32p, _i64, _f32p, _vp, ctypes.c_double, _f64p]
         L.or_bbox.argtypes = [_i64, _f32p, _f32p]
-        L.or_keys.argtypes = [_i64, _f32p, _f32p, _u32p, ctypes.c_int]
+        L.or_keys.argtypes = [_i64, _f32p, _f32p, _u64p, ctypes.c_int, ctypes.c_int]
         L.or_sph_kernel.argtypes = [ctypes.c_double, ctypes.c_double]
         L.or_sph_kernel.restype = ctypes.c_double
         L.or_sph_density.argtypes = [_i64, _f32p, _f32p, _i32p, _f64p]
-        L.or_key_of_cell.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int]
-        L.or_key_of_cell.restype = ctypes.c_uint32
-        L.or_cell_of_key.argtypes = [ctypes.c_uint32, ctypes.c_int, _u32p]
-        L.or_sort.argtypes = [_i64, _u32p, _u32p]
+        L.or_key_of_cell.argtypes = [ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, ctypes.c_int]
+        L.or_key_of_cell.restype = ctypes.c_uint64
+        L.or_cell_of_key.argtypes = [ctypes.c_uint64, ctypes.c_int, ctypes.c_int, _u32p]
+        L.or_sort.argtypes = [_i64, _u64p, _u32p]
         L.or_sort.restype = ctypes.c_int
-        L.or_tree_build.argtypes = [_i64, _u32p, ctypes.c_int, _i64] + [_i32p] * 5
+        L.or_tree_build.argtypes = [_i64, _u64p, ctypes.c_int, ctypes.c_int, _i64] + [_i32p] * 5
         L.or_tree_build.restype = _i64
-        L.or_moments.argtypes = [_i64, _f32p, _u32p, _i32p, _i32p, _i32p, _f32p,
-                                 ctypes.c_double, _f64p, _vp, _f64p, _f64p, ctypes.c_int]
+        L.or_moments.argtypes = [_i64, _f32p, _u64p, _i32p, _i32p, _i32p, _f32p,
+                                 ctypes.c_double, _f64p, _vp, _f64p, _f64p, ctypes.c_int, ctypes.c_int]
         L.or_groups.argtypes = [_i64, _i32p, _i32p, _i32p, _i32p, ctypes.c_int, _i64, _i32p, _i32p]
         L.or_groups.restype = _i64
         L.or_force_groups.argtypes = [_i64, _f32p, _u32p, _i64, _i32p, _i32p, _i32p, _i32p,
@@ -134,39 +135,40 @@ CURVE_MORTON = 0
 CURVE_HILBERT = 1
 
 
-def keys(pos, box, curve=CURVE_MORTON):
-    """Sec. 5 ordering: 30-bit keys (10 bits per axis), Morton or Peano-Hilbert."""
+def keys(pos, box, curve=CURVE_MORTON, max_level=10):
+    """Sec. 5 ordering: keys of max_level bits per axis (10: 30-bit keys,
+    returned as uint32; 21: 63-bit keys, uint64), Morton or Peano-Hilbert."""
     pos = _pos(pos)
-    k = np.zeros(pos.shape[0], dtype=np.uint32)
-    lib().or_keys(pos.shape[0], pos, np.ascontiguousarray(box, dtype=np.float32), k, int(curve))
-    return k
+    k = np.zeros(pos.shape[0], dtype=np.uint64)
+    lib().or_keys(pos.shape[0], pos, np.ascontiguousarray(box, dtype=np.float32), k, int(curve), int(max_level))
+    return k.astype(np.uint32) if max_level <= 10 else k
 
 
-def key_of_cell(x, y, z, curve):
-    """Key of one integer cell (10 bits per axis)."""
-    return int(lib().or_key_of_cell(int(x), int(y), int(z), int(curve)))
+def key_of_cell(x, y, z, curve, nbits=10):
+    """Key of one integer cell (nbits bits per axis)."""
+    return int(lib().or_key_of_cell(int(x), int(y), int(z), int(curve), int(nbits)))
 
 
-def cell_of_key(key, curve):
+def cell_of_key(key, curve, nbits=10):
     """Integer cell (x, y, z) of one key."""
     c = np.zeros(3, dtype=np.uint32)
-    lib().or_cell_of_key(int(key), int(curve), c)
+    lib().or_cell_of_key(int(key), int(curve), int(nbits), c)
     return tuple(int(v) for v in c)
 
 
 def sort(k):
     """Stable sort by key; returns perm with perm[rank] = original index."""
-    k = np.ascontiguousarray(k, dtype=np.uint32)
+    k = np.ascontiguousarray(k, dtype=np.uint64)
     perm = np.zeros(k.shape[0], dtype=np.uint32)
     if lib().or_sort(k.shape[0], k, perm) != 0:
         raise MemoryError("oracle sort")
     return perm
 
 
-def node_capacity(n, n_leaf):
-    """Upper bound on the node count: <= n leaves plus, on each of levels 0..9,
+def node_capacity(n, n_leaf, max_level=10):
+    """Upper bound on the node count: <= n leaves plus, on each of levels 0..max_level-1,
     at most n // (n_leaf + 1) internal nodes."""
-    return int(n + 10 * (n // (n_leaf + 1)) + 1)
+    return int(n + max_level * (n // (n_leaf + 1)) + 1)
 
 
 class Tree:
@@ -185,13 +187,13 @@ class Tree:
                     child_first=self.child_first, nchild=self.nchild)
 
 
-def tree_build(skeys, n_leaf):
-    """Sec. 4.1 octree over Morton-sorted keys (leaf: <= n_leaf or level 10)."""
-    skeys = np.ascontiguousarray(skeys, dtype=np.uint32)
+def tree_build(skeys, n_leaf, max_level=10):
+    """Sec. 4.1 octree over sorted keys (leaf: <= n_leaf particles or level max_level)."""
+    skeys = np.ascontiguousarray(skeys, dtype=np.uint64)
     n = skeys.shape[0]
-    cap = max(node_capacity(n, n_leaf), 1)
+    cap = max(node_capacity(n, n_leaf, max_level), 1)
     arrs = [np.zeros(cap, dtype=np.int32) for _ in range(5)]
-    nn = lib().or_tree_build(n, skeys, int(n_leaf), cap, *arrs)
+    nn = lib().or_tree_build(n, skeys, int(n_leaf), int(max_level), cap, *arrs)
     if nn < 0:
         raise RuntimeError("oracle tree_build: capacity exceeded")
     return Tree(*[a[:nn].copy() for a in arrs])
@@ -202,7 +204,7 @@ class Moments:
         self.com_m, self.quad, self.s_eff, self.side = com_m, quad, s_eff, side
 
 
-def moments(spos, skeys, tree, box, theta, order=1, curve=CURVE_MORTON):
+def moments(spos, skeys, tree, box, theta, order=1, curve=CURVE_MORTON, max_level=10):
     """Sec. 4.4 cell data: mass, centre of mass, Eq. (2) S_eff; quadrupole if order 2."""
     spos = _pos(spos)
     nn = tree.n_nodes
@@ -210,9 +212,9 @@ def moments(spos, skeys, tree, box, theta, order=1, curve=CURVE_MORTON):
     quad = np.zeros((nn, 6), dtype=np.float64) if order >= 2 else None
     s_eff = np.zeros(nn, dtype=np.float64)
     side = np.zeros(nn, dtype=np.float64)
-    lib().or_moments(nn, spos, np.ascontiguousarray(skeys, dtype=np.uint32), tree.level,
+    lib().or_moments(nn, spos, np.ascontiguousarray(skeys, dtype=np.uint64), tree.level,
                      tree.first, tree.count, np.ascontiguousarray(box, dtype=np.float32),
-                     float(theta), com_m, _ptr(quad), s_eff, side, int(curve))
+                     float(theta), com_m, _ptr(quad), s_eff, side, int(curve), int(max_level))
     return Moments(com_m, quad, s_eff, side)
 
 
@@ -296,27 +298,29 @@ def force_particles(spos, perm, tree, mom, eps, t0=0, t1=None, unsoftened_pc=Fal
 class Built:
     """Everything the oracle derives from one particle set before the walk."""
 
-    def __init__(self, pos, n_leaf, G, theta, order, curve=CURVE_MORTON):
+    def __init__(self, pos, n_leaf, G, theta, order, curve=CURVE_MORTON, max_level=10):
         self.pos = _pos(pos)
         self.box = bbox(self.pos)
         self.curve = curve
-        self.keys = keys(self.pos, self.box, curve)
+        self.max_level = max_level
+        self.keys = keys(self.pos, self.box, curve, max_level)
         self.perm = sort(self.keys)
         self.skeys = self.keys[self.perm]
         self.spos = self.pos[self.perm]
-        self.tree = tree_build(self.skeys, n_leaf)
-        self.mom = moments(self.spos, self.skeys, self.tree, self.box, theta, order, curve)
+        self.tree = tree_build(self.skeys, n_leaf, max_level)
+        self.mom = moments(self.spos, self.skeys, self.tree, self.box, theta, order, curve, max_level)
         self.g_first, self.g_count = groups(self.tree, G)
         self.order = order
 
 
-def tree_force(pos, theta, eps, n_leaf=8, G=32, order=1, walk="group", group_mask=None, curve=CURVE_MORTON):
+def tree_force(pos, theta, eps, n_leaf=8, G=32, order=1, walk="group", group_mask=None, curve=CURVE_MORTON,
+               max_level=10):
     """Whole force evaluation: box, keys, sort, tree, moments, groups, walk.
 
     walk="group" (the GPU path's criterion) or "particle" (the paper's).
     Returns (result dict, Built).
     """
-    b = Built(pos, n_leaf, G, theta, order, curve)
+    b = Built(pos, n_leaf, G, theta, order, curve, max_level)
     if walk == "group":
         res = force_groups(b.spos, b.perm, b.tree, b.mom, b.g_first, b.g_count, eps,
                            group_mask=group_mask)

@@ -35,7 +35,6 @@
 #include <omp.h>
 #endif
 
-#define OR_MAX_LEVEL 10
 #define OR_CURVE_MORTON 0
 #define OR_CURVE_HILBERT 1
 
@@ -124,37 +123,37 @@ void or_bbox(int64_t n, const float* pos, float* box)
     box[3] = L;
 }
 
-/* Spread the low 10 bits of v so that bit k moves to bit 3k. */
-static uint32_t or_spread3(uint32_t v)
+/* Spread the low `nbits` bits of v so that bit k moves to bit 3k. */
+static uint64_t or_spread3(uint32_t v, int nbits)
 {
-    uint32_t r = 0;
-    for (int k = 0; k < 10; k++) r |= ((v >> k) & 1u) << (3 * k);
+    uint64_t r = 0;
+    for (int k = 0; k < nbits; k++) r |= (uint64_t)((v >> k) & 1u) << (3 * k);
     return r;
 }
 
 /* Inverse of or_spread3 restricted to `nbits` triples. */
-static uint32_t or_compact3(uint32_t v, int nbits)
+static uint32_t or_compact3(uint64_t v, int nbits)
 {
     uint32_t r = 0;
-    for (int k = 0; k < nbits; k++) r |= ((v >> (3 * k)) & 1u) << k;
+    for (int k = 0; k < nbits; k++) r |= (uint32_t)((v >> (3 * k)) & 1u) << k;
     return r;
 }
 
 /* ------------------------------------------------------------------------
  * Peano-Hilbert order (the ordering Sec. 5 names as better than Morton's),
  * after J. Skilling, "Programming the Hilbert curve", AIP Conf. Proc. 707
- * (2004): the cell's coordinates are turned into the "transposed" index by
- * undoing, from the top level down, the reflections and axis exchanges of
- * the curve's sub-cubes, and are then Gray-coded; the 30-bit index
- * interleaves the three transposed words as the Morton key does (first word
- * in the high bit of each triple).  Level by level, each octree cell is one
- * contiguous index range, so the tree is read off the sorted keys exactly as
- * with Morton keys, only the children's order differs.
+ * (2004): the cell's coordinates (nbits bits each) are turned into the
+ * "transposed" index by undoing, from the top level down, the reflections
+ * and axis exchanges of the curve's sub-cubes, and are then Gray-coded; the
+ * index interleaves the three transposed words as the Morton key does (first
+ * word in the high bit of each triple).  Level by level, each octree cell is
+ * one contiguous index range, so the tree is read off the sorted keys exactly
+ * as with Morton keys, only the children's order differs.
  * ---------------------------------------------------------------------- */
-static uint32_t or_hilbert3(uint32_t x, uint32_t y, uint32_t z)
+static uint64_t or_hilbert3(uint32_t x, uint32_t y, uint32_t z, int nbits)
 {
     uint32_t w[3] = {x, y, z};
-    for (uint32_t q = 1u << 9; q > 1u; q >>= 1) {
+    for (uint32_t q = 1u << (nbits - 1); q > 1u; q >>= 1) {
         const uint32_t low = q - 1u;
         for (int a = 0; a < 3; a++) {
             if (w[a] & q) {
@@ -169,21 +168,21 @@ static uint32_t or_hilbert3(uint32_t x, uint32_t y, uint32_t z)
     w[1] ^= w[0];
     w[2] ^= w[1];
     uint32_t g = 0;
-    for (uint32_t q = 1u << 9; q > 1u; q >>= 1)
+    for (uint32_t q = 1u << (nbits - 1); q > 1u; q >>= 1)
         if (w[2] & q) g ^= q - 1u;
     for (int a = 0; a < 3; a++) w[a] ^= g;
-    return (or_spread3(w[0]) << 2) | (or_spread3(w[1]) << 1) | or_spread3(w[2]);
+    return (or_spread3(w[0], nbits) << 2) | (or_spread3(w[1], nbits) << 1) | or_spread3(w[2], nbits);
 }
 
-/* Inverse of or_hilbert3: cell coordinates of a 30-bit index. */
-static void or_hilbert3_inv(uint32_t h, uint32_t* c)
+/* Inverse of or_hilbert3: cell coordinates of an index. */
+static void or_hilbert3_inv(uint64_t h, int nbits, uint32_t* c)
 {
-    uint32_t w[3] = {or_compact3(h >> 2, 10), or_compact3(h >> 1, 10), or_compact3(h, 10)};
+    uint32_t w[3] = {or_compact3(h >> 2, nbits), or_compact3(h >> 1, nbits), or_compact3(h, nbits)};
     const uint32_t g = w[2] >> 1;                          /* Gray decode */
     w[2] ^= w[1];
     w[1] ^= w[0];
     w[0] ^= g;
-    for (uint32_t q = 2u; q != (1u << 10); q <<= 1) {
+    for (uint32_t q = 2u; q != (1u << nbits); q <<= 1) {
         const uint32_t low = q - 1u;
         for (int a = 2; a >= 0; a--) {
             if (w[a] & q) {
@@ -200,45 +199,50 @@ static void or_hilbert3_inv(uint32_t h, uint32_t* c)
     c[2] = w[2];
 }
 
-/* Integer cell (10 bits per axis) of a key of either order. */
-static void or_key_cell(uint32_t key, int curve, uint32_t* c)
+/* Integer cell (nbits bits per axis) of a key of either order. */
+static void or_key_cell(uint64_t key, int curve, int nbits, uint32_t* c)
 {
     if (curve == OR_CURVE_HILBERT) {
-        or_hilbert3_inv(key, c);
+        or_hilbert3_inv(key, nbits, c);
     } else {
-        c[0] = or_compact3(key >> 2, 10);
-        c[1] = or_compact3(key >> 1, 10);
-        c[2] = or_compact3(key, 10);
+        c[0] = or_compact3(key >> 2, nbits);
+        c[1] = or_compact3(key >> 1, nbits);
+        c[2] = or_compact3(key, nbits);
     }
 }
 
 /* Exported for the pins: key of a cell, and cell of a key. */
-uint32_t or_key_of_cell(uint32_t x, uint32_t y, uint32_t z, int curve)
+uint64_t or_key_of_cell(uint32_t x, uint32_t y, uint32_t z, int curve, int nbits)
 {
-    return curve == OR_CURVE_HILBERT ? or_hilbert3(x, y, z)
-                                     : (or_spread3(x) << 2) | (or_spread3(y) << 1) | or_spread3(z);
+    return curve == OR_CURVE_HILBERT
+               ? or_hilbert3(x, y, z, nbits)
+               : (or_spread3(x, nbits) << 2) | (or_spread3(y, nbits) << 1) | or_spread3(z, nbits);
 }
-void or_cell_of_key(uint32_t key, int curve, uint32_t* c) { or_key_cell(key, curve, c); }
+void or_cell_of_key(uint64_t key, int curve, int nbits, uint32_t* c) { or_key_cell(key, curve, nbits, c); }
 
 /* ------------------------------------------------------------------------
- * Sec. 5 (Morton ordering): 30-bit Morton key, 10 bits per axis.
- * q = (x - xmin) * (1024/L) in FP32 (two rounded ops), integer cell
- * c = min(trunc(q), 1023); bit k of cx, cy, cz goes to key bit 3k+2, 3k+1, 3k.
- * curve = OR_CURVE_HILBERT gives the Peano-Hilbert index of the same cell.
+ * Sec. 5 (Morton ordering): key of max_level bits per axis (10: 30-bit keys;
+ * 21: 63-bit keys).  q = (x - xmin) * inv in FP32 (two rounded ops) with
+ * inv = (1024/L) * 2^(max_level - 10) (the power of two is exact), integer
+ * cell c = min(trunc(q), 2^max_level - 1); bit k of cx, cy, cz goes to key
+ * bit 3k+2, 3k+1, 3k.  curve = OR_CURVE_HILBERT gives the Peano-Hilbert
+ * index of the same cell.  The top 3*10 bits of a 63-bit key are the 30-bit
+ * key of the same particle (the 10-bit cell is the 21-bit cell >> 11).
  * ---------------------------------------------------------------------- */
-void or_keys(int64_t n, const float* pos, const float* box, uint32_t* keys, int curve)
+void or_keys(int64_t n, const float* pos, const float* box, uint64_t* keys, int curve, int max_level)
 {
-    const float inv = 1024.0f / box[3];
+    const float inv = (1024.0f / box[3]) * (float)(1u << (max_level - 10));
+    const uint32_t cmax = (1u << max_level) - 1u;
     for (int64_t i = 0; i < n; i++) {
         uint32_t c[3];
         for (int a = 0; a < 3; a++) {
             const float t = pos[4 * i + a] - box[a];
             const float q = t * inv;
             uint32_t ci = (uint32_t)q;
-            if (ci > 1023u) ci = 1023u;
+            if (ci > cmax) ci = cmax;
             c[a] = ci;
         }
-        keys[i] = or_key_of_cell(c[0], c[1], c[2], curve);
+        keys[i] = or_key_of_cell(c[0], c[1], c[2], curve, max_level);
     }
 }
 
@@ -246,7 +250,7 @@ void or_keys(int64_t n, const float* pos, const float* box, uint32_t* keys, int 
  * Stable sort of indices 0..n-1 by key (plain top-down merge sort).
  * perm[k] = original index of the k-th particle in Morton order.
  * ---------------------------------------------------------------------- */
-static void or_merge_sort(uint32_t* a, uint32_t* tmp, int64_t lo, int64_t hi, const uint32_t* keys)
+static void or_merge_sort(uint32_t* a, uint32_t* tmp, int64_t lo, int64_t hi, const uint64_t* keys)
 {
     if (hi - lo < 2) return;
     const int64_t mid = lo + (hi - lo) / 2;
@@ -262,7 +266,7 @@ static void or_merge_sort(uint32_t* a, uint32_t* tmp, int64_t lo, int64_t hi, co
     memcpy(a + lo, tmp + lo, (size_t)(hi - lo) * sizeof(uint32_t));
 }
 
-int or_sort(int64_t n, const uint32_t* keys, uint32_t* perm)
+int or_sort(int64_t n, const uint64_t* keys, uint32_t* perm)
 {
     uint32_t* tmp = (uint32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(uint32_t));
     if (!tmp) return -1;
@@ -275,11 +279,11 @@ int or_sort(int64_t n, const uint32_t* keys, uint32_t* perm)
 /* ------------------------------------------------------------------------
  * Sec. 4.1 tree construction: recursively split a cube into 8 equal
  * sub-cells.  Here the recursion stops at a cell holding <= n_leaf particles
- * or at level 10 (the resolution of a 30-bit key).  Nodes are emitted level
+ * or at max_level (the key's resolution: 10 or 21).  Nodes are emitted level
  * by level, children in octant order, so node order = (level, first).
  * Returns the node count, or -1 if `cap` is too small.
  * ---------------------------------------------------------------------- */
-int64_t or_tree_build(int64_t n, const uint32_t* skeys, int n_leaf, int64_t cap,
+int64_t or_tree_build(int64_t n, const uint64_t* skeys, int n_leaf, int max_level, int64_t cap,
                       int32_t* level, int32_t* first, int32_t* count,
                       int32_t* child_first, int32_t* nchild)
 {
@@ -290,21 +294,21 @@ int64_t or_tree_build(int64_t n, const uint32_t* skeys, int n_leaf, int64_t cap,
     first[0] = 0;
     count[0] = (int32_t)n;
     int64_t lev_begin = 0, lev_end = 1;
-    for (int l = 0; l <= OR_MAX_LEVEL; l++) {
+    for (int l = 0; l <= max_level; l++) {
         for (int64_t v = lev_begin; v < lev_end; v++) {
-            if (count[v] <= n_leaf || l == OR_MAX_LEVEL) {
+            if (count[v] <= n_leaf || l == max_level) {
                 child_first[v] = -1;
                 nchild[v] = 0;
                 continue;
             }
             /* digit of the sub-cell at level l+1 */
-            const int shift = 3 * (OR_MAX_LEVEL - 1 - l);
+            const int shift = 3 * (max_level - 1 - l);
             child_first[v] = (int32_t)nn;
             nchild[v] = 0;
             int64_t k = first[v];
             const int64_t end = (int64_t)first[v] + count[v];
             while (k < end) {
-                const uint32_t d = (skeys[k] >> shift) & 7u;
+                const uint64_t d = (skeys[k] >> shift) & 7u;
                 int64_t e = k;
                 while (e < end && ((skeys[e] >> shift) & 7u) == d) e++;
                 if (nn >= cap) return -1;
@@ -331,13 +335,14 @@ int64_t or_tree_build(int64_t n, const uint32_t* skeys, int n_leaf, int64_t cap,
  * I_ab = sum m (x_a - c_a)(x_b - c_b), stored (xx, yy, zz, xy, xz, yz).
  * Every node is summed directly over its own particles (not from its
  * children).  A massless node takes its geometric centre as centre of mass.
- * spos: particles in Morton order (x,y,z,m) FP32; skeys: their keys.
+ * spos: particles in Morton order (x,y,z,m) FP32; skeys: their keys
+ * (max_level bits per axis).
  * Outputs per node: com_m (cx,cy,cz,M), quad[6] (may be NULL), s_eff, side.
  * ---------------------------------------------------------------------- */
-void or_moments(int64_t nn, const float* spos, const uint32_t* skeys,
+void or_moments(int64_t nn, const float* spos, const uint64_t* skeys,
                 const int32_t* level, const int32_t* first, const int32_t* count,
                 const float* box, double theta, double* com_m, double* quad,
-                double* s_eff, double* side, int curve)
+                double* s_eff, double* side, int curve, int max_level)
 {
     int64_t v;
 #pragma omp parallel for schedule(dynamic, 64)
@@ -355,9 +360,9 @@ void or_moments(int64_t nn, const float* spos, const uint32_t* skeys,
         /* geometric centre of the level-l cell containing the node */
         const double lside = (double)box[3] / (double)(1u << l);
         uint32_t cell[3];
-        or_key_cell(skeys[b], curve, cell);  /* the first particle's cell, then its level-l ancestor */
-        const double px = cell[0] >> (OR_MAX_LEVEL - l), py = cell[1] >> (OR_MAX_LEVEL - l),
-                     pz = cell[2] >> (OR_MAX_LEVEL - l);
+        or_key_cell(skeys[b], curve, max_level, cell);  /* the first particle's cell, then its level-l ancestor */
+        const double px = cell[0] >> (max_level - l), py = cell[1] >> (max_level - l),
+                     pz = cell[2] >> (max_level - l);
         const double gx = (double)box[0] + (px + 0.5) * lside;
         const double gy = (double)box[1] + (py + 0.5) * lside;
         const double gz = (double)box[2] + (pz + 0.5) * lside;

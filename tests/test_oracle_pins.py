@@ -162,14 +162,14 @@ def test_sort_matches_numpy_stable(orc):
 
 # ------------------------------------------------------------- tree
 
-def _tree_brute(skeys, n_leaf):
+def _tree_brute(skeys, n_leaf, max_level=10):
     """Definition restated: node = non-empty level-l cell whose parent cell has
     > n_leaf particles; sorted by (level, first)."""
     nodes = []
     n = skeys.shape[0]
     parent_count = None
-    for l in range(11):
-        pref = (skeys >> np.uint32(3 * (10 - l))).astype(np.int64)
+    for l in range(max_level + 1):
+        pref = (skeys.astype(np.uint64) >> np.uint64(3 * (max_level - l))).astype(np.int64)
         u, first, cnt = np.unique(pref, return_index=True, return_counts=True)
         counts = dict(zip(u.tolist(), cnt.tolist()))
         for pr, fi, c in zip(u.tolist(), first.tolist(), cnt.tolist()):
@@ -180,21 +180,22 @@ def _tree_brute(skeys, n_leaf):
     return nodes
 
 
+@pytest.mark.parametrize("max_level", [10, 21])
 @pytest.mark.parametrize("n_leaf", [1, 4, 8, 16])
-def test_tree_matches_definition(orc, n_leaf):
+def test_tree_matches_definition(orc, n_leaf, max_level):
     p = workloads.clumpy(3000, seed=4)
     box = orc.bbox(p)
-    k = orc.keys(p, box)
+    k = orc.keys(p, box, max_level=max_level)
     sk = k[orc.sort(k)]
-    t = orc.tree_build(sk, n_leaf)
-    ref = _tree_brute(sk, n_leaf)
+    t = orc.tree_build(sk, n_leaf, max_level)
+    ref = _tree_brute(sk, n_leaf, max_level)
     assert t.n_nodes == len(ref)
     np.testing.assert_array_equal(t.level, [r[0] for r in ref])
     np.testing.assert_array_equal(t.first, [r[1] for r in ref])
     np.testing.assert_array_equal(t.count, [r[2] for r in ref])
     pref = np.array([r[3] for r in ref], np.int64)
     for v in range(t.n_nodes):
-        leaf = t.count[v] <= n_leaf or t.level[v] == 10
+        leaf = t.count[v] <= n_leaf or t.level[v] == max_level
         assert (t.nchild[v] == 0) == leaf
         if not leaf:
             ch = np.arange(t.child_first[v], t.child_first[v] + t.nchild[v])
@@ -209,7 +210,7 @@ def test_tree_matches_definition(orc, n_leaf):
     ends = (t.first[leaves] + t.count[leaves])[order]
     assert lf[0] == 0 and ends[-1] == sk.shape[0]
     np.testing.assert_array_equal(lf[1:], ends[:-1])
-    assert t.n_nodes <= orc.node_capacity(sk.shape[0], n_leaf)
+    assert t.n_nodes <= orc.node_capacity(sk.shape[0], n_leaf, max_level)
 
 
 def test_tree_coincident_particles(orc):
@@ -566,3 +567,69 @@ def test_particle_walk_unsoftened_cells(orc):
     # margins and term magnitudes (monopole parts) are reported per target
     assert np.isfinite(hard["margin"][0]) and hard["margin"][0] > 0
     assert abs(hard["a_abs"][0] / np.linalg.norm(e0) - 1) < 1e-5
+
+
+# ------------------------------------------------------- 63-bit keys (21 levels)
+@pytest.mark.parametrize("curve", [0, 1])
+def test_deep_keys_extend_shallow_keys(orc, curve):
+    # the 10-bit cell is the 21-bit cell shifted by 11 (the scale factor 2^11 is
+    # exact in FP32), so a 63-bit key begins with the particle's 30-bit key
+    for kind in ("clumpy", "plummer", "uniform"):
+        p = workloads.make(kind, 20000, 8)
+        box = orc.bbox(p)
+        k30 = orc.keys(p, box, curve, 10).astype(np.uint64)
+        k63 = orc.keys(p, box, curve, 21)
+        assert k63.dtype == np.uint64 and (k63 < (np.uint64(1) << np.uint64(63))).all()
+        np.testing.assert_array_equal(k63 >> np.uint64(33), k30)
+
+
+def test_deep_keys_hand_corners(orc):
+    # the box's low corner is key 0; the high corner is the last cell 2^21 - 1 on every axis
+    p = np.array([[0.0, 0.0, 0.0, 1.0], [1.0, 1.0, 1.0, 1.0], [0.25, 0.5, 0.75, 1.0]], np.float32)
+    box = orc.bbox(p)
+    k = orc.keys(p, box, 0, 21)
+    assert k[0] == 0 and k[1] == (1 << 63) - 1
+    # (0.25, 0.5, 0.75) -> cells (2^19, 2^20, 3 * 2^19): bits 19/20 of each axis interleaved
+    cx, cy, cz = 1 << 19, 1 << 20, 3 << 19
+    want = 0
+    for b in range(21):
+        want |= (((cx >> b) & 1) << (3 * b + 2)) | (((cy >> b) & 1) << (3 * b + 1)) | (((cz >> b) & 1) << (3 * b))
+    assert int(k[2]) == want
+
+
+def test_deep_hilbert_face_connected(orc):
+    rng = np.random.default_rng(21)
+    for h in rng.integers(0, (1 << 63) - 1, 1500, dtype=np.int64):
+        a, b = np.array(orc.cell_of_key(int(h), 1, 21)), np.array(orc.cell_of_key(int(h) + 1, 1, 21))
+        assert np.abs(a - b).sum() == 1 and (a < (1 << 21)).all()
+        assert orc.key_of_cell(*a, 1, 21) == int(h)
+
+
+def test_deep_tree_removes_overflow_leaves(orc):
+    # at 10 levels the clump cores overflow leaf 8; at 21 levels only particles
+    # sharing one 2^-21 cell could, and the octree above the old leaves is unchanged
+    rng = np.random.default_rng(3)
+    knot = np.concatenate([0.2 + 1e-4 * rng.random((300, 3)), np.full((300, 1), 1e-4)], 1)
+    p = np.concatenate([workloads.clumpy(60000, seed=2), knot]).astype(np.float32)
+    b10 = orc.Built(p, 8, 64, 0.5, 1, max_level=10)
+    b21 = orc.Built(p, 8, 64, 0.5, 1, max_level=21)
+    l10 = b10.tree.nchild == 0
+    assert b10.tree.count[l10].max() > 8
+    l21 = b21.tree.nchild == 0
+    big = l21 & (b21.tree.count > 8)
+    for v in np.nonzero(big)[0]:
+        ks = b21.skeys[b21.tree.first[v]:b21.tree.first[v] + b21.tree.count[v]]
+        assert (ks == ks[0]).all()
+    np.testing.assert_array_equal(b21.perm, b10.perm[np.argsort(b21.keys[b10.perm], kind="stable")])
+    # nodes of levels <= 10 that are not max-depth leaves appear identically in both trees
+    s10 = {(int(l), int(f), int(c)) for l, f, c, ch in zip(b10.tree.level, b10.tree.first, b10.tree.count,
+                                                            b10.tree.nchild) if l < 10 or c <= 8}
+    s21 = {(int(l), int(f), int(c)) for l, f, c in zip(b21.tree.level, b21.tree.first, b21.tree.count) if l <= 10}
+    assert s10 <= s21
+
+
+def test_deep_tree_theta_to_zero_equals_direct(orc):
+    p = workloads.clumpy(3000, seed=5)
+    res, _ = orc.tree_force(p, 1e-4, 0.01, n_leaf=4, G=32, order=2, max_level=21)
+    ref = orc.direct(p, eps=0.01)
+    np.testing.assert_allclose(res["out"], ref, rtol=1e-10, atol=1e-12)
