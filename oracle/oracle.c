@@ -513,6 +513,19 @@ static void or_pc(double xi, double yi, double zi, const double* cm, const doubl
     }
 }
 
+/* A cell term of the walks.  The paper's kernel (Appendix A) reads each
+ * cell as a float4 (x, y, z, m) like a particle, so the term is applied with
+ * the centre of mass and mass rounded to FP32 (the moments themselves are
+ * exact FP64 sums).  Near the FP32 resolution of the coordinates (cells of
+ * 63-bit key trees seen from inside the same dense knot) this rounding is
+ * the leading difference between the FP64 and the stored cell. */
+static void or_pc_cell(double xi, double yi, double zi, const double* cm, const double* qd, double e2,
+                       double* acc)
+{
+    const double c[4] = {(double)(float)cm[0], (double)(float)cm[1], (double)(float)cm[2], (double)(float)cm[3]};
+    or_pc(xi, yi, zi, c, qd, e2, acc);
+}
+
 static void or_pp(double xi, double yi, double zi, const float* pj, double e2, double* acc)
 {
     const double dx = (double)pj[0] - xi, dy = (double)pj[1] - yi, dz = (double)pj[2] - zi;
@@ -609,7 +622,7 @@ int or_force_groups(int64_t n, const float* spos, const uint32_t* perm, int64_t 
             double acc[5] = {0, 0, 0, 0, 0};
             int64_t cnt_pp = 0;
             for (int64_t t = 0; t < npc; t++)
-                or_pc(xi, yi, zi, com_m + 4 * pc[t], quad ? quad + 6 * pc[t] : NULL, e2, acc);
+                or_pc_cell(xi, yi, zi, com_m + 4 * pc[t], quad ? quad + 6 * pc[t] : NULL, e2, acc);
             for (int64_t t = 0; t < npp; t++) {
                 const int64_t b = first[pp[t]], e = b + count[pp[t]];
                 for (int64_t j = b; j < e; j++) {
@@ -726,7 +739,7 @@ int or_force_particles(int64_t n, const float* spos, const uint32_t* perm, int64
                 if (mg < mmin) mmin = mg;
             }
             if (d2 > s_eff[v] && !holds_i) {
-                or_pc(xi, yi, zi, c, quad ? quad + 6 * v : NULL, e2c, acc);
+                or_pc_cell(xi, yi, zi, c, quad ? quad + 6 * v : NULL, e2c, acc);
                 cpc++;
             } else if (nchild[v] == 0) {
                 for (int64_t j = first[v]; j < (int64_t)first[v] + count[v]; j++) {
@@ -1084,7 +1097,7 @@ int or_force_groups_learned(int64_t n, const float* spos, const uint32_t* perm, 
             double acc[5] = {0, 0, 0, 0, 0};
             int64_t cnt_pp = 0;
             for (int64_t t = 0; t < npc; t++)
-                or_pc(xi, yi, zi, com_m + 4 * pc[t], quad ? quad + 6 * pc[t] : NULL, e2, acc);
+                or_pc_cell(xi, yi, zi, com_m + 4 * pc[t], quad ? quad + 6 * pc[t] : NULL, e2, acc);
             for (int64_t t = 0; t < npp; t++)
                 for (int64_t j = first[pp[t]]; j < (int64_t)first[pp[t]] + count[pp[t]]; j++) {
                     if (j == i) continue;
