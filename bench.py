@@ -91,6 +91,8 @@ def parse():
                     help="group: one warp per particle group; particle: the paper's per-particle walk (Fig. 5)")
     ap.add_argument("--curve", default="morton", choices=["morton", "hilbert"],
                     help="particle order (Sec. 5): Morton or Peano-Hilbert keys")
+    ap.add_argument("--max-level", type=int, default=10, choices=[10, 21],
+                    help="deepest tree level: 10 (30-bit keys) or 21 (63-bit keys)")
     ap.add_argument("--unsoftened-cells", action="store_true",
                     help="particle walk: cells without softening (the Appendix A kernel)")
     ap.add_argument("--neighbors", action="store_true",
@@ -196,7 +198,7 @@ def calibrate(ctx, x, idx_t, ref, eps, acc, lo=0.2, hi=1.2, iters=9, walk="group
 
 # ------------------------------------------------------------ CPU oracle
 def oracle_throughput(pos, theta, eps, leaf, G, order, n_groups_sample, seed=0, walk="group",
-                      unsoftened=False, curve=0):
+                      unsoftened=False, curve=0, max_level=10):
     """FP64 CPU oracle (same walk and criterion) on a bounded sample:
     full build, then the walk of a random sample of groups (group walk) or of
     n_groups_sample * G / 4 targets in 8 Morton-contiguous chunks (particle
@@ -204,7 +206,7 @@ def oracle_throughput(pos, theta, eps, leaf, G, order, n_groups_sample, seed=0, 
     scale) / (build + walk * scale)."""
     import oracle
     t0 = time.perf_counter()
-    b = oracle.Built(pos, leaf, G, theta, order, curve)
+    b = oracle.Built(pos, leaf, G, theta, order, curve, max_level)
     t_build = time.perf_counter() - t0
     if walk == "particle":
         n = pos.shape[0]
@@ -381,7 +383,8 @@ def run_ours(args, W):
     vel = torch.zeros_like(x)
     acc = torch.empty_like(x)
     curve = bh.CURVE_HILBERT if args.curve == "hilbert" else bh.CURVE_MORTON
-    ctx = bh.Context(n, device=local, leaf_size=leaf, group_size=G, order=order, curve=curve)
+    ctx = bh.Context(n, device=local, leaf_size=leaf, group_size=G, order=order, curve=curve,
+                     max_level=args.max_level)
     stream = torch.cuda.current_stream()
 
     # FP64 direct sum on 4096 seeded targets: the error judge
@@ -514,6 +517,7 @@ def run_ours(args, W):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": W["desc"], "n": n, "theta": theta, "theta_calibrated": calibrated,
                        "leaf": leaf, "group": G, "order": order, "walk": walk, "curve": args.curve,
+                       "max_level": args.max_level,
                        "unsoftened_cells": uns if walk == "particle" else None,
                        "errors_vs_fp64_direct_4096": errs, "judge_s": t_judge,
                        "interactions_per_step": inter / steps, "pp_per_step": n_pp / steps,
@@ -529,7 +533,7 @@ def run_ours(args, W):
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_throughput(pos_np, theta, eps, leaf, G, order, args.cpu_sample_groups, walk=walk,
-                               unsoftened=uns, curve=curve)
+                               unsoftened=uns, curve=curve, max_level=args.max_level)
         unit_s = "groups" if walk == "group" else "targets"
         line["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
                                 "sample": "FP64 oracle %s walk on the same particles and theta: full build "

@@ -61,6 +61,9 @@ typedef struct bh_config {
     int curve;               /* particle order (Sec. 5): BH_CURVE_MORTON (default) or
                                 BH_CURVE_HILBERT (Peano-Hilbert); the octree is the same,
                                 only the order of children and particles differs */
+    int max_level;           /* deepest tree level: 10 (30-bit keys, default) or 21 (63-bit
+                                keys, uint64 in BH_EXPORT_KEYS); deeper levels split the
+                                dense cells that 10 levels leave as oversized leaves */
 } bh_config;
 
 #define BH_CURVE_MORTON 0
@@ -340,7 +343,7 @@ int bh_stats(bh_ctx* ctx, void* stream, bh_stats_t* out);
  * read the array's current length.
  * Errors: BH_ERR_INVALID, BH_ERR_TOO_LARGE (cap_bytes too small), BH_ERR_STATE. */
 enum {
-    BH_EXPORT_KEYS = 1,        /* uint32[n]   Morton keys in Morton order */
+    BH_EXPORT_KEYS = 1,        /* uint32[n]   sorted keys (uint64[n] when max_level = 21) */
     BH_EXPORT_PERM = 2,        /* uint32[n]   caller index of each Morton-ordered particle */
     BH_EXPORT_SPOS = 3,        /* float4[n]   particles in Morton order */
     BH_EXPORT_NODE_FIRST = 4,  /* int32[nn]   first particle (Morton position) of each node */

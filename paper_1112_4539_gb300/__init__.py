@@ -47,7 +47,8 @@ CURVE_HILBERT = 1
 class BhConfig(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int), ("group_size", ctypes.c_int), ("order", ctypes.c_int),
                 ("fp64_node_threshold", ctypes.c_int), ("block_threads", ctypes.c_int),
-                ("blocks_per_sm", ctypes.c_int), ("max_systems", ctypes.c_int), ("curve", ctypes.c_int)]
+                ("blocks_per_sm", ctypes.c_int), ("max_systems", ctypes.c_int), ("curve", ctypes.c_int),
+                ("max_level", ctypes.c_int)]
 
 
 class BhStats(ctypes.Structure):
@@ -393,13 +394,15 @@ class Context:
               "seff": torch.float32, "quad": torch.float32, "box": torch.float32}.get(what, torch.int32)
         cap = max(self.max_n, 1) * 16 + 64
         if what not in ("keys", "perm", "spos", "group_first", "group_count", "box"):
-            cap = (self.max_n + 10 * (self.max_n // (self.cfg.leaf_size + 1)) + 1) * 32
+            cap = (self.max_n + self.cfg.max_level * (self.max_n // (self.cfg.leaf_size + 1)) + 1) * 32
         buf = torch.empty(cap // 4, dtype=dt, device="cuda:%d" % self.device)
         rc, nb = bh_export(self.h, what, buf, stream)
         _check(rc, "bh_export(%s)" % what)
         a = buf[: nb // 4].cpu().numpy()
         if what in ("keys", "perm"):
             a = a.view(np.uint32)
+        if what == "keys" and self.cfg.max_level > 10:
+            a = a.view(np.uint64)
         if what in ("spos", "com_m"):
             a = a.reshape(-1, 4)
         if what == "quad":

@@ -21,6 +21,7 @@ struct bh_ctx {
     bh_config cfg{};
     int64_t max_n = 0;
     int64_t node_cap = 0;
+    bool deep = false;  // 63-bit keys (21 levels) instead of 30-bit keys (10 levels)
     int64_t n = -1;  // particles of the last tree_build (-1: none)
     bool have_moments = false;
     float theta = 0.f;
@@ -30,9 +31,10 @@ struct bh_ctx {
     bh_dev_ctrl* ctrl = nullptr;
     bh_dev_ctrl* host_ctrl = nullptr;  // pinned staging for read-back
     float4* pos_s = nullptr;
-    uint32_t *keys = nullptr, *keys_alt = nullptr, *vals = nullptr, *vals_alt = nullptr;
+    void *keys = nullptr, *keys_alt = nullptr;   // uint32_t[n] or, deep, uint64_t[n]
+    uint32_t *vals = nullptr, *vals_alt = nullptr;
     unsigned long long* lookback = nullptr;
-    uint8_t* dl = nullptr;
+    uint16_t* dl = nullptr;
     uint32_t* blk = nullptr;
     uint8_t* flags = nullptr;
     int32_t *g_first = nullptr, *g_count = nullptr;
@@ -122,6 +124,7 @@ void bh_config_default(bh_config* cfg)
     cfg->blocks_per_sm = 0;
     cfg->max_systems = 1;
     cfg->curve = BH_CURVE_MORTON;
+    cfg->max_level = 10;
 }
 
 static int validate_config(const bh_config* c)
@@ -134,6 +137,7 @@ static int validate_config(const bh_config* c)
     if (c->blocks_per_sm < 0 || c->blocks_per_sm > 32) return BH_ERR_INVALID;
     if (c->max_systems < 0 || c->max_systems > (1 << 20)) return BH_ERR_INVALID;
     if (c->curve != BH_CURVE_MORTON && c->curve != BH_CURVE_HILBERT) return BH_ERR_INVALID;
+    if (c->max_level != 10 && c->max_level != 21) return BH_ERR_INVALID;
     return BH_OK;
 }
 
@@ -148,7 +152,8 @@ int bh_create(bh_ctx** out, const bh_config* cfg, int64_t max_n, int device)
     if (rc) return rc;
     if (max_n < 1) return BH_ERR_INVALID;
     if (max_n >= (int64_t)1 << 30) return BH_ERR_TOO_LARGE;
-    const int64_t node_cap = max_n + 10 * (max_n / (c.leaf_size + 1)) + 1;
+    // <= max_n leaves plus, on each level above the deepest, <= max_n / (leaf_size + 1) internal nodes
+    const int64_t node_cap = max_n + (int64_t)c.max_level * (max_n / (c.leaf_size + 1)) + 1;
     if (node_cap >= (int64_t)1 << 28) return BH_ERR_TOO_LARGE;  // walk stack packs node ids in 28 bits
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -162,10 +167,13 @@ int bh_create(bh_ctx** out, const bh_config* cfg, int64_t max_n, int device)
     x->cfg = c;
     x->max_n = max_n;
     x->node_cap = node_cap;
+    x->deep = c.max_level == BH_MAX_LEVEL_DEEP;
     cudaDeviceGetAttribute(&x->sm_count, cudaDevAttrMultiProcessorCount, device);
 
     const size_t N = (size_t)max_n, NN = (size_t)node_cap;
-    const size_t sort_tiles = (N + bh::kSortTile - 1) / bh::kSortTile;
+    const int tile = x->deep ? bh::kSortTileDeep : bh::kSortTile;
+    const size_t sort_tiles = (N + tile - 1) / tile;
+    const size_t kb = x->deep ? 8 : 4, nlev = (size_t)c.max_level + 1;
     const size_t lvl_blocks = (N + bh::kLevelTile - 1) / bh::kLevelTile;
     const size_t flag_blocks = (N + bh::kFlagTile - 1) / bh::kFlagTile;
     size_t off = 0;
@@ -176,10 +184,10 @@ int bh_create(bh_ctx** out, const bh_config* cfg, int64_t max_n, int device)
     };
     const size_t o_ctrl = take(sizeof(bh_dev_ctrl));
     const size_t o_pos = take(N * sizeof(float4));
-    const size_t o_keys = take(N * 4), o_keys2 = take(N * 4), o_vals = take(N * 4), o_vals2 = take(N * 4);
+    const size_t o_keys = take(N * kb), o_keys2 = take(N * kb), o_vals = take(N * 4), o_vals2 = take(N * 4);
     const size_t o_look = take(sort_tiles * 256 * sizeof(unsigned long long));
-    const size_t o_dl = take(N);
-    const size_t o_blk = take(std::max(lvl_blocks * 11, flag_blocks) * 4);
+    const size_t o_dl = take(N * 2);
+    const size_t o_blk = take(std::max(lvl_blocks * nlev, flag_blocks) * 4);
     const size_t o_flags = take(flag_blocks * bh::kFlagTile);
     const size_t o_gf = take(N * 4), o_gc = take(N * 4);
     const size_t o_first = take(NN * 4), o_count = take(NN * 4), o_child = take(NN * 4), o_nch = take(NN * 4);
@@ -212,12 +220,12 @@ int bh_create(bh_ctx** out, const bh_config* cfg, int64_t max_n, int device)
     char* b = (char*)x->slab;
     x->ctrl = (bh_dev_ctrl*)(b + o_ctrl);
     x->pos_s = (float4*)(b + o_pos);
-    x->keys = (uint32_t*)(b + o_keys);
-    x->keys_alt = (uint32_t*)(b + o_keys2);
+    x->keys = (void*)(b + o_keys);
+    x->keys_alt = (void*)(b + o_keys2);
     x->vals = (uint32_t*)(b + o_vals);
     x->vals_alt = (uint32_t*)(b + o_vals2);
     x->lookback = (unsigned long long*)(b + o_look);
-    x->dl = (uint8_t*)(b + o_dl);
+    x->dl = (uint16_t*)(b + o_dl);
     x->blk = (uint32_t*)(b + o_blk);
     x->flags = (uint8_t*)(b + o_flags);
     x->g_first = (int32_t*)(b + o_gf);
@@ -280,13 +288,14 @@ int tree_build(bh_ctx* x, const float* d_pos_mass, int64_t n, void* stream)
     bh::launch_init(x->ctrl, s);
     if (N > 0) {
         bh::launch_bbox(pos, N, x->ctrl, grid_for(x), s);
-        bh::launch_keys(pos, N, x->ctrl, x->keys, x->cfg.curve, grid_for(x), s);
+        bh::launch_keys(pos, N, x->ctrl, x->keys, x->cfg.curve, x->deep, grid_for(x), s);
         bh::launch_sort(x->keys, x->keys_alt, x->vals, x->vals_alt, pos, x->pos_s, N, x->lookback,
-                        &x->sort_epoch, x->ctrl, s);
-        bh::launch_tree(x->keys, N, x->cfg.leaf_size, x->dl, x->blk, x->nd, x->node_cap, x->ctrl, grid_for(x), s);
+                        &x->sort_epoch, x->ctrl, x->deep, s);
+        bh::launch_tree(x->keys, x->deep, N, x->cfg.leaf_size, x->dl, x->blk, x->nd, x->node_cap, x->ctrl,
+                        grid_for(x), s);
         bh::launch_groups(x->nd, N, x->cfg.group_size, x->flags, x->blk, x->g_first, x->g_count, x->ctrl,
                           grid_for(x), s);
-        x->launches += bh::kLaunchesBuild - 1;
+        x->launches += bh::launches_build(x->deep) - 1;
     }
     x->launches += 1;
     if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
@@ -303,9 +312,9 @@ int tree_moments(bh_ctx* x, float theta, void* stream)
     DeviceGuard guard(x->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (x->n > 0) {
-        bh::launch_moments(x->pos_s, x->keys, x->nd, x->cfg.order, theta, x->cfg.fp64_node_threshold, x->cfg.curve,
-                           x->ctrl, grid_for(x), s);
-        x->launches += bh::kLaunchesMoments;
+        bh::launch_moments(x->pos_s, x->keys, x->deep, x->nd, x->cfg.order, theta, x->cfg.fp64_node_threshold,
+                           x->cfg.curve, x->ctrl, grid_for(x), s);
+        x->launches += bh::launches_moments(x->deep);
         if (x->mac_learned) {
             bh::launch_mac_nodefeat(x->nd, x->cfg.order, x->mfeat, x->ctrl, grid_for(x), s);
             x->launches += 1;
@@ -365,9 +374,10 @@ int tree_neighbors(bh_ctx* x, const float* d_h, float h, int32_t* d_count, float
     if (d_rho && (((uintptr_t)d_rho & 3u) || !is_device_ptr(d_rho, x->device))) return BH_ERR_INVALID;
     DeviceGuard guard(x->device);
     int rc = bh::launch_sph(x->pos_s, x->vals, x->g_first, x->g_count, x->nd, x->blo, x->bhi, x->cfg.group_size, d_h,
-                            h, d_count, d_rho, x->ctrl, x->sm_count, grid_for(x), (cudaStream_t)stream);
+                            h, d_count, d_rho, x->ctrl, x->sm_count, grid_for(x), x->cfg.max_level,
+                            (cudaStream_t)stream);
     if (rc) return rc;
-    x->launches += bh::kLaunchesSph;
+    x->launches += bh::launches_sph(x->deep);
     if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
     return BH_OK;
 }
@@ -438,7 +448,7 @@ int bh_stats(bh_ctx* x, void* stream, bh_stats_t* out)
     const bh_dev_ctrl& h = *x->host_ctrl;
     std::memset(out, 0, sizeof(*out));
     out->n = x->n < 0 ? 0 : x->n;
-    out->n_nodes = h.level_offset[11];
+    out->n_nodes = h.n_nodes;
     out->n_leaves = h.n_leaves;
     out->n_groups = h.n_groups;
     out->n_pp = (int64_t)h.n_pp;
@@ -460,11 +470,11 @@ int bh_export(bh_ctx* x, int what, void* dst, int64_t cap_bytes, int64_t* out_by
     cudaStream_t s = (cudaStream_t)stream;
     int rc = read_ctrl(x, s);
     if (rc) return rc;
-    const int64_t n = x->n, nn = x->host_ctrl->level_offset[11], ng = x->host_ctrl->n_groups;
+    const int64_t n = x->n, nn = x->host_ctrl->n_nodes, ng = x->host_ctrl->n_groups;
     const void* src = nullptr;
     int64_t bytes = 0;
     switch (what) {
-        case BH_EXPORT_KEYS: src = x->keys; bytes = n * 4; break;
+        case BH_EXPORT_KEYS: src = x->keys; bytes = n * (x->deep ? 8 : 4); break;
         case BH_EXPORT_PERM: src = x->vals; bytes = n * 4; break;
         case BH_EXPORT_SPOS: src = x->pos_s; bytes = n * 16; break;
         case BH_EXPORT_NODE_FIRST: src = x->nd.first; bytes = nn * 4; break;
@@ -654,17 +664,17 @@ int bh_force_batched(bh_ctx* x, const float* d_pos_mass, float theta, float eps,
     const int N = (int)n;
     bh::launch_init(x->ctrl, s);
     bh::launch_batch_sort((const float4*)d_pos_mass, x->sys_off, x->nsys, x->keys, x->keys_alt, x->vals, x->vals_alt,
-                          x->pos_s, x->sys_of, x->sys_box, x->cfg.curve, x->ctrl, s);
-    bh::launch_tree(x->keys, N, x->cfg.leaf_size, x->dl, x->blk, x->nd, x->node_cap, x->ctrl, grid_for(x), s,
-                    x->sys_of, x->sys_off);
+                          x->pos_s, x->sys_of, x->sys_box, x->cfg.curve, x->deep, x->ctrl, s);
+    bh::launch_tree(x->keys, x->deep, N, x->cfg.leaf_size, x->dl, x->blk, x->nd, x->node_cap, x->ctrl, grid_for(x),
+                    s, x->sys_of, x->sys_off);
     bh::launch_groups(x->nd, N, x->cfg.group_size, x->flags, x->blk, x->g_first, x->g_count, x->ctrl, grid_for(x), s);
-    bh::launch_moments(x->pos_s, x->keys, x->nd, x->cfg.order, theta, x->cfg.fp64_node_threshold, x->cfg.curve,
-                       x->ctrl, grid_for(x), s, x->sys_of, x->sys_box);
+    bh::launch_moments(x->pos_s, x->keys, x->deep, x->nd, x->cfg.order, theta, x->cfg.fp64_node_threshold,
+                       x->cfg.curve, x->ctrl, grid_for(x), s, x->sys_of, x->sys_box);
     int rc = bh::launch_walk(x->pos_s, x->vals, x->g_first, x->g_count, x->nd, x->cfg.order, x->cfg.group_size, eps,
                              (float4*)d_acc_pot, x->ctrl, x->sm_count, x->cfg.block_threads, x->cfg.blocks_per_sm, s);
     if (rc) return rc;
-    // init, batch sort, 4 tree, 5 groups, 11 moments, 2 walk
-    x->launches += 2 + 4 + 5 + bh::kLaunchesMoments + bh::kLaunchesForce;
+    // init, batch sort, 4 tree, 5 groups, moments per level, 2 walk
+    x->launches += 2 + 4 + 5 + bh::launches_moments(x->deep) + bh::kLaunchesForce;
     if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
     x->n = n;
     x->theta = theta;

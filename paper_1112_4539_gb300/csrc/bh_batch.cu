@@ -1,9 +1,10 @@
 // bh_batch.cu -- many independent systems in one pass of the build.
 //
 // Each system (a contiguous range of particles, at most kBatchMaxN) gets its
-// own root cube (Sec. 4.1) and Morton ordering (Sec. 5).  One CTA per system
+// own root cube (Sec. 4.1) and key ordering (Sec. 5).  One CTA per system
 // does all of it in a single launch: the per-axis bounds, the keys, a stable
-// LSD radix sort of the system's (key, index) pairs in four 8-bit passes over
+// LSD radix sort of the system's (key, index) pairs in 8-bit passes (4 for
+// 30-bit keys, 8 for 63-bit keys) over
 // global ping-pong buffers (the CTA walks its range tile by tile, ranking each
 // tile stably with warp match-any and carrying the running digit offsets, so
 // no inter-CTA look-back is needed), and the gather into Morton order.  The
@@ -17,11 +18,14 @@ constexpr int kBWarps = kBT / 32;
 constexpr int kBItems = 8;
 constexpr int kBTile = kBT * kBItems;  // 4096 keys per tile
 
+template <typename K>
 __global__ void __launch_bounds__(kBT)
-bh_batch_sort_kernel(const float4* __restrict__ pos, const int32_t* __restrict__ off, int curve, uint32_t* keys,
-                     uint32_t* keys_alt, uint32_t* vals, uint32_t* vals_alt, float4* __restrict__ pos_s,
+bh_batch_sort_kernel(const float4* __restrict__ pos, const int32_t* __restrict__ off, int curve, K* keys,
+                     K* keys_alt, uint32_t* vals, uint32_t* vals_alt, float4* __restrict__ pos_s,
                      uint32_t* __restrict__ sys, float4* __restrict__ sys_box, bh_dev_ctrl* c)
 {
+    constexpr int B = bh_key_traits<K>::kMaxLevel, NP = bh_key_traits<K>::kPasses;
+    constexpr unsigned int CMAX = (1u << B) - 1u;
     __shared__ unsigned int whist[kBWarps][256];
     __shared__ unsigned int base[256], run[256], tcnt[256];
     __shared__ unsigned int red[6][kBWarps];
@@ -66,28 +70,29 @@ bh_batch_sort_kernel(const float4* __restrict__ pos, const int32_t* __restrict__
         sys_box[s] = make_float4(sbox[0], sbox[1], sbox[2], sbox[3]);
     }
     __syncthreads();
-    // ---- keys (q = (x - xmin) * (1024/L), two rounded FP32 ops; c = min(trunc q, 1023))
+    // ---- keys (q = (x - xmin) * (2^B/L), two rounded FP32 ops; c = min(trunc q, 2^B - 1))
     {
-        const float x0 = sbox[0], y0 = sbox[1], z0 = sbox[2], inv = sinv;
+        const float x0 = sbox[0], y0 = sbox[1], z0 = sbox[2], inv = __fmul_rn(sinv, (float)(1u << (B - 10)));
         for (int i = o + tid; i < e; i += kBT) {
             const float4 p = pos[i];
-            const unsigned int cx = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.x, x0), inv)), 1023u);
-            const unsigned int cy = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.y, y0), inv)), 1023u);
-            const unsigned int cz = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.z, z0), inv)), 1023u);
-            keys[i] = curve == BH_CURVE_HILBERT ? bh_key_of<BH_CURVE_HILBERT>(cx, cy, cz)
-                                                : bh_key_of<BH_CURVE_MORTON>(cx, cy, cz);
+            const unsigned int cx = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.x, x0), inv)), CMAX);
+            const unsigned int cy = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.y, y0), inv)), CMAX);
+            const unsigned int cz = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.z, z0), inv)), CMAX);
+            keys[i] = curve == BH_CURVE_HILBERT ? bh_key_of<BH_CURVE_HILBERT, K>(cx, cy, cz)
+                                                : bh_key_of<BH_CURVE_MORTON, K>(cx, cy, cz);
             vals[i] = (uint32_t)i;
         }
     }
     __syncthreads();
-    // ---- four stable 8-bit passes: bits 0-7, 8-15, 16-23, 24-29
-    uint32_t *sk = keys, *sv = vals, *dk = keys_alt, *dv = vals_alt;
+    // ---- stable 8-bit passes from the lowest bits
+    K *sk = keys, *dk = keys_alt;
+    uint32_t *sv = vals, *dv = vals_alt;
     const unsigned int lt = bh_lanemask_lt();
-    for (int pass = 0; pass < 4; pass++) {
+    for (int pass = 0; pass < NP; pass++) {
         const int shift = 8 * pass;
         if (tid < 256) base[tid] = 0u;
         __syncthreads();
-        for (int i = o + tid; i < e; i += kBT) atomicAdd(&base[(sk[i] >> shift) & 255u], 1u);
+        for (int i = o + tid; i < e; i += kBT) atomicAdd(&base[(unsigned int)(sk[i] >> shift) & 255u], 1u);
         __syncthreads();
         // exclusive scan of the 256 digit counts (warps 0..7), barrier outside the branch
         unsigned int v = 0u, incl = 0u;
@@ -112,14 +117,15 @@ bh_batch_sort_kernel(const float4* __restrict__ pos, const int32_t* __restrict__
         for (int t0 = o; t0 < e; t0 += kBTile) {
             for (int i = tid; i < kBWarps * 256; i += kBT) (&whist[0][0])[i] = 0u;
             __syncthreads();
-            uint32_t key[kBItems], val[kBItems], rank[kBItems];
+            K key[kBItems];
+            uint32_t val[kBItems], rank[kBItems];
 #pragma unroll
             for (int k = 0; k < kBItems; k++) {
                 const int p = t0 + w * (32 * kBItems) + k * 32 + lane;
                 const bool ok = p < e;
-                key[k] = ok ? sk[p] : 0u;
+                key[k] = ok ? sk[p] : (K)0;
                 val[k] = ok ? sv[p] : 0u;
-                const unsigned int d = ok ? ((key[k] >> shift) & 255u) : 256u;
+                const unsigned int d = ok ? ((unsigned int)(key[k] >> shift) & 255u) : 256u;
                 const unsigned int peers = __match_any_sync(BH_FULL_MASK, d);
                 unsigned int prior = 0u;
                 if (ok) prior = whist[w][d];
@@ -143,7 +149,7 @@ bh_batch_sort_kernel(const float4* __restrict__ pos, const int32_t* __restrict__
             for (int k = 0; k < kBItems; k++) {
                 const int p = t0 + w * (32 * kBItems) + k * 32 + lane;
                 if (p < e) {
-                    const unsigned int d = (key[k] >> shift) & 255u;
+                    const unsigned int d = (unsigned int)(key[k] >> shift) & 255u;
                     const int dst = o + (int)(base[d] + run[d] + whist[w][d] + rank[k]);
                     if (dst >= o && dst < e) {
                         dk[dst] = key[k];
@@ -155,10 +161,10 @@ bh_batch_sort_kernel(const float4* __restrict__ pos, const int32_t* __restrict__
             if (tid < 256) run[tid] += tcnt[tid];
             __syncthreads();
         }
-        uint32_t* t = sk;
+        K* tk = sk;
         sk = dk;
-        dk = t;
-        t = sv;
+        dk = tk;
+        uint32_t* t = sv;
         sv = dv;
         dv = t;
         __syncthreads();
@@ -171,13 +177,17 @@ bh_batch_sort_kernel(const float4* __restrict__ pos, const int32_t* __restrict__
     }
 }
 
-void launch_batch_sort(const float4* pos, const int32_t* sys_off, int nsys, uint32_t* keys, uint32_t* keys_alt,
+void launch_batch_sort(const float4* pos, const int32_t* sys_off, int nsys, void* keys, void* keys_alt,
                        uint32_t* vals, uint32_t* vals_alt, float4* pos_s, uint32_t* sys, float4* sys_box,
-                       int curve, bh_dev_ctrl* ctrl, cudaStream_t s)
+                       int curve, bool deep, bh_dev_ctrl* ctrl, cudaStream_t s)
 {
     if (nsys <= 0) return;
-    bh_batch_sort_kernel<<<nsys, kBT, 0, s>>>(pos, sys_off, curve, keys, keys_alt, vals, vals_alt, pos_s, sys,
-                                              sys_box, ctrl);
+    if (deep)
+        bh_batch_sort_kernel<bh_key64><<<nsys, kBT, 0, s>>>(pos, sys_off, curve, (bh_key64*)keys, (bh_key64*)keys_alt,
+                                                            vals, vals_alt, pos_s, sys, sys_box, ctrl);
+    else
+        bh_batch_sort_kernel<uint32_t><<<nsys, kBT, 0, s>>>(pos, sys_off, curve, (uint32_t*)keys, (uint32_t*)keys_alt,
+                                                            vals, vals_alt, pos_s, sys, sys_box, ctrl);
 }
 
 }  // namespace bh

@@ -3,9 +3,11 @@
 // Everything here belongs to the CUDA library; nothing is shared with the CPU
 // oracle.  Tree conventions (Sec. 4.1, Sec. 5 of the paper, with this
 // library's readings):
-//   * 30-bit Morton keys, 10 bits per axis, x in the high bit of each triple;
-//   * node = non-empty cell of the 2^l grid (l = 0..10) whose parent cell holds
-//     more than n_leaf particles; leaf = holds <= n_leaf particles or l == 10;
+//   * keys of 10 bits per axis (30-bit, uint32) or 21 bits per axis (63-bit,
+//     uint64), x in the high bit of each triple, Morton or Peano-Hilbert order;
+//   * node = non-empty cell of the 2^l grid (l = 0..L, L = 10 or 21) whose
+//     parent cell holds more than n_leaf particles; leaf = holds <= n_leaf
+//     particles or l == L;
 //   * nodes are stored breadth first (sorted by level, then first particle),
 //     so the children of a node are contiguous.
 #pragma once
@@ -15,7 +17,9 @@
 
 #include "../../include/bhtree.h"
 
-#define BH_MAX_LEVEL 10
+#define BH_MAX_LEVEL 10        // deepest level of 30-bit keys
+#define BH_MAX_LEVEL_DEEP 21   // deepest level of 63-bit keys
+#define BH_LEVEL_SLOTS 23      // level-indexed arrays: levels 0..21 and the total
 #define BH_FULL_MASK 0xffffffffu
 
 // ------------------------------------------------------------------ control
@@ -27,10 +31,12 @@ struct bh_dev_ctrl {
     float inv;                   // 1024 / L
     unsigned int status;         // first device-side error, as -BH_ERR_* (0 = ok)
     unsigned int abort;          // set with status: waiting kernels give up early
-    unsigned int hist[4][256];   // upfront digit histograms of the 4 sort passes
-    unsigned int tile_ctr[4];    // onesweep tile tickets, one per pass
-    unsigned int level_total[12];
-    unsigned int level_offset[12];  // first node of each level; [11] = node count
+    unsigned int hist[8][256];   // upfront digit histograms of the sort passes (4 or 8)
+    unsigned int tile_ctr[8];    // onesweep tile tickets, one per pass
+    unsigned int level_total[BH_LEVEL_SLOTS];
+    unsigned int level_offset[BH_LEVEL_SLOTS];  // first node of each level; entries past the
+                                                // deepest level hold the node count
+    unsigned int n_nodes;        // node count of the last build
     unsigned int n_leaves;
     unsigned int max_leaf;
     unsigned int n_groups;
@@ -60,6 +66,22 @@ __device__ __forceinline__ float bh_ord2f(unsigned int u)
     return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
 
+// Key width: 30-bit keys (10 levels, 4 sort passes of 8 bits) or 63-bit keys
+// (21 levels, 8 passes).
+template <typename K>
+struct bh_key_traits;
+template <>
+struct bh_key_traits<uint32_t> {
+    static constexpr int kMaxLevel = BH_MAX_LEVEL;
+    static constexpr int kPasses = 4;
+};
+template <>
+struct bh_key_traits<unsigned long long> {
+    static constexpr int kMaxLevel = BH_MAX_LEVEL_DEEP;
+    static constexpr int kPasses = 8;
+};
+typedef unsigned long long bh_key64;
+
 // Spread the low 10 bits of v to every third bit (bit k -> bit 3k).
 __device__ __forceinline__ unsigned int bh_spread3(unsigned int v)
 {
@@ -80,17 +102,44 @@ __device__ __forceinline__ unsigned int bh_compact3(unsigned int v)
     v = (v | (v >> 16)) & 0x000003ffu;
     return v;
 }
-
-// 30-bit Peano-Hilbert index of a cell (10 bits per axis), the ordering Sec. 5
-// names as better than Morton's.  Skilling's construction ("Programming the
-// Hilbert curve", 2004): from the top level down, the bits below the level
-// are reflected in x when an axis has the level's bit set, else exchanged
-// between x and that axis; the three words are then Gray-coded and
-// interleaved as a Morton key (x in the high bit of each triple).
-__device__ __forceinline__ unsigned int bh_hilbert3(unsigned int x, unsigned int y, unsigned int z)
+// 21-bit versions for 63-bit keys: the same doubling steps on 64-bit words.
+__device__ __forceinline__ unsigned long long bh_spread3_21(unsigned int v32)
 {
+    unsigned long long v = v32 & 0x1fffffu;
+    v = (v | (v << 32)) & 0x001f00000000ffffull;
+    v = (v | (v << 16)) & 0x001f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+__device__ __forceinline__ unsigned int bh_compact3_21(unsigned long long v)
+{
+    v &= 0x1249249249249249ull;
+    v = (v | (v >> 2)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v >> 4)) & 0x100f00f00f00f00full;
+    v = (v | (v >> 8)) & 0x001f0000ff0000ffull;
+    v = (v | (v >> 16)) & 0x001f00000000ffffull;
+    v = (v | (v >> 32)) & 0x00000000001fffffull;
+    return (unsigned int)v;
+}
+__device__ __forceinline__ uint32_t bh_spread3_k(unsigned int v, uint32_t) { return bh_spread3(v); }
+__device__ __forceinline__ bh_key64 bh_spread3_k(unsigned int v, bh_key64) { return bh_spread3_21(v); }
+__device__ __forceinline__ unsigned int bh_compact3_k(uint32_t v) { return bh_compact3(v); }
+__device__ __forceinline__ unsigned int bh_compact3_k(bh_key64 v) { return bh_compact3_21(v); }
+
+// Peano-Hilbert index of a cell (B = 10 or 21 bits per axis), the ordering
+// Sec. 5 names as better than Morton's.  Skilling's construction
+// ("Programming the Hilbert curve", 2004): from the top level down, the bits
+// below the level are reflected in x when an axis has the level's bit set,
+// else exchanged between x and that axis; the three words are then
+// Gray-coded and interleaved as a Morton key (x in the high bit of each triple).
+template <typename K>
+__device__ __forceinline__ K bh_hilbert3(unsigned int x, unsigned int y, unsigned int z)
+{
+    constexpr int B = bh_key_traits<K>::kMaxLevel;
 #pragma unroll
-    for (int lv = 9; lv >= 1; lv--) {
+    for (int lv = B - 1; lv >= 1; lv--) {
         const unsigned int bit = 1u << lv, below = bit - 1u;
         if (x & bit) x ^= below;
         if (y & bit) {
@@ -112,25 +161,27 @@ __device__ __forceinline__ unsigned int bh_hilbert3(unsigned int x, unsigned int
     z ^= y;
     unsigned int g = 0u;
 #pragma unroll
-    for (int lv = 9; lv >= 1; lv--)
+    for (int lv = B - 1; lv >= 1; lv--)
         if (z & (1u << lv)) g ^= (1u << lv) - 1u;
     x ^= g;
     y ^= g;
     z ^= g;
-    return (bh_spread3(x) << 2) | (bh_spread3(y) << 1) | bh_spread3(z);
+    return (bh_spread3_k(x, K()) << 2) | (bh_spread3_k(y, K()) << 1) | bh_spread3_k(z, K());
 }
 // Cell of a Peano-Hilbert index (inverse of bh_hilbert3).
-__device__ __forceinline__ void bh_hilbert3_cell(unsigned int h, unsigned int& x, unsigned int& y, unsigned int& z)
+template <typename K>
+__device__ __forceinline__ void bh_hilbert3_cell(K h, unsigned int& x, unsigned int& y, unsigned int& z)
 {
-    x = bh_compact3(h >> 2);
-    y = bh_compact3(h >> 1);
-    z = bh_compact3(h);
+    constexpr int B = bh_key_traits<K>::kMaxLevel;
+    x = bh_compact3_k((K)(h >> 2));
+    y = bh_compact3_k((K)(h >> 1));
+    z = bh_compact3_k(h);
     const unsigned int g = z >> 1;
     z ^= y;
     y ^= x;
     x ^= g;
 #pragma unroll
-    for (int lv = 1; lv <= 9; lv++) {
+    for (int lv = 1; lv <= B - 1; lv++) {
         const unsigned int bit = 1u << lv, below = bit - 1u;
         if (z & bit) {
             x ^= below;
@@ -150,25 +201,26 @@ __device__ __forceinline__ void bh_hilbert3_cell(unsigned int h, unsigned int& x
     }
 }
 // Key of a cell, and cell of a key, for the context's order.
-template <int CURVE>
-__device__ __forceinline__ unsigned int bh_key_of(unsigned int x, unsigned int y, unsigned int z)
+template <int CURVE, typename K>
+__device__ __forceinline__ K bh_key_of(unsigned int x, unsigned int y, unsigned int z)
 {
-    return CURVE == BH_CURVE_HILBERT ? bh_hilbert3(x, y, z)
-                                     : (bh_spread3(x) << 2) | (bh_spread3(y) << 1) | bh_spread3(z);
+    return CURVE == BH_CURVE_HILBERT ? bh_hilbert3<K>(x, y, z)
+                                     : (bh_spread3_k(x, K()) << 2) | (bh_spread3_k(y, K()) << 1) |
+                                           bh_spread3_k(z, K());
 }
-__device__ __forceinline__ void bh_cell_of(unsigned int key, int curve, unsigned int& x, unsigned int& y,
-                                           unsigned int& z)
+template <typename K>
+__device__ __forceinline__ void bh_cell_of(K key, int curve, unsigned int& x, unsigned int& y, unsigned int& z)
 {
     if (curve == BH_CURVE_HILBERT) {
-        bh_hilbert3_cell(key, x, y, z);
+        bh_hilbert3_cell<K>(key, x, y, z);
     } else {
-        x = bh_compact3(key >> 2);
-        y = bh_compact3(key >> 1);
-        z = bh_compact3(key);
+        x = bh_compact3_k((K)(key >> 2));
+        y = bh_compact3_k((K)(key >> 1));
+        z = bh_compact3_k(key);
     }
 }
 
-// Deepest level whose cell holds both keys (0..10); keys of one cell share
+// Deepest level whose cell holds both keys (0..L); keys of one cell share
 // their top 3*l bits.
 __device__ __forceinline__ int bh_common_level(unsigned int a, unsigned int b)
 {
@@ -176,6 +228,14 @@ __device__ __forceinline__ int bh_common_level(unsigned int a, unsigned int b)
     if (x == 0u) return BH_MAX_LEVEL;
     return (BH_MAX_LEVEL - 1) - (31 - __clz((int)x)) / 3;
 }
+__device__ __forceinline__ int bh_common_level(unsigned long long a, unsigned long long b)
+{
+    const unsigned long long x = a ^ b;
+    if (x == 0ull) return BH_MAX_LEVEL_DEEP;
+    return (BH_MAX_LEVEL_DEEP - 1) - (63 - __clzll((long long)x)) / 3;
+}
+
+
 
 // Root cube from the reduced bounds (same rule as the build's first kernel).
 __device__ __forceinline__ void bh_box_from_minmax(const unsigned int* mm, float* box, float* inv)
@@ -245,34 +305,37 @@ namespace bh {
 
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per tile
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 keys per tile (30-bit keys)
+constexpr int kSortTileDeep = kSortTile / 2;           // 2048 keys per tile (63-bit keys)
 constexpr int kLevelTile = 2048;                       // positions per node-build block
 constexpr int kFlagTile = 4096;                        // positions per group-compaction block
 
 void launch_init(bh_dev_ctrl* ctrl, cudaStream_t s);
 void launch_bbox(const float4* pos, int n, bh_dev_ctrl* ctrl, int grid, cudaStream_t s);
-void launch_keys(const float4* pos, int n, bh_dev_ctrl* ctrl, uint32_t* keys, int curve, int grid,
+// keys: uint32_t[n] (30-bit keys) or, with deep, bh_key64[n] (63-bit keys)
+void launch_keys(const float4* pos, int n, bh_dev_ctrl* ctrl, void* keys, int curve, bool deep, int grid,
                  cudaStream_t s);
-void launch_sort(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
-                 const float4* pos, float4* pos_s, int n, unsigned long long* lookback,
-                 unsigned int* epoch, bh_dev_ctrl* ctrl, cudaStream_t s);
+void launch_sort(void* keys, void* keys_alt, uint32_t* vals, uint32_t* vals_alt, const float4* pos, float4* pos_s,
+                 int n, unsigned long long* lookback, unsigned int* epoch, bh_dev_ctrl* ctrl, bool deep,
+                 cudaStream_t s);
 // sys / sys_off / sys_box: several independent systems (system of each
 // Morton position, first particle of each system + total, root cube of each);
 // null for a single system.
-void launch_tree(const uint32_t* keys, int n, int n_leaf, uint8_t* dl, uint32_t* blk_lvl,
+// dl: uint16_t[n] scratch; blk_lvl: (deepest level + 1) * ceil(n / kLevelTile) words
+void launch_tree(const void* keys, bool deep, int n, int n_leaf, uint16_t* dl, uint32_t* blk_lvl,
                  const bh_nodes& nd, int64_t node_cap, bh_dev_ctrl* ctrl, int grid, cudaStream_t s,
                  const uint32_t* sys = nullptr, const int32_t* sys_off = nullptr);
 void launch_groups(const bh_nodes& nd, int n, int G, uint8_t* flags, uint32_t* blk, int32_t* g_first,
                    int32_t* g_count, bh_dev_ctrl* ctrl, int grid, cudaStream_t s);
-void launch_moments(const float4* pos_s, const uint32_t* keys, const bh_nodes& nd, int order,
+void launch_moments(const float4* pos_s, const void* keys, bool deep, const bh_nodes& nd, int order,
                     float theta, int fp64_threshold, int curve, bh_dev_ctrl* ctrl, int grid, cudaStream_t s,
                     const uint32_t* sys = nullptr, const float4* sys_box = nullptr);
 // One CTA per system: root cube, keys, stable radix sort and gather of each
 // system's particles (systems contiguous, each <= kBatchMaxN particles).
 constexpr int kBatchMaxN = 65536;
-void launch_batch_sort(const float4* pos, const int32_t* sys_off, int nsys, uint32_t* keys, uint32_t* keys_alt,
+void launch_batch_sort(const float4* pos, const int32_t* sys_off, int nsys, void* keys, void* keys_alt,
                        uint32_t* vals, uint32_t* vals_alt, float4* pos_s, uint32_t* sys, float4* sys_box,
-                       int curve, bh_dev_ctrl* ctrl, cudaStream_t s);
+                       int curve, bool deep, bh_dev_ctrl* ctrl, cudaStream_t s);
 }  // namespace bh
 struct bh_mlp_dev;
 namespace bh {
@@ -298,12 +361,13 @@ int launch_pwalk(const float4* pos_s, const uint32_t* perm, const bh_nodes& nd, 
 
 int launch_sph(const float4* pos_s, const uint32_t* perm, const int32_t* g_first, const int32_t* g_count,
                const bh_nodes& nd, float4* blo, float4* bhi, int G, const float* h, float h_const, int32_t* count,
-               float* rho, bh_dev_ctrl* ctrl, int sm_count, int grid, cudaStream_t s);
+               float* rho, bh_dev_ctrl* ctrl, int sm_count, int grid, int max_level, cudaStream_t s);
 
-constexpr int kLaunchesBuild = 16;   // init, bbox, keys, 4 sort passes, 4 tree, 5 groups
-constexpr int kLaunchesMoments = 11; // one per level
+// launches per call (deep = 63-bit keys: 8 sort passes, 22 levels)
+inline int launches_build(bool deep) { return deep ? 20 : 16; }  // init, bbox, keys, sort passes, 4 tree, 5 groups
+inline int launches_moments(bool deep) { return deep ? 22 : 11; }  // one per level
 constexpr int kLaunchesForce = 2;    // counter reset, walk
 constexpr int kLaunchesPWalk = 4;    // parent links, next links, counter reset, walk
-constexpr int kLaunchesSph = 13;     // 11 node-box levels, counter reset, walk
+inline int launches_sph(bool deep) { return launches_moments(deep) + 2; }  // node boxes per level, reset, walk
 
 }  // namespace bh

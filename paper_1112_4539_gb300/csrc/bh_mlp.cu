@@ -29,7 +29,7 @@ __device__ __forceinline__ float bh_quad_aniso(const float4& q0, const float4& q
 __global__ void __launch_bounds__(256) bh_mac_nodefeat_kernel(bh_nodes nd, int order, float4* __restrict__ mfeat,
                                                               const bh_dev_ctrl* __restrict__ c)
 {
-    const int nn = (int)c->level_offset[11];
+    const int nn = (int)c->n_nodes;
     if (nn == 0) return;
     const float mtot = nd.com_m[0].w, L = c->box[3];
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
@@ -50,7 +50,7 @@ void launch_mac_nodefeat(const bh_nodes& nd, int order, float4* mfeat, bh_dev_ct
 
 // ------------------------------------------------------------ labels
 constexpr int kLabelWarps = 4;
-constexpr int kLabelStack = 96;   // DFS, <= 7 pending siblings per level + 1
+constexpr int kLabelStack = 160;  // DFS: <= 7 pending siblings on each of 21 levels, + 8
 constexpr int kLabelSlots = 8;    // members per lane (groups of up to 256)
 
 struct LabelArgs {

@@ -22,13 +22,13 @@
 namespace bh {
 
 constexpr int kPWalkThreads = 128;
-constexpr int kLinkDepthCap = 32;  // > the 11 levels of a 30-bit key tree
+constexpr int kLinkDepthCap = 32;  // > the 22 levels of a 63-bit key tree
 
 // parent of every node; roots (level 0, one per system) get -1
 __global__ void bh_parent_kernel(const int4* __restrict__ rec, int32_t* __restrict__ parent,
                                  const bh_dev_ctrl* __restrict__ c)
 {
-    const int nn = (int)c->level_offset[11], n_roots = (int)c->level_offset[1];
+    const int nn = (int)c->n_nodes, n_roots = (int)c->level_offset[1];
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
         const int4 r = rec[v];
         if (v < n_roots) parent[v] = -1;
@@ -40,7 +40,7 @@ __global__ void bh_parent_kernel(const int4* __restrict__ rec, int32_t* __restri
 __global__ void bh_next_kernel(const int4* __restrict__ rec, const int32_t* __restrict__ parent,
                                int32_t* __restrict__ next, bh_dev_ctrl* __restrict__ c)
 {
-    const int nn = (int)c->level_offset[11];
+    const int nn = (int)c->n_nodes;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
         int u = v, nx = -1, d = 0;
         for (; d < kLinkDepthCap; d++) {

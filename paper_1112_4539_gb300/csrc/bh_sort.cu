@@ -21,13 +21,14 @@ __global__ void bh_init_kernel(bh_dev_ctrl* c)
         c->minmax[t] = 0xffffffffu;
         c->minmax[3 + t] = 0u;
     }
-    for (int i = t; i < 4 * 256; i += blockDim.x) (&c->hist[0][0])[i] = 0u;
-    if (t < 4) c->tile_ctr[t] = 0u;
-    if (t < 12) {
+    for (int i = t; i < 8 * 256; i += blockDim.x) (&c->hist[0][0])[i] = 0u;
+    if (t < 8) c->tile_ctr[t] = 0u;
+    if (t < BH_LEVEL_SLOTS) {
         c->level_total[t] = 0u;
         c->level_offset[t] = 0u;
     }
     if (t == 0) {
+        c->n_nodes = 0u;
         c->status = 0u;
         c->abort = 0u;
         c->n_leaves = 0u;
@@ -81,14 +82,16 @@ void launch_bbox(const float4* pos, int n, bh_dev_ctrl* ctrl, int grid, cudaStre
 // c = min(trunc(q), 1023); bit k of cx, cy, cz -> key bit 3k+2, 3k+1, 3k.
 // The four digit histograms of the sort (bits 0-7, 8-15, 16-23, 24-29) are
 // accumulated on the way.
-template <int CURVE>
+template <int CURVE, typename K>
 __global__ void __launch_bounds__(256) bh_keys_kernel(const float4* __restrict__ pos, int n, bh_dev_ctrl* c,
-                                                      uint32_t* __restrict__ keys)
+                                                      K* __restrict__ keys)
 {
-    __shared__ unsigned int sh[4][256];
+    constexpr int B = bh_key_traits<K>::kMaxLevel, NP = bh_key_traits<K>::kPasses;
+    constexpr unsigned int CMAX = (1u << B) - 1u;
+    __shared__ unsigned int sh[NP][256];
     __shared__ float sbox[4];
     __shared__ float sinv;
-    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&sh[0][0])[i] = 0u;
+    for (int i = threadIdx.x; i < NP * 256; i += blockDim.x) (&sh[0][0])[i] = 0u;
     if (threadIdx.x == 0) {
         bh_box_from_minmax(c->minmax, sbox, &sinv);
         if (blockIdx.x == 0) {
@@ -100,30 +103,37 @@ __global__ void __launch_bounds__(256) bh_keys_kernel(const float4* __restrict__
         }
     }
     __syncthreads();
-    const float x0 = sbox[0], y0 = sbox[1], z0 = sbox[2], inv = sinv;
+    // 2^(B - 10) * (1024 / L): the power of two is exact, so the 10-bit cell is the B-bit cell >> (B - 10)
+    const float x0 = sbox[0], y0 = sbox[1], z0 = sbox[2], inv = __fmul_rn(sinv, (float)(1u << (B - 10)));
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const float4 p = pos[i];
-        const unsigned int cx = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.x, x0), inv)), 1023u);
-        const unsigned int cy = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.y, y0), inv)), 1023u);
-        const unsigned int cz = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.z, z0), inv)), 1023u);
-        const unsigned int k = bh_key_of<CURVE>(cx, cy, cz);
+        const unsigned int cx = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.x, x0), inv)), CMAX);
+        const unsigned int cy = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.y, y0), inv)), CMAX);
+        const unsigned int cz = min(__float2uint_rz(__fmul_rn(__fsub_rn(p.z, z0), inv)), CMAX);
+        const K k = bh_key_of<CURVE, K>(cx, cy, cz);
         keys[i] = k;
-        atomicAdd(&sh[0][k & 255u], 1u);
-        atomicAdd(&sh[1][(k >> 8) & 255u], 1u);
-        atomicAdd(&sh[2][(k >> 16) & 255u], 1u);
-        atomicAdd(&sh[3][(k >> 24) & 255u], 1u);
+#pragma unroll
+        for (int d = 0; d < NP; d++) atomicAdd(&sh[d][(unsigned int)(k >> (8 * d)) & 255u], 1u);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
+    for (int i = threadIdx.x; i < NP * 256; i += blockDim.x) {
         const unsigned int v = (&sh[0][0])[i];
         if (v) atomicAdd(&(&c->hist[0][0])[i], v);
     }
 }
 
-void launch_keys(const float4* pos, int n, bh_dev_ctrl* ctrl, uint32_t* keys, int curve, int grid, cudaStream_t s)
+void launch_keys(const float4* pos, int n, bh_dev_ctrl* ctrl, void* keys, int curve, bool deep, int grid,
+                 cudaStream_t s)
 {
-    if (curve == BH_CURVE_HILBERT) bh_keys_kernel<BH_CURVE_HILBERT><<<grid, 256, 0, s>>>(pos, n, ctrl, keys);
-    else bh_keys_kernel<BH_CURVE_MORTON><<<grid, 256, 0, s>>>(pos, n, ctrl, keys);
+    if (deep) {
+        bh_key64* k = (bh_key64*)keys;
+        if (curve == BH_CURVE_HILBERT) bh_keys_kernel<BH_CURVE_HILBERT, bh_key64><<<grid, 256, 0, s>>>(pos, n, ctrl, k);
+        else bh_keys_kernel<BH_CURVE_MORTON, bh_key64><<<grid, 256, 0, s>>>(pos, n, ctrl, k);
+    } else {
+        uint32_t* k = (uint32_t*)keys;
+        if (curve == BH_CURVE_HILBERT) bh_keys_kernel<BH_CURVE_HILBERT, uint32_t><<<grid, 256, 0, s>>>(pos, n, ctrl, k);
+        else bh_keys_kernel<BH_CURVE_MORTON, uint32_t><<<grid, 256, 0, s>>>(pos, n, ctrl, k);
+    }
 }
 
 // ------------------------------------------------------------- onesweep
@@ -157,15 +167,18 @@ __device__ __forceinline__ unsigned int bh_block_excl_scan256(unsigned int v, un
     return base + incl - v;
 }
 
-template <bool FIRST, bool LAST>
+// K = uint32_t (30-bit keys, 16 items per thread) or bh_key64 (63-bit keys,
+// 8 items, so that a tile's keys fit the static shared memory).
+template <typename K, int ITEMS, bool FIRST, bool LAST>
 __global__ void __launch_bounds__(kSortThreads)
-bh_onesweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+bh_onesweep_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
                    uint32_t* __restrict__ vout, const float4* __restrict__ pos, float4* __restrict__ pos_s, int n,
                    int shift, int pass, unsigned int epoch, unsigned long long* lookback, bh_dev_ctrl* c)
 {
     constexpr int W = kSortThreads / 32;
-    __shared__ uint32_t s_keys[kSortTile];
-    __shared__ uint32_t s_vals[kSortTile];
+    constexpr int TILE = kSortThreads * ITEMS;
+    __shared__ K s_keys[TILE];
+    __shared__ uint32_t s_vals[TILE];
     __shared__ unsigned int s_whist[W][256];
     __shared__ unsigned int s_start[256];  // tile-local start of each digit
     __shared__ int s_base[256];            // global position of a digit's first tile-local slot
@@ -177,26 +190,27 @@ bh_onesweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict_
     for (int i = tid; i < W * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0u;
     __syncthreads();
     const int tile = s_tile;
-    const int base = tile * kSortTile;
+    const int base = tile * TILE;
     if (base >= n) return;
-    const int tile_n = min(kSortTile, n - base);
+    const int tile_n = min(TILE, n - base);
 
-    // warp-striped load: item k of lane l of warp w is tile position w*512 + k*32 + l
-    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+    // warp-striped load: item k of lane l of warp w is tile position w*32*ITEMS + k*32 + l
+    K key[ITEMS];
+    uint32_t val[ITEMS], rank[ITEMS];
 #pragma unroll
-    for (int k = 0; k < kSortItems; k++) {
-        const int p = base + w * (32 * kSortItems) + k * 32 + lane;
+    for (int k = 0; k < ITEMS; k++) {
+        const int p = base + w * (32 * ITEMS) + k * 32 + lane;
         const bool ok = p < n;
-        key[k] = ok ? kin[p] : 0xffffffffu;
+        key[k] = ok ? kin[p] : ~(K)0;
         val[k] = FIRST ? (uint32_t)p : (ok ? vin[p] : 0u);
     }
     // stable rank within the warp, item by item
     const unsigned int lt = bh_lanemask_lt();
 #pragma unroll
-    for (int k = 0; k < kSortItems; k++) {
-        const int p = base + w * (32 * kSortItems) + k * 32 + lane;
+    for (int k = 0; k < ITEMS; k++) {
+        const int p = base + w * (32 * ITEMS) + k * 32 + lane;
         const bool ok = p < n;
-        const unsigned int d = ok ? ((key[k] >> shift) & 255u) : 256u;
+        const unsigned int d = ok ? ((unsigned int)(key[k] >> shift) & 255u) : 256u;
         const unsigned int peers = __match_any_sync(BH_FULL_MASK, d);
         unsigned int prior = 0u;
         if (ok) prior = s_whist[w][d];
@@ -257,10 +271,10 @@ bh_onesweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict_
 
     // scatter into shared memory in sorted order
 #pragma unroll
-    for (int k = 0; k < kSortItems; k++) {
-        const int p = base + w * (32 * kSortItems) + k * 32 + lane;
+    for (int k = 0; k < ITEMS; k++) {
+        const int p = base + w * (32 * ITEMS) + k * 32 + lane;
         if (p < n) {
-            const unsigned int dg = (key[k] >> shift) & 255u;
+            const unsigned int dg = (unsigned int)(key[k] >> shift) & 255u;
             const unsigned int sp = s_start[dg] + s_whist[w][dg] + rank[k];
             s_keys[sp] = key[k];
             s_vals[sp] = val[k];
@@ -269,9 +283,9 @@ bh_onesweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict_
     __syncthreads();
     // write out: runs of equal digits go to consecutive global positions
     for (int i = tid; i < tile_n; i += kSortThreads) {
-        const uint32_t kk = s_keys[i];
+        const K kk = s_keys[i];
         const uint32_t vv = s_vals[i];
-        const int dest = s_base[(kk >> shift) & 255u] + i;
+        const int dest = s_base[(unsigned int)(kk >> shift) & 255u] + i;
         if (dest >= 0 && dest < n) {
             kout[dest] = kk;
             vout[dest] = vv;
@@ -280,22 +294,47 @@ bh_onesweep_kernel(const uint32_t* __restrict__ kin, const uint32_t* __restrict_
     }
 }
 
-// Four passes: bits 0-7, 8-15, 16-23, 24-29.  keys/vals end in keys/vals;
-// vals[k] = caller index of the k-th particle in Morton order.
-void launch_sort(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals, uint32_t* vals_alt, const float4* pos,
-                 float4* pos_s, int n, unsigned long long* lookback, unsigned int* epoch, bh_dev_ctrl* ctrl,
+// Passes of 8 bits from the lowest (4 for 30-bit keys, 8 for 63-bit keys;
+// an even count, so keys/vals end where they started); the last pass also
+// gathers the particles.  vals[k] = caller index of the k-th particle in key order.
+template <typename K, int ITEMS>
+static void bh_sort_passes(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, const float4* pos,
+                           float4* pos_s, int n, unsigned long long* lookback, unsigned int* epoch, bh_dev_ctrl* ctrl,
+                           cudaStream_t s)
+{
+    constexpr int NP = bh_key_traits<K>::kPasses;
+    const int tiles = (n + kSortThreads * ITEMS - 1) / (kSortThreads * ITEMS);
+    K *ka = keys, *kb = keys_alt;
+    uint32_t *va = vals, *vb = vals_alt;
+    for (int p = 0; p < NP; p++) {
+        if (p == 0)
+            bh_onesweep_kernel<K, ITEMS, true, false><<<tiles, kSortThreads, 0, s>>>(ka, nullptr, kb, vb, pos, pos_s,
+                                                                                     n, 0, 0, ++*epoch, lookback,
+                                                                                     ctrl);
+        else if (p == NP - 1)
+            bh_onesweep_kernel<K, ITEMS, false, true><<<tiles, kSortThreads, 0, s>>>(ka, va, kb, vb, pos, pos_s, n,
+                                                                                     8 * p, p, ++*epoch, lookback,
+                                                                                     ctrl);
+        else
+            bh_onesweep_kernel<K, ITEMS, false, false><<<tiles, kSortThreads, 0, s>>>(ka, va, kb, vb, pos, pos_s, n,
+                                                                                      8 * p, p, ++*epoch, lookback,
+                                                                                      ctrl);
+        K* tk = ka; ka = kb; kb = tk;
+        uint32_t* tv = va; va = vb; vb = tv;
+    }
+}
+
+void launch_sort(void* keys, void* keys_alt, uint32_t* vals, uint32_t* vals_alt, const float4* pos, float4* pos_s,
+                 int n, unsigned long long* lookback, unsigned int* epoch, bh_dev_ctrl* ctrl, bool deep,
                  cudaStream_t s)
 {
     if (n <= 0) return;
-    const int tiles = (n + kSortTile - 1) / kSortTile;
-    bh_onesweep_kernel<true, false><<<tiles, kSortThreads, 0, s>>>(keys, nullptr, keys_alt, vals_alt, pos, pos_s,
-                                                                     n, 0, 0, ++*epoch, lookback, ctrl);
-    bh_onesweep_kernel<false, false><<<tiles, kSortThreads, 0, s>>>(keys_alt, vals_alt, keys, vals, pos, pos_s, n,
-                                                                      8, 1, ++*epoch, lookback, ctrl);
-    bh_onesweep_kernel<false, false><<<tiles, kSortThreads, 0, s>>>(keys, vals, keys_alt, vals_alt, pos, pos_s, n,
-                                                                      16, 2, ++*epoch, lookback, ctrl);
-    bh_onesweep_kernel<false, true><<<tiles, kSortThreads, 0, s>>>(keys_alt, vals_alt, keys, vals, pos, pos_s, n,
-                                                                     24, 3, ++*epoch, lookback, ctrl);
+    if (deep)
+        bh_sort_passes<bh_key64, kSortItems / 2>((bh_key64*)keys, (bh_key64*)keys_alt, vals, vals_alt, pos, pos_s,
+                                                 n, lookback, epoch, ctrl, s);
+    else
+        bh_sort_passes<uint32_t, kSortItems>((uint32_t*)keys, (uint32_t*)keys_alt, vals, vals_alt, pos, pos_s, n,
+                                             lookback, epoch, ctrl, s);
 }
 
 }  // namespace bh

@@ -23,7 +23,7 @@
 
 namespace bh {
 
-constexpr int kSphStackCap = 352;   // ranges of <= 8 siblings; same bound as the gravity walk
+constexpr int kSphStackCap = 704;   // ranges of <= 8 siblings; same bound as the gravity walk
 constexpr int kSphRing = 64;
 
 // ------------------------------------------------------------ node boxes
@@ -318,9 +318,9 @@ __global__ void bh_sph_reset_kernel(bh_dev_ctrl* c)
 
 int launch_sph(const float4* pos_s, const uint32_t* perm, const int32_t* g_first, const int32_t* g_count,
                const bh_nodes& nd, float4* blo, float4* bhi, int G, const float* h, float h_const, int32_t* count,
-               float* rho, bh_dev_ctrl* ctrl, int sm_count, int grid, cudaStream_t s)
+               float* rho, bh_dev_ctrl* ctrl, int sm_count, int grid, int max_level, cudaStream_t s)
 {
-    for (int lev = BH_MAX_LEVEL; lev >= 0; lev--)
+    for (int lev = max_level; lev >= 0; lev--)
         bh_node_box_kernel<<<grid, 256, 0, s>>>(pos_s, nd.rec, blo, bhi, lev, ctrl);
     bh_sph_reset_kernel<<<1, 1, 0, s>>>(ctrl);
     SphParams P;

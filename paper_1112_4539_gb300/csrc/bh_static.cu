@@ -65,11 +65,13 @@ extern "C" int bh_tree_force_static(const float* d_pos_mass, int64_t n, const bh
         c.order = 1;
         c.fp64_node_threshold = 4096;
         c.block_threads = 128;
+        c.max_level = 10;
     }
     if (c.leaf_size < 1 || c.leaf_size > 64 || c.group_size < 1 || c.group_size > 256 ||
         (c.order != 1 && c.order != 2) || c.fp64_node_threshold < 1 ||
         (c.block_threads != 64 && c.block_threads != 128) || c.blocks_per_sm < 0 ||
-        c.blocks_per_sm > 32 || (c.curve != BH_CURVE_MORTON && c.curve != BH_CURVE_HILBERT))
+        c.blocks_per_sm > 32 || (c.curve != BH_CURVE_MORTON && c.curve != BH_CURVE_HILBERT) ||
+        c.max_level != 10)  // the fixed scratch holds 30-bit keys only
         return BH_ERR_INVALID;
     if (n < 0 || !(theta > 0.0f) || !std::isfinite(theta) || !(eps >= 0.0f) || !std::isfinite(eps))
         return BH_ERR_INVALID;
@@ -95,7 +97,7 @@ extern "C" int bh_tree_force_static(const float* d_pos_mass, int64_t n, const bh
     (void)tiles;
     const size_t o_pos = take(N * sizeof(float4));
     const size_t o_keys = take(N * 4), o_keys2 = take(N * 4), o_vals = take(N * 4), o_vals2 = take(N * 4);
-    const size_t o_dl = take(N);
+    const size_t o_dl = take(N * 2);
     const size_t o_blk = take((lvl_blocks * 11 > flag_blocks ? lvl_blocks * 11 : flag_blocks) * 4);
     const size_t o_flags = take(flag_blocks * bh::kFlagTile);
     const size_t o_gf = take(N * 4), o_gc = take(N * 4);
@@ -165,14 +167,14 @@ extern "C" int bh_tree_force_static(const float* d_pos_mass, int64_t n, const bh
     const float4* pos = (const float4*)d_pos_mass;
     bh::launch_init(ctrl, s);
     bh::launch_bbox(pos, N32, ctrl, grid, s);
-    bh::launch_keys(pos, N32, ctrl, keys, c.curve, grid, s);
+    bh::launch_keys(pos, N32, ctrl, keys, c.curve, false, grid, s);
     bh::launch_sort(keys, keys_alt, vals, vals_alt, pos, pos_s, N32, (unsigned long long*)(b + o_look), &sd.epoch,
-                    ctrl, s);
-    bh::launch_tree(keys, N32, c.leaf_size, (uint8_t*)(b + o_dl), (uint32_t*)(b + o_blk), nd, (int64_t)NN, ctrl, grid,
-                    s);
+                    ctrl, false, s);
+    bh::launch_tree(keys, false, N32, c.leaf_size, (uint16_t*)(b + o_dl), (uint32_t*)(b + o_blk), nd, (int64_t)NN,
+                    ctrl, grid, s);
     bh::launch_groups(nd, N32, c.group_size, (uint8_t*)(b + o_flags), (uint32_t*)(b + o_blk), g_first, g_count,
                       ctrl, grid, s);
-    bh::launch_moments(pos_s, keys, nd, c.order, theta, c.fp64_node_threshold, c.curve, ctrl, grid, s);
+    bh::launch_moments(pos_s, keys, false, nd, c.order, theta, c.fp64_node_threshold, c.curve, ctrl, grid, s);
     int rc = bh::launch_walk(pos_s, vals, g_first, g_count, nd, c.order, c.group_size, eps, (float4*)d_acc_pot, ctrl,
                              sd.sm_count, c.block_threads, c.blocks_per_sm, s);
     if (rc) return rc;

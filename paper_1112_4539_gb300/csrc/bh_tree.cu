@@ -1,14 +1,15 @@
 // bh_tree.cu -- octree over Morton-sorted keys, cell moments, walk groups.
 //
 // Sec. 4.1 builds the octree by recursive subdivision of the root cube; here
-// the same tree is read off the sorted keys in parallel.  For Morton position
-// k let d_k be the deepest level whose cell holds both particles k-1 and k
-// (-1 for k = 0): the cells starting at k are those of levels d_k+1 .. 10.
+// the same tree is read off the sorted keys in parallel (keys of L = 10 or
+// 21 levels).  For sorted position k let d_k be the deepest level whose cell
+// holds both particles k-1 and k (-1 for k = 0): the cells starting at k are
+// those of levels d_k+1 .. L.
 // A level-l cell is a node iff its parent cell holds more than n_leaf
 // particles; a window of n_leaf+1 consecutive particles shares a level-l cell
 // iff its end keys share their top 3l bits, so with W_k = the largest such
 // shared level over the windows containing k, the nodes containing k are the
-// levels 0 .. lambda_k = min(10, W_k + 1), the deepest being k's leaf.  Node
+// levels 0 .. lambda_k = min(L, W_k + 1), the deepest being k's leaf.  Node
 // (k, l) therefore exists for d_k < l <= lambda_k.  Breadth-first order
 // (level, then first particle) gives each node its index by a per-level rank.
 //
@@ -27,18 +28,20 @@ constexpr int kMaxLeaf = 64;
 constexpr int kLeafFp64 = 32;
 
 // ------------------------------------------------------------ pass 1
-// dl[k] = (d_k + 1) | (lambda_k << 4); per-block node counts per level.
+// dl[k] = (d_k + 1) | (lambda_k << 5); per-block node counts per level.
 // With several independent systems (sys = system of each Morton position,
 // systems contiguous), particles of different systems share no cell: a
 // system's first particle starts a root, and windows never span systems.
+template <typename K>
 __global__ void __launch_bounds__(kLvlThreads)
-bh_levels_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ sys, int n, int n_leaf,
-                 uint8_t* __restrict__ dl, uint32_t* __restrict__ blk_lvl, int nblk)
+bh_levels_kernel(const K* __restrict__ keys, const uint32_t* __restrict__ sys, int n, int n_leaf,
+                 uint16_t* __restrict__ dl, uint32_t* __restrict__ blk_lvl, int nblk)
 {
-    __shared__ uint32_t sk[kLevelTile + 2 * kMaxLeaf + 2];
+    constexpr int L = bh_key_traits<K>::kMaxLevel;
+    __shared__ K sk[kLevelTile + 2 * kMaxLeaf + 2];
     __shared__ uint32_t ss[kLevelTile + 2 * kMaxLeaf + 2];
     __shared__ int8_t sw[kLevelTile + kMaxLeaf + 1];
-    __shared__ unsigned int scnt[kLvlThreads / 32][12];
+    __shared__ unsigned int scnt[kLvlThreads / 32][L + 1];
     const int tid = threadIdx.x;
     const int base = blockIdx.x * kLevelTile;
     const int lo = base - n_leaf - 1;
@@ -46,7 +49,7 @@ bh_levels_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__
     for (int i = tid; i < span; i += kLvlThreads) {
         const int p = lo + i;
         const bool in = p >= 0 && p < n;
-        sk[i] = in ? keys[p] : 0u;
+        sk[i] = in ? keys[p] : (K)0;
         ss[i] = (in && sys) ? sys[p] : 0u;
     }
     __syncthreads();
@@ -59,9 +62,9 @@ bh_levels_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__
         sw[i] = (int8_t)wv;
     }
     __syncthreads();
-    unsigned int cnt[11];
+    unsigned int cnt[L + 1];
 #pragma unroll
-    for (int l = 0; l < 11; l++) cnt[l] = 0u;
+    for (int l = 0; l <= L; l++) cnt[l] = 0u;
     for (int r = 0; r < kLvlPer; r++) {
         const int k = base + tid * kLvlPer + r;
         if (k >= n) break;
@@ -69,19 +72,19 @@ bh_levels_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__
         int W = -1;
         const int j0 = max(0, k - n_leaf);
         for (int j = j0; j <= k; j++) W = max(W, (int)sw[j - (base - n_leaf)]);
-        const int lam = min(BH_MAX_LEVEL, W + 1);
-        dl[k] = (uint8_t)((d + 1) | (lam << 4));
+        const int lam = min(L, W + 1);
+        dl[k] = (uint16_t)((d + 1) | (lam << 5));
 #pragma unroll
-        for (int l = 0; l < 11; l++) cnt[l] += (l > d && l <= lam) ? 1u : 0u;
+        for (int l = 0; l <= L; l++) cnt[l] += (l > d && l <= lam) ? 1u : 0u;
     }
     const int lane = tid & 31, w = tid >> 5;
 #pragma unroll
-    for (int l = 0; l < 11; l++) {
+    for (int l = 0; l <= L; l++) {
         const unsigned int s = __reduce_add_sync(BH_FULL_MASK, cnt[l]);
         if (lane == 0) scnt[w][l] = s;
     }
     __syncthreads();
-    if (tid < 11) {
+    if (tid <= L) {
         unsigned int s = 0u;
         for (int i = 0; i < kLvlThreads / 32; i++) s += scnt[i][tid];
         blk_lvl[(size_t)tid * nblk + blockIdx.x] = s;
@@ -140,19 +143,20 @@ __device__ unsigned int bh_scan_segment(uint32_t* a, int len, unsigned int* wtot
 }
 
 // ------------------------------------------------------------ pass 2
-__global__ void __launch_bounds__(1024) bh_level_scan_kernel(uint32_t* blk_lvl, int nblk, bh_dev_ctrl* c,
+// nlev = deepest level + 1; level_offset[l] for l >= nlev holds the node count.
+__global__ void __launch_bounds__(1024) bh_level_scan_kernel(uint32_t* blk_lvl, int nblk, int nlev, bh_dev_ctrl* c,
                                                              long long node_cap)
 {
     __shared__ unsigned int wtot[33];
-    __shared__ unsigned int tot[11];
-    for (int l = 0; l < 11; l++) {
+    __shared__ unsigned int tot[BH_LEVEL_SLOTS];
+    for (int l = 0; l < nlev; l++) {
         const unsigned int t = bh_scan_segment(blk_lvl + (size_t)l * nblk, nblk, wtot);
         if (threadIdx.x == 0) tot[l] = t;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned long long run = 0ull;
-        for (int l = 0; l < 11; l++) {
+        for (int l = 0; l < nlev; l++) {
             c->level_total[l] = tot[l];
             c->level_offset[l] = (unsigned int)run;
             run += tot[l];
@@ -160,39 +164,41 @@ __global__ void __launch_bounds__(1024) bh_level_scan_kernel(uint32_t* blk_lvl, 
         if ((long long)run > node_cap) {
             bh_set_error(c, BH_ERR_CAPACITY);
             run = 0ull;  // later kernels see an empty tree
-            for (int l = 0; l < 11; l++) c->level_offset[l] = 0u;
+            for (int l = 0; l < nlev; l++) c->level_offset[l] = 0u;
         }
-        c->level_offset[11] = (unsigned int)run;
+        for (int l = nlev; l < BH_LEVEL_SLOTS; l++) c->level_offset[l] = (unsigned int)run;
+        c->n_nodes = (unsigned int)run;
     }
 }
 
 // ------------------------------------------------------------ pass 3
 // Write (first, level, child) of every node at its breadth-first index.
+template <int L>
 __global__ void __launch_bounds__(kLvlThreads)
-bh_node_write_kernel(const uint8_t* __restrict__ dl, int n, const uint32_t* __restrict__ blk_lvl, int nblk,
+bh_node_write_kernel(const uint16_t* __restrict__ dl, int n, const uint32_t* __restrict__ blk_lvl, int nblk,
                      const bh_dev_ctrl* __restrict__ c, int32_t* __restrict__ nfirst, uint8_t* __restrict__ nlevel,
                      int32_t* __restrict__ nchildidx)
 {
-    __shared__ unsigned int swt[kLvlThreads / 32][11];
+    __shared__ unsigned int swt[kLvlThreads / 32][L + 1];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int base = blockIdx.x * kLevelTile;
-    if (c->level_offset[11] == 0u) return;  // capacity error (or empty)
-    uint8_t my[kLvlPer];
-    unsigned int cnt[11];
+    if (c->n_nodes == 0u) return;  // capacity error (or empty)
+    uint16_t my[kLvlPer];
+    unsigned int cnt[L + 1];
 #pragma unroll
-    for (int l = 0; l < 11; l++) cnt[l] = 0u;
+    for (int l = 0; l <= L; l++) cnt[l] = 0u;
 #pragma unroll
     for (int r = 0; r < kLvlPer; r++) {
         const int k = base + tid * kLvlPer + r;
-        my[r] = (k < n) ? dl[k] : (uint8_t)(11 | (0 << 4));  // d+1 = 11 > lambda: no node
-        const int d = (int)(my[r] & 15) - 1, lam = my[r] >> 4;
+        my[r] = (k < n) ? dl[k] : (uint16_t)(L + 1);  // d+1 = L+1 > lambda = 0: no node
+        const int d = (int)(my[r] & 31) - 1, lam = my[r] >> 5;
 #pragma unroll
-        for (int l = 0; l < 11; l++) cnt[l] += (l > d && l <= lam) ? 1u : 0u;
+        for (int l = 0; l <= L; l++) cnt[l] += (l > d && l <= lam) ? 1u : 0u;
     }
     // per-level exclusive scan over the block (thread order = position order)
-    unsigned int ex[11];
+    unsigned int ex[L + 1];
 #pragma unroll
-    for (int l = 0; l < 11; l++) {
+    for (int l = 0; l <= L; l++) {
         unsigned int incl = cnt[l];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -204,7 +210,7 @@ bh_node_write_kernel(const uint8_t* __restrict__ dl, int n, const uint32_t* __re
     }
     __syncthreads();
 #pragma unroll
-    for (int l = 0; l < 11; l++) {
+    for (int l = 0; l <= L; l++) {
         unsigned int b = c->level_offset[l] + blk_lvl[(size_t)l * nblk + blockIdx.x];
         for (int i = 0; i < w; i++) b += swt[i][l];
         ex[l] += b;
@@ -212,10 +218,10 @@ bh_node_write_kernel(const uint8_t* __restrict__ dl, int n, const uint32_t* __re
 #pragma unroll
     for (int r = 0; r < kLvlPer; r++) {
         const int k = base + tid * kLvlPer + r;
-        const int d = (int)(my[r] & 15) - 1, lam = my[r] >> 4;
+        const int d = (int)(my[r] & 31) - 1, lam = my[r] >> 5;
         int below = -1;  // index of node (k, l+1)
 #pragma unroll
-        for (int l = 10; l >= 0; l--) {
+        for (int l = L; l >= 0; l--) {
             if (l > d && l <= lam) {
                 const int idx = (int)ex[l]++;
                 nfirst[idx] = k;
@@ -230,11 +236,13 @@ bh_node_write_kernel(const uint8_t* __restrict__ dl, int n, const uint32_t* __re
 // ------------------------------------------------------------ pass 4
 // Particle count of each node (end of its key range by galloping search),
 // number of children, packed walk record, leaf statistics.
+template <typename K>
 __global__ void __launch_bounds__(256)
-bh_node_finalize_kernel(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ sys,
+bh_node_finalize_kernel(const K* __restrict__ keys, const uint32_t* __restrict__ sys,
                         const int32_t* __restrict__ sys_off, int n, bh_nodes nd, bh_dev_ctrl* c)
 {
-    const int nn = (int)c->level_offset[11];
+    constexpr int L = bh_key_traits<K>::kMaxLevel;
+    const int nn = (int)c->n_nodes;
     unsigned int leaves = 0u, maxleaf = 0u;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
         const int l = nd.level[v];
@@ -243,8 +251,8 @@ bh_node_finalize_kernel(const uint32_t* __restrict__ keys, const uint32_t* __res
         const int seg_end = sys ? sys_off[sys[k] + 1] : n;
         int end = seg_end;
         if (l > 0) {
-            const int sh = 3 * (BH_MAX_LEVEL - l);
-            const unsigned int target = ((keys[k] >> sh) + 1u) << sh;
+            const int sh = 3 * (L - l);
+            const K target = ((keys[k] >> sh) + (K)1) << sh;
             int lo = k, hi = k + 1, step = 1;
             while (hi < seg_end && keys[hi] < target) {
                 lo = hi;
@@ -282,16 +290,28 @@ bh_node_finalize_kernel(const uint32_t* __restrict__ keys, const uint32_t* __res
     }
 }
 
-void launch_tree(const uint32_t* keys, int n, int n_leaf, uint8_t* dl, uint32_t* blk_lvl, const bh_nodes& nd,
+template <typename K>
+static void bh_tree_t(const K* keys, int n, int n_leaf, uint16_t* dl, uint32_t* blk_lvl, const bh_nodes& nd,
+                      int64_t node_cap, bh_dev_ctrl* ctrl, int grid, cudaStream_t s, const uint32_t* sys,
+                      const int32_t* sys_off)
+{
+    constexpr int L = bh_key_traits<K>::kMaxLevel;
+    const int nblk = (n + kLevelTile - 1) / kLevelTile;
+    bh_levels_kernel<K><<<nblk, kLvlThreads, 0, s>>>(keys, sys, n, n_leaf, dl, blk_lvl, nblk);
+    bh_level_scan_kernel<<<1, 1024, 0, s>>>(blk_lvl, nblk, L + 1, ctrl, (long long)node_cap);
+    bh_node_write_kernel<L><<<nblk, kLvlThreads, 0, s>>>(dl, n, blk_lvl, nblk, ctrl, nd.first, nd.level, nd.child);
+    bh_node_finalize_kernel<K><<<grid, 256, 0, s>>>(keys, sys, sys_off, n, nd, ctrl);
+}
+
+void launch_tree(const void* keys, bool deep, int n, int n_leaf, uint16_t* dl, uint32_t* blk_lvl, const bh_nodes& nd,
                  int64_t node_cap, bh_dev_ctrl* ctrl, int grid, cudaStream_t s, const uint32_t* sys,
                  const int32_t* sys_off)
 {
     if (n <= 0) return;
-    const int nblk = (n + kLevelTile - 1) / kLevelTile;
-    bh_levels_kernel<<<nblk, kLvlThreads, 0, s>>>(keys, sys, n, n_leaf, dl, blk_lvl, nblk);
-    bh_level_scan_kernel<<<1, 1024, 0, s>>>(blk_lvl, nblk, ctrl, (long long)node_cap);
-    bh_node_write_kernel<<<nblk, kLvlThreads, 0, s>>>(dl, n, blk_lvl, nblk, ctrl, nd.first, nd.level, nd.child);
-    bh_node_finalize_kernel<<<grid, 256, 0, s>>>(keys, sys, sys_off, n, nd, ctrl);
+    if (deep)
+        bh_tree_t<bh_key64>((const bh_key64*)keys, n, n_leaf, dl, blk_lvl, nd, node_cap, ctrl, grid, s, sys, sys_off);
+    else
+        bh_tree_t<uint32_t>((const uint32_t*)keys, n, n_leaf, dl, blk_lvl, nd, node_cap, ctrl, grid, s, sys, sys_off);
 }
 
 // ------------------------------------------------------------ groups
@@ -302,7 +322,7 @@ void launch_tree(const uint32_t* keys, int n, int n_leaf, uint8_t* dl, uint32_t*
 __global__ void __launch_bounds__(256) bh_group_mark_kernel(bh_nodes nd, int G, uint8_t* __restrict__ flags,
                                                             const bh_dev_ctrl* __restrict__ c)
 {
-    const int nn = (int)c->level_offset[11];
+    const int nn = (int)c->n_nodes;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nn; v += gridDim.x * blockDim.x) {
         const int4 r = nd.rec[v];
         if (v < (int)c->level_offset[1]) {  // a root (one per system)
@@ -460,12 +480,23 @@ __device__ __forceinline__ void bh_leaf_moments(const float4* __restrict__ pos_s
     }
 }
 
+// Nodes whose moments are combined in FP64: those above the particle-count
+// threshold; leaves holding more than kLeafFp64 particles (a sequential FP32
+// sum of k equal masses is off by up to ~k * 3e-9 relative, 1e-5 at k = 3000);
+// and nodes below level 10 (63-bit keys), whose cells are so small that the
+// FP32 centre of mass, good to ~6e-8 of the coordinate scale, would leave
+// their second moments with a relative error of ~(6e-8 * scale) / side.
+__device__ __forceinline__ bool bh_node_fp64(int count, bool leaf, int level, int fp64_threshold)
+{
+    return count >= fp64_threshold || (leaf && count > kLeafFp64) || level > BH_MAX_LEVEL;
+}
+
 template <typename R>
 __device__ __forceinline__ void bh_child_moments(const bh_nodes& nd, int cidx, int fp64_threshold, int order,
                                                  bh_mom<R>& o)
 {
     const int cc = nd.count[cidx];
-    if (sizeof(R) == 8 && (cc >= fp64_threshold || (nd.child[cidx] < 0 && cc > kLeafFp64))) {
+    if (sizeof(R) == 8 && bh_node_fp64(cc, nd.child[cidx] < 0, nd.level[cidx], fp64_threshold)) {
         const bh_double4 c = nd.com64[cidx];
         o.cx = (R)c.x; o.cy = (R)c.y; o.cz = (R)c.z; o.M = (R)c.w;
         if (order >= 2)
@@ -514,14 +545,15 @@ __device__ __forceinline__ void bh_internal_moments(const bh_nodes& nd, int ch, 
     }
 }
 
-template <int ORDER>
+template <int ORDER, typename K>
 __global__ void __launch_bounds__(256)
-bh_moments_level_kernel(const float4* __restrict__ pos_s, const uint32_t* __restrict__ keys, bh_nodes nd, int lev,
+bh_moments_level_kernel(const float4* __restrict__ pos_s, const K* __restrict__ keys, bh_nodes nd, int lev,
                         float theta, int fp64_threshold, int curve, const bh_dev_ctrl* __restrict__ c,
                         const uint32_t* __restrict__ sys, const float4* __restrict__ sys_box)
 {
+    constexpr int L = bh_key_traits<K>::kMaxLevel;
     const int v0 = (int)c->level_offset[lev], v1 = (int)c->level_offset[lev + 1];
-    if (c->level_offset[11] == 0u) return;
+    if (c->n_nodes == 0u) return;
     const float4 gbox = make_float4(c->box[0], c->box[1], c->box[2], c->box[3]);
     for (int v = v0 + blockIdx.x * blockDim.x + threadIdx.x; v < v1; v += gridDim.x * blockDim.x) {
         const int4 r = nd.rec[v];
@@ -530,15 +562,12 @@ bh_moments_level_kernel(const float4* __restrict__ pos_s, const uint32_t* __rest
         const float xmin = bx.x, ymin = bx.y, zmin = bx.z;
         const float side = ldexpf(bx.w, -lev);  // exact: power-of-two scaling
         const float opening = side / theta;
-        // FP64 above the threshold, and for leaves holding more than 32 particles
-        // (only level-10 leaves can): a sequential FP32 sum of k equal masses is
-        // off by up to ~k * 3e-9 relative (1e-5 at k = 3000)
-        const bool f64 = r.y >= fp64_threshold || (r.z < 0 && r.y > kLeafFp64);
+        const bool f64 = bh_node_fp64(r.y, r.z < 0, lev, fp64_threshold);
         // geometric centre of the node's level-lev cell: the ancestor of the
         // first particle's cell, decoded from its key
         unsigned int ix, iy, iz;
-        bh_cell_of(keys[r.x], curve, ix, iy, iz);
-        const int sh = BH_MAX_LEVEL - lev;
+        bh_cell_of<K>(keys[r.x], curve, ix, iy, iz);
+        const int sh = L - lev;
         const float gx = xmin + ((float)(ix >> sh) + 0.5f) * side;
         const float gy = ymin + ((float)(iy >> sh) + 0.5f) * side;
         const float gz = zmin + ((float)(iz >> sh) + 0.5f) * side;
@@ -582,18 +611,31 @@ bh_moments_level_kernel(const float4* __restrict__ pos_s, const uint32_t* __rest
     }
 }
 
-void launch_moments(const float4* pos_s, const uint32_t* keys, const bh_nodes& nd, int order, float theta,
+template <typename K>
+static void bh_moments_t(const float4* pos_s, const K* keys, const bh_nodes& nd, int order, float theta,
+                         int fp64_threshold, int curve, bh_dev_ctrl* ctrl, int grid, cudaStream_t s,
+                         const uint32_t* sys, const float4* sys_box)
+{
+    for (int lev = bh_key_traits<K>::kMaxLevel; lev >= 0; lev--) {
+        if (order >= 2)
+            bh_moments_level_kernel<2, K><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, curve,
+                                                               ctrl, sys, sys_box);
+        else
+            bh_moments_level_kernel<1, K><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, curve,
+                                                               ctrl, sys, sys_box);
+    }
+}
+
+void launch_moments(const float4* pos_s, const void* keys, bool deep, const bh_nodes& nd, int order, float theta,
                     int fp64_threshold, int curve, bh_dev_ctrl* ctrl, int grid, cudaStream_t s, const uint32_t* sys,
                     const float4* sys_box)
 {
-    for (int lev = BH_MAX_LEVEL; lev >= 0; lev--) {
-        if (order >= 2)
-            bh_moments_level_kernel<2><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, curve,
-                                                            ctrl, sys, sys_box);
-        else
-            bh_moments_level_kernel<1><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, curve,
-                                                            ctrl, sys, sys_box);
-    }
+    if (deep)
+        bh_moments_t<bh_key64>(pos_s, (const bh_key64*)keys, nd, order, theta, fp64_threshold, curve, ctrl, grid, s,
+                               sys, sys_box);
+    else
+        bh_moments_t<uint32_t>(pos_s, (const uint32_t*)keys, nd, order, theta, fp64_threshold, curve, ctrl, grid, s,
+                               sys, sys_box);
 }
 
 }  // namespace bh

@@ -20,13 +20,14 @@
 // 32 nodes; all entries above the deepest one touched are consumed, so after
 // a pop the stack holds only levels below those popped, and the pushes of one
 // pop (<= 32 ranges) are the only entries of their levels.  Hence at most 33
-// ranges per level 1..10 are ever stored: kStackCap = 352 cannot overflow
-// (overflow is still checked and reported as BH_ERR_CAPACITY).
+// ranges per level 1..21 are ever stored (21 = the deepest level of 63-bit
+// keys): kStackCap = 704 cannot overflow (overflow is still checked and
+// reported as BH_ERR_CAPACITY).
 #include "bh_mlp.cuh"
 
 namespace bh {
 
-constexpr int kStackCap = 352;
+constexpr int kStackCap = 704;
 constexpr int kRing = 64;   // sources per ring (two tiles of 32), stored as 32 even/odd pairs
 // unroll factors of the per-tile pair loops (tuning constants: larger factors
 // overflow the instruction cache, as every T-slot variant of the loops is
