@@ -316,6 +316,19 @@ __global__ void bh_sph_reset_kernel(bh_dev_ctrl* c)
     c->n_pc = 0ull;
 }
 
+// persistent grid: as many blocks per SM as the registers and shared memory allow
+template <int T>
+static int bh_sph_launch(const SphParams& P, int sm_count, cudaStream_t s)
+{
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, bh_sph_kernel<T>, 128, 0) != cudaSuccess || bps < 1) {
+        cudaGetLastError();
+        bps = 4;
+    }
+    bh_sph_kernel<T><<<sm_count * bps, 128, 0, s>>>(P);
+    return BH_OK;
+}
+
 int launch_sph(const float4* pos_s, const uint32_t* perm, const int32_t* g_first, const int32_t* g_count,
                const bh_nodes& nd, float4* blo, float4* bhi, int G, const float* h, float h_const, int32_t* count,
                float* rho, bh_dev_ctrl* ctrl, int sm_count, int grid, int max_level, cudaStream_t s)
@@ -337,15 +350,13 @@ int launch_sph(const float4* pos_s, const uint32_t* perm, const int32_t* g_first
     P.rho = rho;
     P.ctrl = ctrl;
     const int T = G <= 32 ? 1 : G <= 64 ? 2 : G <= 96 ? 3 : G <= 128 ? 4 : 8;
-    const int blocks = sm_count * 4;
     switch (T) {
-        case 1: bh_sph_kernel<1><<<blocks, 128, 0, s>>>(P); break;
-        case 2: bh_sph_kernel<2><<<blocks, 128, 0, s>>>(P); break;
-        case 3: bh_sph_kernel<3><<<blocks, 128, 0, s>>>(P); break;
-        case 4: bh_sph_kernel<4><<<blocks, 128, 0, s>>>(P); break;
-        default: bh_sph_kernel<8><<<blocks, 128, 0, s>>>(P); break;
+        case 1: return bh_sph_launch<1>(P, sm_count, s);
+        case 2: return bh_sph_launch<2>(P, sm_count, s);
+        case 3: return bh_sph_launch<3>(P, sm_count, s);
+        case 4: return bh_sph_launch<4>(P, sm_count, s);
+        default: return bh_sph_launch<8>(P, sm_count, s);
     }
-    return BH_OK;
 }
 
 }  // namespace bh
