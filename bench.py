@@ -95,6 +95,8 @@ def parse():
                     help="deepest tree level: 10 (30-bit keys) or 21 (63-bit keys)")
     ap.add_argument("--unsoftened-cells", action="store_true",
                     help="particle walk: cells without softening (the Appendix A kernel)")
+    ap.add_argument("--cpu-report", action="store_true",
+                    help="FP64 oracle on the host (1 thread and all threads) against the GPU, N=4096 and N=2^20")
     ap.add_argument("--neighbors", action="store_true",
                     help="neighbour search + SPH density on Plummer spheres (no bench line)")
     ap.add_argument("--accuracy-sweep", action="store_true",
@@ -748,8 +750,67 @@ def run_neighbors(args):
     return 0
 
 
+def run_cpu_report(args):
+    """The FP64 oracle on this machine's host cores against the GPU path, on
+    the small Plummer configuration (N=4096, monopole, theta 0.5, leaf 8,
+    G 64) and on Plummer N=2^20 (quadrupole, theta 0.6, leaf 16, G 96):
+    whole tree evaluations (build + group walk) with one thread and with all
+    threads, the FP64 direct sum on the 4096 seeded targets (one thread: a
+    512-target subset, scaled), and the GPU's whole evaluation.  Prints one
+    JSON object."""
+    import os as _os
+
+    import torch
+
+    import oracle
+    import paper_1112_4539_gb300 as bh
+    bh.lib()
+    cores = oracle.num_threads()
+    rows = []
+    for name, n, theta, order, leaf, G in (("plummer4096", 4096, 0.5, 1, 8, 64),
+                                           ("plummer1m", 1 << 20, 0.6, 2, 16, 96)):
+        pos = workloads.make("plummer", n, 0 if n == 4096 else 1)
+        eps = 0.01
+        row = dict(config=name, n=n, theta=theta, order=order, leaf=leaf, G=G)
+        for threads in (1, cores):
+            oracle.set_threads(threads)
+            t0 = time.perf_counter()
+            res, _ = oracle.tree_force(pos, theta, eps, n_leaf=leaf, G=G, order=order)
+            row["oracle_tree_s_%dthreads" % threads] = time.perf_counter() - t0
+            row["interactions"] = int(res["n_pp"].sum() + res["n_pc"].sum())
+            idx = workloads.sample_targets(n, 4096, seed=101)
+            sub = idx if threads > 1 else idx[:512]
+            t0 = time.perf_counter()
+            oracle.direct(pos, pos[sub], sub.astype(np.int64), eps)
+            row["oracle_direct_4096_s_%dthreads" % threads] = (time.perf_counter() - t0) * idx.size / sub.size
+        oracle.set_threads(cores)
+        x = torch.from_numpy(pos).cuda()
+        ctx = bh.Context(n, leaf_size=leaf, group_size=G, order=order)
+        acc = torch.empty_like(x)
+        for _ in range(3):
+            ctx.evaluate(x, theta, eps, acc)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            ctx.evaluate(x, theta, eps, acc)
+        e1.record()
+        torch.cuda.synchronize()
+        row["gpu_s"] = e0.elapsed_time(e1) / 10 * 1e-3
+        row["gpu_speedup_vs_1thread"] = row["oracle_tree_s_1threads"] / row["gpu_s"]
+        row["gpu_speedup_vs_%dthreads" % cores] = row["oracle_tree_s_%dthreads" % cores] / row["gpu_s"]
+        ctx.close()
+        rows.append(row)
+    print(json.dumps({"cpu_report": "FP64 oracle (group walk, same criterion) vs the GPU path; whole evaluations",
+                      "host_cores": cores, "nproc": _os.cpu_count(), "gpu": torch.cuda.get_device_name(),
+                      "rows": rows}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.cpu_report:
+        return run_cpu_report(args)
     if args.accuracy_sweep:
         return run_accuracy_sweep(args)
     if args.neighbors:
