@@ -109,6 +109,21 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def whole_job(count, ms, world, device):
+    """Whole-job totals of replicas (one independent system per rank): the
+    sum of the counted units over ranks and the slowest rank's time.  A
+    single process returns its own values; otherwise all ranks take part."""
+    if world <= 1:
+        return float(count), float(ms)
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(count)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.SUM)
+    mm = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(mm, op=dist.ReduceOp.MAX)
+    return float(tt.item()), float(mm.item())
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi samples (SM clock and throttle reasons) while running."""
@@ -454,14 +469,7 @@ def run_ours(args, W):
     inter = n_pp + n_pc
     launches = s1["launches"] - s0["launches"]
     # whole job: sum of interactions over ranks / slowest rank
-    tot_inter, max_ms = float(inter), t_ms
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([float(inter)], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        mm = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(mm, op=dist.ReduceOp.MAX)
-        tot_inter, max_ms = float(tt.item()), float(mm.item())
+    tot_inter, max_ms = whole_job(inter, t_ms, world, dev)
     value = tot_inter / (max_ms * 1e-3) / 1e9
 
     # end to end through the public API with host buffers (pinned), copies timed
@@ -488,14 +496,7 @@ def run_ours(args, W):
     sb = ctx.stats()
     e2e_ms = f0.elapsed_time(f1)
     e2e_inter = float((sb["n_pp_total"] - sa["n_pp_total"]) + (sb["n_pc_total"] - sa["n_pc_total"]))
-    e2e_max = e2e_ms
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([e2e_inter], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        mm = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(mm, op=dist.ReduceOp.MAX)
-        e2e_inter, e2e_max = float(tt.item()), float(mm.item())
+    e2e_inter, e2e_max = whole_job(e2e_inter, e2e_ms, world, dev)
     e2e_value = e2e_inter / (e2e_max * 1e-3) / 1e9
 
     # roofline of the dominant kernel (the walk): FP32 CUDA-core arithmetic
@@ -599,14 +600,7 @@ def run_batched(args, W):
     n_pp = s1["n_pp_total"] - s0["n_pp_total"]
     n_pc = s1["n_pc_total"] - s0["n_pc_total"]
     inter = float(n_pp + n_pc)
-    tot_inter, max_ms = inter, t_ms
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([inter], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.SUM)
-        mm = torch.tensor([t_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(mm, op=dist.ReduceOp.MAX)
-        tot_inter, max_ms = float(tt.item()), float(mm.item())
+    tot_inter, max_ms = whole_job(inter, t_ms, world, dev)
     value = tot_inter / (max_ms * 1e-3) / 1e9
     # the per-system loop of plain launches (same configuration)
     single = bh.Context(int(np.max(np.diff(offs))), device=local, order=order, **cfg)
