@@ -2,19 +2,22 @@
 // flow, Sec. 4.4; Fig. 3 / Fig. 5 walk, Eq. 1 interactions, Eq. 2 criterion).
 //
 // The paper walks the tree once per particle with the next/more pointers of
-// Fig. 5.  Here one warp walks the tree once for a whole group of up to 32*T
-// Morton-contiguous particles (the GRAPE-style shared interaction list of
-// Sec. 4.2, built on the device): nodes are tested 32 at a time, one per lane,
-// against the group's bounding box.  A node is accepted when the squared
-// distance from its centre of mass to the box exceeds S_eff (Eq. 2 made
-// conservative for every member) and it holds no group member; accepted
-// nodes become particle-cell sources, rejected leaves contribute their
-// particles as particle-particle sources, other rejected nodes are opened.
+// Fig. 5 (bh_pwalk.cu has that form).  Here one warp walks the tree once for
+// a whole group of up to 32*T key-contiguous particles (the GRAPE-style
+// shared interaction list of Sec. 4.2, built on the device): nodes are tested
+// 32 at a time, one per lane, against the group's bounding box.  A node is
+// accepted when the squared distance from its centre of mass to the box
+// exceeds S_eff (Eq. 2 made conservative for every member) and it holds no
+// group member; accepted nodes become particle-cell sources, rejected leaves
+// contribute their particles as particle-particle sources, other rejected
+// nodes are opened.
 // Sources go through a 64-entry ring in shared memory and are evaluated in
-// tiles of 32: every lane applies each source to its T targets (FP32,
-// rsqrtf), each tile's partial sums are added to the running totals with
-// Kahan compensation.  The group's own particles are applied once, as a
-// masked "self" tile, so the target itself is excluded by index.
+// tiles of 32: every lane applies each source to its T targets in FP32 with
+// rsqrtf, two sources per packed f32x2 instruction; each tile's partial sums
+// are added to the running totals with Kahan compensation.  A target slot
+// holding few targets is split across source phases (see Layout).  The
+// group's own particles are applied once, as a masked "self" tile, so the
+// target itself is excluded by index.
 //
 // Stack bound: entries are ranges of <= 8 sibling nodes.  A pop takes the top
 // 32 nodes; all entries above the deepest one touched are consumed, so after
