@@ -89,6 +89,8 @@ def parse():
     ap.add_argument("--cpu-sample-groups", type=int, default=6000)
     ap.add_argument("--walk", default="group", choices=["group", "particle"],
                     help="group: one warp per particle group; particle: the paper's per-particle walk (Fig. 5)")
+    ap.add_argument("--walk-kernel", default="one-warp", choices=["one-warp", "paired"],
+                    help="group walk kernel: one warp walks and evaluates, or warp pairs (walker + evaluator)")
     ap.add_argument("--curve", default="morton", choices=["morton", "hilbert"],
                     help="particle order (Sec. 5): Morton or Peano-Hilbert keys")
     ap.add_argument("--max-level", type=int, default=10, choices=[10, 21],
@@ -454,8 +456,9 @@ def run_ours(args, W):
     vel = torch.zeros_like(x)
     acc = torch.empty_like(x)
     curve = bh.CURVE_HILBERT if args.curve == "hilbert" else bh.CURVE_MORTON
+    variant = bh.WALK_PAIRED if args.walk_kernel == "paired" else bh.WALK_ONE_WARP
     ctx = bh.Context(n, device=local, leaf_size=leaf, group_size=G, order=order, curve=curve,
-                     max_level=args.max_level)
+                     max_level=args.max_level, walk_variant=variant)
     stream = torch.cuda.current_stream()
 
     # FP64 direct sum on 4096 seeded targets: the error judge
@@ -555,7 +558,8 @@ def run_ours(args, W):
             "warmup": args.warmup, "ms_per_step": max_ms / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": W["desc"], "n": n, "theta": theta, "theta_calibrated": calibrated,
-                       "leaf": leaf, "group": G, "order": order, "walk": walk, "curve": args.curve,
+                       "leaf": leaf, "group": G, "order": order, "walk": walk, "walk_kernel": args.walk_kernel,
+                       "curve": args.curve,
                        "max_level": args.max_level,
                        "unsoftened_cells": uns if walk == "particle" else None,
                        "errors_vs_fp64_direct_4096": errs, "judge_s": t_judge,

@@ -64,7 +64,15 @@ typedef struct bh_config {
     int max_level;           /* deepest tree level: 10 (30-bit keys, default) or 21 (63-bit
                                 keys, uint64 in BH_EXPORT_KEYS); deeper levels split the
                                 dense cells that 10 levels leave as oversized leaves */
+    int walk_variant;        /* tree_force kernel: BH_WALK_ONE_WARP (default: each warp walks
+                                its group and evaluates the tiles it builds) or
+                                BH_WALK_PAIRED (warp pairs: one walks and builds tiles, one
+                                evaluates them; same tiles in the same order, so the same
+                                bits).  The paired kernel serves G <= 96 with the plain
+                                criterion; other cases take the one-warp kernel */
 } bh_config;
+
+enum { BH_WALK_ONE_WARP = 0, BH_WALK_PAIRED = 1 };
 
 #define BH_CURVE_MORTON 0
 #define BH_CURVE_HILBERT 1

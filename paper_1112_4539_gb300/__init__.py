@@ -42,13 +42,15 @@ STATIC_MAX_N = 32768
 PWALK_UNSOFTENED_CELLS = 1
 CURVE_MORTON = 0
 CURVE_HILBERT = 1
+WALK_ONE_WARP = 0
+WALK_PAIRED = 1
 
 
 class BhConfig(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int), ("group_size", ctypes.c_int), ("order", ctypes.c_int),
                 ("fp64_node_threshold", ctypes.c_int), ("block_threads", ctypes.c_int),
                 ("blocks_per_sm", ctypes.c_int), ("max_systems", ctypes.c_int), ("curve", ctypes.c_int),
-                ("max_level", ctypes.c_int)]
+                ("max_level", ctypes.c_int), ("walk_variant", ctypes.c_int)]
 
 
 class BhStats(ctypes.Structure):

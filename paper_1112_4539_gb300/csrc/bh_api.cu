@@ -125,6 +125,7 @@ void bh_config_default(bh_config* cfg)
     cfg->max_systems = 1;
     cfg->curve = BH_CURVE_MORTON;
     cfg->max_level = 10;
+    cfg->walk_variant = BH_WALK_ONE_WARP;
 }
 
 static int validate_config(const bh_config* c)
@@ -138,6 +139,7 @@ static int validate_config(const bh_config* c)
     if (c->max_systems < 0 || c->max_systems > (1 << 20)) return BH_ERR_INVALID;
     if (c->curve != BH_CURVE_MORTON && c->curve != BH_CURVE_HILBERT) return BH_ERR_INVALID;
     if (c->max_level != 10 && c->max_level != 21) return BH_ERR_INVALID;
+    if (c->walk_variant != BH_WALK_ONE_WARP && c->walk_variant != BH_WALK_PAIRED) return BH_ERR_INVALID;
     return BH_OK;
 }
 
@@ -338,7 +340,7 @@ int tree_force(bh_ctx* x, float eps, float* d_acc_pot, void* stream)
     bh::WalkLearned wl{x->mfeat, x->mlp, x->theta};
     int rc = bh::launch_walk(x->pos_s, x->vals, x->g_first, x->g_count, x->nd, x->cfg.order, x->cfg.group_size,
                              eps, (float4*)d_acc_pot, x->ctrl, x->sm_count, x->cfg.block_threads,
-                             x->cfg.blocks_per_sm, s, x->mac_learned ? &wl : nullptr);
+                             x->cfg.blocks_per_sm, s, x->mac_learned ? &wl : nullptr, x->cfg.walk_variant);
     if (rc) return rc;
     x->launches += bh::kLaunchesForce;
     if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
@@ -671,7 +673,8 @@ int bh_force_batched(bh_ctx* x, const float* d_pos_mass, float theta, float eps,
     bh::launch_moments(x->pos_s, x->keys, x->deep, x->nd, x->cfg.order, theta, x->cfg.fp64_node_threshold,
                        x->cfg.curve, x->ctrl, grid_for(x), s, x->sys_of, x->sys_box);
     int rc = bh::launch_walk(x->pos_s, x->vals, x->g_first, x->g_count, x->nd, x->cfg.order, x->cfg.group_size, eps,
-                             (float4*)d_acc_pot, x->ctrl, x->sm_count, x->cfg.block_threads, x->cfg.blocks_per_sm, s);
+                             (float4*)d_acc_pot, x->ctrl, x->sm_count, x->cfg.block_threads, x->cfg.blocks_per_sm, s,
+                             nullptr, x->cfg.walk_variant);
     if (rc) return rc;
     // init, batch sort, 4 tree, 5 groups, moments per level, 2 walk
     x->launches += 2 + 4 + 5 + bh::launches_moments(x->deep) + bh::kLaunchesForce;

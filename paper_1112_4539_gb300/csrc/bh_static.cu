@@ -71,7 +71,8 @@ extern "C" int bh_tree_force_static(const float* d_pos_mass, int64_t n, const bh
         (c.order != 1 && c.order != 2) || c.fp64_node_threshold < 1 ||
         (c.block_threads != 64 && c.block_threads != 128) || c.blocks_per_sm < 0 ||
         c.blocks_per_sm > 32 || (c.curve != BH_CURVE_MORTON && c.curve != BH_CURVE_HILBERT) ||
-        c.max_level != 10)  // the fixed scratch holds 30-bit keys only
+        c.max_level != 10 ||  // the fixed scratch holds 30-bit keys only
+        (c.walk_variant != BH_WALK_ONE_WARP && c.walk_variant != BH_WALK_PAIRED))
         return BH_ERR_INVALID;
     if (n < 0 || !(theta > 0.0f) || !std::isfinite(theta) || !(eps >= 0.0f) || !std::isfinite(eps))
         return BH_ERR_INVALID;
@@ -176,7 +177,7 @@ extern "C" int bh_tree_force_static(const float* d_pos_mass, int64_t n, const bh
                       ctrl, grid, s);
     bh::launch_moments(pos_s, keys, false, nd, c.order, theta, c.fp64_node_threshold, c.curve, ctrl, grid, s);
     int rc = bh::launch_walk(pos_s, vals, g_first, g_count, nd, c.order, c.group_size, eps, (float4*)d_acc_pot, ctrl,
-                             sd.sm_count, c.block_threads, c.blocks_per_sm, s);
+                             sd.sm_count, c.block_threads, c.blocks_per_sm, s, nullptr, c.walk_variant);
     if (rc) return rc;
     if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
     if (h_status) {

@@ -252,8 +252,9 @@ __device__ __forceinline__ void bh_eval_points(const float4* __restrict__ ra, co
 }
 
 // One tile (16 pairs) of quadrupole cells on the first NF slots of every lane.
-template <int T, int NF>
-__device__ __forceinline__ void bh_eval_quads(const WarpQuad& Q, int p0, f2 eps2, const Tgt<T>& X, Acc<T>& A)
+// QC: any staging with the six pair arrays a..f of WarpQuad (pairs p0..p0+15).
+template <int T, int NF, class QC>
+__device__ __forceinline__ void bh_eval_quads(const QC& Q, int p0, f2 eps2, const Tgt<T>& X, Acc<T>& A)
 {
     Part<T> P;
 #pragma unroll
@@ -304,8 +305,8 @@ __device__ __forceinline__ void bh_split_points(const Layout& L, const float4* _
     for (int i = p; i < p + np; i++) bh_pp2(ra[i], rb[i], eps2, x, y, z, ax, ay, az, ap);
     bh_split_add<T>(L, A, bh_split_sum(L, ax), bh_split_sum(L, ay), bh_split_sum(L, az), bh_split_sum(L, ap));
 }
-template <int T>
-__device__ __forceinline__ void bh_split_quads(const Layout& L, const WarpQuad& Q, int p0, f2 eps2, const Tgt<T>& X,
+template <int T, class QC>
+__device__ __forceinline__ void bh_split_quads(const Layout& L, const QC& Q, int p0, f2 eps2, const Tgt<T>& X,
                                                Acc<T>& A)
 {
     f2 x, y, z, ax = make_float2(0.f, 0.f), ay = ax, az = ax, ap = ax, aq = ax;
@@ -331,16 +332,16 @@ __device__ __forceinline__ void bh_points(const Layout& L, const float4* __restr
     else if (L.nf > 0) bh_eval_points<T, T>(ra, rb, eps2, X, A);
     if (L.split) bh_split_points<T>(L, ra, rb, eps2, X, A);
 }
-template <int T>
-__device__ __forceinline__ void bh_quads(const Layout& L, const WarpQuad& Q, int p0, f2 eps2, const Tgt<T>& X,
+template <int T, class QC>
+__device__ __forceinline__ void bh_quads(const Layout& L, const QC& Q, int p0, f2 eps2, const Tgt<T>& X,
                                          Acc<T>& A)
 {
-    if (T > 1 && L.nf == 1) bh_eval_quads<T, 1>(Q, p0, eps2, X, A);
-    else if (T > 2 && L.nf == 2) bh_eval_quads<T, (T > 2 ? 2 : T)>(Q, p0, eps2, X, A);
-    else if (T > 3 && L.nf == 3) bh_eval_quads<T, (T > 3 ? 3 : T)>(Q, p0, eps2, X, A);
-    else if (T > 4 && L.nf == 4) bh_eval_quads<T, (T > 4 ? 4 : T)>(Q, p0, eps2, X, A);
-    else if (L.nf > 0) bh_eval_quads<T, T>(Q, p0, eps2, X, A);
-    if (L.split) bh_split_quads<T>(L, Q, p0, eps2, X, A);
+    if (T > 1 && L.nf == 1) bh_eval_quads<T, 1, QC>(Q, p0, eps2, X, A);
+    else if (T > 2 && L.nf == 2) bh_eval_quads<T, (T > 2 ? 2 : T), QC>(Q, p0, eps2, X, A);
+    else if (T > 3 && L.nf == 3) bh_eval_quads<T, (T > 3 ? 3 : T), QC>(Q, p0, eps2, X, A);
+    else if (T > 4 && L.nf == 4) bh_eval_quads<T, (T > 4 ? 4 : T), QC>(Q, p0, eps2, X, A);
+    else if (L.nf > 0) bh_eval_quads<T, T, QC>(Q, p0, eps2, X, A);
+    if (L.split) bh_split_quads<T, QC>(L, Q, p0, eps2, X, A);
 }
 
 // The group's own particles on its members, target itself masked.
@@ -604,7 +605,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
             // ---- drain: quadrupole tiles, point tiles, particle fills
             if (ORDER >= 2) {
                 while (q_cnt >= 32) {
-                    bh_quads<T>(L, *Q, q_head >> 1, eps2v, X, A);
+                    bh_quads<T, WarpQuad>(L, *Q, q_head >> 1, eps2v, X, A);
                     q_head ^= 32;
                     q_cnt -= 32;
                 }
@@ -651,7 +652,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
                 bh_put_quad(*Q, q_head + lane, bh_pad_source(), make_float4(0.f, 0.f, 0.f, 0.f),
                             make_float4(0.f, 0.f, 0.f, 0.f));
             __syncwarp();
-            bh_quads<T>(L, *Q, q_head >> 1, eps2v, X, A);
+            bh_quads<T, WarpQuad>(L, *Q, q_head >> 1, eps2v, X, A);
         }
         if (ring_cnt > 0) {
             if (lane >= ring_cnt) bh_put_point(S, ring_head + lane, bh_pad_source());
@@ -682,6 +683,427 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
         atomicAdd(&ctrl->cum_pp, cnt_pp);
         atomicAdd(&ctrl->cum_pc, cnt_pc);
     }
+}
+
+// ------------------------------------------------------------ warp-specialised walk
+// The same walk and the same tiles, split between two warps of a pair: the
+// walker warp tests nodes, builds the source tiles and hands each full tile
+// to its evaluator warp through a ring of kWsSlots shared-memory slots; the
+// evaluator holds the group's targets and applies the tiles in the order they
+// were handed over, which is the order of the one-warp kernel, so the results
+// are the same bits.  While an evaluator works through a tile its walker
+// already builds the next ones.  Slots are guarded by mbarriers (one "full",
+// one "empty" per slot, 32 arrivals each); every wait is bounded and gives up
+// with BH_ERR_DEVICE_TIMEOUT.  A block holds four pairs: warps 0-3 walk,
+// warps 4-7 evaluate.
+#ifndef BH_WS_SLOTS
+#define BH_WS_SLOTS 4
+#endif
+constexpr int kWsSlots = BH_WS_SLOTS;
+constexpr int kWsPairs = 4;
+constexpr int kWsSpinLimit = 1 << 24;
+constexpr unsigned long long kWsTimeoutNs = 1000000000ull;
+enum : int { kWsPoints = 0, kWsQuads = 1, kWsBegin = 2, kWsEnd = 3, kWsExit = 4 };
+
+struct WsTile {  // 32 sources as 16 pairs, laid out as WarpSmem (points: a, b) and WarpQuad (cells: a..f)
+    float4 a[16], b[16], c[16], d[16], e[16], f[16];
+};
+struct WsChannel {
+    WsTile tile[kWsSlots];
+    int kind[kWsSlots];
+    int arg[kWsSlots];
+    unsigned long long full[kWsSlots];
+    unsigned long long empty[kWsSlots];
+};
+
+__device__ __forceinline__ unsigned int bh_smem_addr(const void* p)
+{
+    return static_cast<unsigned int>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void bh_mbar_init(unsigned long long* b, unsigned int count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bh_smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bh_mbar_arrive(unsigned long long* b)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bh_smem_addr(b))
+                 : "memory");
+}
+__device__ __forceinline__ bool bh_mbar_try_wait(unsigned long long* b, unsigned int parity)
+{
+    unsigned int ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bh_smem_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+// Wait for the phase of the given parity to complete.  False (with the error
+// recorded) once about a second has passed on the global timer, after
+// kWsSpinLimit polls, or as soon as another warp has aborted.
+__device__ __forceinline__ unsigned long long bh_globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool bh_mbar_wait(unsigned long long* b, unsigned int parity, bh_dev_ctrl* c)
+{
+    if (bh_mbar_try_wait(b, parity)) return true;
+    const unsigned long long t0 = bh_globaltimer();
+    for (int i = 0; i < kWsSpinLimit; i++) {
+        if (bh_mbar_try_wait(b, parity)) return true;
+        if ((i & 63) == 63) {
+            if (*(volatile unsigned int*)&c->abort) return false;
+            if (bh_globaltimer() - t0 > kWsTimeoutNs) break;
+        }
+    }
+    bh_set_error(c, BH_ERR_DEVICE_TIMEOUT);
+    return false;
+}
+
+// Walker side: claim the next slot (waiting until its evaluator has released
+// it), let fill() write the tile, publish it.  False if the wait gave up.
+template <class Fill>
+__device__ __forceinline__ bool bh_ws_send(WsChannel& C, int& item, int kind, int arg, bh_dev_ctrl* ctrl,
+                                           Fill fill)
+{
+    const int s = item % kWsSlots;
+    const unsigned int use = (unsigned int)(item / kWsSlots);
+    const bool ok = bh_mbar_wait(&C.empty[s], (use & 1u) ^ 1u, ctrl);
+    if (__any_sync(BH_FULL_MASK, !ok)) return false;
+    fill(C.tile[s]);
+    if ((threadIdx.x & 31) == 0) {
+        C.kind[s] = kind;
+        C.arg[s] = arg;
+    }
+    __syncwarp();
+    bh_mbar_arrive(&C.full[s]);
+    item++;
+    return true;
+}
+
+template <int T>
+__host__ __device__ constexpr int bh_ws_min_blocks() { return T <= 1 ? 3 : 2; }
+
+template <int T, int ORDER>
+__global__ void __launch_bounds__(256, bh_ws_min_blocks<T>()) bh_walk_ws_kernel(WalkParams P)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int pair = wib & (kWsPairs - 1);
+    const bool walker = wib < kWsPairs;
+    WsChannel& C = reinterpret_cast<WsChannel*>(smem_raw)[pair];
+    unsigned char* base = smem_raw + kWsPairs * sizeof(WsChannel);
+    WarpSmem& S = reinterpret_cast<WarpSmem*>(base)[pair];
+    base += kWsPairs * sizeof(WarpSmem);
+    WarpQuad* Q = nullptr;
+    if (ORDER >= 2) {
+        Q = reinterpret_cast<WarpQuad*>(base) + pair;
+        base += kWsPairs * sizeof(WarpQuad);
+    }
+    float* kcol = reinterpret_cast<float*>(base + (size_t)pair * bh_kahan_smem_bytes<T>()) + lane;
+    if (walker && lane < kWsSlots) {
+        bh_mbar_init(&C.full[lane], 32u);
+        bh_mbar_init(&C.empty[lane], 32u);
+    }
+    __syncthreads();
+
+    const unsigned int lt = bh_lanemask_lt();
+    const float eps2 = P.eps2;
+    bh_dev_ctrl* ctrl = P.ctrl;
+    int item = 0;
+
+    if (walker) {
+        const int ng = (int)ctrl->n_groups;
+        const int n_roots = (int)ctrl->level_offset[1];
+        unsigned long long cnt_pp = 0ull, cnt_pc = 0ull;
+        bool alive = true;
+        auto send_quads = [&](int p0) {
+            return bh_ws_send(C, item, kWsQuads, 0, ctrl, [&](WsTile& t) {
+                if (lane < 16) {
+                    t.a[lane] = Q->a[p0 + lane]; t.b[lane] = Q->b[p0 + lane]; t.c[lane] = Q->c[p0 + lane];
+                    t.d[lane] = Q->d[p0 + lane]; t.e[lane] = Q->e[p0 + lane]; t.f[lane] = Q->f[p0 + lane];
+                }
+            });
+        };
+        auto send_points = [&](int p0) {
+            return bh_ws_send(C, item, kWsPoints, 0, ctrl, [&](WsTile& t) {
+                if (lane < 16) {
+                    t.a[lane] = S.ra[p0 + lane];
+                    t.b[lane] = S.rb[p0 + lane];
+                }
+            });
+        };
+        auto no_tile = [](WsTile&) {};
+        for (;;) {
+            int g = 0;
+            if (lane == 0) g = (int)atomicAdd(&ctrl->group_ctr, 1u);
+            g = __shfl_sync(BH_FULL_MASK, g, 0);
+            if (g >= ng) break;
+            int ab = 0;
+            if (lane == 0) ab = (int)*(volatile unsigned int*)&ctrl->abort;
+            if (__shfl_sync(BH_FULL_MASK, ab, 0)) break;
+            const int gb = P.g_first[g], gc = P.g_count[g], ge = gb + gc;
+            unsigned int lo0 = 0xffffffffu, lo1 = 0xffffffffu, lo2 = 0xffffffffu, hi0 = 0u, hi1 = 0u, hi2 = 0u;
+            for (int o = lane; o < gc; o += 32) {
+                const float4 q = P.pos_s[gb + o];
+                lo0 = min(lo0, bh_f2ord(q.x)); lo1 = min(lo1, bh_f2ord(q.y)); lo2 = min(lo2, bh_f2ord(q.z));
+                hi0 = max(hi0, bh_f2ord(q.x)); hi1 = max(hi1, bh_f2ord(q.y)); hi2 = max(hi2, bh_f2ord(q.z));
+            }
+            const float bx0 = bh_ord2f(__reduce_min_sync(BH_FULL_MASK, lo0));
+            const float by0 = bh_ord2f(__reduce_min_sync(BH_FULL_MASK, lo1));
+            const float bz0 = bh_ord2f(__reduce_min_sync(BH_FULL_MASK, lo2));
+            const float bx1 = bh_ord2f(__reduce_max_sync(BH_FULL_MASK, hi0));
+            const float by1 = bh_ord2f(__reduce_max_sync(BH_FULL_MASK, hi1));
+            const float bz1 = bh_ord2f(__reduce_max_sync(BH_FULL_MASK, hi2));
+            if (!(alive = bh_ws_send(C, item, kWsBegin, g, ctrl, no_tile))) break;
+            cnt_pp += (unsigned long long)gc * (unsigned long long)(gc - 1);
+
+            int sp = 1, ring_head = 0, ring_cnt = 0, q_head = 0, q_cnt = 0;
+            int root = 0;
+            for (int hi = n_roots; hi - root > 1;) {
+                const int mid = (root + hi) >> 1;
+                if (P.rec[mid].x <= gb) root = mid;
+                else hi = mid;
+            }
+            if (lane == 0) S.stack[0] = (uint32_t)root << 3;
+            __syncwarp();
+            bool overflow = false;
+            while (sp > 0 && alive) {
+                int c = 0;
+                uint32_t e = 0u;
+                if (lane < sp) {
+                    e = S.stack[sp - 1 - lane];
+                    c = (int)(e & 7u) + 1;
+                }
+                const int incl = bh_warp_incl_scan(c);
+                const int excl = incl - c;
+                const int take = max(0, min(c, 32 - excl));
+                const int st = (int)(e >> 3);
+                for (int t = 0; t < take; t++) S.staging[excl + t] = (uint32_t)(st + t);
+                const bool full = (lane < sp) && (take == c);
+                const int nfull = __popc(__ballot_sync(BH_FULL_MASK, full));
+                const int npop = min(__shfl_sync(BH_FULL_MASK, incl, 31), 32);
+                __syncwarp();
+                if (lane == nfull && lane < sp && take > 0)
+                    S.stack[sp - 1 - lane] = ((uint32_t)(st + take) << 3) | (uint32_t)(c - take - 1);
+                sp -= nfull;
+                const bool has = lane < npop;
+                const int v = has ? (int)S.staging[lane] : 0;
+                __syncwarp();
+
+                float4 cm = make_float4(0.f, 0.f, 0.f, 0.f);
+                float se = 0.f;
+                int4 r = make_int4(0, 0, -1, 0);
+                if (has) {
+                    cm = P.com_m[v];
+                    se = P.seff[v];
+                    r = P.rec[v];
+                }
+                const float dx = fmaxf(fmaxf(bx0 - cm.x, cm.x - bx1), 0.0f);
+                const float dy = fmaxf(fmaxf(by0 - cm.y, cm.y - by1), 0.0f);
+                const float dz = fmaxf(fmaxf(bz0 - cm.z, cm.z - bz1), 0.0f);
+                const float d2 = dx * dx + dy * dy + dz * dz;
+                const bool member = (r.x < ge) && (r.x + r.y > gb);
+                const bool acc = has && (d2 > se) && !member;
+                const bool leaf = has && !acc && (r.z < 0);
+                const bool opn = has && !acc && (r.z >= 0);
+
+                const unsigned int om = __ballot_sync(BH_FULL_MASK, opn);
+                const int npush = __popc(om);
+                if (sp + npush > kStackCap) {
+                    overflow = true;
+                    break;
+                }
+                if (opn) S.stack[sp + __popc(om & lt)] = ((uint32_t)r.z << 3) | (uint32_t)(r.w - 1);
+                sp += npush;
+
+                const unsigned int am = __ballot_sync(BH_FULL_MASK, acc);
+                const int nacc = __popc(am);
+                cnt_pc += (unsigned long long)nacc * (unsigned long long)gc;
+                if (ORDER >= 2) {
+                    if (acc) {
+                        const int slot = (q_head + q_cnt + __popc(am & lt)) & (kRing - 1);
+                        bh_put_quad(*Q, slot, cm, P.quad[2 * (size_t)v], P.quad[2 * (size_t)v + 1]);
+                    }
+                    q_cnt += nacc;
+                } else {
+                    if (acc) bh_put_point(S, (ring_head + ring_cnt + __popc(am & lt)) & (kRing - 1), cm);
+                    ring_cnt += nacc;
+                }
+
+                const int a0 = r.x, a1 = r.x + r.y;
+                const bool pa = leaf && (a0 < gb);
+                const bool pb = leaf && (a1 > ge);
+                const int pa_n = pa ? (min(a1, gb) - a0) : 0;
+                const int pb_s = max(a0, ge);
+                const int pb_n = pb ? (a1 - pb_s) : 0;
+                const unsigned int ma = __ballot_sync(BH_FULL_MASK, pa), mb = __ballot_sync(BH_FULL_MASK, pb);
+                int lq_n = __popc(ma) + __popc(mb);
+                if (pa) S.leafq[__popc(ma & lt)] = make_int2(a0, pa_n);
+                if (pb) S.leafq[__popc(ma) + __popc(mb & lt)] = make_int2(pb_s, pb_n);
+                cnt_pp += (unsigned long long)__reduce_add_sync(BH_FULL_MASK, (unsigned int)(pa_n + pb_n)) *
+                          (unsigned long long)gc;
+                __syncwarp();
+
+                if (ORDER >= 2) {
+                    while (q_cnt >= 32 && alive) {
+                        __syncwarp();
+                        alive = send_quads(q_head >> 1);
+                        q_head ^= 32;
+                        q_cnt -= 32;
+                    }
+                }
+                int lq_pos = 0;
+                while (alive) {
+                    if (ring_cnt >= 32) {
+                        __syncwarp();
+                        alive = send_points(ring_head >> 1);
+                        ring_head ^= 32;
+                        ring_cnt -= 32;
+                        continue;
+                    }
+                    if (lq_pos >= lq_n) break;
+                    int c2 = 0;
+                    int2 q = make_int2(0, 0);
+                    if (lq_pos + lane < lq_n) {
+                        q = S.leafq[lq_pos + lane];
+                        c2 = q.y;
+                    }
+                    const int inc2 = bh_warp_incl_scan(c2);
+                    const int ex2 = inc2 - c2;
+                    const int take2 = max(0, min(c2, 32 - ex2));
+                    for (int t = 0; t < take2; t++) S.staging[ex2 + t] = (uint32_t)(q.x + t);
+                    const bool full2 = (lq_pos + lane < lq_n) && (take2 == c2);
+                    const int nf2 = __popc(__ballot_sync(BH_FULL_MASK, full2));
+                    const int nfill = min(__shfl_sync(BH_FULL_MASK, inc2, 31), 32);
+                    __syncwarp();
+                    if (lane == nf2 && lq_pos + lane < lq_n && take2 > 0)
+                        S.leafq[lq_pos + lane] = make_int2(q.x + take2, c2 - take2);
+                    lq_pos += nf2;
+                    if (lane < nfill)
+                        bh_put_point(S, (ring_head + ring_cnt + lane) & (kRing - 1), P.pos_s[S.staging[lane]]);
+                    ring_cnt += nfill;
+                    __syncwarp();
+                }
+            }
+            if (!alive) break;
+            if (overflow) {
+                if (lane == 0) bh_set_error(ctrl, BH_ERR_CAPACITY);
+                break;
+            }
+            // flush the partial tiles (padded with far, massless sources), then close the group
+            if (ORDER >= 2 && q_cnt > 0) {
+                if (lane >= q_cnt)
+                    bh_put_quad(*Q, q_head + lane, bh_pad_source(), make_float4(0.f, 0.f, 0.f, 0.f),
+                                make_float4(0.f, 0.f, 0.f, 0.f));
+                __syncwarp();
+                if (!(alive = send_quads(q_head >> 1))) break;
+            }
+            if (ring_cnt > 0) {
+                if (lane >= ring_cnt) bh_put_point(S, ring_head + lane, bh_pad_source());
+                __syncwarp();
+                if (!(alive = send_points(ring_head >> 1))) break;
+            }
+            if (!(alive = bh_ws_send(C, item, kWsEnd, g, ctrl, no_tile))) break;
+        }
+        if (alive) bh_ws_send(C, item, kWsExit, 0, ctrl, no_tile);
+        if (lane == 0) {
+            atomicAdd(&ctrl->n_pp, cnt_pp);
+            atomicAdd(&ctrl->n_pc, cnt_pc);
+            atomicAdd(&ctrl->cum_pp, cnt_pp);
+            atomicAdd(&ctrl->cum_pc, cnt_pc);
+        }
+        return;
+    }
+
+    // ---- evaluator
+    const f2 eps2v = make_float2(eps2, eps2);
+    int gb = 0, gc = 0;
+    Layout L;
+    L.nf = 1; L.split = false; L.lg = 5;
+    float xi[T], yi[T], zi[T], mi[T];
+    Tgt<T> X;
+    Acc<T> A;
+#if BH_KAHAN_SMEM
+    A.kc = kcol;
+#endif
+    for (;;) {
+        const int s = item % kWsSlots;
+        const unsigned int use = (unsigned int)(item / kWsSlots);
+        const bool ok = bh_mbar_wait(&C.full[s], use & 1u, ctrl);
+        if (__any_sync(BH_FULL_MASK, !ok)) break;
+        const int kind = C.kind[s];
+        if (kind == kWsExit) break;
+        if (kind == kWsBegin) {
+            const int g = C.arg[s];
+            gb = P.g_first[g];
+            gc = P.g_count[g];
+            const int tn = (gc + 31) >> 5;
+            const int kl = gc - 32 * (tn - 1);
+            L.split = (T <= 4) && (kl <= kSplitMax);
+            L.nf = L.split ? tn - 1 : tn;
+            L.lg = L.split ? (kl > 1 ? 32 - __clz(kl - 1) : 0) : 5;
+            const int lmask = (1 << L.lg) - 1;
+#pragma unroll
+            for (int t = 0; t < T; t++) {
+                const int o = t * 32 + ((L.split && t == L.nf) ? (lane & lmask) : lane);
+                float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (o < gc) q = P.pos_s[gb + o];
+                xi[t] = q.x; yi[t] = q.y; zi[t] = q.z; mi[t] = q.w;
+            }
+#pragma unroll
+            for (int t = 0; t < T; t++) {
+                A.x[t] = A.y[t] = A.z[t] = A.p[t] = 0.0f;
+                A.c(t, 0) = A.c(t, 1) = A.c(t, 2) = A.c(t, 3) = 0.0f;
+            }
+            bh_eval_self<T>(gc, L, eps2, xi, yi, zi, mi, A);
+#pragma unroll
+            for (int t = 0; t < T; t++) {
+                X.x[t] = make_float2(xi[t], xi[t]);
+                X.y[t] = make_float2(yi[t], yi[t]);
+                X.z[t] = make_float2(zi[t], zi[t]);
+            }
+        } else if (kind == kWsQuads) {
+            if (ORDER >= 2) bh_quads<T, WsTile>(L, C.tile[s], 0, eps2v, X, A);
+        } else if (kind == kWsPoints) {
+            bh_points<T>(L, C.tile[s].a, C.tile[s].b, eps2v, X, A);
+        } else if (kind == kWsEnd) {
+#pragma unroll
+            for (int t = 0; t < T; t++) {
+                float4 f = make_float4(A.x[t] - A.c(t, 0), A.y[t] - A.c(t, 1), A.z[t] - A.c(t, 2), A.p[t] - A.c(t, 3));
+                if (L.split && t == L.nf) {
+                    for (int off = 1 << L.lg; off < 32; off <<= 1) {
+                        f.x += __shfl_xor_sync(BH_FULL_MASK, f.x, off);
+                        f.y += __shfl_xor_sync(BH_FULL_MASK, f.y, off);
+                        f.z += __shfl_xor_sync(BH_FULL_MASK, f.z, off);
+                        f.w += __shfl_xor_sync(BH_FULL_MASK, f.w, off);
+                    }
+                }
+                const int o = t * 32 + lane;
+                if (o < gc) P.out[P.perm[gb + o]] = f;
+            }
+        }
+        __syncwarp();
+        bh_mbar_arrive(&C.empty[s]);
+        item++;
+    }
+}
+
+template <int T, int ORDER>
+static int bh_walk_ws_launch(const WalkParams& P, int sm_count, cudaStream_t s)
+{
+    const size_t smem = kWsPairs * (sizeof(WsChannel) + sizeof(WarpSmem) + (ORDER >= 2 ? sizeof(WarpQuad) : 0) +
+                                    bh_kahan_smem_bytes<T>());
+    auto kern = bh_walk_ws_kernel<T, ORDER>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return BH_ERR_CUDA;
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, 256, smem) != cudaSuccess || bps < 1) bps = 1;
+    kern<<<sm_count * bps, 256, smem, s>>>(P);
+    return BH_OK;
 }
 
 __global__ void bh_walk_reset_kernel(bh_dev_ctrl* c)
@@ -739,7 +1161,7 @@ static int bh_walk_dispatch(const WalkParams& P, int order, int G, int sm_count,
 
 int launch_walk(const float4* pos_s, const uint32_t* perm, const int32_t* g_first, const int32_t* g_count,
                 const bh_nodes& nd, int order, int G, float eps, float4* out, bh_dev_ctrl* ctrl, int sm_count,
-                int block_threads, int blocks_per_sm, cudaStream_t s, const WalkLearned* learned)
+                int block_threads, int blocks_per_sm, cudaStream_t s, const WalkLearned* learned, int walk_variant)
 {
     bh_walk_reset_kernel<<<1, 1, 0, s>>>(ctrl);
     WalkParams P;
@@ -762,6 +1184,21 @@ int launch_walk(const float4* pos_s, const uint32_t* perm, const int32_t* g_firs
         P.mlp = learned->mlp;
         P.theta_guard = learned->theta_guard;
         return bh_walk_dispatch<true>(P, order, G, sm_count, block_threads, blocks_per_sm, s);
+    }
+    if (walk_variant == BH_WALK_PAIRED && G <= 96) {
+        const int T = G <= 32 ? 1 : G <= 64 ? 2 : 3;
+        if (order >= 2) {
+            switch (T) {
+                case 1: return bh_walk_ws_launch<1, 2>(P, sm_count, s);
+                case 2: return bh_walk_ws_launch<2, 2>(P, sm_count, s);
+                default: return bh_walk_ws_launch<3, 2>(P, sm_count, s);
+            }
+        }
+        switch (T) {
+            case 1: return bh_walk_ws_launch<1, 1>(P, sm_count, s);
+            case 2: return bh_walk_ws_launch<2, 1>(P, sm_count, s);
+            default: return bh_walk_ws_launch<3, 1>(P, sm_count, s);
+        }
     }
     return bh_walk_dispatch<false>(P, order, G, sm_count, block_threads, blocks_per_sm, s);
 }
