@@ -335,6 +335,20 @@ int bh_mlp_forward(bh_ctx* ctx, const float* d_params, const float* d_X, int64_t
 int bh_tree_force_static(const float* d_pos_mass, int64_t n, const bh_config* cfg, float theta, float eps,
                          float* d_acc_pot, int* h_status, void* stream);
 
+/* Failure-path self-test: launches one bounded device wait that nothing
+ * will satisfy, of the kind the library's kernels use, so that a deployment
+ * can check that such a wait ends and is reported.
+ *   which = BH_SELFTEST_TILE_RING: the paired walk's mbarrier wait (gives up
+ *           after one second of %globaltimer time or 2^22 polls, whichever
+ *           comes first);
+ *   which = BH_SELFTEST_LOOKBACK:  the sort's decoupled look-back wait
+ *           (gives up after 2^22 polls, well under a second).
+ * Asynchronous on `stream`; afterwards bh_status returns
+ * BH_ERR_DEVICE_TIMEOUT (and clears it) and the context stays usable.
+ * Errors: BH_ERR_INVALID (null context, unknown `which`), BH_ERR_CUDA. */
+enum { BH_SELFTEST_TILE_RING = 0, BH_SELFTEST_LOOKBACK = 1 };
+int bh_selftest_wait(bh_ctx* ctx, int which, void* stream);
+
 /* Synchronise `stream` and return the context's device status as a BH_*
  * code (BH_OK if no device-side error was recorded since the last call;
  * the status is then cleared). */

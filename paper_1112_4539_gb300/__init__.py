@@ -34,7 +34,7 @@ SYMBOLS = ["bh_version", "bh_strerror", "bh_config_default", "bh_create", "bh_de
            "tree_moments", "tree_force", "tree_force_particles", "tree_neighbors", "direct_force", "bh_kick_drift",
            "bh_status", "bh_stats", "bh_export", "bh_tree_force_static", "bh_mac_set", "bh_mac_label",
            "bh_mlp_train", "bh_mlp_grad", "bh_mlp_forward", "bh_batch_layout", "bh_force_batched", "bh_graph_capture_batched",
-           "bh_graph_launch", "bh_graph_destroy"]
+           "bh_graph_launch", "bh_graph_destroy", "bh_selftest_wait"]
 BATCH_MAX_N = 65536
 MLP_NPARAM = 1313
 MLP_ACT = 135  # floats of training scratch per sample
@@ -44,6 +44,8 @@ CURVE_MORTON = 0
 CURVE_HILBERT = 1
 WALK_ONE_WARP = 0
 WALK_PAIRED = 1
+SELFTEST_TILE_RING = 0
+SELFTEST_LOOKBACK = 1
 
 
 class BhConfig(ctypes.Structure):
@@ -135,6 +137,8 @@ def lib():
         L.bh_graph_launch.argtypes = [vp, vp]
         L.bh_graph_launch.restype = i32
         L.bh_graph_destroy.argtypes = [vp]
+        L.bh_selftest_wait.argtypes = [vp, i32, vp]
+        L.bh_selftest_wait.restype = i32
         L.bh_status.argtypes = [vp, vp]
         L.bh_status.restype = i32
         L.bh_stats.argtypes = [vp, vp, ctypes.POINTER(BhStats)]
@@ -303,6 +307,12 @@ class BatchedGraph:
             self.close()
         except Exception:
             pass
+
+
+def bh_selftest_wait(h, which, stream=None):
+    """Launch one bounded device wait that nothing satisfies (SELFTEST_TILE_RING or
+    SELFTEST_LOOKBACK); bh_status reports BH_ERR_DEVICE_TIMEOUT afterwards."""
+    return lib().bh_selftest_wait(h, int(which), _stream(stream))
 
 
 def bh_status(h, stream=None):

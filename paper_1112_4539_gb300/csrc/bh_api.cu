@@ -425,6 +425,18 @@ static int read_ctrl(bh_ctx* x, cudaStream_t s)
     return BH_OK;
 }
 
+int bh_selftest_wait(bh_ctx* x, int which, void* stream)
+{
+    if (!x || (which != BH_SELFTEST_TILE_RING && which != BH_SELFTEST_LOOKBACK)) return BH_ERR_INVALID;
+    DeviceGuard guard(x->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (which == BH_SELFTEST_TILE_RING) bh::launch_selftest_ring(x->ctrl, s);
+    else bh::launch_selftest_lookback(x->ctrl, s);
+    x->launches += 1;
+    if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
+    return BH_OK;
+}
+
 int bh_status(bh_ctx* x, void* stream)
 {
     if (!x) return BH_ERR_INVALID;

@@ -349,6 +349,9 @@ int launch_walk(const float4* pos_s, const uint32_t* perm, const int32_t* g_firs
                 const bh_nodes& nd, int order, int G, float eps, float4* out, bh_dev_ctrl* ctrl,
                 int sm_count, int block_threads, int blocks_per_sm, cudaStream_t s,
                 const WalkLearned* learned = nullptr, int walk_variant = 0);
+// failure-path self-tests: one bounded wait that nothing satisfies
+void launch_selftest_ring(bh_dev_ctrl* c, cudaStream_t s);
+void launch_selftest_lookback(bh_dev_ctrl* c, cudaStream_t s);
 int launch_direct(const float4* src, int n_src, const float4* tgt, const int64_t* self, int n_tgt,
                   double eps, void* out, int precision, cudaStream_t s);
 void launch_kick_drift(float4* pos, float4* vel, const float4* acc, int n, float dt_kick, float dt_drift, int grid,

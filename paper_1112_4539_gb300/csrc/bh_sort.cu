@@ -144,6 +144,21 @@ void launch_keys(const float4* pos, int n, bh_dev_ctrl* ctrl, void* keys, int cu
 constexpr unsigned int kFlagAgg = 1u, kFlagPrefix = 2u;
 constexpr int kSpinLimit = 1 << 22;
 
+// Wait until the look-back word at q belongs to this pass (epoch) and carries
+// a flag.  False after kSpinLimit polls or once another block has aborted.
+__device__ __forceinline__ bool bh_lookback_wait(const volatile unsigned long long* q, unsigned int epoch,
+                                                 const bh_dev_ctrl* c, unsigned long long& st)
+{
+    st = *q;
+    int spins = 0;
+    while ((unsigned int)(st >> 32) != epoch || ((st >> 30) & 3ull) == 0ull) {
+        if (++spins > kSpinLimit || *(const volatile unsigned int*)&c->abort) return false;
+        __nanosleep(32);
+        st = *q;
+    }
+    return true;
+}
+
 __device__ __forceinline__ unsigned long long bh_status_word(unsigned int epoch, unsigned int flag, unsigned int v)
 {
     return ((unsigned long long)epoch << 32) | ((unsigned long long)flag << 30) | (unsigned long long)(v & 0x3fffffffu);
@@ -246,18 +261,11 @@ bh_onesweep_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin, 
         int j = tile - 1;
         bool timed_out = false;
         while (j >= 0) {
-            const volatile unsigned long long* q = lookback + (size_t)j * 256 + d;
-            unsigned long long st = *q;
-            int spins = 0;
-            while ((unsigned int)(st >> 32) != epoch || ((st >> 30) & 3ull) == 0ull) {
-                if (++spins > kSpinLimit || *(volatile unsigned int*)&c->abort) {
-                    timed_out = true;
-                    break;
-                }
-                __nanosleep(32);
-                st = *q;
+            unsigned long long st;
+            if (!bh_lookback_wait(lookback + (size_t)j * 256 + d, epoch, c, st)) {
+                timed_out = true;
+                break;
             }
-            if (timed_out) break;
             prefix += (unsigned int)(st & 0x3fffffffull);
             if (((st >> 30) & 3ull) == kFlagPrefix) break;
             j--;
@@ -335,6 +343,23 @@ void launch_sort(void* keys, void* keys_alt, uint32_t* vals, uint32_t* vals_alt,
     else
         bh_sort_passes<uint32_t, kSortItems>((uint32_t*)keys, (uint32_t*)keys_alt, vals, vals_alt, pos, pos_s, n,
                                              lookback, epoch, ctrl, s);
+}
+
+// Self-test of the failure path: one look-back wait on a word that no block
+// will ever publish.  It gives up after kSpinLimit polls and records
+// BH_ERR_DEVICE_TIMEOUT, as the sort pass would.
+__global__ void bh_selftest_lookback_kernel(bh_dev_ctrl* c)
+{
+    __shared__ unsigned long long word;
+    word = 0ull;  // epoch 0, no flag
+    __syncthreads();
+    unsigned long long st;
+    if (!bh_lookback_wait(&word, 1u, c, st)) bh_set_error(c, BH_ERR_DEVICE_TIMEOUT);
+}
+
+void launch_selftest_lookback(bh_dev_ctrl* c, cudaStream_t s)
+{
+    bh_selftest_lookback_kernel<<<1, 32, 0, s>>>(c);
 }
 
 }  // namespace bh

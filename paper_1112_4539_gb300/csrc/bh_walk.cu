@@ -695,13 +695,16 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
 // already builds the next ones.  Slots are guarded by mbarriers (one "full",
 // one "empty" per slot, 32 arrivals each); every wait is bounded and gives up
 // with BH_ERR_DEVICE_TIMEOUT.  A block holds four pairs: warps 0-3 walk,
-// warps 4-7 evaluate.
+// warps 4-7 evaluate.  On a 16M-particle clumpy set this kernel is slower than
+// the one-warp kernel: there the other warps' evaluation already hides the
+// walk, and two evaluator warps per scheduler issue less of it than four
+// mixed warps.  It is selected only on request (walk_variant).
 #ifndef BH_WS_SLOTS
 #define BH_WS_SLOTS 4
 #endif
 constexpr int kWsSlots = BH_WS_SLOTS;
 constexpr int kWsPairs = 4;
-constexpr int kWsSpinLimit = 1 << 24;
+constexpr int kWsSpinLimit = 1 << 22;
 constexpr unsigned long long kWsTimeoutNs = 1000000000ull;
 enum : int { kWsPoints = 0, kWsQuads = 1, kWsBegin = 2, kWsEnd = 3, kWsExit = 4 };
 
@@ -740,8 +743,9 @@ __device__ __forceinline__ bool bh_mbar_try_wait(unsigned long long* b, unsigned
     return ok != 0u;
 }
 // Wait for the phase of the given parity to complete.  False (with the error
-// recorded) once about a second has passed on the global timer, after
-// kWsSpinLimit polls, or as soon as another warp has aborted.
+// recorded) once a second has passed on the global timer or after
+// kWsSpinLimit polls, whichever comes first; false at once when another warp
+// has aborted.
 __device__ __forceinline__ unsigned long long bh_globaltimer()
 {
     unsigned long long t;
@@ -1104,6 +1108,22 @@ static int bh_walk_ws_launch(const WalkParams& P, int sm_count, cudaStream_t s)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, 256, smem) != cudaSuccess || bps < 1) bps = 1;
     kern<<<sm_count * bps, 256, smem, s>>>(P);
     return BH_OK;
+}
+
+// Self-test of the failure path: one warp waits on a tile-ring mbarrier that
+// nothing will arrive on.  bh_mbar_wait gives up within a second and
+// records BH_ERR_DEVICE_TIMEOUT, as a stalled pair of the paired walk would.
+__global__ void bh_selftest_ring_kernel(bh_dev_ctrl* c)
+{
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) bh_mbar_init(&bar, 32u);
+    __syncthreads();
+    bh_mbar_wait(&bar, 0u, c);
+}
+
+void launch_selftest_ring(bh_dev_ctrl* c, cudaStream_t s)
+{
+    bh_selftest_ring_kernel<<<1, 32, 0, s>>>(c);
 }
 
 __global__ void bh_walk_reset_kernel(bh_dev_ctrl* c)

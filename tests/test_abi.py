@@ -73,6 +73,7 @@ def test_null_context_and_args(L):
     assert L.tree_moments(None, ctypes.c_float(0.5), None) == bh.BH_ERR_INVALID
     assert L.tree_force(None, ctypes.c_float(0.01), None, None) == bh.BH_ERR_INVALID
     assert L.bh_status(None, None) == bh.BH_ERR_INVALID
+    assert L.bh_selftest_wait(None, bh.SELFTEST_TILE_RING, None) == bh.BH_ERR_INVALID
     # direct_force validates sizes, precision and eps before any CUDA call
     assert L.direct_force(None, -1, None, None, 1, 0.0, None, 32, None) == bh.BH_ERR_INVALID
     assert L.direct_force(None, 1, None, None, 1, 0.0, None, 16, None) == bh.BH_ERR_INVALID
