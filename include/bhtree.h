@@ -69,7 +69,9 @@ typedef struct bh_config {
                                 BH_WALK_PAIRED (warp pairs: one walks and builds tiles, one
                                 evaluates them; same tiles in the same order, so the same
                                 bits).  The paired kernel serves G <= 96 with the plain
-                                criterion; other cases take the one-warp kernel */
+                                criterion, in blocks of 256 threads sized by occupancy
+                                (block_threads and blocks_per_sm do not apply to it);
+                                other cases take the one-warp kernel */
 } bh_config;
 
 enum { BH_WALK_ONE_WARP = 0, BH_WALK_PAIRED = 1 };
