@@ -14,22 +14,32 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
 
 
-def _compile(openmp):
-    os.makedirs(OUT_DIR, exist_ok=True)
-    tmp = LIB + ".tmp.%d" % os.getpid()
+def compile_to(src, out, openmp=True):
+    """Compile one oracle source file into the shared library `out`.
+    Returns (ok, compiler messages)."""
+    tmp = out + ".tmp.%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off",
-           "-fno-fast-math", "-Wall", SRC, "-o", tmp, "-lm"]
+           "-fno-fast-math", "-Wall", src, "-o", tmp, "-lm"]
     if openmp:
         cmd.insert(1, "-fopenmp")
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         return False, r.stderr
-    os.replace(tmp, LIB)
+    os.replace(tmp, out)
     return True, ""
 
 
+def _compile(openmp):
+    os.makedirs(OUT_DIR, exist_ok=True)
+    return compile_to(SRC, LIB, openmp)
+
+
 def build(force=False):
-    """Build liboracle.so if it is missing or older than its source."""
+    """Build liboracle.so if it is missing or older than its source.
+    The environment variable ORACLE_LIB names a prebuilt library to use
+    instead (the mutation check of the pins loads planted-mistake copies)."""
+    if os.environ.get("ORACLE_LIB"):
+        return os.environ["ORACLE_LIB"]
     if (not force and os.path.exists(LIB)
             and os.path.getmtime(LIB) >= os.path.getmtime(SRC)):
         return LIB

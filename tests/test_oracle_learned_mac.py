@@ -32,12 +32,20 @@ def test_forward_hand_networks(orc):
 
 
 def test_forward_bf16_emulation(orc):
-    # bfloat16 keeps 8 significant bits: 1 + 2^-9 rounds to 1, 1 + 5*2^-9 to 1 + 2^-7
-    X = np.zeros((2, 6))
-    X[:, 0] = [1 + 2 ** -9, 1 + 5 * 2 ** -9]
+    # bfloat16 keeps 8 significant bits (a unit in the last place of 1 is 2^-7) and
+    # rounds to nearest, ties to even: 1 + 2^-9 -> 1, 1 + 5*2^-9 -> 1 + 2^-7,
+    # 1 + 3*2^-9 -> 1 + 2^-7 (up: truncation would give 1), the ties 1 + 2^-8 -> 1
+    # and 1 + 3*2^-8 -> 1 + 2^-6 (to the even neighbour), and the same for -x
+    v = [1 + 2 ** -9, 1 + 5 * 2 ** -9, 1 + 3 * 2 ** -9, 1 + 2 ** -8, 1 + 3 * 2 ** -8]
+    want = [1.0, 1 + 2 ** -7, 1 + 2 ** -7, 1.0, 1 + 2 ** -6]
     P = _path_net(k=0)
+    X = np.zeros((len(v), 6))
+    X[:, 0] = v
     np.testing.assert_allclose(orc.mlp_forward(P, X, bf16=False), X[:, 0], rtol=0, atol=0)
-    np.testing.assert_allclose(orc.mlp_forward(P, X, bf16=True), [1.0, 1 + 2 ** -7], rtol=0, atol=0)
+    np.testing.assert_allclose(orc.mlp_forward(P, X, bf16=True), want, rtol=0, atol=0)
+    # negative inputs through a negated path: w1 = -1 makes the hidden unit -(-x) = x
+    Pn = _path_net(w1=-1.0, k=0)
+    np.testing.assert_allclose(orc.mlp_forward(Pn, -X, bf16=True), want, rtol=0, atol=0)
 
 
 def test_loss_weights_and_gradient(orc):

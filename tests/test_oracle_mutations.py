@@ -1,0 +1,227 @@
+"""Mutation check of the oracle's pins.
+
+Each entry below plants one plausible mistake in a scratch copy of
+oracle/oracle.c: a dropped term, a wrong sign, index or coefficient, a
+transposed operand, a changed comparison.  The copy is compiled into a
+temporary library, and the pins named beside the mistake run against it in
+a child pytest process (ORACLE_LIB points the oracle package at the copy).
+The check passes only if the child run fails, i.e. some pin catches the
+mistake.  The unmodified source, compiled the same way, must pass every pin
+named here, so a failure of a planted copy is due to its mistake.
+
+Snippets must occur exactly once in the source; when the oracle changes, an
+entry that no longer matches fails loudly instead of testing nothing.
+"""
+import concurrent.futures as cf
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+P = "tests/test_oracle_pins.py::"
+H = "tests/test_oracle_hilbert.py::"
+S = "tests/test_oracle_sph.py::"
+L = "tests/test_oracle_learned_mac.py::"
+
+# name: (snippet, replacement, pins expected to catch it)
+MUTATIONS = {
+    "direct_softening_exponent": (
+        "const double mr3 = m * rinv * rinv * rinv;\n            ax += mr3 * dx;",
+        "const double mr3 = m * rinv * rinv;\n            ax += mr3 * dx;",
+        [P + "test_two_body_closed_form", P + "test_direct_gradient_of_potential"]),
+    "direct_potential_sign": (
+        "            phi -= m * rinv;",
+        "            phi += m * rinv;",
+        [P + "test_two_body_closed_form", P + "test_direct_gradient_of_potential"]),
+    "direct_self_index": (
+        "if (j == skip) continue;",
+        "if (j == skip - 1) continue;",
+        [P + "test_two_body_closed_form", P + "test_direct_momentum_conservation"]),
+    "bbox_degenerate_side": (
+        "if (!(L > 0.0f) || !isfinite(inv)) L = 1.0f;",
+        "(void)inv;",
+        [P + "test_bbox_degenerate"]),
+    "morton_bit_order": (
+        ": (or_spread3(x, nbits) << 2) | (or_spread3(y, nbits) << 1) | or_spread3(z, nbits);",
+        ": (or_spread3(z, nbits) << 2) | (or_spread3(y, nbits) << 1) | or_spread3(x, nbits);",
+        [P + "test_morton_golden", P + "test_morton_random_vs_independent"]),
+    "key_rounding_not_truncation": (
+        "uint32_t ci = (uint32_t)q;",
+        "uint32_t ci = (uint32_t)(q + 0.5f);",
+        [P + "test_morton_golden", P + "test_morton_random_vs_independent"]),
+    "sort_not_stable": (
+        "if (keys[a[j]] < keys[a[i]]) tmp[k++] = a[j++];",
+        "if (keys[a[j]] <= keys[a[i]]) tmp[k++] = a[j++];",
+        [P + "test_sort_matches_numpy_stable"]),
+    "tree_leaf_rule": (
+        "if (count[v] <= n_leaf || l == max_level) {",
+        "if (count[v] < n_leaf || l == max_level) {",
+        [P + "test_tree_matches_definition", P + "test_tree_coincident_particles"]),
+    "s_eff_theta_placement": (
+        "const double t = lside / theta + s;",
+        "const double t = lside * theta + s;",
+        [P + "test_s_eff_hand_example"]),
+    "s_eff_offset_dropped": (
+        "const double t = lside / theta + s;",
+        "const double t = lside / theta;",
+        [P + "test_s_eff_hand_example"]),
+    "moment_cross_term": (
+        "q[4] += m * y0 * y2;",
+        "q[4] += m * y0 * y1;",
+        [P + "test_moments_root_and_parallel_axis", P + "test_multipole_convergence_orders"]),
+    "quadrupole_potential_sign": (
+        "acc[3] -= 0.5 * (3.0 * q * g5 - T * g3);",
+        "acc[3] += 0.5 * (3.0 * q * g5 - T * g3);",
+        [P + "test_quadrupole_gradient", P + "test_quadrupole_textbook_at_zero_softening"]),
+    "quadrupole_coefficient": (
+        "const double c = 1.5 * T * g5 - 7.5 * q * g7;",
+        "const double c = 1.5 * T * g5 - 5.0 * q * g7;",
+        [P + "test_quadrupole_gradient", P + "test_quadrupole_textbook_at_zero_softening"]),
+    "quadrupole_transposed_operand": (
+        "const double Ir1 = qd[3] * rx + qd[1] * ry + qd[5] * rz;",
+        "const double Ir1 = qd[3] * rx + qd[1] * ry + qd[4] * rz;",
+        [P + "test_quadrupole_gradient", P + "test_quadrupole_textbook_at_zero_softening"]),
+    "group_box_distance": (
+        "if (c[a] < lo[a]) t = lo[a] - c[a];\n                else if (c[a] > hi[a]) t = c[a] - hi[a];\n"
+        "                d2 += t * t;\n            }\n            const double S = s_eff[v];\n"
+        "            const int holds_member",
+        "if (c[a] < lo[a]) t = hi[a] - c[a];\n                else if (c[a] > hi[a]) t = c[a] - hi[a];\n"
+        "                d2 += t * t;\n            }\n            const double S = s_eff[v];\n"
+        "            const int holds_member",
+        [P + "test_group_criterion_is_conservative", P + "test_group_walk_follows_the_pinned_lists"]),
+    "group_member_nodes_accepted": (
+        "const int holds_member = first[v] < ge && (int64_t)first[v] + count[v] > gb;\n"
+        "            if (!holds_member) {\n                const double mg",
+        "const int holds_member = 0;\n"
+        "            if (!holds_member) {\n                const double mg",
+        [P + "test_nodes_holding_members_are_opened", P + "test_group_walk_follows_the_pinned_lists"]),
+    "groups_not_greedy": (
+        "if (run_first >= 0 && run_count + count[ch] <= G) {",
+        "if (run_first >= 0 && run_count + count[ch] < G) {",
+        [P + "test_groups_greedy_maximal"]),
+    "hilbert_gray_step_dropped": (
+        "    w[1] ^= w[0];\n    w[2] ^= w[1];\n    uint32_t g = 0;",
+        "    w[1] ^= w[0];\n    uint32_t g = 0;",
+        [H + "test_first_level_is_gray_code", H + "test_level3_curve_is_face_connected"]),
+    "hilbert_reflection_axis": (
+        "w[0] ^= low;                              /* reflect */",
+        "w[1] ^= low;                              /* reflect */",
+        [H + "test_level3_curve_is_face_connected", H + "test_deep_curve_face_connected_and_invertible"]),
+    "hilbert_inverse_axis_order": (
+        "for (int a = 2; a >= 0; a--) {",
+        "for (int a = 0; a < 3; a++) {",
+        [H + "test_deep_curve_face_connected_and_invertible"]),
+    "sph_kernel_coefficient": (
+        "if (q <= 0.5) return c * (1.0 - 6.0 * q * q + 6.0 * q * q * q);",
+        "if (q <= 0.5) return c * (1.0 - 6.0 * q * q + 5.0 * q * q * q);",
+        [S + "test_kernel_normalised_and_continuous"]),
+    "sph_radius_not_strict": (
+        "if (r2 < h2) {",
+        "if (r2 <= h2) {",
+        [S + "test_lattice_counts_and_density"]),
+    "sph_self_term_dropped": (
+        "double r = (double)pos[4 * i + 3] * or_sph_kernel(0.0, hi);",
+        "double r = 0.0;",
+        [S + "test_lattice_counts_and_density"]),
+    "bf16_truncates": (
+        "u += 0x7fffu + lsb;",
+        "u += 0u * lsb;",
+        [L + "test_forward_bf16_emulation"]),
+    "adam_no_bias_correction": (
+        "P[k] -= lr * (m[k] / c1) / (sqrt(v[k] / c2) + eps);",
+        "P[k] -= lr * m[k] / (sqrt(v[k]) + eps);",
+        [L + "test_adam_closed_form"]),
+    "pp_softening_doubled": (
+        "    const double r2 = dx * dx + dy * dy + dz * dz + e2;\n    const double rinv = 1.0 / sqrt(r2);",
+        "    const double r2 = dx * dx + dy * dy + dz * dz + 2.0 * e2;\n    const double rinv = 1.0 / sqrt(r2);",
+        [P + "test_theta_to_zero_equals_direct"]),
+    "particle_walk_self_term": (
+        "if (first[v] != i) {",
+        "if (first[v] != i || 1) {",
+        [P + "test_theta_to_zero_equals_direct"]),
+    "particle_walk_cells_always_softened": (
+        "const double e2c = unsoftened_pc ? 0.0 : e2;",
+        "const double e2c = e2;",
+        [P + "test_particle_walk_unsoftened_cells"]),
+    "com_not_divided_by_mass": (
+        "cx = sx / M;",
+        "cx = sx;",
+        [P + "test_moments_root_and_parallel_axis"]),
+    "cell_centre_off_by_half": (
+        "const double gx = (double)box[0] + (px + 0.5) * lside;",
+        "const double gx = (double)box[0] + px * lside;",
+        [P + "test_s_eff_hand_example"]),
+    "tree_digit_shift": (
+        "const int shift = 3 * (max_level - 1 - l);",
+        "const int shift = 3 * (max_level - l);",
+        [P + "test_tree_matches_definition"]),
+    "groups_chunk_size": (
+        "OR_EMIT(first[ch] + k, (count[ch] - k < G) ? (count[ch] - k) : G);",
+        "OR_EMIT(first[ch] + k, (count[ch] - k < G) ? (count[ch] - k) : G - 1);",
+        [P + "test_groups_cut_oversized_leaves_into_chunks_of_G"]),
+    "feature_group_radius": (
+        "r2 += 0.25 * (hi[a] - lo[a]) * (hi[a] - lo[a]);",
+        "r2 += 0.5 * (hi[a] - lo[a]) * (hi[a] - lo[a]);",
+        [L + "test_features_hand_case"]),
+    "feature_anisotropy_cross_terms": (
+        "sqrt(a0 * a0 + a1 * a1 + a2 * a2 + 2 * (qd[3] * qd[3] + qd[4] * qd[4] + qd[5] * qd[5]))",
+        "sqrt(a0 * a0 + a1 * a1 + a2 * a2 + (qd[3] * qd[3] + qd[4] * qd[4] + qd[5] * qd[5]))",
+        [L + "test_features_hand_case"]),
+    "label_against_total_not_node": (
+        "const double e = sqrt(dx * dx + dy * dy + dz * dz) / a_tot[i];",
+        "const double e = sqrt(dx * dx + dy * dy + dz * dz);",
+        [L + "test_labels_exact_cases"]),
+    "loss_weight_on_wrong_side": (
+        "const double w = (yh < Y[i]) ? under_weight : 1.0;",
+        "const double w = (yh > Y[i]) ? under_weight : 1.0;",
+        [L + "test_loss_weights_and_gradient"]),
+}
+
+
+def _pins(ids):
+    env = dict(os.environ)
+    return subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", "-m", "not gpu"]
+                          + ids, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+
+
+@pytest.fixture(scope="module")
+def mutants(tmp_path_factory):
+    from oracle import build as ob
+    src = open(SRC).read()
+    d = tmp_path_factory.mktemp("oracle_mutants")
+
+    def one(item):
+        name, (old, new, _) = item
+        if name == "_control":
+            text = src
+        else:
+            assert src.count(old) == 1, "snippet of %s occurs %d times" % (name, src.count(old))
+            text = src.replace(old, new)
+        c = d / (name + ".c")
+        c.write_text(text)
+        out = str(d / (name + ".so"))
+        ok, err = ob.compile_to(str(c), out)
+        assert ok, name + ": " + err
+        return name, out
+
+    items = list(MUTATIONS.items()) + [("_control", ("", "", []))]
+    with cf.ThreadPoolExecutor(8) as ex:
+        return dict(ex.map(one, items))
+
+
+def test_unmodified_oracle_passes_the_named_pins(mutants, monkeypatch):
+    ids = sorted({t for _, _, ts in MUTATIONS.values() for t in ts})
+    monkeypatch.setenv("ORACLE_LIB", mutants["_control"])
+    r = _pins(ids)
+    assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-2000:]
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_planted_mistake_fails_a_pin(mutants, monkeypatch, name):
+    monkeypatch.setenv("ORACLE_LIB", mutants[name])
+    r = _pins(MUTATIONS[name][2])
+    assert r.returncode != 0, "no pin caught the planted mistake %r:\n%s" % (name, r.stdout[-2000:])

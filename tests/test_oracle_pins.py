@@ -322,6 +322,24 @@ def test_groups_partition(orc, G):
         assert leaf, (f, c)
 
 
+@pytest.mark.parametrize("n_leaf,G", [(8, 32), (64, 32)])
+def test_groups_cut_oversized_leaves_into_chunks_of_G(orc, n_leaf, G):
+    # a leaf holding more than G particles (a level-10 cell of 200 coincident
+    # particles, or any leaf when n_leaf > G) becomes the groups
+    # [first + kG, first + min((k+1)G, count)), k = 0, 1, ...
+    knot = np.concatenate([np.full((200, 3), 0.3), np.full((200, 1), 1e-4)], 1)
+    p = np.concatenate([workloads.clumpy(3000, seed=20), knot]).astype(np.float32)
+    box, perm, sk, sp, t, m = _built(orc, p, n_leaf=n_leaf)
+    gf, gc = orc.groups(t, G)
+    groups = set(zip(gf.tolist(), gc.tolist()))
+    big = [v for v in range(t.n_nodes) if t.nchild[v] == 0 and t.count[v] > G]
+    assert big
+    for v in big:
+        f, c = int(t.first[v]), int(t.count[v])
+        for k in range(0, c, G):
+            assert (f + k, min(G, c - k)) in groups, (v, k)
+
+
 def test_groups_greedy_maximal(orc):
     p = workloads.plummer(5000, seed=10)
     box, perm, sk, sp, t, m = _built(orc, p, n_leaf=8)
@@ -515,6 +533,25 @@ def test_nodes_holding_members_are_opened(orc):
     res, _ = orc.tree_force(p, 1.0, 0.01, walk="particle")
     ea, _ = orc.rel_err(res["out"], d)
     assert np.isfinite(ea).all() and ea.mean() < 0.05
+
+
+@pytest.mark.parametrize("theta", [0.6, 1.0, 2.0])
+def test_group_walk_follows_the_pinned_lists(orc, theta):
+    # The force walk decides acceptance in its own loop; its per-target counts
+    # must be those of the accepted-node and opened-leaf lists that the tests
+    # above pin (conservative criterion, exact coverage, member-holding nodes
+    # opened): n_pc = accepted nodes, n_pp = particles of opened leaves minus
+    # the target itself.  Above theta = 1/sqrt(3) Eq. (2) alone can accept a
+    # node holding members; at theta = 2 it does so for many groups.
+    p = workloads.clumpy(4000, seed=14)
+    res, b = orc.tree_force(p, theta, 0.01, n_leaf=8, G=32, order=2, walk="group")
+    t = b.tree
+    for g in range(b.g_first.shape[0]):
+        gb, gc = int(b.g_first[g]), int(b.g_count[g])
+        pc, pp = orc.group_lists(b.spos, t, b.mom, gb, gc)
+        o = b.perm[gb:gb + gc]
+        assert (res["n_pc"][o] == len(pc)).all()
+        assert (res["n_pp"][o] == int(t.count[pp].sum()) - 1).all()
 
 
 def test_term_magnitude_sum(orc):
