@@ -141,10 +141,14 @@ def test_learned_walk_limits(orc):
     always[-1] = -100.0
     never = np.zeros(NP)
     never[-1] = 100.0
-    ref = orc.force_groups(b.spos, b.perm, b.tree, b.mom, b.g_first, b.g_count, eps)
-    r = orc.force_groups_learned(b, always, fmin, fmax, 1e-3, eps, tg, tfb)
-    np.testing.assert_allclose(r["out"], ref["out"], rtol=1e-13, atol=0)
-    np.testing.assert_array_equal(r["n_pc"], ref["n_pc"])
+    # always-accept: the guard's plain group walk, also at a guard theta of 4,
+    # where Eq. (2) alone would accept many nodes that hold group members
+    for tgx in (tg, 4.0):
+        bx = orc.Built(pos, 8, 64, tgx, 2)
+        ref = orc.force_groups(bx.spos, bx.perm, bx.tree, bx.mom, bx.g_first, bx.g_count, eps)
+        r = orc.force_groups_learned(bx, always, fmin, fmax, 1e-3, eps, tgx, tfb)
+        np.testing.assert_allclose(r["out"], ref["out"], rtol=1e-13, atol=0)
+        np.testing.assert_array_equal(r["n_pc"], ref["n_pc"])
     r = orc.force_groups_learned(b, never, fmin, fmax, 1e-3, eps, tg, tfb)
     d = orc.direct(pos, eps=eps)
     ea, ep = orc.rel_err(r["out"], d)

@@ -175,6 +175,34 @@ MUTATIONS = {
         "const double e = sqrt(dx * dx + dy * dy + dz * dz) / a_tot[i];",
         "const double e = sqrt(dx * dx + dy * dy + dz * dz);",
         [L + "test_labels_exact_cases"]),
+    "deep_key_scale": (
+        "const float inv = (1024.0f / box[3]) * (float)(1u << (max_level - 10));",
+        "const float inv = (1024.0f / box[3]) * (float)(1u << (max_level - 11));",
+        [P + "test_deep_keys_extend_shallow_keys", P + "test_deep_keys_hand_corners"]),
+    "cell_centre_axes_swapped": (
+        "const double px = cell[0] >> (max_level - l), py = cell[1] >> (max_level - l),",
+        "const double px = cell[1] >> (max_level - l), py = cell[0] >> (max_level - l),",
+        [P + "test_s_eff_hand_example", H + "test_same_octree_for_both_orders"]),
+    "sph_kernel_outer_piece": (
+        "if (q <= 1.0) return c * 2.0 * (1.0 - q) * (1.0 - q) * (1.0 - q);",
+        "if (q <= 1.0) return c * 2.0 * (1.0 - q) * (1.0 - q);",
+        [S + "test_kernel_normalised_and_continuous"]),
+    "term_magnitude_distance_dropped": (
+        "acc[4] += fabs(mr3) * sqrt(dx * dx + dy * dy + dz * dz);",
+        "acc[4] += fabs(mr3);",
+        [P + "test_term_magnitude_sum"]),
+    "learned_network_decision_inverted": (
+        "accept = yh < ltau;",
+        "accept = yh > ltau;",
+        [L + "test_learned_walk_limits"]),
+    "learned_fallback_theta": (
+        "const double t = side[v] / theta_fb + (s > 0 ? s : 0);",
+        "const double t = side[v] / theta_guard + (s > 0 ? s : 0);",
+        [L + "test_learned_walk_limits"]),
+    "learned_guard_ignores_members": (
+        "const int member = first[v] < ge && (int64_t)first[v] + count[v] > gb;\n            int accept = 0;",
+        "const int member = 0;\n            int accept = 0;",
+        [L + "test_learned_walk_limits"]),
     "loss_weight_on_wrong_side": (
         "const double w = (yh < Y[i]) ? under_weight : 1.0;",
         "const double w = (yh > Y[i]) ? under_weight : 1.0;",

@@ -271,7 +271,11 @@ def test_s_eff_hand_example(orc):
     # cell [0,2]^3 holds both: centre (1,1,1), COM (0.75,0.5,0.5),
     # s = sqrt(0.0625 + 0.25 + 0.25) = 0.75, l = 2, theta = 0.5:
     # S_eff = (2/0.5 + 0.75)^2 = 22.5625.  A far particle at (4,4,4) fixes L = 4.
-    p = np.array([[0.5, 0.5, 0.5, 3.0], [1.5, 0.5, 0.5, 1.0], [4.0, 4.0, 4.0, 1.0]], np.float32)
+    # The level-1 cell [2,4]x[0,2]x[0,2] (cell coordinates (1,0,0), centre
+    # (3,1,1)) holds (2.5,0.5,0.5) and (3.5,1.5,0.5), m = 1: COM (3,1,0.5),
+    # s = 0.5, S_eff = (4 + 0.5)^2 = 20.25; its centre tells the axes apart.
+    p = np.array([[0.5, 0.5, 0.5, 3.0], [1.5, 0.5, 0.5, 1.0], [4.0, 4.0, 4.0, 1.0],
+                  [2.5, 0.5, 0.5, 1.0], [3.5, 1.5, 0.5, 1.0]], np.float32)
     p0 = np.array([[0.0, 0.0, 0.0, 0.0]], np.float32)
     p = np.concatenate([p0, p])  # massless particle at the origin fixes xmin = 0
     box, perm, sk, sp, t, m = _built(orc, p, n_leaf=1, theta=0.5)
@@ -280,8 +284,11 @@ def test_s_eff_hand_example(orc):
     np.testing.assert_allclose(m.com_m[v], [0.75, 0.5, 0.5, 4.0], rtol=1e-15)
     assert abs(m.side[v] - 2.0) < 1e-15
     assert abs(m.s_eff[v] - 22.5625) < 1e-12
-    # root: l = 4, centre (2,2,2), COM = (0.5*3+1.5+4, 0.5*3+0.5+4, same)/5
-    com0 = np.array([7.0, 6.0, 6.0]) / 5.0
+    v2 = [i for i in range(t.n_nodes) if t.level[i] == 1 and t.count[i] == 2][0]
+    np.testing.assert_allclose(m.com_m[v2], [3.0, 1.0, 0.5, 2.0], rtol=1e-15)
+    assert abs(m.s_eff[v2] - 20.25) < 1e-12
+    # root: l = 4, centre (2,2,2), COM = (1.5+1.5+4+2.5+3.5, 1.5+0.5+4+0.5+1.5, 1.5+0.5+4+0.5+0.5)/7
+    com0 = np.array([13.0, 8.0, 7.0]) / 7.0
     s0 = np.linalg.norm(com0 - 2.0)
     assert abs(m.s_eff[0] - (4 / 0.5 + s0) ** 2) < 1e-12
 
