@@ -749,7 +749,7 @@ def run_neighbors(args):
     import paper_1112_4539_gb300 as bh
     bh.lib()
     rows = []
-    for n, G, leaf in ((1 << 20, 64, 16), (1 << 20, 32, 16), (1 << 24, 64, 16)):
+    for n, G, leaf in ((1 << 20, 64, 16), (1 << 20, 32, 16), (1 << 24, 64, 16), (1 << 24, 32, 16)):
         pos = workloads.make("plummer", n, 1)
         x = torch.from_numpy(pos).cuda()
         h = torch.from_numpy(workloads.plummer_search_radii(pos, 64).astype(np.float32)).cuda()
