@@ -377,16 +377,23 @@ void mlp_pack(const float* P, const float* fmin, const float* fmax, float ltau, 
 {
     std::memset(out, 0, sizeof(*out));
     auto pack = [](float lo, float hi) { return (uint32_t)bf16_bits(lo) | ((uint32_t)bf16_bits(hi) << 16); };
+    // word w of a row of K = 32 holds k = 2w, 2w + 1; k-step s, lane t of the
+    // quad takes words 8s + t and 8s + t + 4
+    auto word32 = [&](int off, int w) { return pack(P[off + 2 * w], P[off + 2 * w + 1]); };
     for (int j = 0; j < 32; j++) {
-        for (int w = 0; w < 8; w++) {
+        for (int w = 0; w < 4; w++) {
             const int k0 = 2 * w, k1 = 2 * w + 1;
             out->w1[j][w] = pack(k0 < BH_MLP_NF ? P[j * BH_MLP_NF + k0] : 0.f, k1 < BH_MLP_NF ? P[j * BH_MLP_NF + k1] : 0.f);
         }
-        for (int w = 0; w < 16; w++) out->w2[j][w] = pack(P[kOffW2 + j * 32 + 2 * w], P[kOffW2 + j * 32 + 2 * w + 1]);
+        for (int ks = 0; ks < 2; ks++)
+            for (int t = 0; t < 4; t++)
+                out->w2[j][ks][t] = make_uint2(word32(kOffW2 + j * 32, 8 * ks + t), word32(kOffW2 + j * 32, 8 * ks + t + 4));
         out->b1[j] = P[kOffB1 + j];
         out->b2[j] = P[kOffB2 + j];
     }
-    for (int w = 0; w < 16; w++) out->w3[0][w] = pack(P[kOffW3 + 2 * w], P[kOffW3 + 2 * w + 1]);
+    for (int ks = 0; ks < 2; ks++)
+        for (int t = 0; t < 4; t++)
+            out->w3[0][ks][t] = make_uint2(word32(kOffW3, 8 * ks + t), word32(kOffW3, 8 * ks + t + 4));
     out->b3[0] = P[kOffB3];
     for (int k = 0; k < 8; k++) {
         out->fmin[k] = k < BH_MLP_NF ? fmin[k] : -INFINITY;
