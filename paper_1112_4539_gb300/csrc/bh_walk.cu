@@ -48,6 +48,7 @@ constexpr int kQuadUnroll = BH_QUAD_UNROLL;
 // side) so that the interaction arithmetic runs on packed f32x2 operations:
 // one instruction computes the same step for two sources.
 struct WarpSmem {
+    float gbox[8];              // the group's box: xmin, ymin, zmin, radius, xmax, ymax, zmax, -
     uint32_t stack[kStackCap];  // (first node << 3) | (count - 1)
     uint32_t staging[32];
     int2 leafq[64];             // pending particle ranges (first, count)
@@ -394,6 +395,19 @@ __device__ __forceinline__ void bh_eval_self(int gc, const Layout& L, float eps2
 
 __device__ __forceinline__ float4 bh_pad_source() { return make_float4(1e18f, 1e18f, 1e18f, 0.0f); }
 
+// The group box is read from shared memory at every batch of node tests
+// rather than held in six registers across the walk: the tile loops of the
+// three-slot kernel are at the register limit.  The load is explicit so that
+// the compiler does not hoist it back into registers.
+__device__ __forceinline__ float4 bh_lds4(const float* p)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(static_cast<unsigned int>(__cvta_generic_to_shared(p))));
+    return v;
+}
+
 // resident blocks of 128 threads per SM (register budget 65536 / (128 * b))
 #ifndef BH_WALK_MINB3
 #define BH_WALK_MINB3 4
@@ -466,15 +480,23 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
             }
             xi[t] = q.x; yi[t] = q.y; zi[t] = q.z; mi[t] = q.w;
         }
-        const float bx0 = bh_ord2f(__reduce_min_sync(BH_FULL_MASK, lo0));
-        const float by0 = bh_ord2f(__reduce_min_sync(BH_FULL_MASK, lo1));
-        const float bz0 = bh_ord2f(__reduce_min_sync(BH_FULL_MASK, lo2));
-        const float bx1 = bh_ord2f(__reduce_max_sync(BH_FULL_MASK, hi0));
-        const float by1 = bh_ord2f(__reduce_max_sync(BH_FULL_MASK, hi1));
-        const float bz1 = bh_ord2f(__reduce_max_sync(BH_FULL_MASK, hi2));
-        // group centre and radius (features of the learned criterion)
-        const float gcx = 0.5f * (bx0 + bx1), gcy = 0.5f * (by0 + by1), gcz = 0.5f * (bz0 + bz1);
-        const float grg = 0.5f * sqrtf((bx1 - bx0) * (bx1 - bx0) + (by1 - by0) * (by1 - by0) + (bz1 - bz0) * (bz1 - bz0));
+        {
+            const float bx0 = bh_ord2f(__reduce_min_sync(BH_FULL_MASK, lo0));
+            const float by0 = bh_ord2f(__reduce_min_sync(BH_FULL_MASK, lo1));
+            const float bz0 = bh_ord2f(__reduce_min_sync(BH_FULL_MASK, lo2));
+            const float bx1 = bh_ord2f(__reduce_max_sync(BH_FULL_MASK, hi0));
+            const float by1 = bh_ord2f(__reduce_max_sync(BH_FULL_MASK, hi1));
+            const float bz1 = bh_ord2f(__reduce_max_sync(BH_FULL_MASK, hi2));
+            if (lane == 0) {
+                S.gbox[0] = bx0; S.gbox[1] = by0; S.gbox[2] = bz0;
+                S.gbox[4] = bx1; S.gbox[5] = by1; S.gbox[6] = bz1;
+                // half diagonal (a feature of the learned criterion)
+                S.gbox[3] = LEARNED ? 0.5f * sqrtf((bx1 - bx0) * (bx1 - bx0) + (by1 - by0) * (by1 - by0) +
+                                                   (bz1 - bz0) * (bz1 - bz0))
+                                    : 0.0f;
+            }
+            __syncwarp();
+        }
 
         Acc<T> A;
 #if BH_KAHAN_SMEM
@@ -541,6 +563,8 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
                 se = P.seff[v];
                 r = P.rec[v];
             }
+            const float4 gb0 = bh_lds4(S.gbox), gb1 = bh_lds4(S.gbox + 4);
+            const float bx0 = gb0.x, by0 = gb0.y, bz0 = gb0.z, bx1 = gb1.x, by1 = gb1.y, bz1 = gb1.z;
             const float dx = fmaxf(fmaxf(bx0 - cm.x, cm.x - bx1), 0.0f);
             const float dy = fmaxf(fmaxf(by0 - cm.y, cm.y - by1), 0.0f);
             const float dz = fmaxf(fmaxf(bz0 - cm.z, cm.z - bz1), 0.0f);
@@ -550,6 +574,9 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
             if (LEARNED && __ballot_sync(BH_FULL_MASK, acc)) {
                 // the guard passed: the network decides (the plain criterion at
                 // theta_fb when a feature lies outside the training range)
+                // group centre and radius (features of the learned criterion)
+                const float gcx = 0.5f * (bx0 + bx1), gcy = 0.5f * (by0 + by1), gcz = 0.5f * (bz0 + bz1);
+                const float grg = gb0.w;
                 const float4 nf = has ? P.mfeat[v] : make_float4(0.f, 0.f, 0.f, 0.f);
                 float f[BH_MLP_NF], side;
                 bool inr = bh_mac_features(cm, nf, gcx, gcy, gcz, grg, boxL, f, side);
