@@ -49,6 +49,7 @@ constexpr int kQuadUnroll = BH_QUAD_UNROLL;
 // one instruction computes the same step for two sources.
 struct WarpSmem {
     float gbox[8];              // the group's box: xmin, ymin, zmin, radius, xmax, ymax, zmax, -
+    unsigned long long tot[2];  // interactions so far: particle-particle, particle-cell
     uint32_t stack[kStackCap];  // (first node << 3) | (count - 1)
     uint32_t staging[32];
     int2 leafq[64];             // pending particle ranges (first, count)
@@ -446,7 +447,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
     const int ng = (int)ctrl->n_groups;
     const int n_roots = (int)ctrl->level_offset[1];
     const float boxL = LEARNED ? ctrl->box[3] : 1.0f;
-    unsigned long long cnt_pp = 0ull, cnt_pc = 0ull;
+    if (lane == 0) S.tot[0] = S.tot[1] = 0ull;
 
     for (;;) {
         int g = 0;
@@ -516,7 +517,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
             X.z[t] = make_float2(zi[t], zi[t]);
         }
         const f2 eps2v = make_float2(eps2, eps2);
-        cnt_pp += (unsigned long long)gc * (unsigned long long)(gc - 1);
+        unsigned int g_pc = 0u, g_pp = 0u;  // accepted nodes, particles of opened leaves
 
         int sp = 1, ring_head = 0, ring_cnt = 0, q_head = 0, q_cnt = 0;
         // root of the group's system: the last level-0 node starting at or before gb
@@ -602,7 +603,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
             // ---- accept: cell sources
             const unsigned int am = __ballot_sync(BH_FULL_MASK, acc);
             const int nacc = __popc(am);
-            cnt_pc += (unsigned long long)nacc * (unsigned long long)gc;
+            g_pc += (unsigned int)nacc;
             if (ORDER >= 2) {
                 if (acc) {
                     const int slot = (q_head + q_cnt + __popc(am & lt)) & (kRing - 1);
@@ -625,8 +626,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
             int lq_n = __popc(ma) + __popc(mb);
             if (pa) S.leafq[__popc(ma & lt)] = make_int2(a0, pa_n);
             if (pb) S.leafq[__popc(ma) + __popc(mb & lt)] = make_int2(pb_s, pb_n);
-            cnt_pp += (unsigned long long)__reduce_add_sync(BH_FULL_MASK, (unsigned int)(pa_n + pb_n)) *
-                      (unsigned long long)gc;
+            g_pp += __reduce_add_sync(BH_FULL_MASK, (unsigned int)(pa_n + pb_n));
             __syncwarp();
 
             // ---- drain: quadrupole tiles, point tiles, particle fills
@@ -673,6 +673,10 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
             if (lane == 0) bh_set_error(ctrl, BH_ERR_CAPACITY);
             break;
         }
+        if (lane == 0) {
+            S.tot[0] += ((unsigned long long)g_pp + (unsigned long long)(gc - 1)) * (unsigned long long)gc;
+            S.tot[1] += (unsigned long long)g_pc * (unsigned long long)gc;
+        }
         // ---- flush the partial tiles (padded with far, massless sources)
         if (ORDER >= 2 && q_cnt > 0) {
             if (lane >= q_cnt)
@@ -705,6 +709,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
         }
     }
     if (lane == 0) {
+        const unsigned long long cnt_pp = S.tot[0], cnt_pc = S.tot[1];
         atomicAdd(&ctrl->n_pp, cnt_pp);
         atomicAdd(&ctrl->n_pc, cnt_pc);
         atomicAdd(&ctrl->cum_pp, cnt_pp);
