@@ -211,6 +211,32 @@ def test_learned_walk_limits_vs_oracle(bh, orc):
     ctx.close()
 
 
+@pytest.mark.parametrize("curve,max_level,tg", [(0, 10, 4.0), (1, 21, 1.0), (1, 21, 4.0)])
+def test_learned_always_accept_equals_plain_walk(bh, curve, max_level, tg):
+    # A network that accepts everything in range leaves the guard alone: the
+    # learned kernel must then give the plain walk's bits at the guard's
+    # theta, for both orders and 63-bit keys.  At theta = 4 Eq. (2) alone would
+    # accept many nodes that hold group members; neither kernel may.
+    rng = np.random.default_rng(43)
+    knot = np.concatenate([0.3 + 1e-4 * rng.random((300, 3)), np.full((300, 1), 1.0 / 20000)], 1)
+    pos = np.concatenate([workloads.clumpy(19700, seed=43), knot]).astype(np.float32)
+    x = _cuda(pos)
+    eps = 1e-3
+    ctx = bh.Context(pos.shape[0], leaf_size=8, group_size=64, order=2, curve=curve, max_level=max_level)
+    plain = ctx.evaluate(x, tg, eps).cpu().numpy()
+    assert ctx.status() == 0
+    st0 = ctx.stats()
+    always = np.zeros(NP, np.float32)
+    always[-1] = -100.0
+    assert bh.bh_mac_set(ctx.h, always, np.full(6, -1e9, np.float32), np.full(6, 1e9, np.float32), 1e-3, 0.5) == 0
+    got = ctx.evaluate(x, tg, eps).cpu().numpy()
+    assert ctx.status() == 0
+    st1 = ctx.stats()
+    np.testing.assert_array_equal(got, plain)
+    assert (st1["n_pp"], st1["n_pc"]) == (st0["n_pp"], st0["n_pc"])
+    ctx.close()
+
+
 def test_learned_walk_trained_network_vs_oracle(bh, orc):
     # A trained network takes many decisions next to the threshold, where the
     # tensor-core prediction and the oracle's bfloat16 emulation may differ by
