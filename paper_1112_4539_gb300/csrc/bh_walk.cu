@@ -32,16 +32,21 @@ namespace bh {
 
 constexpr int kStackCap = 704;
 constexpr int kRing = 64;   // sources per ring (two tiles of 32), stored as 32 even/odd pairs
-// unroll factors of the per-tile pair loops (tuning constants: larger factors
-// overflow the instruction cache, as every T-slot variant of the loops is
-// live at once across the SM's warps)
+// unroll factors of the per-tile pair loops (tuning constants, measured:
+// larger factors overflow the instruction cache, as every T-slot variant of
+// the loops is live at once across the SM's warps)
 #ifndef BH_POINT_UNROLL
-#define BH_POINT_UNROLL 2
+#define BH_POINT_UNROLL 4          // plain criterion (the learned walk's larger code keeps 2)
+#endif
+#ifndef BH_POINT_UNROLL_LEARNED
+#define BH_POINT_UNROLL_LEARNED 2
 #endif
 #ifndef BH_QUAD_UNROLL
 #define BH_QUAD_UNROLL 1
 #endif
 constexpr int kPointUnroll = BH_POINT_UNROLL;
+constexpr int kPointUnrollLearned = BH_POINT_UNROLL_LEARNED;
+constexpr int kPointUnrollPaired = 2;
 constexpr int kQuadUnroll = BH_QUAD_UNROLL;
 
 // Sources are staged negated and as pairs (ring positions 2p, 2p+1 side by
@@ -236,15 +241,16 @@ struct Tgt {
     f2 x[T], y[T], z[T];
 };
 
-// One tile (16 pairs) of point sources on the first NF slots of every lane.
-template <int T, int NF>
+// One tile (16 pairs) of point sources on the first NF slots of every lane,
+// the pair loop unrolled PU times.
+template <int T, int NF, int PU>
 __device__ __forceinline__ void bh_eval_points(const float4* __restrict__ ra, const float4* __restrict__ rb,
                                                f2 eps2, const Tgt<T>& X, Acc<T>& A)
 {
     Part<T> P;
 #pragma unroll
     for (int t = 0; t < NF; t++) P.x[t] = P.y[t] = P.z[t] = P.p[t] = make_float2(0.f, 0.f);
-#pragma unroll kPointUnroll
+#pragma unroll PU
     for (int j = 0; j < 16; j++) {
         const float4 sa = ra[j], sb = rb[j];
 #pragma unroll
@@ -323,15 +329,15 @@ __device__ __forceinline__ void bh_split_quads(const Layout& L, const QC& Q, int
 // Dispatch on the warp-uniform layout.  Every bh_eval_* instance is reached
 // from one call site only (they are inlined: a second site would double the
 // code of the hottest loop).
-template <int T>
+template <int T, int PU = kPointUnroll>
 __device__ __forceinline__ void bh_points(const Layout& L, const float4* __restrict__ ra,
                                           const float4* __restrict__ rb, f2 eps2, const Tgt<T>& X, Acc<T>& A)
 {
-    if (T > 1 && L.nf == 1) bh_eval_points<T, 1>(ra, rb, eps2, X, A);
-    else if (T > 2 && L.nf == 2) bh_eval_points<T, (T > 2 ? 2 : T)>(ra, rb, eps2, X, A);
-    else if (T > 3 && L.nf == 3) bh_eval_points<T, (T > 3 ? 3 : T)>(ra, rb, eps2, X, A);
-    else if (T > 4 && L.nf == 4) bh_eval_points<T, (T > 4 ? 4 : T)>(ra, rb, eps2, X, A);
-    else if (L.nf > 0) bh_eval_points<T, T>(ra, rb, eps2, X, A);
+    if (T > 1 && L.nf == 1) bh_eval_points<T, 1, PU>(ra, rb, eps2, X, A);
+    else if (T > 2 && L.nf == 2) bh_eval_points<T, (T > 2 ? 2 : T), PU>(ra, rb, eps2, X, A);
+    else if (T > 3 && L.nf == 3) bh_eval_points<T, (T > 3 ? 3 : T), PU>(ra, rb, eps2, X, A);
+    else if (T > 4 && L.nf == 4) bh_eval_points<T, (T > 4 ? 4 : T), PU>(ra, rb, eps2, X, A);
+    else if (L.nf > 0) bh_eval_points<T, T, PU>(ra, rb, eps2, X, A);
     if (L.split) bh_split_points<T>(L, ra, rb, eps2, X, A);
 }
 template <int T, class QC>
@@ -640,7 +646,8 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
             int lq_pos = 0;
             for (;;) {
                 if (ring_cnt >= 32) {
-                    bh_points<T>(L, S.ra + (ring_head >> 1), S.rb + (ring_head >> 1), eps2v, X, A);
+                    bh_points<T, LEARNED ? kPointUnrollLearned : kPointUnroll>(L, S.ra + (ring_head >> 1), S.rb + (ring_head >> 1),
+                                                                        eps2v, X, A);
                     ring_head ^= 32;
                     ring_cnt -= 32;
                     continue;
@@ -688,7 +695,8 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
         if (ring_cnt > 0) {
             if (lane >= ring_cnt) bh_put_point(S, ring_head + lane, bh_pad_source());
             __syncwarp();
-            bh_points<T>(L, S.ra + (ring_head >> 1), S.rb + (ring_head >> 1), eps2v, X, A);
+            bh_points<T, LEARNED ? kPointUnrollLearned : kPointUnroll>(L, S.ra + (ring_head >> 1), S.rb + (ring_head >> 1),
+                                                                        eps2v, X, A);
         }
         __syncwarp();
         // ---- write (ax, ay, az, phi) in the caller's order; a split slot first
@@ -1105,7 +1113,7 @@ __global__ void __launch_bounds__(256, bh_ws_min_blocks<T>()) bh_walk_ws_kernel(
         } else if (kind == kWsQuads) {
             if (ORDER >= 2) bh_quads<T, WsTile>(L, C.tile[s], 0, eps2v, X, A);
         } else if (kind == kWsPoints) {
-            bh_points<T>(L, C.tile[s].a, C.tile[s].b, eps2v, X, A);
+            bh_points<T, kPointUnrollPaired>(L, C.tile[s].a, C.tile[s].b, eps2v, X, A);
         } else if (kind == kWsEnd) {
 #pragma unroll
             for (int t = 0; t < T; t++) {
