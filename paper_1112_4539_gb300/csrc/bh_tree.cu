@@ -491,6 +491,96 @@ __device__ __forceinline__ bool bh_node_fp64(int count, bool leaf, int level, in
     return count >= fp64_threshold || (leaf && count > kLeafFp64) || level > BH_MAX_LEVEL;
 }
 
+__device__ __forceinline__ double bh_warp_sum(double x)
+{
+    // butterfly: every lane ends with the same sum (IEEE addition commutes)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(BH_FULL_MASK, x, o);
+    return x;
+}
+__device__ __forceinline__ float bh_warp_sumf(float x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(BH_FULL_MASK, x, o);
+    return x;
+}
+
+// Leaves holding more than kLeafFp64 particles (oversized leaves at the
+// deepest level, or any leaf when n_leaf > 32) need no other node: a whole
+// warp takes each one before the level passes, its lanes striding over the
+// particles, and stores the FP64 moments; the level kernel then reads them
+// as it reads a child's.  Summed by one thread, a leaf of hundreds of
+// particles was the tail of the deepest level's launch.
+template <int ORDER>
+__global__ void __launch_bounds__(256) bh_bigleaf_moments_kernel(const float4* __restrict__ pos_s, bh_nodes nd,
+                                                                  const bh_dev_ctrl* __restrict__ c)
+{
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    const int nn = (int)c->n_nodes;
+    for (int base = warp * 32; base < nn; base += nw * 32) {
+        const int v = base + lane;
+        int4 r = make_int4(0, 0, 0, 0);
+        if (v < nn) r = nd.rec[v];
+        unsigned int big = __ballot_sync(BH_FULL_MASK, v < nn && r.z < 0 && r.y > kLeafFp64);
+        while (big) {
+            const int src = __ffs(big) - 1;
+            big &= big - 1u;
+            const int k = __shfl_sync(BH_FULL_MASK, r.x, src), cnt = __shfl_sync(BH_FULL_MASK, r.y, src);
+            // FP32 lane partials of at most count/32 terms, summed across the
+            // warp; the mass with a Kahan compensation and the centre of mass
+            // in FP64.  Offsets are taken from the first particle, so the
+            // relative errors (< (count/32 + 5) * 6e-8 of the offset sums and
+            // second moments) stay far below what the moment bars allow.
+            const float4 p0 = pos_s[k];
+            float kM = 0.f, kc = 0.f, psx = 0.f, psy = 0.f, psz = 0.f;
+            for (int j = k + lane; j < k + cnt; j += 32) {
+                const float4 p = pos_s[j];
+                const float y = __fsub_rn(p.w, kc), t = __fadd_rn(kM, y);
+                kc = __fsub_rn(__fsub_rn(t, kM), y);
+                kM = t;
+                psx = fmaf(p.w, p.x - p0.x, psx);
+                psy = fmaf(p.w, p.y - p0.y, psy);
+                psz = fmaf(p.w, p.z - p0.z, psz);
+            }
+            const double M = bh_warp_sum((double)kM - (double)kc);
+            psx = bh_warp_sumf(psx);
+            psy = bh_warp_sumf(psy);
+            psz = bh_warp_sumf(psz);
+            const bool massless = !(M != 0.0);
+            const double x0 = p0.x, y0 = p0.y, z0 = p0.z;
+            const double cx = massless ? x0 : x0 + (double)psx / M;
+            const double cy = massless ? y0 : y0 + (double)psy / M;
+            const double cz = massless ? z0 : z0 + (double)psz / M;
+            double q[6] = {0, 0, 0, 0, 0, 0};
+            if (ORDER >= 2) {
+                // y = x - COM as (x - x0) - (COM - x0), both offsets small
+                const float ox = (float)(cx - x0), oy = (float)(cy - y0), oz = (float)(cz - z0);
+                float pq[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int j = k + lane; j < k + cnt; j += 32) {
+                    const float4 p = pos_s[j];
+                    const float a = (p.x - p0.x) - ox, b = (p.y - p0.y) - oy, e = (p.z - p0.z) - oz;
+                    const float ma = p.w * a, mb = p.w * b;
+                    pq[0] = fmaf(ma, a, pq[0]);
+                    pq[1] = fmaf(mb, b, pq[1]);
+                    pq[2] = fmaf(p.w * e, e, pq[2]);
+                    pq[3] = fmaf(ma, b, pq[3]);
+                    pq[4] = fmaf(ma, e, pq[4]);
+                    pq[5] = fmaf(mb, e, pq[5]);
+                }
+#pragma unroll
+                for (int i = 0; i < 6; i++) q[i] = (double)bh_warp_sumf(pq[i]);
+            }
+            if (lane == 0) {
+                const int w = base + src;
+                nd.com64[w] = bh_double4{cx, cy, cz, M};
+                if (ORDER >= 2)
+                    for (int i = 0; i < 6; i++) nd.quad64[(size_t)w * 6 + i] = q[i];
+            }
+        }
+    }
+}
+
 template <typename R>
 __device__ __forceinline__ void bh_child_moments(const bh_nodes& nd, int cidx, int fp64_threshold, int order,
                                                  bh_mom<R>& o)
@@ -575,8 +665,18 @@ bh_moments_level_kernel(const float4* __restrict__ pos_s, const K* __restrict__ 
         bool massless;
         if (f64) {
             bh_mom<double> o;
-            if (r.z < 0) bh_leaf_moments<double, ORDER>(pos_s, r.x, r.y, o, massless);
-            else bh_internal_moments<double, ORDER>(nd, r.z, r.w, fp64_threshold, o, massless);
+            if (r.z < 0 && r.y > kLeafFp64) {
+                // taken by bh_bigleaf_moments_kernel
+                const bh_double4 m4 = nd.com64[v];
+                o.cx = m4.x; o.cy = m4.y; o.cz = m4.z; o.M = m4.w;
+                massless = !(o.M != 0.0);
+                if (ORDER >= 2)
+                    for (int i = 0; i < 6; i++) o.q[i] = nd.quad64[(size_t)v * 6 + i];
+            } else if (r.z < 0) {
+                bh_leaf_moments<double, ORDER>(pos_s, r.x, r.y, o, massless);
+            } else {
+                bh_internal_moments<double, ORDER>(nd, r.z, r.w, fp64_threshold, o, massless);
+            }
             if (massless) {
                 o.cx = gx; o.cy = gy; o.cz = gz;
             }
@@ -616,6 +716,8 @@ static void bh_moments_t(const float4* pos_s, const K* keys, const bh_nodes& nd,
                          int fp64_threshold, int curve, bh_dev_ctrl* ctrl, int grid, cudaStream_t s,
                          const uint32_t* sys, const float4* sys_box)
 {
+    if (order >= 2) bh_bigleaf_moments_kernel<2><<<grid, 256, 0, s>>>(pos_s, nd, ctrl);
+    else bh_bigleaf_moments_kernel<1><<<grid, 256, 0, s>>>(pos_s, nd, ctrl);
     for (int lev = bh_key_traits<K>::kMaxLevel; lev >= 0; lev--) {
         if (order >= 2)
             bh_moments_level_kernel<2, K><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, curve,
