@@ -117,7 +117,24 @@ def test_labels_exact_cases(orc):
     assert single.any()
     assert (Y[single] == -12).all()          # a one-particle cell is exact: floor value
     assert (Y <= 0.5).all() and (Y >= -12).all()
-    # descending: children of a labelled node appear only when its label exceeds the floor
+    # descending: a labelled internal node's guard-passing children are labelled
+    # exactly when its label exceeds log10(descend_above) = -6
+    groups = np.arange(0, b.g_first.size, 7)
+    have = set(zip(pg.tolist(), pn.tolist()))
+    for k in range(0, X.shape[0], 5):
+        v = int(pn[k])
+        if t.nchild[v] == 0:
+            continue
+        g = groups[pg[k]]
+        gb, ge = int(b.g_first[g]), int(b.g_first[g] + b.g_count[g])
+        mem = b.spos[gb:ge, :3].astype(np.float64)
+        lo, hi = mem.min(0), mem.max(0)
+        for c in range(t.child_first[v], t.child_first[v] + t.nchild[v]):
+            com = b.mom.com_m[c, :3]
+            d2 = float((np.maximum(np.maximum(lo - com, com - hi), 0.0) ** 2).sum())
+            member = t.first[c] < ge and t.first[c] + t.count[c] > gb
+            if d2 > b.mom.s_eff[c] and not member:
+                assert ((int(pg[k]), c) in have) == bool(Y[k] > -6), (k, c)
     # independent recomputation of a few labels by brute force
     rng = np.random.default_rng(1)
     for k in rng.choice(np.nonzero(~single)[0], 10, replace=False):
@@ -153,10 +170,13 @@ def test_learned_walk_limits(orc):
     d = orc.direct(pos, eps=eps)
     ea, ep = orc.rel_err(r["out"], d)
     assert ea.max() < 1e-12 and ep.max() < 1e-12 and (r["n_pc"] == 0).all()
-    # every feature out of range: the fallback is the plain criterion at theta_fb
-    r = orc.force_groups_learned(b, always, np.full(6, 1e9), np.full(6, -1e9), 1e-3, eps, tg, tfb)
+    # every feature out of range (below, above, or both ends of an empty range):
+    # the fallback is the plain criterion at theta_fb
     bf = orc.Built(pos, 8, 64, tfb, 2)
     ref = orc.force_groups(bf.spos, bf.perm, bf.tree, bf.mom, bf.g_first, bf.g_count, eps)
-    ok = (ref["margin"] > 1e-9) & (r["margin_geo"] > 1e-9)
-    np.testing.assert_allclose(r["out"][ok], ref["out"][ok], rtol=1e-12, atol=0)
-    assert ok.mean() > 0.95
+    for lo, hi in ((np.full(6, 1e9), np.full(6, -1e9)), (np.full(6, 1e9), np.full(6, 2e9)),
+                   (np.full(6, -2e9), np.full(6, -1e9))):
+        r = orc.force_groups_learned(b, always, lo, hi, 1e-3, eps, tg, tfb)
+        ok = (ref["margin"] > 1e-9) & (r["margin_geo"] > 1e-9)
+        np.testing.assert_allclose(r["out"][ok], ref["out"][ok], rtol=1e-12, atol=0)
+        assert ok.mean() > 0.95

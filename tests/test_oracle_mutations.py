@@ -203,6 +203,46 @@ MUTATIONS = {
         "const int member = first[v] < ge && (int64_t)first[v] + count[v] > gb;\n            int accept = 0;",
         "const int member = 0;\n            int accept = 0;",
         [L + "test_learned_walk_limits"]),
+    "particle_walk_leaf_of_one_as_cell": (
+        "            if (count[v] == 1) {",
+        "            if (count[v] == 0) {",
+        [P + "test_particle_walk_single_particle_leaves_are_particles"]),
+    "particle_walk_holds_target_ignored": (
+        "const int holds_i = first[v] <= i && i < (int64_t)first[v] + count[v];",
+        "const int holds_i = 0;",
+        [P + "test_particle_walk_equals_group_walk_of_single_particles"]),
+    "groups_root_chunks": (
+        "OR_EMIT(first[0] + k, (count[0] - k < G) ? (count[0] - k) : G);",
+        "OR_EMIT(first[0] + k, G);",
+        [P + "test_groups_of_a_root_leaf"]),
+    "feature_mass_fraction_base": (
+        "f[1] = (cm[3] > 0 && mtot > 0) ? log10(cm[3] / mtot) : -30.0;",
+        "f[1] = (cm[3] > 0 && mtot > 0) ? log(cm[3] / mtot) : -30.0;",
+        [L + "test_features_hand_case"]),
+    "feature_level_scale": (
+        "f[4] = level / 10.0;",
+        "f[4] = level / 21.0;",
+        [L + "test_features_hand_case"]),
+    "relu_gradient_gate": (
+        "dh2[k] = h2[k] > 0 ? dy * W3[k] : 0;",
+        "dh2[k] = dy * W3[k];",
+        [L + "test_loss_weights_and_gradient"]),
+    "adam_second_moment": (
+        "v[k] = b2 * v[k] + (1 - b2) * g[k] * g[k];",
+        "v[k] = b2 * v[k] + (1 - b2) * fabs(g[k]);",
+        [L + "test_adam_closed_form"]),
+    "training_pairs_no_descent": (
+        "if (worst > descend_above && nchild[v] > 0)",
+        "if (worst > descend_above && nchild[v] < 0)",
+        [L + "test_labels_exact_cases"]),
+    "learned_range_check_dropped": (
+        "if (f[k] < fmin[k] || f[k] > fmax[k]) inrange = 0;",
+        "if (f[k] < fmin[k] && f[k] > fmax[k]) inrange = 0;",
+        [L + "test_learned_walk_limits"]),
+    "learned_fallback_offset": (
+        "const double s = sqrt(S) - side[v] / theta_guard;",
+        "const double s = sqrt(S);",
+        [L + "test_learned_walk_limits"]),
     "loss_weight_on_wrong_side": (
         "const double w = (yh < Y[i]) ? under_weight : 1.0;",
         "const double w = (yh > Y[i]) ? under_weight : 1.0;",

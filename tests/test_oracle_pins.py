@@ -347,6 +347,18 @@ def test_groups_cut_oversized_leaves_into_chunks_of_G(orc, n_leaf, G):
             assert (f + k, min(G, c - k)) in groups, (v, k)
 
 
+def test_groups_of_a_root_leaf(orc):
+    # n <= n_leaf: the root is the only node, a leaf; with n > G it is cut into
+    # chunks of G, the last one short
+    p = workloads.plummer(50, seed=24)
+    box, perm, sk, sp, t, m = _built(orc, p, n_leaf=64)
+    assert t.n_nodes == 1 and t.nchild[0] == 0
+    gf, gc = orc.groups(t, 32)
+    assert list(zip(gf.tolist(), gc.tolist())) == [(0, 32), (32, 18)]
+    gf, gc = orc.groups(t, 64)
+    assert list(zip(gf.tolist(), gc.tolist())) == [(0, 50)]
+
+
 def test_groups_greedy_maximal(orc):
     p = workloads.plummer(5000, seed=10)
     box, perm, sk, sp, t, m = _built(orc, p, n_leaf=8)
@@ -559,6 +571,34 @@ def test_group_walk_follows_the_pinned_lists(orc, theta):
         o = b.perm[gb:gb + gc]
         assert (res["n_pc"][o] == len(pc)).all()
         assert (res["n_pp"][o] == int(t.count[pp].sum()) - 1).all()
+
+
+def test_particle_walk_single_particle_leaves_are_particles(orc):
+    # A leaf holding one particle always gives a particle term (never a cell
+    # term), whatever the criterion says: here the far particle C sits alone in
+    # its level-1 cell, which Eq. (2) at theta = 1 would accept from A and B,
+    # so A and B see only particle terms; C sees the cell {A, B}.
+    p = np.array([[0.0, 0.0, 0.0, 1.0], [0.01, 0.0, 0.0, 1.0], [1.0, 1.0, 1.0, 1.0]], np.float32)
+    res, b = orc.tree_force(p, 1.0, 0.01, n_leaf=1, walk="particle")
+    assert list(res["n_pc"]) == [0, 0, 1] and list(res["n_pp"]) == [2, 2, 0]
+    ea, ep = orc.rel_err(res["out"][:2], orc.direct(p, eps=0.01)[:2])
+    assert ea.max() < 1e-12 and ep.max() < 1e-12
+
+
+@pytest.mark.parametrize("theta", [0.5, 1.0, 4.0])
+def test_particle_walk_equals_group_walk_of_single_particles(orc, theta):
+    # With groups of one particle the group walk's box is the particle itself,
+    # so its (pinned) criterion is the per-particle walk's: the same nodes are
+    # accepted and the same leaves opened.  A one-particle node is a particle
+    # term in one walk and an exact cell term (zero quadrupole) in the other,
+    # so the forces agree to rounding; above theta = 1/sqrt(3) this also pins
+    # that the per-particle walk never accepts a node holding its target.
+    p = workloads.clumpy(3000, seed=25)
+    rp, _ = orc.tree_force(p, theta, 0.01, n_leaf=8, G=1, order=2, walk="particle")
+    rg, _ = orc.tree_force(p, theta, 0.01, n_leaf=8, G=1, order=2, walk="group")
+    ea, ep = orc.rel_err(rp["out"], rg["out"])
+    assert ea.max() < 1e-10 and ep.max() < 1e-10, (ea.max(), ep.max())
+    assert (rp["n_pp"] + rp["n_pc"] == rg["n_pp"] + rg["n_pc"]).all()
 
 
 def test_term_magnitude_sum(orc):
