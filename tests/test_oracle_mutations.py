@@ -243,6 +243,38 @@ MUTATIONS = {
         "const double s = sqrt(S) - side[v] / theta_guard;",
         "const double s = sqrt(S);",
         [L + "test_learned_walk_limits"]),
+    "bbox_side_smallest_extent": (
+        "        if (d > L) L = d;",
+        "        if (d < L || L == 0.0f) L = d;",
+        [P + "test_bbox_matches_numpy", P + "test_morton_golden"]),
+    "hilbert_inverse_gray_decode": (
+        "const uint32_t g = w[2] >> 1;                          /* Gray decode */",
+        "const uint32_t g = w[2] >> 2;                          /* Gray decode */",
+        [H + "test_deep_curve_face_connected_and_invertible"]),
+    "morton_decode_axis": (
+        "        c[0] = or_compact3(key >> 2, nbits);",
+        "        c[0] = or_compact3(key >> 1, nbits);",
+        [P + "test_s_eff_hand_example"]),
+    "tree_child_level": (
+        "                level[nn] = l + 1;",
+        "                level[nn] = l;",
+        [P + "test_tree_matches_definition"]),
+    "cell_side_per_level": (
+        "const double lside = (double)box[3] / (double)(1u << l);",
+        "const double lside = (double)box[3] / (double)(1u << (l + 1));",
+        [P + "test_s_eff_hand_example"]),
+    "massless_node_centre": (
+        "            cx = gx;",
+        "            cx = 0.0;",
+        [P + "test_massless_node_takes_cell_centre"]),
+    "cell_monopole_sign": (
+        "    acc[0] -= M * g3 * rx;",
+        "    acc[0] += M * g3 * rx;",
+        [P + "test_quadrupole_gradient", P + "test_multipole_convergence_orders"]),
+    "pp_force_sign": (
+        "    acc[0] += mr3 * dx;",
+        "    acc[0] -= mr3 * dx;",
+        [P + "test_theta_to_zero_equals_direct"]),
     "loss_weight_on_wrong_side": (
         "const double w = (yh < Y[i]) ? under_weight : 1.0;",
         "const double w = (yh > Y[i]) ? under_weight : 1.0;",

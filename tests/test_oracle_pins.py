@@ -265,6 +265,20 @@ def test_moments_root_and_parallel_axis(orc):
         assert abs(m.com_m[ch, 3].sum() - m.com_m[v, 3]) <= 1e-14
 
 
+def test_massless_node_takes_cell_centre(orc):
+    # R14: a node of massless particles has the geometric centre of its cell as
+    # centre of mass, so s = 0 and S_eff = (l / theta)^2.  Box: origin 0.1,
+    # side 0.8; the massless pair sits in the level-1 cell with origin 0.1 and
+    # side 0.4, centre 0.3 on each axis.
+    p = np.array([[0.1, 0.1, 0.1, 0.0], [0.125, 0.1, 0.1, 0.0], [0.9, 0.9, 0.9, 1.0]], np.float32)
+    box, perm, sk, sp, t, m = _built(orc, p, n_leaf=1, theta=0.5)
+    v = [i for i in range(t.n_nodes) if t.level[i] == 1 and t.count[i] == 2][0]
+    assert m.com_m[v, 3] == 0.0
+    np.testing.assert_allclose(m.com_m[v, :3], [0.3, 0.3, 0.3], rtol=0, atol=1e-7)
+    side = float(box[3]) / 2
+    assert abs(m.s_eff[v] - (side / 0.5) ** 2) < 1e-12
+
+
 def test_s_eff_hand_example(orc):
     # Eq. (2) for a hand-made case: box [0,4]^3 (origin 0, L = 4).  Particles at
     # (0.5,0.5,0.5) m=3 and (1.5,0.5,0.5) m=1.  With n_leaf = 1 the level-1
