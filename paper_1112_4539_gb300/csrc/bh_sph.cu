@@ -23,6 +23,9 @@
 
 namespace bh {
 
+#ifndef BH_SPH_LEAF_FILTER
+#define BH_SPH_LEAF_FILTER 1
+#endif
 constexpr int kSphStackCap = 704;   // ranges of <= 8 siblings; same bound as the gravity walk
 constexpr int kSphRing = 64;
 
@@ -177,6 +180,12 @@ __global__ void __launch_bounds__(128) bh_sph_kernel(SphParams P)
             hmax = fmaxf(hmax, __shfl_xor_sync(BH_FULL_MASK, hmax, o));
         }
         const float reach2 = hmax * hmax * (1.0f + 1e-5f);
+#if BH_SPH_LEAF_FILTER
+        // each target's own reach for the leaf filter (-1: no target in the slot)
+        float reach_t[T];
+#pragma unroll
+        for (int t = 0; t < T; t++) reach_t[t] = (t * 32 + lane < gc) ? h2[t] * (1.0f + 1e-5f) : -1.0f;
+#endif
 
         // root of the group's system
         int root = 0;
@@ -216,16 +225,42 @@ __global__ void __launch_bounds__(128) bh_sph_kernel(SphParams P)
             // distance_test: the node's box against the group's box
             int4 r = make_int4(0, 0, -1, 0);
             bool near = false;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
             if (has) {
                 r = P.rec[v];
-                const float4 a = P.blo[v], b = P.bhi[v];
+                a = P.blo[v];
+                b = P.bhi[v];
                 const float gx = fmaxf(fmaxf(a.x - bx1, bx0 - b.x), 0.0f);
                 const float gy = fmaxf(fmaxf(a.y - by1, by0 - b.y), 0.0f);
                 const float gz = fmaxf(fmaxf(a.z - bz1, bz0 - b.z), 0.0f);
                 near = gx * gx + gy * gy + gz * gz <= reach2;
             }
-            const bool leaf = near && r.z < 0;
+            bool leaf = near && r.z < 0;
             const bool opn = near && r.z >= 0;
+#if BH_SPH_LEAF_FILTER
+            // per-target filter: a leaf near the group's box is kept only when
+            // its box lies within reach of at least one target of the warp
+            {
+                unsigned int lm0 = __ballot_sync(BH_FULL_MASK, leaf), keep = 0u;
+                while (lm0) {
+                    const int q = __ffs(lm0) - 1;
+                    lm0 &= lm0 - 1u;
+                    const float lx0 = __shfl_sync(BH_FULL_MASK, a.x, q), ly0 = __shfl_sync(BH_FULL_MASK, a.y, q);
+                    const float lz0 = __shfl_sync(BH_FULL_MASK, a.z, q), lx1 = __shfl_sync(BH_FULL_MASK, b.x, q);
+                    const float ly1 = __shfl_sync(BH_FULL_MASK, b.y, q), lz1 = __shfl_sync(BH_FULL_MASK, b.z, q);
+                    bool hit = false;
+#pragma unroll
+                    for (int t = 0; t < T; t++) {
+                        const float dx = fmaxf(fmaxf(lx0 - xi[t], xi[t] - lx1), 0.0f);
+                        const float dy = fmaxf(fmaxf(ly0 - yi[t], yi[t] - ly1), 0.0f);
+                        const float dz = fmaxf(fmaxf(lz0 - zi[t], zi[t] - lz1), 0.0f);
+                        hit = hit || (dx * dx + dy * dy + dz * dz <= reach_t[t]);
+                    }
+                    if (__any_sync(BH_FULL_MASK, hit)) keep |= 1u << q;
+                }
+                leaf = leaf && ((keep >> lane) & 1u);
+            }
+#endif
             const unsigned int om = __ballot_sync(BH_FULL_MASK, opn);
             if (sp + __popc(om) > kSphStackCap) {
                 overflow = true;
