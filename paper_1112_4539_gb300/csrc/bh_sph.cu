@@ -8,8 +8,9 @@
 // particles: a node is skipped when its particles' bounding box lies farther
 // than the group's largest radius from the group's bounding box (with a
 // 1e-5 relative allowance, so FP32 rounding of the box gap can never skip a
-// neighbour), a leaf contributes all its particles as candidates, other
-// nodes are opened.  Candidates go through a 64-entry ring in shared memory
+// neighbour), a leaf contributes all its particles as candidates when its
+// box is also within reach of at least one target of the warp (each with its
+// own radius), other nodes are opened.  Candidates go through a 64-entry ring in shared memory
 // and are tested 32 at a time against each lane's T targets.
 //
 // Pair rule (identical to the oracle's): d = x_j - x_i per axis in FP32,
