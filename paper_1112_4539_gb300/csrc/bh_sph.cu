@@ -10,8 +10,9 @@
 // 1e-5 relative allowance, so FP32 rounding of the box gap can never skip a
 // neighbour), a leaf contributes all its particles as candidates when its
 // box is also within reach of at least one target of the warp (each with its
-// own radius), other nodes are opened.  Candidates go through a 64-entry ring in shared memory
-// and are tested 32 at a time against each lane's T targets.
+// own radius), other nodes are opened.  Candidates go through a 64-entry
+// ring in shared memory and are tested 32 at a time against each lane's T
+// targets.
 //
 // Pair rule (identical to the oracle's): d = x_j - x_i per axis in FP32,
 // r2 = fma(dz, dz, fma(dy, dy, dx * dx)), j != i is a neighbour iff
