@@ -226,14 +226,15 @@ def bh_kick_drift(h, pos, vel, acc, dt_kick, dt_drift, stream=None):
                                ctypes.c_float(dt_kick), ctypes.c_float(dt_drift), _stream(stream))
 
 
-def bh_tree_force_static(pos, theta, eps, out, cfg=None, stream=None):
+def bh_tree_force_static(pos, theta, eps, out, cfg=None, stream=None, status=True):
     """Force evaluation without any device allocation (fixed scratch, n <= 32768).
-    Returns (rc, device status)."""
+    Returns (rc, device status); with status=False the call does not
+    synchronise (as inside a CUDA graph capture) and the status is None."""
     st = ctypes.c_int(0)
     rc = lib().bh_tree_force_static(_dptr(pos), int(pos.shape[0]), ctypes.byref(cfg) if cfg is not None else None,
-                                    ctypes.c_float(theta), ctypes.c_float(eps), _dptr(out), ctypes.byref(st),
-                                    _stream(stream))
-    return rc, st.value
+                                    ctypes.c_float(theta), ctypes.c_float(eps), _dptr(out),
+                                    ctypes.byref(st) if status else None, _stream(stream))
+    return rc, (st.value if status else None)
 
 
 def _f32host(a):

@@ -50,3 +50,41 @@ def test_static_entry_matches_context_path_twice():
     big = torch.zeros((bh.STATIC_MAX_N + 1, 4), dtype=torch.float32, device="cuda:0")
     rc, _ = bh.bh_tree_force_static(big, theta, eps, torch.empty_like(big))
     assert rc == bh.BH_ERR_TOO_LARGE
+
+
+def test_static_entry_replays_from_a_cuda_graph():
+    # The reason for the entry point: captured once into a CUDA graph (after a
+    # first, synchronous call on the device), the graph replays the whole
+    # evaluation on whatever particles the input buffer holds, with the bits of
+    # a direct call.
+    import torch
+    from paper_1112_4539_gb300 import _build
+    _build.build()
+    import paper_1112_4539_gb300 as bh
+
+    n, theta, eps = 20000, 0.5, 0.01
+    cfg = bh.config(leaf_size=8, group_size=64, order=2)
+    x = torch.from_numpy(workloads.plummer(n, seed=30)).to("cuda:0")
+    out = torch.empty_like(x)
+    rc, st = bh.bh_tree_force_static(x, theta, eps, out, cfg)
+    assert rc == bh.BH_OK and st == bh.BH_OK
+    ref1 = out.clone()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=side):
+        rc, st = bh.bh_tree_force_static(x, theta, eps, out, cfg, status=False)
+    assert rc == bh.BH_OK and st is None
+    out.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref1)
+    # new particles in the same buffer
+    x.copy_(torch.from_numpy(workloads.clumpy(n, seed=31)).to("cuda:0"))
+    g.replay()
+    torch.cuda.synchronize()
+    ref2 = torch.empty_like(x)
+    rc, st = bh.bh_tree_force_static(x, theta, eps, ref2, cfg)
+    assert rc == bh.BH_OK and st == bh.BH_OK
+    assert torch.equal(out, ref2)
+    del g
