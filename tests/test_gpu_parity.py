@@ -343,3 +343,29 @@ def test_full_size_clumpy_sampled(bh, orc):
         sel[b.perm[b.g_first[g]:b.g_first[g] + b.g_count[g]]] = True
     _check_force(got, res["out"], res["margin"], mask=sel, a_abs=res["a_abs"])
     ctx.close()
+
+
+def test_two_contexts_on_two_streams(bh):
+    # Each context owns its workspace: two evaluations in flight on two
+    # streams at once give the bits each gives alone.
+    import torch
+    pa = workloads.plummer(60000, seed=61)
+    pb = workloads.clumpy(50000, seed=62)
+    xa, xb = _cuda(pa), _cuda(pb)
+    ca = bh.Context(60000, leaf_size=8, group_size=64, order=2)
+    cb = bh.Context(50000, leaf_size=16, group_size=96, order=1)
+    ref_a = ca.evaluate(xa, 0.5, 0.01).clone()
+    ref_b = cb.evaluate(xb, 0.6, 1e-3).clone()
+    torch.cuda.synchronize()
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    oa, ob = torch.empty_like(xa), torch.empty_like(xb)
+    for _ in range(3):
+        with torch.cuda.stream(sa):
+            ca.evaluate(xa, 0.5, 0.01, oa, stream=sa)
+        with torch.cuda.stream(sb):
+            cb.evaluate(xb, 0.6, 1e-3, ob, stream=sb)
+    torch.cuda.synchronize()
+    assert ca.status() == 0 and cb.status() == 0
+    assert torch.equal(oa, ref_a) and torch.equal(ob, ref_b)
+    ca.close()
+    cb.close()
