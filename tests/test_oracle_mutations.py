@@ -275,6 +275,47 @@ MUTATIONS = {
         "    acc[0] += mr3 * dx;",
         "    acc[0] -= mr3 * dx;",
         [P + "test_theta_to_zero_equals_direct"]),
+    "quadrupole_g7_exponent": (
+        "const double g5 = g3 * g2, g7 = g5 * g2;",
+        "const double g5 = g3 * g2, g7 = g5 * g1;",
+        [P + "test_quadrupole_gradient", P + "test_quadrupole_textbook_at_zero_softening"]),
+    "cell_potential_sign": (
+        "    acc[3] -= M * g1;",
+        "    acc[3] += M * g1;",
+        [P + "test_quadrupole_gradient", P + "test_multipole_convergence_orders"]),
+    "pp_potential_sign": (
+        "    acc[3] -= m * rinv;",
+        "    acc[3] += m * rinv;",
+        [P + "test_theta_to_zero_equals_direct"]),
+    "pp_softening_exponent": (
+        "    const double mr3 = m * rinv * rinv * rinv;\n    acc[0] += mr3 * dx;",
+        "    const double mr3 = m * rinv * rinv;\n    acc[0] += mr3 * dx;",
+        [P + "test_theta_to_zero_equals_direct"]),
+    "s_eff_not_squared": (
+        "        s_eff[v] = t * t;",
+        "        s_eff[v] = t;",
+        [P + "test_s_eff_hand_example"]),
+    "moment_diagonal_term": (
+        "                q[0] += m * y0 * y0;",
+        "                q[0] += m * y0 * y1;",
+        [P + "test_moments_root_and_parallel_axis", P + "test_multipole_convergence_orders"]),
+    "groups_run_not_reset": (
+        "                    run_first = -1;",
+        "                    (void)0;",
+        [P + "test_groups_partition", P + "test_groups_greedy_maximal"]),
+    "groups_oversized_child_not_chunked": (
+        "                    if (nchild[ch] == 0)",
+        "                    if (nchild[ch] < 0)",
+        [P + "test_groups_cut_oversized_leaves_into_chunks_of_G", P + "test_groups_partition"]),
+    "particle_walk_cell_count": (
+        "                cpc++;",
+        "                cpc += 2;",
+        [P + "test_particle_walk_single_particle_leaves_are_particles",
+         P + "test_particle_walk_equals_group_walk_of_single_particles"]),
+    "sph_count_increment": (
+        "                c++;",
+        "                c += (r2 > 0.0f);",
+        [S + "test_coincident_particles_are_neighbours"]),
     "loss_weight_on_wrong_side": (
         "const double w = (yh < Y[i]) ? under_weight : 1.0;",
         "const double w = (yh > Y[i]) ? under_weight : 1.0;",

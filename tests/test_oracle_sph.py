@@ -65,3 +65,18 @@ def test_counts_match_kdtree(orc, kind, n, seed):
         want = pos[i, 3] * orc.sph_kernel(0.0, h[i]) + sum(
             pos[j, 3] * orc.sph_kernel(np.linalg.norm(x[j] - x[i]), h[i]) for j in js)
         assert rho[i] == pytest.approx(want, rel=1e-5)
+
+
+def test_coincident_particles_are_neighbours(orc):
+    # R19: distinct particles at the same position are neighbours (their
+    # distance 0 is below any radius); only the particle itself is excluded
+    from scipy.spatial import cKDTree
+    rng = np.random.default_rng(9)
+    knot = np.tile(np.array([[0.5, 0.5, 0.5, 1.0]], np.float32), (40, 1))
+    rest = np.concatenate([rng.random((500, 3)), np.ones((500, 1))], 1).astype(np.float32)
+    pos = np.concatenate([knot, rest])
+    h = np.full(pos.shape[0], 0.1, np.float32)
+    count, rho = orc.sph_density(pos, h)
+    t = cKDTree(pos[:, :3].astype(np.float64))
+    want = np.array([len(t.query_ball_point(pos[i, :3], 0.1 * (1 - 1e-6))) - 1 for i in range(40)])
+    assert (count[:40] == want).all() and (want >= 39).all()
