@@ -81,6 +81,8 @@ def lib():
                                               _i32p, _i32p, _vp, _f64p, _f64p, _f64p, ctypes.c_double,
                                               ctypes.c_double, _f64p, _vp, _vp, _vp, _vp]
         L.or_force_groups_learned.restype = ctypes.c_int
+        L.or_kick_drift.argtypes = [_i64, _f64p, _f64p, _f64p, ctypes.c_double, ctypes.c_double]
+        L.or_set_cell_rounding.argtypes = [ctypes.c_int]
         L.or_num_threads.restype = ctypes.c_int
         L.or_set_threads.argtypes = [ctypes.c_int]
         _lib = L
@@ -329,6 +331,35 @@ def tree_force(pos, theta, eps, n_leaf=8, G=32, order=1, walk="group", group_mas
     else:
         raise ValueError(walk)
     return res, b
+
+
+def kick_drift(pos, vel, acc, dt_kick, dt_drift):
+    """Sec. 1's orbit loop, one leapfrog update: v += a dt_kick, then
+    x += v dt_drift (with the updated v).  pos, vel, acc: (n, 4); returns new
+    FP64 copies of pos and vel (component 3 of each unchanged)."""
+    p = np.array(pos, dtype=np.float64, order="C", copy=True)
+    v = np.array(vel, dtype=np.float64, order="C", copy=True)
+    a = np.ascontiguousarray(acc, dtype=np.float64)
+    if not (p.shape == v.shape == a.shape and p.ndim == 2 and p.shape[1] == 4):
+        raise ValueError("pos, vel and acc must be (n, 4) arrays")
+    lib().or_kick_drift(p.shape[0], p, v, a, float(dt_kick), float(dt_drift))
+    return p, v
+
+
+class cell_rounding:
+    """Context manager: cell terms of the walks with (True, the default) or
+    without (False) the FP32 rounding of the stored cell's centre and mass."""
+
+    def __init__(self, on):
+        self.on = bool(on)
+
+    def __enter__(self):
+        lib().or_set_cell_rounding(int(self.on))
+        return self
+
+    def __exit__(self, *exc):
+        lib().or_set_cell_rounding(1)
+        return False
 
 
 def pc_eval(x, com_m, quad=None, eps=0.0):

@@ -14,7 +14,7 @@
  * IEEE round-to-nearest and no contraction, exactly as the GPU kernel does
  * (this file must be compiled with -ffp-contract=off).
  *
- * Conventions (readings of the paper, listed in the design notes):
+ * Conventions (readings of the paper where it is silent or ambiguous):
  *   - sign: accelerations are attractive and the potential is negative,
  *     phi_i = -sum m_j / sqrt(r^2 + eps^2)  (the paper's p_i is -phi_i);
  *   - the self term is excluded by index (Eq. 1, j != i);
@@ -519,9 +519,20 @@ static void or_pc(double xi, double yi, double zi, const double* cm, const doubl
  * exact FP64 sums).  Near the FP32 resolution of the coordinates (cells of
  * 63-bit key trees seen from inside the same dense knot) this rounding is
  * the leading difference between the FP64 and the stored cell. */
+static int or_cell_fp32 = 1;
+
+/* Switch the FP32 rounding of the cell record on (1, the default) or off (0:
+ * cell terms use the exact FP64 centre of mass and mass).  For tests that
+ * show where the rounding matters and where it does not. */
+void or_set_cell_rounding(int on) { or_cell_fp32 = on != 0; }
+
 static void or_pc_cell(double xi, double yi, double zi, const double* cm, const double* qd, double e2,
                        double* acc)
 {
+    if (!or_cell_fp32) {
+        or_pc(xi, yi, zi, cm, qd, e2, acc);
+        return;
+    }
     const double c[4] = {(double)(float)cm[0], (double)(float)cm[1], (double)(float)cm[2], (double)(float)cm[3]};
     or_pc(xi, yi, zi, c, qd, e2, acc);
 }
@@ -760,6 +771,26 @@ int or_force_particles(int64_t n, const float* spos, const uint32_t* perm, int64
         free(stack);
     }
     return err;
+}
+
+/* ------------------------------------------------------------------------
+ * The orbit loop around the force evaluation (Sec. 1: compute the forces,
+ * integrate the orbits, repeat), as one leapfrog update per particle:
+ *   v <- v + a dt_kick,   then   x <- x + v dt_drift   (the updated v).
+ * A kick-drift-kick step of length dt is a kick by dt/2 with the forces at
+ * the start, a drift by dt, new forces, and a kick by dt/2; the second half
+ * kick and the next step's first half kick may be merged into one kick by dt.
+ * pos, vel: n x 4 FP64, components 0..2 updated in place (3 untouched);
+ * acc: n x 4 FP64 (ax, ay, az, phi).
+ * ---------------------------------------------------------------------- */
+void or_kick_drift(int64_t n, double* pos, double* vel, const double* acc, double dt_kick, double dt_drift)
+{
+    for (int64_t i = 0; i < n; i++) {
+        for (int a = 0; a < 3; a++) {
+            vel[4 * i + a] = vel[4 * i + a] + acc[4 * i + a] * dt_kick;
+            pos[4 * i + a] = pos[4 * i + a] + vel[4 * i + a] * dt_drift;
+        }
+    }
 }
 
 /* One particle-cell term at target x (for the quadrupole pins). */

@@ -26,6 +26,9 @@ P = "tests/test_oracle_pins.py::"
 H = "tests/test_oracle_hilbert.py::"
 S = "tests/test_oracle_sph.py::"
 L = "tests/test_oracle_learned_mac.py::"
+F = "tests/test_oracle_leapfrog.py::"
+KD = ("            vel[4 * i + a] = vel[4 * i + a] + acc[4 * i + a] * dt_kick;\n"
+      "            pos[4 * i + a] = pos[4 * i + a] + vel[4 * i + a] * dt_drift;")
 
 # name: (snippet, replacement, pins expected to catch it)
 MUTATIONS = {
@@ -320,6 +323,24 @@ MUTATIONS = {
         "const double w = (yh < Y[i]) ? under_weight : 1.0;",
         "const double w = (yh > Y[i]) ? under_weight : 1.0;",
         [L + "test_loss_weights_and_gradient"]),
+    "leapfrog_drift_with_old_velocity": (
+        KD,
+        "            pos[4 * i + a] = pos[4 * i + a] + vel[4 * i + a] * dt_drift;\n"
+        "            vel[4 * i + a] = vel[4 * i + a] + acc[4 * i + a] * dt_kick;",
+        [F + "test_one_update_by_hand", F + "test_harmonic_oscillator_closed_form"]),
+    "leapfrog_kick_sign": (
+        "vel[4 * i + a] + acc[4 * i + a] * dt_kick;",
+        "vel[4 * i + a] - acc[4 * i + a] * dt_kick;",
+        [F + "test_harmonic_oscillator_closed_form", F + "test_two_body_circular_orbit"]),
+    "leapfrog_steps_swapped": (
+        KD,
+        "            vel[4 * i + a] = vel[4 * i + a] + acc[4 * i + a] * dt_drift;\n"
+        "            pos[4 * i + a] = pos[4 * i + a] + vel[4 * i + a] * dt_kick;",
+        [F + "test_harmonic_oscillator_closed_form", F + "test_two_body_circular_orbit"]),
+    "leapfrog_component_index": (
+        "acc[4 * i + a] * dt_kick;",
+        "acc[4 * i + (a + 1) % 3] * dt_kick;",
+        [F + "test_one_update_by_hand", F + "test_two_body_circular_orbit"]),
 }
 
 
