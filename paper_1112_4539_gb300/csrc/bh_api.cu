@@ -25,7 +25,6 @@ struct bh_ctx {
     int64_t n = -1;  // particles of the last tree_build (-1: none)
     bool have_moments = false;
     float theta = 0.f;
-    unsigned int sort_epoch = 0;
     int64_t launches = 0;
     void* slab = nullptr;
     bh_dev_ctrl* ctrl = nullptr;
@@ -291,8 +290,8 @@ int tree_build(bh_ctx* x, const float* d_pos_mass, int64_t n, void* stream)
     if (N > 0) {
         bh::launch_bbox(pos, N, x->ctrl, grid_for(x), s);
         bh::launch_keys(pos, N, x->ctrl, x->keys, x->cfg.curve, x->deep, grid_for(x), s);
-        bh::launch_sort(x->keys, x->keys_alt, x->vals, x->vals_alt, pos, x->pos_s, N, x->lookback,
-                        &x->sort_epoch, x->ctrl, x->deep, s);
+        bh::launch_sort(x->keys, x->keys_alt, x->vals, x->vals_alt, pos, x->pos_s, N, x->lookback, x->ctrl,
+                        x->deep, s);
         bh::launch_tree(x->keys, x->deep, N, x->cfg.leaf_size, x->dl, x->blk, x->nd, x->node_cap, x->ctrl,
                         grid_for(x), s);
         bh::launch_groups(x->nd, N, x->cfg.group_size, x->flags, x->blk, x->g_first, x->g_count, x->ctrl,

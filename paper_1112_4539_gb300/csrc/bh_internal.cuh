@@ -45,7 +45,9 @@ struct bh_dev_ctrl {
     unsigned long long n_pc;
     unsigned long long cum_pp;   // since context creation (never reset)
     unsigned long long cum_pc;
-    unsigned int pad[8];
+    unsigned int build_seq;      // builds since the block was zeroed (never reset): the sort
+                                 // passes of build b use look-back epochs 8 b + 1 .. 8 b + 8
+    unsigned int pad[7];
 };
 
 // Record a device-side error (first one wins) and raise the abort flag.
@@ -316,7 +318,7 @@ void launch_bbox(const float4* pos, int n, bh_dev_ctrl* ctrl, int grid, cudaStre
 void launch_keys(const float4* pos, int n, bh_dev_ctrl* ctrl, void* keys, int curve, bool deep, int grid,
                  cudaStream_t s);
 void launch_sort(void* keys, void* keys_alt, uint32_t* vals, uint32_t* vals_alt, const float4* pos, float4* pos_s,
-                 int n, unsigned long long* lookback, unsigned int* epoch, bh_dev_ctrl* ctrl, bool deep,
+                 int n, unsigned long long* lookback, bh_dev_ctrl* ctrl, bool deep,
                  cudaStream_t s);
 // sys / sys_off / sys_box: several independent systems (system of each
 // Morton position, first particle of each system + total, root cube of each);

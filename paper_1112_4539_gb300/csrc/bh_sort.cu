@@ -37,6 +37,7 @@ __global__ void bh_init_kernel(bh_dev_ctrl* c)
         c->group_ctr = 0u;
         c->n_pp = 0ull;
         c->n_pc = 0ull;
+        c->build_seq += 1u;  // new look-back epochs for this build's sort passes
     }
 }
 
@@ -140,7 +141,10 @@ void launch_keys(const float4* pos, int n, bh_dev_ctrl* ctrl, void* keys, int cu
 // Look-back status word: epoch (32 bits) | flag (2 bits) | value (30 bits).
 // flag 1 = tile aggregate only, 2 = inclusive prefix.  The epoch changes at
 // every pass, so stale words from earlier passes read as "not ready" and the
-// array never needs clearing.
+// array never needs clearing.  It is derived on the device from the control
+// block's build counter (advanced by bh_init_kernel at every build), never
+// passed from the host: a build replayed from a CUDA graph still gets epochs
+// that no earlier execution wrote.
 constexpr unsigned int kFlagAgg = 1u, kFlagPrefix = 2u;
 constexpr int kSpinLimit = 1 << 22;
 
@@ -188,8 +192,9 @@ template <typename K, int ITEMS, bool FIRST, bool LAST>
 __global__ void __launch_bounds__(kSortThreads)
 bh_onesweep_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
                    uint32_t* __restrict__ vout, const float4* __restrict__ pos, float4* __restrict__ pos_s, int n,
-                   int shift, int pass, unsigned int epoch, unsigned long long* lookback, bh_dev_ctrl* c)
+                   int shift, int pass, unsigned long long* lookback, bh_dev_ctrl* c)
 {
+    const unsigned int epoch = c->build_seq * 8u + (unsigned int)pass + 1u;
     constexpr int W = kSortThreads / 32;
     constexpr int TILE = kSortThreads * ITEMS;
     __shared__ K s_keys[TILE];
@@ -307,8 +312,7 @@ bh_onesweep_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin, 
 // gathers the particles.  vals[k] = caller index of the k-th particle in key order.
 template <typename K, int ITEMS>
 static void bh_sort_passes(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, const float4* pos,
-                           float4* pos_s, int n, unsigned long long* lookback, unsigned int* epoch, bh_dev_ctrl* ctrl,
-                           cudaStream_t s)
+                           float4* pos_s, int n, unsigned long long* lookback, bh_dev_ctrl* ctrl, cudaStream_t s)
 {
     constexpr int NP = bh_key_traits<K>::kPasses;
     const int tiles = (n + kSortThreads * ITEMS - 1) / (kSortThreads * ITEMS);
@@ -317,15 +321,15 @@ static void bh_sort_passes(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_
     for (int p = 0; p < NP; p++) {
         if (p == 0)
             bh_onesweep_kernel<K, ITEMS, true, false><<<tiles, kSortThreads, 0, s>>>(ka, nullptr, kb, vb, pos, pos_s,
-                                                                                     n, 0, 0, ++*epoch, lookback,
+                                                                                     n, 0, 0, lookback,
                                                                                      ctrl);
         else if (p == NP - 1)
             bh_onesweep_kernel<K, ITEMS, false, true><<<tiles, kSortThreads, 0, s>>>(ka, va, kb, vb, pos, pos_s, n,
-                                                                                     8 * p, p, ++*epoch, lookback,
+                                                                                     8 * p, p, lookback,
                                                                                      ctrl);
         else
             bh_onesweep_kernel<K, ITEMS, false, false><<<tiles, kSortThreads, 0, s>>>(ka, va, kb, vb, pos, pos_s, n,
-                                                                                      8 * p, p, ++*epoch, lookback,
+                                                                                      8 * p, p, lookback,
                                                                                       ctrl);
         K* tk = ka; ka = kb; kb = tk;
         uint32_t* tv = va; va = vb; vb = tv;
@@ -333,16 +337,15 @@ static void bh_sort_passes(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_
 }
 
 void launch_sort(void* keys, void* keys_alt, uint32_t* vals, uint32_t* vals_alt, const float4* pos, float4* pos_s,
-                 int n, unsigned long long* lookback, unsigned int* epoch, bh_dev_ctrl* ctrl, bool deep,
-                 cudaStream_t s)
+                 int n, unsigned long long* lookback, bh_dev_ctrl* ctrl, bool deep, cudaStream_t s)
 {
     if (n <= 0) return;
     if (deep)
         bh_sort_passes<bh_key64, kSortItems / 2>((bh_key64*)keys, (bh_key64*)keys_alt, vals, vals_alt, pos, pos_s,
-                                                 n, lookback, epoch, ctrl, s);
+                                                 n, lookback, ctrl, s);
     else
         bh_sort_passes<uint32_t, kSortItems>((uint32_t*)keys, (uint32_t*)keys_alt, vals, vals_alt, pos, pos_s, n,
-                                             lookback, epoch, ctrl, s);
+                                             lookback, ctrl, s);
 }
 
 // Self-test of the failure path: one look-back wait on a word that no block

@@ -29,7 +29,6 @@ static __device__ __align__(256) unsigned char g_bh_static_scratch[BH_STATIC_SCR
 struct StaticDevice {
     bool ready = false;
     unsigned char* base = nullptr;  // device address of g_bh_static_scratch on this device
-    unsigned int epoch = 0;         // onesweep look-back epoch (continues across calls)
     int sm_count = 1;
 };
 constexpr int kMaxDevices = 64;
@@ -169,8 +168,8 @@ extern "C" int bh_tree_force_static(const float* d_pos_mass, int64_t n, const bh
     bh::launch_init(ctrl, s);
     bh::launch_bbox(pos, N32, ctrl, grid, s);
     bh::launch_keys(pos, N32, ctrl, keys, c.curve, false, grid, s);
-    bh::launch_sort(keys, keys_alt, vals, vals_alt, pos, pos_s, N32, (unsigned long long*)(b + o_look), &sd.epoch,
-                    ctrl, false, s);
+    bh::launch_sort(keys, keys_alt, vals, vals_alt, pos, pos_s, N32, (unsigned long long*)(b + o_look), ctrl,
+                    false, s);
     bh::launch_tree(keys, false, N32, c.leaf_size, (uint16_t*)(b + o_dl), (uint32_t*)(b + o_blk), nd, (int64_t)NN,
                     ctrl, grid, s);
     bh::launch_groups(nd, N32, c.group_size, (uint8_t*)(b + o_flags), (uint32_t*)(b + o_blk), g_first, g_count,

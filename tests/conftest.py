@@ -18,3 +18,22 @@ def orc():
     import oracle
     oracle.lib()
     return oracle
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    """One line on the force-parity comparisons of the run: how many targets
+    were checked, how many were judged against the term-magnitude floor, and
+    the largest errors relative to |a| alone."""
+    mod = sys.modules.get("test_gpu_parity")
+    log = getattr(mod, "PARITY_LOG", None) if mod else None
+    if not log:
+        return
+    chk = sum(r["checked"] for r in log)
+    flo = sum(r["floored_frac"] * r["checked"] for r in log)
+    terminalreporter.write_line(
+        "force parity: %d comparisons, %d targets checked, %d near ties, %.2f%% judged against 0.1 sum|a_term| "
+        "(largest fraction %.2f%%); max error vs |a|: %.2e (other targets), %.2e (floored targets); "
+        "max phi error %.2e" % (len(log), chk, sum(r["near_tie"] for r in log), 100.0 * flo / max(chk, 1),
+                                100.0 * max(r["floored_frac"] for r in log),
+                                max(r["max_err_unfloored"] for r in log), max(r["max_err_floored_vs_a"] for r in log),
+                                max(r["max_err_phi"] for r in log)))

@@ -11,9 +11,17 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _run(extra_env=None):
     env = dict(os.environ)
     env.update(extra_env or {})
-    return subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
+    return _timed_run(env)
+
+
+def _timed_run(env):
+    import time
+    t0 = time.perf_counter()
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
                            "--cpu-sample-groups", "200"], cwd=ROOT, env=env, capture_output=True, text=True,
                           timeout=600)
+    r.wall_s = time.perf_counter() - t0
+    return r
 
 
 def test_reference_arm_prints_one_contract_line():
@@ -33,6 +41,8 @@ def test_reference_arm_prints_one_contract_line():
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["unit"] == d["unit"]
     assert d["config"]["n"] == 1 << 24
+    # the timed steps are measured, not extrapolated: they fit inside the run
+    assert d["ms_per_step"] * (d["steps"] + d["warmup"]) * 1e-3 <= r.wall_s
 
 
 def test_reference_arm_other_ranks_exit_without_work():

@@ -79,12 +79,21 @@ def test_static_entry_replays_from_a_cuda_graph():
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(out, ref1)
-    # new particles in the same buffer
-    x.copy_(torch.from_numpy(workloads.clumpy(n, seed=31)).to("cuda:0"))
-    g.replay()
-    torch.cuda.synchronize()
-    ref2 = torch.empty_like(x)
-    rc, st = bh.bh_tree_force_static(x, theta, eps, ref2, cfg)
-    assert rc == bh.BH_OK and st == bh.BH_OK
-    assert torch.equal(out, ref2)
+    # new particles in the same buffer, alternating with the first set: every
+    # replay's sort takes fresh look-back epochs from the device's build
+    # counter, so no replay can read a word an earlier replay left behind
+    sets = [torch.from_numpy(workloads.plummer(n, seed=30)).to("cuda:0"),
+            torch.from_numpy(workloads.clumpy(n, seed=31)).to("cuda:0")]
+    refs = []
+    for s in sets:
+        r = torch.empty_like(x)
+        rc, st = bh.bh_tree_force_static(s, theta, eps, r, cfg)
+        assert rc == bh.BH_OK and st == bh.BH_OK
+        refs.append(r)
+    for k in range(6):
+        x.copy_(sets[(k + 1) % 2])
+        out.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, refs[(k + 1) % 2]), k
     del g
