@@ -37,3 +37,8 @@ def pytest_terminal_summary(terminalreporter, exitstatus, config):
                                 100.0 * max(r["floored_frac"] for r in log),
                                 max(r["max_err_unfloored"] for r in log), max(r["max_err_floored_vs_a"] for r in log),
                                 max(r["max_err_phi"] for r in log)))
+    for r in log:
+        terminalreporter.write_line(
+            "  %-40s checked %8d  near ties %6d  floored %5.2f%%  max err vs |a| %.2e / floored %.2e  phi %.2e"
+            % (r["case"], r["checked"], r["near_tie"], 100.0 * r["floored_frac"], r["max_err_unfloored"],
+               r["max_err_floored_vs_a"], r["max_err_phi"]))
