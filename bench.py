@@ -89,8 +89,9 @@ def parse():
     ap.add_argument("--cpu-sample-groups", type=int, default=6000)
     ap.add_argument("--walk", default="group", choices=["group", "particle"],
                     help="group: one warp per particle group; particle: the paper's per-particle walk (Fig. 5)")
-    ap.add_argument("--walk-kernel", default="one-warp", choices=["one-warp", "paired"],
-                    help="group walk kernel: one warp walks and evaluates, or warp pairs (walker + evaluator)")
+    ap.add_argument("--walk-kernel", default="one-warp", choices=["one-warp", "paired", "tma"],
+                    help="group walk kernel: one warp walks and evaluates, warp pairs (walker + evaluator), "
+                         "or one warp with TMA-staged node and particle tiles")
     ap.add_argument("--curve", default="morton", choices=["morton", "hilbert"],
                     help="particle order (Sec. 5): Morton or Peano-Hilbert keys")
     ap.add_argument("--max-level", type=int, default=10, choices=[10, 21],
@@ -463,7 +464,7 @@ def run_ours(args, W):
     vel = torch.zeros_like(x)
     acc = torch.empty_like(x)
     curve = bh.CURVE_HILBERT if args.curve == "hilbert" else bh.CURVE_MORTON
-    variant = bh.WALK_PAIRED if args.walk_kernel == "paired" else bh.WALK_ONE_WARP
+    variant = {"paired": bh.WALK_PAIRED, "tma": bh.WALK_TMA}.get(args.walk_kernel, bh.WALK_ONE_WARP)
     ctx = bh.Context(n, device=local, leaf_size=leaf, group_size=G, order=order, curve=curve,
                      max_level=args.max_level, walk_variant=variant)
     stream = torch.cuda.current_stream()

@@ -71,10 +71,17 @@ typedef struct bh_config {
                                 bits).  The paired kernel serves G <= 96 with the plain
                                 criterion, in blocks of 256 threads sized by occupancy
                                 (block_threads and blocks_per_sm do not apply to it);
-                                other cases take the one-warp kernel */
+                                other cases take the one-warp kernel.
+                                BH_WALK_TMA: the one-warp walk with its node records
+                                and leaf particles staged into shared memory by bulk
+                                asynchronous copies (cp.async.bulk), the next batch of
+                                node records copied while the current tiles are
+                                evaluated; same tiles in the same order, so the same
+                                bits as BH_WALK_ONE_WARP.  With the learned criterion
+                                the one-warp kernel runs */
 } bh_config;
 
-enum { BH_WALK_ONE_WARP = 0, BH_WALK_PAIRED = 1 };
+enum { BH_WALK_ONE_WARP = 0, BH_WALK_PAIRED = 1, BH_WALK_TMA = 2 };
 
 #define BH_CURVE_MORTON 0
 #define BH_CURVE_HILBERT 1
@@ -344,11 +351,14 @@ int bh_tree_force_static(const float* d_pos_mass, int64_t n, const bh_config* cf
  *           after one second of %globaltimer time or 2^22 polls, whichever
  *           comes first);
  *   which = BH_SELFTEST_LOOKBACK:  the sort's decoupled look-back wait
- *           (gives up after 2^22 polls, well under a second).
+ *           (gives up after 2^22 polls, well under a second);
+ *   which = BH_SELFTEST_TMA:       the TMA-staged walk's wait for its bulk
+ *           copies, on an mbarrier told to expect 16 bytes that no copy
+ *           delivers (gives up like the tile ring's wait).
  * Asynchronous on `stream`; afterwards bh_status returns
  * BH_ERR_DEVICE_TIMEOUT (and clears it) and the context stays usable.
  * Errors: BH_ERR_INVALID (null context, unknown `which`), BH_ERR_CUDA. */
-enum { BH_SELFTEST_TILE_RING = 0, BH_SELFTEST_LOOKBACK = 1 };
+enum { BH_SELFTEST_TILE_RING = 0, BH_SELFTEST_LOOKBACK = 1, BH_SELFTEST_TMA = 2 };
 int bh_selftest_wait(bh_ctx* ctx, int which, void* stream);
 
 /* Synchronise `stream` and return the context's device status as a BH_*

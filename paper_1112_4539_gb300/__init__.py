@@ -44,8 +44,10 @@ CURVE_MORTON = 0
 CURVE_HILBERT = 1
 WALK_ONE_WARP = 0
 WALK_PAIRED = 1
+WALK_TMA = 2
 SELFTEST_TILE_RING = 0
 SELFTEST_LOOKBACK = 1
+SELFTEST_TMA = 2
 
 
 class BhConfig(ctypes.Structure):

@@ -138,7 +138,8 @@ static int validate_config(const bh_config* c)
     if (c->max_systems < 0 || c->max_systems > (1 << 20)) return BH_ERR_INVALID;
     if (c->curve != BH_CURVE_MORTON && c->curve != BH_CURVE_HILBERT) return BH_ERR_INVALID;
     if (c->max_level != 10 && c->max_level != 21) return BH_ERR_INVALID;
-    if (c->walk_variant != BH_WALK_ONE_WARP && c->walk_variant != BH_WALK_PAIRED) return BH_ERR_INVALID;
+    if (c->walk_variant != BH_WALK_ONE_WARP && c->walk_variant != BH_WALK_PAIRED && c->walk_variant != BH_WALK_TMA)
+        return BH_ERR_INVALID;
     return BH_OK;
 }
 
@@ -199,6 +200,7 @@ int bh_create(bh_ctx** out, const bh_config* cfg, int64_t max_n, int device)
     const size_t o_quad = c.order >= 2 ? take(NN * 2 * sizeof(float4)) : 0;
     const size_t o_com64 = take(NN * sizeof(bh_double4));
     const size_t o_quad64 = c.order >= 2 ? take(NN * 6 * sizeof(double)) : 0;
+    const size_t o_wrec = take(NN * bh_wrec_f4(c.order) * sizeof(float4));
     const size_t o_mfeat = take(NN * sizeof(float4));
     const size_t o_mlp = take(sizeof(bh_mlp_dev));
     const size_t S = (size_t)std::max(1, c.max_systems);
@@ -242,6 +244,7 @@ int bh_create(bh_ctx** out, const bh_config* cfg, int64_t max_n, int device)
     x->nd.quad = c.order >= 2 ? (float4*)(b + o_quad) : nullptr;
     x->nd.com64 = (bh_double4*)(b + o_com64);
     x->nd.quad64 = c.order >= 2 ? (double*)(b + o_quad64) : nullptr;
+    x->nd.wrec = (float4*)(b + o_wrec);
     x->mfeat = (float4*)(b + o_mfeat);
     x->mlp = (bh_mlp_dev*)(b + o_mlp);
     x->sys_of = (uint32_t*)(b + o_sys);
@@ -426,10 +429,12 @@ static int read_ctrl(bh_ctx* x, cudaStream_t s)
 
 int bh_selftest_wait(bh_ctx* x, int which, void* stream)
 {
-    if (!x || (which != BH_SELFTEST_TILE_RING && which != BH_SELFTEST_LOOKBACK)) return BH_ERR_INVALID;
+    if (!x || (which != BH_SELFTEST_TILE_RING && which != BH_SELFTEST_LOOKBACK && which != BH_SELFTEST_TMA))
+        return BH_ERR_INVALID;
     DeviceGuard guard(x->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (which == BH_SELFTEST_TILE_RING) bh::launch_selftest_ring(x->ctrl, s);
+    else if (which == BH_SELFTEST_TMA) bh::launch_selftest_tma(x->ctrl, s);
     else bh::launch_selftest_lookback(x->ctrl, s);
     x->launches += 1;
     if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;

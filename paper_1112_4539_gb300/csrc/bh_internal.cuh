@@ -299,7 +299,15 @@ struct bh_nodes {
     float4* quad;     // 2 per node: (xx, yy, zz, xy), (xz, yz, 1.5 T, 0.5 T)
     bh_double4* com64;   // FP64 centre of mass + mass (nodes above the FP64 threshold)
     double* quad64;   // 6 per node (FP64 nodes, order 2)
+    // walk records for the TMA-staged walk (nullptr: not kept): one contiguous
+    // record per node, so a range of siblings is one bulk copy.  float4 0 =
+    // (centre of mass, M); float4 1 = (first, count, child << 3 | (nchild - 1)
+    // or -1 for a leaf, S_eff) as bits; order 2 adds the two quad float4s.
+    float4* wrec = nullptr;
 };
+
+// float4s per walk record
+__host__ __device__ constexpr int bh_wrec_f4(int order) { return order >= 2 ? 4 : 2; }
 
 // --------------------------------------------------------------- launches
 // (bodies in the .cu files; all are stream-ordered and take device pointers)
@@ -353,6 +361,7 @@ int launch_walk(const float4* pos_s, const uint32_t* perm, const int32_t* g_firs
                 const WalkLearned* learned = nullptr, int walk_variant = 0);
 // failure-path self-tests: one bounded wait that nothing satisfies
 void launch_selftest_ring(bh_dev_ctrl* c, cudaStream_t s);
+void launch_selftest_tma(bh_dev_ctrl* c, cudaStream_t s);
 void launch_selftest_lookback(bh_dev_ctrl* c, cudaStream_t s);
 int launch_direct(const float4* src, int n_src, const float4* tgt, const int64_t* self, int n_tgt,
                   double eps, void* out, int precision, cudaStream_t s);

@@ -71,7 +71,8 @@ extern "C" int bh_tree_force_static(const float* d_pos_mass, int64_t n, const bh
         (c.block_threads != 64 && c.block_threads != 128) || c.blocks_per_sm < 0 ||
         c.blocks_per_sm > 32 || (c.curve != BH_CURVE_MORTON && c.curve != BH_CURVE_HILBERT) ||
         c.max_level != 10 ||  // the fixed scratch holds 30-bit keys only
-        (c.walk_variant != BH_WALK_ONE_WARP && c.walk_variant != BH_WALK_PAIRED))
+        (c.walk_variant != BH_WALK_ONE_WARP && c.walk_variant != BH_WALK_PAIRED &&
+         c.walk_variant != BH_WALK_TMA))  // TMA: no walk records kept here, the one-warp kernel runs
         return BH_ERR_INVALID;
     if (n < 0 || !(theta > 0.0f) || !std::isfinite(theta) || !(eps >= 0.0f) || !std::isfinite(eps))
         return BH_ERR_INVALID;

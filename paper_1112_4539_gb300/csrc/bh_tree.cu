@@ -703,10 +703,23 @@ bh_moments_level_kernel(const float4* __restrict__ pos_s, const K* __restrict__ 
         const float s = sqrtf(dx * dx + dy * dy + dz * dz);
         const float t = opening + s;
         nd.seff[v] = t * t;
+        float4 qa = make_float4(0.f, 0.f, 0.f, 0.f), qb = qa;
         if (ORDER >= 2) {
             const float T = q[0] + q[1] + q[2];
-            nd.quad[2 * (size_t)v] = make_float4(q[0], q[1], q[2], q[3]);
-            nd.quad[2 * (size_t)v + 1] = make_float4(q[4], q[5], 1.5f * T, 0.5f * T);
+            qa = make_float4(q[0], q[1], q[2], q[3]);
+            qb = make_float4(q[4], q[5], 1.5f * T, 0.5f * T);
+            nd.quad[2 * (size_t)v] = qa;
+            nd.quad[2 * (size_t)v + 1] = qb;
+        }
+        if (nd.wrec) {
+            float4* w = nd.wrec + (size_t)v * bh_wrec_f4(ORDER);
+            const int chn = r.z < 0 ? -1 : (r.z << 3) | (r.w - 1);
+            w[0] = make_float4(cx, cy, cz, M);
+            w[1] = make_float4(__int_as_float(r.x), __int_as_float(r.y), __int_as_float(chn), t * t);
+            if (ORDER >= 2) {
+                w[2] = qa;
+                w[3] = qb;
+            }
         }
     }
 }

@@ -112,6 +112,7 @@ struct WalkParams {
     const float4* mfeat;     // node-constant features
     const bh_mlp_dev* mlp;   // network (global copy)
     float theta_guard;       // theta of the S_eff in use (the guard)
+    const float4* wrec;      // walk records (TMA-staged walk)
 };
 
 // Running totals of a lane's T targets with their Kahan compensations, the
@@ -1150,6 +1151,438 @@ static int bh_walk_ws_launch(const WalkParams& P, int sm_count, cudaStream_t s)
     return BH_OK;
 }
 
+// ------------------------------------------------------------ TMA-staged walk
+// The one-warp walk with its memory traffic moved onto bulk asynchronous
+// copies (cp.async.bulk, global -> this CTA's shared memory, completed on an
+// mbarrier):
+//   * node tiles: each popped range of siblings is one copy of its walk
+//     records (centre of mass and mass, first/count/children/S_eff, the
+//     quadrupole) into the warp's node landing area, record i of the pop at
+//     slot i; the next pop is taken and its copies issued as soon as this
+//     pop's pushes are done, so they land while this pop's tiles are
+//     evaluated;
+//   * particle tiles: each batch of up to 32 particles of rejected leaves is
+//     one copy per leaf range into the particle landing area, issued before
+//     the point tiles that precede it are evaluated.
+// The landed records are converted into the same negated pair rings, in the
+// same order, as the one-warp kernel's, so the tiles and the results are the
+// same bits.  Waits are bounded (BH_ERR_DEVICE_TIMEOUT); every copy reads
+// this GPU's own memory and lands in this CTA's shared memory.
+__device__ __forceinline__ void bh_mbar_expect_tx(unsigned long long* b, unsigned int bytes)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                     bh_smem_addr(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+// bytes (a multiple of 16) from global src to shared dst, both 16-byte aligned
+__device__ __forceinline__ void bh_bulk_g2s(void* dst, const void* src, unsigned int bytes, unsigned long long* b)
+{
+    asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     bh_smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(bh_smem_addr(b))
+                 : "memory");
+}
+// order this thread's earlier generic-proxy accesses of shared memory before
+// its later async-proxy ones (a landing area is refilled after it was read)
+__device__ __forceinline__ void bh_fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// Wait for this warp's own copies: no early exit on another warp's abort
+// (copies of valid addresses always complete); false after a second on the
+// global timer or kWsSpinLimit polls, with BH_ERR_DEVICE_TIMEOUT recorded.
+__device__ __forceinline__ bool bh_mbar_wait_own(unsigned long long* b, unsigned int parity, bh_dev_ctrl* c)
+{
+    if (bh_mbar_try_wait(b, parity)) return true;
+    const unsigned long long t0 = bh_globaltimer();
+    for (int i = 0; i < kWsSpinLimit; i++) {
+        if (bh_mbar_try_wait(b, parity)) return true;
+        if ((i & 63) == 63 && bh_globaltimer() - t0 > kWsTimeoutNs) break;
+    }
+    bh_set_error(c, BH_ERR_DEVICE_TIMEOUT);
+    return false;
+}
+
+template <int ORDER>
+struct TmaLanding {
+    float4 node[32 * bh_wrec_f4(ORDER)];  // the pop's walk records, record i at slot i
+    float4 part[32];                       // a batch of particles of rejected leaves
+    unsigned long long bar_node, bar_part;
+};
+
+template <int T, int ORDER>
+__global__ void __launch_bounds__(128, bh_walk_min_blocks<T, false>()) bh_walk_tma_kernel(WalkParams P)
+{
+    constexpr int RF = bh_wrec_f4(ORDER);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    WarpSmem& S = reinterpret_cast<WarpSmem*>(smem_raw)[wib];
+    unsigned char* base = smem_raw + (size_t)nwarps * sizeof(WarpSmem);
+    WarpQuad* Q = nullptr;
+    if (ORDER >= 2) {
+        Q = reinterpret_cast<WarpQuad*>(base) + wib;
+        base += (size_t)nwarps * sizeof(WarpQuad);
+    }
+    TmaLanding<ORDER>& LD = reinterpret_cast<TmaLanding<ORDER>*>(base)[wib];
+    base += (size_t)nwarps * sizeof(TmaLanding<ORDER>);
+    float* kcol = reinterpret_cast<float*>(base + (size_t)wib * bh_kahan_smem_bytes<T>()) + lane;
+    if (lane == 0) {
+        bh_mbar_init(&LD.bar_node, 1u);
+        bh_mbar_init(&LD.bar_part, 1u);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    unsigned int ph_node = 0u, ph_part = 0u;      // phases to wait for next
+    bool node_out = false, part_out = false;      // a copy batch is in flight (warp-uniform)
+
+    const unsigned int lt = bh_lanemask_lt();
+    const float eps2 = P.eps2;
+    bh_dev_ctrl* ctrl = P.ctrl;
+    const int ng = (int)ctrl->n_groups;
+    const int n_roots = (int)ctrl->level_offset[1];
+    if (lane == 0) S.tot[0] = S.tot[1] = 0ull;
+    bool alive = true;
+
+    for (;;) {
+        int g = 0;
+        if (lane == 0) g = (int)atomicAdd(&ctrl->group_ctr, 1u);
+        g = __shfl_sync(BH_FULL_MASK, g, 0);
+        if (g >= ng) break;
+        int ab = 0;
+        if (lane == 0) ab = (int)*(volatile unsigned int*)&ctrl->abort;
+        if (__shfl_sync(BH_FULL_MASK, ab, 0)) break;
+        const int gb = P.g_first[g], gc = P.g_count[g], ge = gb + gc;
+        const int tn = (gc + 31) >> 5;
+        Layout L;
+        {
+            const int kl = gc - 32 * (tn - 1);
+            L.split = (T <= 4) && (kl <= kSplitMax);
+            L.nf = L.split ? tn - 1 : tn;
+            L.lg = L.split ? (kl > 1 ? 32 - __clz(kl - 1) : 0) : 5;
+        }
+        const int lmask = (1 << L.lg) - 1;
+
+        float xi[T], yi[T], zi[T], mi[T];
+        unsigned int lo0 = 0xffffffffu, lo1 = 0xffffffffu, lo2 = 0xffffffffu, hi0 = 0u, hi1 = 0u, hi2 = 0u;
+#pragma unroll
+        for (int t = 0; t < T; t++) {
+            const int o = t * 32 + ((L.split && t == L.nf) ? (lane & lmask) : lane);
+            float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (o < gc) {
+                q = P.pos_s[gb + o];
+                lo0 = min(lo0, bh_f2ord(q.x)); lo1 = min(lo1, bh_f2ord(q.y)); lo2 = min(lo2, bh_f2ord(q.z));
+                hi0 = max(hi0, bh_f2ord(q.x)); hi1 = max(hi1, bh_f2ord(q.y)); hi2 = max(hi2, bh_f2ord(q.z));
+            }
+            xi[t] = q.x; yi[t] = q.y; zi[t] = q.z; mi[t] = q.w;
+        }
+        {
+            const float bx0 = bh_ord2f(__reduce_min_sync(BH_FULL_MASK, lo0));
+            const float by0 = bh_ord2f(__reduce_min_sync(BH_FULL_MASK, lo1));
+            const float bz0 = bh_ord2f(__reduce_min_sync(BH_FULL_MASK, lo2));
+            const float bx1 = bh_ord2f(__reduce_max_sync(BH_FULL_MASK, hi0));
+            const float by1 = bh_ord2f(__reduce_max_sync(BH_FULL_MASK, hi1));
+            const float bz1 = bh_ord2f(__reduce_max_sync(BH_FULL_MASK, hi2));
+            if (lane == 0) {
+                S.gbox[0] = bx0; S.gbox[1] = by0; S.gbox[2] = bz0; S.gbox[3] = 0.0f;
+                S.gbox[4] = bx1; S.gbox[5] = by1; S.gbox[6] = bz1;
+            }
+            __syncwarp();
+        }
+
+        Acc<T> A;
+#if BH_KAHAN_SMEM
+        A.kc = kcol;
+#endif
+#pragma unroll
+        for (int t = 0; t < T; t++) {
+            A.x[t] = A.y[t] = A.z[t] = A.p[t] = 0.0f;
+            A.c(t, 0) = A.c(t, 1) = A.c(t, 2) = A.c(t, 3) = 0.0f;
+        }
+        bh_eval_self<T>(gc, L, eps2, xi, yi, zi, mi, A);
+        Tgt<T> X;
+#pragma unroll
+        for (int t = 0; t < T; t++) {
+            X.x[t] = make_float2(xi[t], xi[t]);
+            X.y[t] = make_float2(yi[t], yi[t]);
+            X.z[t] = make_float2(zi[t], zi[t]);
+        }
+        const f2 eps2v = make_float2(eps2, eps2);
+        unsigned int g_pc = 0u, g_pp = 0u;
+
+        int sp = 1, ring_head = 0, ring_cnt = 0, q_head = 0, q_cnt = 0;
+        int root = 0;
+        for (int hi = n_roots; hi - root > 1;) {
+            const int mid = (root + hi) >> 1;
+            if (P.rec[mid].x <= gb) root = mid;
+            else hi = mid;
+        }
+        if (lane == 0) S.stack[0] = (uint32_t)root << 3;
+        __syncwarp();
+
+        // Pop the top 32 nodes (ranges of siblings) and issue one copy of
+        // walk records per range; returns the number of nodes popped.
+        auto pop_issue = [&]() -> int {
+            int c = 0;
+            uint32_t e = 0u;
+            if (lane < sp) {
+                e = S.stack[sp - 1 - lane];
+                c = (int)(e & 7u) + 1;
+            }
+            const int incl = bh_warp_incl_scan(c);
+            const int excl = incl - c;
+            const int take = max(0, min(c, 32 - excl));
+            const int st = (int)(e >> 3);
+            const bool full = (lane < sp) && (take == c);
+            const int nfull = __popc(__ballot_sync(BH_FULL_MASK, full));
+            const int npop = min(__shfl_sync(BH_FULL_MASK, incl, 31), 32);
+            __syncwarp();
+            if (lane == nfull && lane < sp && take > 0)
+                S.stack[sp - 1 - lane] = ((uint32_t)(st + take) << 3) | (uint32_t)(c - take - 1);
+            sp -= nfull;
+            if (npop > 0) {
+                // the expected bytes are the sum of the ranges' copies (sum of take = npop)
+                bh_fence_proxy_async();
+                if (lane == 0) bh_mbar_expect_tx(&LD.bar_node, (unsigned int)(npop * RF * 16));
+                __syncwarp();
+                if (take > 0)
+                    bh_bulk_g2s(&LD.node[excl * RF], P.wrec + (size_t)st * RF, (unsigned int)(take * RF * 16),
+                                &LD.bar_node);
+                node_out = true;
+            }
+            __syncwarp();
+            return npop;
+        };
+        // Take the next batch of up to 32 particles from the pending leaf
+        // ranges at lq_pos and issue their copies; returns the batch size.
+        auto fill_issue = [&](int& lq_pos, int lq_n) -> int {
+            int c2 = 0;
+            int2 q = make_int2(0, 0);
+            if (lq_pos + lane < lq_n) {
+                q = S.leafq[lq_pos + lane];
+                c2 = q.y;
+            }
+            const int inc2 = bh_warp_incl_scan(c2);
+            const int ex2 = inc2 - c2;
+            const int take2 = max(0, min(c2, 32 - ex2));
+            const bool full2 = (lq_pos + lane < lq_n) && (take2 == c2);
+            const int nf2 = __popc(__ballot_sync(BH_FULL_MASK, full2));
+            const int nfill = min(__shfl_sync(BH_FULL_MASK, inc2, 31), 32);
+            __syncwarp();
+            if (lane == nf2 && lq_pos + lane < lq_n && take2 > 0)
+                S.leafq[lq_pos + lane] = make_int2(q.x + take2, c2 - take2);
+            lq_pos += nf2;
+            bh_fence_proxy_async();
+            if (lane == 0) bh_mbar_expect_tx(&LD.bar_part, (unsigned int)(nfill * 16));
+            __syncwarp();
+            if (take2 > 0) bh_bulk_g2s(&LD.part[ex2], P.pos_s + q.x, (unsigned int)(take2 * 16), &LD.bar_part);
+            part_out = true;
+            __syncwarp();
+            return nfill;
+        };
+
+        bool overflow = false;
+        int npop = pop_issue();
+        while (npop > 0) {
+            // ---- the pop's records have landed: test the nodes
+            if (!(alive = __all_sync(BH_FULL_MASK, bh_mbar_wait_own(&LD.bar_node, ph_node, ctrl)))) break;
+            ph_node ^= 1u;
+            node_out = false;
+            const bool has = lane < npop;
+            float4 cm = make_float4(0.f, 0.f, 0.f, 0.f), qa = cm, qb = cm;
+            int rfirst = 0, rcount = 0, rchn = -1;
+            float se = 0.f;
+            if (has) {
+                cm = LD.node[lane * RF];
+                const float4 w1 = LD.node[lane * RF + 1];
+                rfirst = __float_as_int(w1.x);
+                rcount = __float_as_int(w1.y);
+                rchn = __float_as_int(w1.z);
+                se = w1.w;
+                if (ORDER >= 2) {
+                    qa = LD.node[lane * RF + 2];
+                    qb = LD.node[lane * RF + 3];
+                }
+            }
+            const float4 gb0 = bh_lds4(S.gbox), gb1 = bh_lds4(S.gbox + 4);
+            const float dx = fmaxf(fmaxf(gb0.x - cm.x, cm.x - gb1.x), 0.0f);
+            const float dy = fmaxf(fmaxf(gb0.y - cm.y, cm.y - gb1.y), 0.0f);
+            const float dz = fmaxf(fmaxf(gb0.z - cm.z, cm.z - gb1.z), 0.0f);
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            const bool member = (rfirst < ge) && (rfirst + rcount > gb);
+            const bool acc = has && (d2 > se) && !member;
+            const bool leaf = has && !acc && (rchn < 0);
+            const bool opn = has && !acc && (rchn >= 0);
+
+            // ---- open: push child ranges
+            const unsigned int om = __ballot_sync(BH_FULL_MASK, opn);
+            const int npush = __popc(om);
+            if (sp + npush > kStackCap) {
+                overflow = true;
+                break;
+            }
+            if (opn) S.stack[sp + __popc(om & lt)] = (uint32_t)rchn;
+            sp += npush;
+
+            // ---- accept: cell sources (records already in registers)
+            const unsigned int am = __ballot_sync(BH_FULL_MASK, acc);
+            const int nacc = __popc(am);
+            g_pc += (unsigned int)nacc;
+            if (ORDER >= 2) {
+                if (acc) bh_put_quad(*Q, (q_head + q_cnt + __popc(am & lt)) & (kRing - 1), cm, qa, qb);
+                q_cnt += nacc;
+            } else {
+                if (acc) bh_put_point(S, (ring_head + ring_cnt + __popc(am & lt)) & (kRing - 1), cm);
+                ring_cnt += nacc;
+            }
+
+            // ---- rejected leaves: particle ranges outside the group
+            const int a0 = rfirst, a1 = rfirst + rcount;
+            const bool pa = leaf && (a0 < gb);
+            const bool pb = leaf && (a1 > ge);
+            const int pa_n = pa ? (min(a1, gb) - a0) : 0;
+            const int pb_s = max(a0, ge);
+            const int pb_n = pb ? (a1 - pb_s) : 0;
+            const unsigned int ma = __ballot_sync(BH_FULL_MASK, pa), mb = __ballot_sync(BH_FULL_MASK, pb);
+            const int lq_n = __popc(ma) + __popc(mb);
+            if (pa) S.leafq[__popc(ma & lt)] = make_int2(a0, pa_n);
+            if (pb) S.leafq[__popc(ma) + __popc(mb & lt)] = make_int2(pb_s, pb_n);
+            g_pp += __reduce_add_sync(BH_FULL_MASK, (unsigned int)(pa_n + pb_n));
+            __syncwarp();
+
+            // ---- the next pop: its records land while this pop's tiles run
+            npop = pop_issue();
+            int lq_pos = 0, nfill = 0;
+            bool pending = false;
+            if (lq_pos < lq_n) {
+                nfill = fill_issue(lq_pos, lq_n);
+                pending = true;
+            }
+
+            // ---- drain: quadrupole tiles, point tiles, particle batches
+            if (ORDER >= 2) {
+                while (q_cnt >= 32) {
+                    bh_quads<T, WarpQuad>(L, *Q, q_head >> 1, eps2v, X, A);
+                    q_head ^= 32;
+                    q_cnt -= 32;
+                }
+            }
+            for (;;) {
+                if (ring_cnt >= 32) {
+                    bh_points<T, kPointUnroll>(L, S.ra + (ring_head >> 1), S.rb + (ring_head >> 1), eps2v, X, A);
+                    ring_head ^= 32;
+                    ring_cnt -= 32;
+                    continue;
+                }
+                if (!pending) break;
+                if (!(alive = __all_sync(BH_FULL_MASK, bh_mbar_wait_own(&LD.bar_part, ph_part, ctrl)))) break;
+                ph_part ^= 1u;
+                part_out = false;
+                pending = false;
+                if (lane < nfill) bh_put_point(S, (ring_head + ring_cnt + lane) & (kRing - 1), LD.part[lane]);
+                ring_cnt += nfill;
+                __syncwarp();
+                if (lq_pos < lq_n) {
+                    nfill = fill_issue(lq_pos, lq_n);
+                    pending = true;
+                }
+            }
+            if (!alive) break;
+        }
+        if (!alive) break;
+        if (overflow) {
+            // the next pop was not issued (the loop ended at the push); nothing is in flight
+            if (lane == 0) bh_set_error(ctrl, BH_ERR_CAPACITY);
+            break;
+        }
+        if (lane == 0) {
+            S.tot[0] += ((unsigned long long)g_pp + (unsigned long long)(gc - 1)) * (unsigned long long)gc;
+            S.tot[1] += (unsigned long long)g_pc * (unsigned long long)gc;
+        }
+        // ---- flush the partial tiles (padded with far, massless sources)
+        if (ORDER >= 2 && q_cnt > 0) {
+            if (lane >= q_cnt)
+                bh_put_quad(*Q, q_head + lane, bh_pad_source(), make_float4(0.f, 0.f, 0.f, 0.f),
+                            make_float4(0.f, 0.f, 0.f, 0.f));
+            __syncwarp();
+            bh_quads<T, WarpQuad>(L, *Q, q_head >> 1, eps2v, X, A);
+        }
+        if (ring_cnt > 0) {
+            if (lane >= ring_cnt) bh_put_point(S, ring_head + lane, bh_pad_source());
+            __syncwarp();
+            bh_points<T, kPointUnroll>(L, S.ra + (ring_head >> 1), S.rb + (ring_head >> 1), eps2v, X, A);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < T; t++) {
+            float4 f = make_float4(A.x[t] - A.c(t, 0), A.y[t] - A.c(t, 1), A.z[t] - A.c(t, 2), A.p[t] - A.c(t, 3));
+            if (L.split && t == L.nf) {
+                for (int off = 1 << L.lg; off < 32; off <<= 1) {
+                    f.x += __shfl_xor_sync(BH_FULL_MASK, f.x, off);
+                    f.y += __shfl_xor_sync(BH_FULL_MASK, f.y, off);
+                    f.z += __shfl_xor_sync(BH_FULL_MASK, f.z, off);
+                    f.w += __shfl_xor_sync(BH_FULL_MASK, f.w, off);
+                }
+            }
+            const int o = t * 32 + lane;
+            if (o < gc) P.out[P.perm[gb + o]] = f;
+        }
+    }
+    // a wait gave up: wait once more (bounded) for copies still in flight
+    // into this warp's landing areas before the block's shared memory goes
+    if (node_out) bh_mbar_wait_own(&LD.bar_node, ph_node, ctrl);
+    if (part_out) bh_mbar_wait_own(&LD.bar_part, ph_part, ctrl);
+    if (lane == 0) {
+        const unsigned long long cnt_pp = S.tot[0], cnt_pc = S.tot[1];
+        atomicAdd(&ctrl->n_pp, cnt_pp);
+        atomicAdd(&ctrl->n_pc, cnt_pc);
+        atomicAdd(&ctrl->cum_pp, cnt_pp);
+        atomicAdd(&ctrl->cum_pc, cnt_pc);
+    }
+}
+
+template <int T, int ORDER>
+static int bh_walk_tma_launch_t(const WalkParams& P, int sm_count, int block_threads, int blocks_per_sm,
+                                cudaStream_t s)
+{
+    const int nw = block_threads / 32;
+    const size_t smem = (size_t)nw * (sizeof(WarpSmem) + (ORDER >= 2 ? sizeof(WarpQuad) : 0) +
+                                      sizeof(TmaLanding<ORDER>) + bh_kahan_smem_bytes<T>());
+    auto kern = bh_walk_tma_kernel<T, ORDER>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return BH_ERR_CUDA;
+    int bps = blocks_per_sm;
+    if (bps <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, block_threads, smem) != cudaSuccess || bps < 1)
+            bps = 1;
+    }
+    kern<<<sm_count * bps, block_threads, smem, s>>>(P);
+    return BH_OK;
+}
+
+static int bh_walk_tma_dispatch(const WalkParams& P, int order, int G, int sm_count, int block_threads,
+                                int blocks_per_sm, cudaStream_t s)
+{
+    const int T = G <= 32 ? 1 : G <= 64 ? 2 : G <= 96 ? 3 : G <= 128 ? 4 : 8;
+    if (order >= 2) {
+        switch (T) {
+            case 1: return bh_walk_tma_launch_t<1, 2>(P, sm_count, block_threads, blocks_per_sm, s);
+            case 2: return bh_walk_tma_launch_t<2, 2>(P, sm_count, block_threads, blocks_per_sm, s);
+            case 3: return bh_walk_tma_launch_t<3, 2>(P, sm_count, block_threads, blocks_per_sm, s);
+            case 4: return bh_walk_tma_launch_t<4, 2>(P, sm_count, block_threads, blocks_per_sm, s);
+            default: return bh_walk_tma_launch_t<8, 2>(P, sm_count, block_threads, blocks_per_sm, s);
+        }
+    }
+    switch (T) {
+        case 1: return bh_walk_tma_launch_t<1, 1>(P, sm_count, block_threads, blocks_per_sm, s);
+        case 2: return bh_walk_tma_launch_t<2, 1>(P, sm_count, block_threads, blocks_per_sm, s);
+        case 3: return bh_walk_tma_launch_t<3, 1>(P, sm_count, block_threads, blocks_per_sm, s);
+        case 4: return bh_walk_tma_launch_t<4, 1>(P, sm_count, block_threads, blocks_per_sm, s);
+        default: return bh_walk_tma_launch_t<8, 1>(P, sm_count, block_threads, blocks_per_sm, s);
+    }
+}
+
 // Self-test of the failure path: one warp waits on a tile-ring mbarrier that
 // nothing will arrive on.  bh_mbar_wait gives up within a second and
 // records BH_ERR_DEVICE_TIMEOUT, as a stalled pair of the paired walk would.
@@ -1164,6 +1597,28 @@ __global__ void bh_selftest_ring_kernel(bh_dev_ctrl* c)
 void launch_selftest_ring(bh_dev_ctrl* c, cudaStream_t s)
 {
     bh_selftest_ring_kernel<<<1, 32, 0, s>>>(c);
+}
+
+// Self-test of the TMA-staged walk's wait: the mbarrier is told to expect 16
+// bytes (as a batch of copies would) but no copy is issued, so
+// bh_mbar_wait_own gives up within a second and records BH_ERR_DEVICE_TIMEOUT.
+// Nothing is in flight when the kernel returns.
+__global__ void bh_selftest_tma_kernel(bh_dev_ctrl* c)
+{
+    __shared__ unsigned long long bar;
+    if (threadIdx.x == 0) {
+        bh_mbar_init(&bar, 1u);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    if (threadIdx.x == 0) bh_mbar_expect_tx(&bar, 16u);
+    __syncwarp();
+    bh_mbar_wait_own(&bar, 0u, c);
+}
+
+void launch_selftest_tma(bh_dev_ctrl* c, cudaStream_t s)
+{
+    bh_selftest_tma_kernel<<<1, 32, 0, s>>>(c);
 }
 
 __global__ void bh_walk_reset_kernel(bh_dev_ctrl* c)
@@ -1239,12 +1694,15 @@ int launch_walk(const float4* pos_s, const uint32_t* perm, const int32_t* g_firs
     P.mfeat = nullptr;
     P.mlp = nullptr;
     P.theta_guard = 1.0f;
+    P.wrec = nd.wrec;
     if (learned) {
         P.mfeat = learned->mfeat;
         P.mlp = learned->mlp;
         P.theta_guard = learned->theta_guard;
         return bh_walk_dispatch<true>(P, order, G, sm_count, block_threads, blocks_per_sm, s);
     }
+    if (walk_variant == BH_WALK_TMA && nd.wrec)
+        return bh_walk_tma_dispatch(P, order, G, sm_count, block_threads, blocks_per_sm, s);
     if (walk_variant == BH_WALK_PAIRED && G <= 96) {
         const int T = G <= 32 ? 1 : G <= 64 ? 2 : 3;
         if (order >= 2) {

@@ -1,7 +1,8 @@
 """Bounded device waits end, are reported, and leave the context usable.
 
-The library's kernels wait in two places: the paired walk's tile ring
-(mbarriers) and the sort's decoupled look-back.  bh_selftest_wait launches
+The library's kernels wait in three places: the paired walk's tile ring
+(mbarriers), the sort's decoupled look-back and the TMA-staged walk's
+mbarriers for its bulk copies.  bh_selftest_wait launches
 one such wait that nothing will satisfy, through the same device functions;
 the test checks that it gives up on its own, that bh_status reports
 BH_ERR_DEVICE_TIMEOUT once (then clears it), and that the next force
@@ -30,11 +31,11 @@ def bh():
     return m
 
 
-@pytest.mark.parametrize("which", [0, 1])
+@pytest.mark.parametrize("which", [0, 1, 2])
 def test_bounded_wait_times_out_and_context_recovers(bh, which):
     pos = workloads.plummer(4096, seed=0)
     x = _cuda(pos)
-    for variant in (bh.WALK_ONE_WARP, bh.WALK_PAIRED):
+    for variant in (bh.WALK_ONE_WARP, bh.WALK_PAIRED, bh.WALK_TMA):
         ctx = bh.Context(4096, leaf_size=8, group_size=64, order=2, walk_variant=variant)
         ref = ctx.evaluate(x, 0.5, 0.01).cpu().numpy()
         assert ctx.status() == bh.BH_OK

@@ -135,4 +135,4 @@ def test_paired_large_group_takes_one_warp_kernel(bh):
 
 def test_invalid_variant_rejected(bh):
     with pytest.raises(bh.BhError):
-        bh.Context(100, walk_variant=2)
+        bh.Context(100, walk_variant=3)

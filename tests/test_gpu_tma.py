@@ -1,0 +1,136 @@
+"""The TMA-staged walk kernel (bh_config.walk_variant = BH_WALK_TMA) against
+the one-warp kernel.
+
+The TMA kernel moves the walk's loads onto bulk asynchronous copies: the walk
+records of each popped range of sibling nodes and the particles of each
+batch of rejected leaves are copied into shared memory by cp.async.bulk and
+completed on mbarriers; the next pop's records are copied while the current
+tiles are evaluated.  The landed records are turned into the same source
+tiles, in the same order, as the one-warp kernel's, so every output must
+carry the same bits and the interaction counts must agree (the one-warp
+kernel is held to the oracle by the parity suites; the TMA kernel also meets
+the oracle bar directly below).  The sets cover both orders, every target
+slot count (G from 17 to 256), split and unsplit last slots, tiny systems,
+large leaves, 63-bit keys, the Hilbert order and several systems in one call.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from test_gpu_parity import MARGIN, _check_force, _cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bh():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1112_4539_gb300 import _build
+    _build.build()
+    import paper_1112_4539_gb300 as m
+    m.lib()
+    return m
+
+
+def _both(bh, pos, theta, eps, **cfg):
+    x = _cuda(pos)
+    res = []
+    for variant in (bh.WALK_ONE_WARP, bh.WALK_TMA):
+        ctx = bh.Context(max(pos.shape[0], 1), walk_variant=variant, **cfg)
+        out = ctx.evaluate(x, theta, eps).cpu().numpy()
+        assert ctx.status() == 0
+        st = ctx.stats()
+        res.append((out, st["n_pp"], st["n_pc"]))
+        ctx.close()
+    return res
+
+
+@pytest.mark.parametrize("kind,n,seed,theta,eps,leaf,G,order", [
+    ("plummer", 4096, 0, 0.5, 0.01, 8, 64, 1),
+    ("clumpy", 100003, 2, 0.525, 1e-3, 16, 96, 2),   # the benchmark's configuration
+    ("clumpy", 100003, 2, 0.6, 1e-3, 16, 96, 1),
+    ("uniform", 65537, 7, 0.8, 0.01, 1, 32, 2),
+    ("sphere", 30001, 5, 1.0, 0.01, 8, 80, 2),       # last slot of 16: split into 2 phases
+    ("plummer", 50000, 3, 0.4, 0.01, 4, 50, 2),      # last slot of 18: not split
+    ("plummer", 20000, 9, 0.5, 0.01, 8, 40, 1),      # last slot of 8: 4 phases
+    ("clumpy", 40000, 8, 0.5, 1e-3, 16, 17, 2),      # T = 1 with a split slot
+    ("plummer", 30000, 11, 0.5, 0.01, 8, 128, 2),    # T = 4
+    ("clumpy", 30000, 12, 0.6, 1e-3, 8, 256, 1),     # T = 8
+    ("clumpy", 30000, 12, 0.6, 1e-3, 64, 200, 2),    # leaves of up to 64 particles
+])
+def test_tma_bits_equal_one_warp(bh, kind, n, seed, theta, eps, leaf, G, order):
+    pos = workloads.make(kind, n, seed)
+    (a, pp_a, pc_a), (b, pp_b, pc_b) = _both(bh, pos, theta, eps, leaf_size=leaf, group_size=G, order=order)
+    np.testing.assert_array_equal(a, b)
+    assert (pp_a, pc_a) == (pp_b, pc_b)
+
+
+@pytest.mark.parametrize("n", [1, 2, 31, 33, 97])
+def test_tma_tiny_systems(bh, n):
+    pos = workloads.plummer(n, seed=40 + n)
+    (a, _, _), (b, _, _) = _both(bh, pos, 0.5, 0.01, leaf_size=8, group_size=96, order=2)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_tma_knot_deep_keys_and_hilbert(bh):
+    # a 400-particle knot: level-10 leaves far larger than a particle batch
+    rng = np.random.default_rng(4)
+    knot = np.concatenate([0.3 + 1e-4 * rng.random((400, 3)), np.full((400, 1), 1.0 / 30011)], 1)
+    pos = np.concatenate([workloads.clumpy(30011 - 400, seed=4), knot]).astype(np.float32)
+    for curve in (0, 1):
+        for max_level in (10, 21):
+            (a, pa, ca), (b, pb, cb) = _both(bh, pos, 0.6, 1e-3, leaf_size=16, group_size=96, order=2,
+                                             curve=curve, max_level=max_level)
+            np.testing.assert_array_equal(a, b)
+            assert (pa, ca) == (pb, cb)
+
+
+def test_tma_against_oracle(bh, orc):
+    pos = workloads.clumpy(30007, seed=2)
+    ctx = bh.Context(pos.shape[0], leaf_size=16, group_size=96, order=2, walk_variant=bh.WALK_TMA)
+    got = ctx.evaluate(_cuda(pos), 0.525, 1e-3).cpu().numpy().astype(np.float64)
+    assert ctx.status() == 0
+    ref, _ = orc.tree_force(pos, 0.525, 1e-3, n_leaf=16, G=96, order=2, walk="group")
+    _check_force(got, ref["out"], ref["margin"], a_abs=ref["a_abs"], case="clumpy 30007, TMA walk")
+    st = ctx.stats()
+    if (ref["margin"] >= MARGIN).all():
+        assert st["n_pp"] == int(ref["n_pp"].sum()) and st["n_pc"] == int(ref["n_pc"].sum())
+    ctx.close()
+
+
+def test_tma_batched(bh):
+    import torch
+    sizes = [1, 300, 65536, 0, 1025, 20000]
+    parts = [workloads.plummer(s, seed=90 + k) if s else np.zeros((0, 4), np.float32) for k, s in enumerate(sizes)]
+    pos = np.concatenate(parts)
+    offs = np.zeros(len(sizes) + 1, np.int64)
+    offs[1:] = np.cumsum(sizes)
+    x = _cuda(pos)
+    outs = []
+    for variant in (bh.WALK_ONE_WARP, bh.WALK_TMA):
+        ctx = bh.Context(pos.shape[0], leaf_size=8, group_size=96, order=2, max_systems=len(sizes),
+                         walk_variant=variant)
+        assert bh.bh_batch_layout(ctx.h, offs) == 0
+        out = torch.full_like(x, float("nan"))
+        assert bh.bh_force_batched(ctx.h, x, 0.5, 0.01, out) == 0
+        assert ctx.status() == 0
+        outs.append(out.cpu().numpy())
+        ctx.close()
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
+def test_tma_repeated_and_interleaved_with_other_kernels(bh):
+    # landing areas and mbarrier phases start afresh in every launch: repeated
+    # evaluations, and evaluations between other kernels' launches, keep their bits
+    import torch
+    pos = workloads.clumpy(60000, seed=13)
+    x = _cuda(pos)
+    ctx = bh.Context(pos.shape[0], leaf_size=16, group_size=96, order=2, walk_variant=bh.WALK_TMA)
+    ref = ctx.evaluate(x, 0.525, 1e-3).clone()
+    for _ in range(3):
+        out = ctx.evaluate(x, 0.525, 1e-3)
+        assert torch.equal(out, ref)
+        ctx.neighbors(x, 0.01)
+    assert ctx.status() == 0
+    ctx.close()
