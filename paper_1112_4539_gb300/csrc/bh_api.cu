@@ -245,7 +245,6 @@ int bh_create(bh_ctx** out, const bh_config* cfg, int64_t max_n, int device)
     x->nd.com64 = (bh_double4*)(b + o_com64);
     x->nd.quad64 = c.order >= 2 ? (double*)(b + o_quad64) : nullptr;
     x->nd.wrec = (float4*)(b + o_wrec);
-    x->nd.wrec_stride = (int64_t)NN;
     x->mfeat = (float4*)(b + o_mfeat);
     x->mlp = (bh_mlp_dev*)(b + o_mlp);
     x->sys_of = (uint32_t*)(b + o_sys);

@@ -299,14 +299,11 @@ struct bh_nodes {
     float4* quad;     // 2 per node: (xx, yy, zz, xy), (xz, yz, 1.5 T, 0.5 T)
     bh_double4* com64;   // FP64 centre of mass + mass (nodes above the FP64 threshold)
     double* quad64;   // 6 per node (FP64 nodes, order 2)
-    // walk records for the TMA-staged walk (nullptr: not kept), one float4
-    // array per component so that a range of siblings is one bulk copy per
-    // component and each lane reads its node's components from consecutive
-    // 16-byte slots: component 0 = (centre of mass, M); 1 = (first, count,
-    // child << 3 | (nchild - 1) or -1 for a leaf, S_eff) as bits; order 2 adds
-    // the two quad float4s.  Component c of node v is wrec[c * wrec_stride + v].
+    // walk records for the TMA-staged walk (nullptr: not kept): one contiguous
+    // record per node, so a range of siblings is one bulk copy.  float4 0 =
+    // (centre of mass, M); float4 1 = (first, count, child << 3 | (nchild - 1)
+    // or -1 for a leaf, S_eff) as bits; order 2 adds the two quad float4s.
     float4* wrec = nullptr;
-    int64_t wrec_stride = 0;
 };
 
 // float4s per walk record

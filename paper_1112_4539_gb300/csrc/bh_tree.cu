@@ -712,14 +712,13 @@ bh_moments_level_kernel(const float4* __restrict__ pos_s, const K* __restrict__ 
             nd.quad[2 * (size_t)v + 1] = qb;
         }
         if (nd.wrec) {
-            float4* w = nd.wrec + v;
-            const size_t st = (size_t)nd.wrec_stride;
+            float4* w = nd.wrec + (size_t)v * bh_wrec_f4(ORDER);
             const int chn = r.z < 0 ? -1 : (r.z << 3) | (r.w - 1);
             w[0] = make_float4(cx, cy, cz, M);
-            w[st] = make_float4(__int_as_float(r.x), __int_as_float(r.y), __int_as_float(chn), t * t);
+            w[1] = make_float4(__int_as_float(r.x), __int_as_float(r.y), __int_as_float(chn), t * t);
             if (ORDER >= 2) {
-                w[2 * st] = qa;
-                w[3 * st] = qb;
+                w[2] = qa;
+                w[3] = qb;
             }
         }
     }

@@ -112,7 +112,7 @@ struct WalkParams {
     const float4* mfeat;     // node-constant features
     const bh_mlp_dev* mlp;   // network (global copy)
     float theta_guard;       // theta of the S_eff in use (the guard)
-    const float4* wrec[4];   // walk-record component arrays (TMA-staged walk)
+    const float4* wrec;      // walk records (TMA-staged walk)
 };
 
 // Running totals of a lane's T targets with their Kahan compensations, the
@@ -1155,12 +1155,10 @@ static int bh_walk_ws_launch(const WalkParams& P, int sm_count, cudaStream_t s)
 // The one-warp walk with its memory traffic moved onto bulk asynchronous
 // copies (cp.async.bulk, global -> this CTA's shared memory, completed on an
 // mbarrier):
-//   * node tiles: each popped range of siblings is one copy per component
-//     of its walk records (centre of mass and mass, first/count/children/
-//     S_eff, the quadrupole) into the warp's node landing area, record i of
-//     the pop at slot i of each component (so every lane reads its record
-//     from consecutive 16-byte slots, without bank conflicts); the next pop
-//     is taken and its copies issued as soon as this
+//   * node tiles: each popped range of siblings is one copy of its walk
+//     records (centre of mass and mass, first/count/children/S_eff, the
+//     quadrupole) into the warp's node landing area, record i of the pop at
+//     slot i; the next pop is taken and its copies issued as soon as this
 //     pop's pushes are done, so they land while this pop's tiles are
 //     evaluated;
 //   * particle tiles: each batch of up to 32 particles of rejected leaves is
@@ -1208,15 +1206,10 @@ __device__ __forceinline__ bool bh_mbar_wait_own(unsigned long long* b, unsigned
 
 template <int ORDER>
 struct TmaLanding {
-    float4 node[bh_wrec_f4(ORDER)][32];  // the pop's walk records: component c of record i at [c][i]
-    float4 part[32];                      // a batch of particles of rejected leaves
+    float4 node[32 * bh_wrec_f4(ORDER)];  // the pop's walk records, record i at slot i
+    float4 part[32];                       // a batch of particles of rejected leaves
     unsigned long long bar_node, bar_part;
 };
-// Fence generic-proxy reads of a landing area before the async copies that
-// refill it (1), or rely on the warp barrier between them alone (0).
-#ifndef BH_TMA_FENCE
-#define BH_TMA_FENCE 1
-#endif
 
 template <int T, int ORDER>
 __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, false>()) bh_walk_tma_kernel(WalkParams P)
@@ -1350,14 +1343,12 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, false>()) bh_walk_t
             sp -= nfull;
             if (npop > 0) {
                 // the expected bytes are the sum of the ranges' copies (sum of take = npop)
-                if (BH_TMA_FENCE) bh_fence_proxy_async();
+                bh_fence_proxy_async();
                 if (lane == 0) bh_mbar_expect_tx(&LD.bar_node, (unsigned int)(npop * RF * 16));
                 __syncwarp();
-                if (take > 0) {
-#pragma unroll
-                    for (int k = 0; k < RF; k++)
-                        bh_bulk_g2s(&LD.node[k][excl], P.wrec[k] + st, (unsigned int)(take * 16), &LD.bar_node);
-                }
+                if (take > 0)
+                    bh_bulk_g2s(&LD.node[excl * RF], P.wrec + (size_t)st * RF, (unsigned int)(take * RF * 16),
+                                &LD.bar_node);
                 node_out = true;
             }
             __syncwarp();
@@ -1382,7 +1373,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, false>()) bh_walk_t
             if (lane == nf2 && lq_pos + lane < lq_n && take2 > 0)
                 S.leafq[lq_pos + lane] = make_int2(q.x + take2, c2 - take2);
             lq_pos += nf2;
-            if (BH_TMA_FENCE) bh_fence_proxy_async();
+            bh_fence_proxy_async();
             if (lane == 0) bh_mbar_expect_tx(&LD.bar_part, (unsigned int)(nfill * 16));
             __syncwarp();
             if (take2 > 0) bh_bulk_g2s(&LD.part[ex2], P.pos_s + q.x, (unsigned int)(take2 * 16), &LD.bar_part);
@@ -1403,15 +1394,15 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, false>()) bh_walk_t
             int rfirst = 0, rcount = 0, rchn = -1;
             float se = 0.f;
             if (has) {
-                cm = LD.node[0][lane];
-                const float4 w1 = LD.node[1][lane];
+                cm = LD.node[lane * RF];
+                const float4 w1 = LD.node[lane * RF + 1];
                 rfirst = __float_as_int(w1.x);
                 rcount = __float_as_int(w1.y);
                 rchn = __float_as_int(w1.z);
                 se = w1.w;
                 if (ORDER >= 2) {
-                    qa = LD.node[2][lane];
-                    qb = LD.node[3][lane];
+                    qa = LD.node[lane * RF + 2];
+                    qb = LD.node[lane * RF + 3];
                 }
             }
             const float4 gb0 = bh_lds4(S.gbox), gb1 = bh_lds4(S.gbox + 4);
@@ -1703,7 +1694,7 @@ int launch_walk(const float4* pos_s, const uint32_t* perm, const int32_t* g_firs
     P.mfeat = nullptr;
     P.mlp = nullptr;
     P.theta_guard = 1.0f;
-    for (int k = 0; k < 4; k++) P.wrec[k] = nd.wrec ? nd.wrec + (size_t)k * nd.wrec_stride : nullptr;
+    P.wrec = nd.wrec;
     if (learned) {
         P.mfeat = learned->mfeat;
         P.mlp = learned->mlp;
