@@ -86,6 +86,8 @@ def parse():
     ap.add_argument("--leaf", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-criterion comparison")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="headline run only: skip the TMA-walk, 512-system and fresh-4M blocks")
     ap.add_argument("--cpu-sample-groups", type=int, default=6000)
     ap.add_argument("--walk", default="group", choices=["group", "particle"],
                     help="group: one warp per particle group; particle: the paper's per-particle walk (Fig. 5)")
@@ -588,6 +590,20 @@ def run_ours(args, W):
 
     if not args.no_learned and walk == "group" and os.path.exists(WEIGHTS):
         line["learned_mac"] = learned_comparison(bh, ctx, x0, idx_t, ref, eps, theta, G, leaf, order)
+    if args.workload == "clumpy16m" and walk == "group" and world == 1 and not args.no_extra:
+        # the other configurations of the benchmark, measured in the same run
+        ref_out = torch.empty_like(x0)
+        ctx.evaluate(x0, theta, eps, ref_out)
+        if args.walk_kernel == "one-warp":
+            line["tma_walk"] = tma_block(bh, local, x0, theta, eps, leaf, G, order, ref_out)
+            line["tma_walk"]["one_warp_walk_ms"] = walk_ms
+        ctx.close()
+        ctx = None
+        torch.cuda.empty_cache()
+        line["batched512"] = batched_block(local)
+        if not args.no_learned and os.path.exists(WEIGHTS):
+            line["learned_fresh4m"] = {name: learned_fresh_block(bh, local, name)
+                                       for name in ("clumpy4m", "plummer4m")}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_throughput(pos_np, theta, eps, leaf, G, order, args.cpu_sample_groups, walk=walk,
@@ -599,7 +615,8 @@ def run_ours(args, W):
                                           "built before, in %.2f s (not in the rate); a whole evaluation at this "
                                           "rate: about %.0f s" % (walk, cb["groups"], cb["ng"], unit_s, cb["t_walk"],
                                                                   cb["t_build"], cb["s_per_eval_estimate"])}
-    ctx.close()
+    if ctx is not None:
+        ctx.close()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
@@ -607,20 +624,16 @@ def run_ours(args, W):
     return 0
 
 
-def run_batched(args, W):
+def batched_measure(W, local, rank, steps, warmup, world=1, dev=None):
     """All systems per step in one graph replay (tuned launch configuration),
-    against a loop of per-system evaluations with plain launches."""
+    against a loop of per-system evaluations with plain launches, and end to
+    end with host copies.  Returns a dict of the measurements."""
     import torch
 
     import paper_1112_4539_gb300 as bh
     from paper_1112_4539_gb300 import autotune
 
-    rank, local, world = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+    dev = dev or torch.device("cuda", local)
     pos_np, offs = workloads.batched_plummer(W["nsys"], W["nmin"], W["nmax"], seed=W["seed"] + rank)
     n, nsys = pos_np.shape[0], W["nsys"]
     x = torch.from_numpy(pos_np).to(dev)
@@ -632,7 +645,7 @@ def run_batched(args, W):
     l0 = ctx.stats()["launches"]
     graph = bh.BatchedGraph(ctx, x, theta, eps, out)
     per_eval_launches = ctx.stats()["launches"] - l0
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         graph.launch()
     torch.cuda.synchronize()
     if world > 1:
@@ -643,7 +656,7 @@ def run_batched(args, W):
     time.sleep(0.3)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         graph.launch()
     e1.record()
     torch.cuda.synchronize()
@@ -656,8 +669,6 @@ def run_batched(args, W):
     n_pp = s1["n_pp_total"] - s0["n_pp_total"]
     n_pc = s1["n_pc_total"] - s0["n_pc_total"]
     inter = float(n_pp + n_pc)
-    tot_inter, max_ms = whole_job(inter, t_ms, world, dev)
-    value = tot_inter / (max_ms * 1e-3) / 1e9
     # the per-system loop of plain launches (same configuration)
     single = bh.Context(int(np.max(np.diff(offs))), device=local, order=order, **cfg)
     xs = [x[offs[k]:offs[k + 1]].contiguous() for k in range(nsys)]
@@ -679,38 +690,126 @@ def run_batched(args, W):
     h_out = torch.empty_like(h_pos).pin_memory()
     g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     g0.record()
-    for _ in range(args.steps):
+    for _ in range(steps):
         x.copy_(h_pos, non_blocking=True)
         graph.launch()
         h_out.copy_(out, non_blocking=True)
     g1.record()
     torch.cuda.synchronize()
     e2e_ms = g0.elapsed_time(g1)
+    graph.close()
+    ctx.close()
+    return dict(t_ms=t_ms, n_pp=n_pp, n_pc=n_pc, inter=inter, n=n, nsys=nsys, cfg=cfg, table=table,
+                per_eval_launches=per_eval_launches, loop_ms=loop_ms, same=same, e2e_ms=e2e_ms,
+                h2d=int(h_pos.numel() * 4), d2h=int(h_out.numel() * 4), clocks=clk)
+
+
+def run_batched(args, W):
+    """All systems per step in one graph replay; prints the JSON line."""
+    import torch
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    m = batched_measure(W, local, rank, args.steps, args.warmup, world, dev)
+    tot_inter, max_ms = whole_job(m["inter"], m["t_ms"], world, dev)
+    value = tot_inter / (max_ms * 1e-3) / 1e9
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    flops = (n_pp * FLOPS_PP + n_pc * (FLOPS_PC_QUAD if order >= 2 else FLOPS_PP)) / args.steps
-    achieved = flops / (t_ms / args.steps * 1e-3) / 1e12
+    order = W["order"]
+    flops = (m["n_pp"] * FLOPS_PP + m["n_pc"] * (FLOPS_PC_QUAD if order >= 2 else FLOPS_PP)) / args.steps
+    achieved = flops / (m["t_ms"] / args.steps * 1e-3) / 1e12
     peak = sms * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": W["desc"], "n_total": n, "n_systems": nsys, "theta": theta, "order": order,
-                       "tuned": cfg, "tuning_table": table, "interactions_per_step": inter / args.steps,
+            "config": {"workload": W["desc"], "n_total": m["n"], "n_systems": m["nsys"], "theta": W["theta"],
+                       "order": order, "tuned": m["cfg"], "tuning_table": m["table"],
+                       "interactions_per_step": m["inter"] / args.steps,
                        "l2": "inputs 126 MB, tree work arrays > L2 (no flush)"},
-            "per_system_loop": {"ms_per_step": loop_ms, "launches": nsys * 30, "identical_results": same,
-                                "speedup_of_graph": loop_ms / (max_ms / args.steps)},
-            "e2e": {"value": inter / (e2e_ms * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(h_pos.numel() * 4),
-                    "d2h_bytes_per_step": int(h_out.numel() * 4), "ms_per_step": e2e_ms / args.steps},
-            "gpu_launches": per_eval_launches * args.steps,
+            "per_system_loop": {"ms_per_step": m["loop_ms"], "launches": m["nsys"] * 30,
+                                "identical_results": m["same"],
+                                "speedup_of_graph": m["loop_ms"] / (max_ms / args.steps)},
+            "e2e": {"value": m["inter"] / (m["e2e_ms"] * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": m["h2d"],
+                    "d2h_bytes_per_step": m["d2h"], "ms_per_step": m["e2e_ms"] / args.steps},
+            "gpu_launches": m["per_eval_launches"] * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": None, "kernel": "whole batched evaluation (graph replay)"},
-            "clocks": clk}
-    graph.close()
-    ctx.close()
+            "clocks": m["clocks"]}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def batched_block(local):
+    """The 512-system workload as a block of the headline line: one graph
+    replay of all systems per evaluation against the per-system loop."""
+    W = WORKLOADS["batched512"]
+    steps = 10
+    m = batched_measure(W, local, 0, steps, 3)
+    ms = m["t_ms"] / steps
+    return {"workload": W["desc"], "n_total": m["n"], "n_systems": m["nsys"], "tuned": m["cfg"],
+            "ms_per_eval": ms, "ginteractions_per_s": m["inter"] / (m["t_ms"] * 1e-3) / 1e9,
+            "per_system_loop_ms": m["loop_ms"], "speedup_of_graph": m["loop_ms"] / ms,
+            "identical_results": m["same"], "e2e_ms_per_eval": m["e2e_ms"] / steps, "steps": steps,
+            "clocks": m["clocks"]}
+
+
+def learned_fresh_block(bh, local, name):
+    """The learned criterion against theta on a fresh 4,194,304-particle set
+    (seed 4, not in the training data): theta and tau each bisected to
+    p99 = 1e-3 against the FP64 direct judge, then whole evaluations timed."""
+    import torch
+    W = WORKLOADS[name]
+    dev = torch.device("cuda", local)
+    pos = workloads.make(W["kind"], W["n"], W["seed"])
+    x = torch.from_numpy(pos).to(dev)
+    ctx = bh.Context(W["n"], device=local, leaf_size=W["leaf"], group_size=W["G"], order=W["order"])
+    idx = workloads.sample_targets(W["n"], 4096, seed=101)
+    idx_t = torch.from_numpy(idx).to(dev)
+    ref = torch.empty((idx.size, 4), dtype=torch.float64, device=dev)
+    assert bh.direct_force(x, x[idx_t].contiguous(), idx_t, W["eps"], ref, 64) == 0
+    acc = torch.empty_like(x)
+    clocks = ClockSampler(local)
+    clocks.start()
+    theta = calibrate(ctx, x, idx_t, ref, W["eps"], acc)
+    res = learned_comparison(bh, ctx, x, idx_t, ref, W["eps"], theta, W["G"], W["leaf"], W["order"])
+    res["clocks"] = clocks.stop()
+    res["workload"] = W["desc"]
+    ctx.close()
+    return res
+
+
+def tma_block(bh, local, x, theta, eps, leaf, G, order, ref_out):
+    """The TMA-staged walk kernel on the headline particles: whole evaluations
+    and walk time, and whether its forces carry the one-warp kernel's bits."""
+    import torch
+    ctx = bh.Context(x.shape[0], device=local, leaf_size=leaf, group_size=G, order=order, walk_variant=bh.WALK_TMA)
+    acc = torch.empty_like(x)
+    ctx.evaluate(x, theta, eps, acc)
+    same = bool(torch.equal(acc, ref_out))
+    walk, tot = [], []
+    for _ in range(4):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        ctx.build(x)
+        ctx.moments(theta)
+        e1.record()
+        ctx.force(eps, acc)
+        e2.record()
+        torch.cuda.synchronize()
+        walk.append(e1.elapsed_time(e2))
+        tot.append(e0.elapsed_time(e2))
+    assert ctx.status() == 0
+    ctx.close()
+    return {"kernel": "bh_walk_tma_kernel", "ms_per_eval": float(np.median(tot)), "walk_ms": float(np.median(walk)),
+            "same_bits_as_one_warp": same,
+            "staging": "node walk records per sibling range and leaf-particle batches by cp.async.bulk into "
+                       "shared memory (mbarrier completion)"}
 
 
 def run_accuracy_sweep(args):
