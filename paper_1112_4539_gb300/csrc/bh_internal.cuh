@@ -302,12 +302,15 @@ struct bh_nodes {
     // walk records for the TMA-staged walk (nullptr: not kept): one contiguous
     // record per node, so a range of siblings is one bulk copy.  float4 0 =
     // (centre of mass, M); float4 1 = (first, count, child << 3 | (nchild - 1)
-    // or -1 for a leaf, S_eff) as bits; order 2 adds the two quad float4s.
+    // or -1 for a leaf, S_eff) as bits; order 2 adds the two quad float4s;
+    // one float4 of padding makes the record an odd number of float4s, so
+    // that 8 lanes reading records i..i+7 from shared memory hit 8 distinct
+    // bank quads (no conflicts).
     float4* wrec = nullptr;
 };
 
-// float4s per walk record
-__host__ __device__ constexpr int bh_wrec_f4(int order) { return order >= 2 ? 4 : 2; }
+// float4s per walk record (with its padding)
+__host__ __device__ constexpr int bh_wrec_f4(int order) { return order >= 2 ? 5 : 3; }
 
 // --------------------------------------------------------------- launches
 // (bodies in the .cu files; all are stream-ordered and take device pointers)

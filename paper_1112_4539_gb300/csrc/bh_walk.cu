@@ -1204,6 +1204,12 @@ __device__ __forceinline__ bool bh_mbar_wait_own(unsigned long long* b, unsigned
     return false;
 }
 
+// Particles of rejected leaves: staged by bulk copies (1) or by one load per
+// lane (0; the node records still arrive by bulk copies).
+#ifndef BH_TMA_PARTICLES
+#define BH_TMA_PARTICLES 1
+#endif
+
 template <int ORDER>
 struct TmaLanding {
     float4 node[32 * bh_wrec_f4(ORDER)];  // the pop's walk records, record i at slot i
@@ -1455,7 +1461,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, false>()) bh_walk_t
             npop = pop_issue();
             int lq_pos = 0, nfill = 0;
             bool pending = false;
-            if (lq_pos < lq_n) {
+            if (BH_TMA_PARTICLES && lq_pos < lq_n) {
                 nfill = fill_issue(lq_pos, lq_n);
                 pending = true;
             }
@@ -1475,6 +1481,33 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, false>()) bh_walk_t
                     ring_cnt -= 32;
                     continue;
                 }
+#if !BH_TMA_PARTICLES
+                if (lq_pos >= lq_n) break;
+                {
+                    int c2 = 0;
+                    int2 q = make_int2(0, 0);
+                    if (lq_pos + lane < lq_n) {
+                        q = S.leafq[lq_pos + lane];
+                        c2 = q.y;
+                    }
+                    const int inc2 = bh_warp_incl_scan(c2);
+                    const int ex2 = inc2 - c2;
+                    const int take2 = max(0, min(c2, 32 - ex2));
+                    for (int t = 0; t < take2; t++) S.staging[ex2 + t] = (uint32_t)(q.x + t);
+                    const bool full2 = (lq_pos + lane < lq_n) && (take2 == c2);
+                    const int nf2 = __popc(__ballot_sync(BH_FULL_MASK, full2));
+                    const int nfl = min(__shfl_sync(BH_FULL_MASK, inc2, 31), 32);
+                    __syncwarp();
+                    if (lane == nf2 && lq_pos + lane < lq_n && take2 > 0)
+                        S.leafq[lq_pos + lane] = make_int2(q.x + take2, c2 - take2);
+                    lq_pos += nf2;
+                    if (lane < nfl)
+                        bh_put_point(S, (ring_head + ring_cnt + lane) & (kRing - 1), P.pos_s[S.staging[lane]]);
+                    ring_cnt += nfl;
+                    __syncwarp();
+                }
+                continue;
+#endif
                 if (!pending) break;
                 if (!(alive = __all_sync(BH_FULL_MASK, bh_mbar_wait_own(&LD.bar_part, ph_part, ctrl)))) break;
                 ph_part ^= 1u;
