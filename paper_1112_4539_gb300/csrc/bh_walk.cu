@@ -1161,9 +1161,11 @@ static int bh_walk_ws_launch(const WalkParams& P, int sm_count, cudaStream_t s)
 //     slot i; the next pop is taken and its copies issued as soon as this
 //     pop's pushes are done, so they land while this pop's tiles are
 //     evaluated;
-//   * particle tiles: each batch of up to 32 particles of rejected leaves is
-//     one copy per leaf range into the particle landing area, issued before
-//     the point tiles that precede it are evaluated.
+//   * particle tiles: the particles of a pop's rejected leaves (up to 128 per
+//     round) are one copy per leaf range into the particle landing area,
+//     issued with the next pop's node copies, before the pop's quadrupole
+//     tiles are evaluated; the point ring is then filled from the landing
+//     area in the same 32-particle slices as the one-warp kernel's.
 // The landed records are converted into the same negated pair rings, in the
 // same order, as the one-warp kernel's, so the tiles and the results are the
 // same bits.  Waits are bounded (BH_ERR_DEVICE_TIMEOUT); every copy reads
@@ -1204,16 +1206,13 @@ __device__ __forceinline__ bool bh_mbar_wait_own(unsigned long long* b, unsigned
     return false;
 }
 
-// Particles of rejected leaves: staged by bulk copies (1) or by one load per
-// lane (0; the node records still arrive by bulk copies).
-#ifndef BH_TMA_PARTICLES
-#define BH_TMA_PARTICLES 1
-#endif
+// Particles of rejected leaves landed per round of copies (a multiple of 32).
+constexpr int kTmaPartCap = 128;
 
 template <int ORDER>
 struct TmaLanding {
     float4 node[32 * bh_wrec_f4(ORDER)];  // the pop's walk records, record i at slot i
-    float4 part[32];                       // a batch of particles of rejected leaves
+    float4 part[kTmaPartCap];              // a round of particles of rejected leaves
     unsigned long long bar_node, bar_part;
 };
 
@@ -1360,9 +1359,10 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, false>()) bh_walk_t
             __syncwarp();
             return npop;
         };
-        // Take the next batch of up to 32 particles from the pending leaf
-        // ranges at lq_pos and issue their copies; returns the batch size.
-        auto fill_issue = [&](int& lq_pos, int lq_n) -> int {
+        // Take the next round of up to kTmaPartCap particles from the pending
+        // leaf ranges at lq_pos (at most 32 ranges) and issue their copies;
+        // returns the round's particle count.
+        auto round_issue = [&](int& lq_pos, int lq_n) -> int {
             int c2 = 0;
             int2 q = make_int2(0, 0);
             if (lq_pos + lane < lq_n) {
@@ -1371,21 +1371,21 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, false>()) bh_walk_t
             }
             const int inc2 = bh_warp_incl_scan(c2);
             const int ex2 = inc2 - c2;
-            const int take2 = max(0, min(c2, 32 - ex2));
+            const int take2 = max(0, min(c2, kTmaPartCap - ex2));
             const bool full2 = (lq_pos + lane < lq_n) && (take2 == c2);
             const int nf2 = __popc(__ballot_sync(BH_FULL_MASK, full2));
-            const int nfill = min(__shfl_sync(BH_FULL_MASK, inc2, 31), 32);
+            const int nround = min(__shfl_sync(BH_FULL_MASK, inc2, 31), kTmaPartCap);
             __syncwarp();
             if (lane == nf2 && lq_pos + lane < lq_n && take2 > 0)
                 S.leafq[lq_pos + lane] = make_int2(q.x + take2, c2 - take2);
             lq_pos += nf2;
             bh_fence_proxy_async();
-            if (lane == 0) bh_mbar_expect_tx(&LD.bar_part, (unsigned int)(nfill * 16));
+            if (lane == 0) bh_mbar_expect_tx(&LD.bar_part, (unsigned int)(nround * 16));
             __syncwarp();
             if (take2 > 0) bh_bulk_g2s(&LD.part[ex2], P.pos_s + q.x, (unsigned int)(take2 * 16), &LD.bar_part);
             part_out = true;
             __syncwarp();
-            return nfill;
+            return nround;
         };
 
         bool overflow = false;
@@ -1459,14 +1459,14 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, false>()) bh_walk_t
 
             // ---- the next pop: its records land while this pop's tiles run
             npop = pop_issue();
-            int lq_pos = 0, nfill = 0;
+            int lq_pos = 0, pbase = 0, pavail = 0;
             bool pending = false;
-            if (BH_TMA_PARTICLES && lq_pos < lq_n) {
-                nfill = fill_issue(lq_pos, lq_n);
+            if (lq_pos < lq_n) {
+                pavail = round_issue(lq_pos, lq_n);
                 pending = true;
             }
 
-            // ---- drain: quadrupole tiles, point tiles, particle batches
+            // ---- drain: quadrupole tiles, then point tiles fed from the landed rounds
             if (ORDER >= 2) {
                 while (q_cnt >= 32) {
                     bh_quads<T, WarpQuad>(L, *Q, q_head >> 1, eps2v, X, A);
@@ -1481,45 +1481,29 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, false>()) bh_walk_t
                     ring_cnt -= 32;
                     continue;
                 }
-#if !BH_TMA_PARTICLES
-                if (lq_pos >= lq_n) break;
-                {
-                    int c2 = 0;
-                    int2 q = make_int2(0, 0);
-                    if (lq_pos + lane < lq_n) {
-                        q = S.leafq[lq_pos + lane];
-                        c2 = q.y;
+                if (pbase < pavail) {
+                    if (pending) {
+                        if (!(alive = __all_sync(BH_FULL_MASK, bh_mbar_wait_own(&LD.bar_part, ph_part, ctrl))))
+                            break;
+                        ph_part ^= 1u;
+                        part_out = false;
+                        pending = false;
                     }
-                    const int inc2 = bh_warp_incl_scan(c2);
-                    const int ex2 = inc2 - c2;
-                    const int take2 = max(0, min(c2, 32 - ex2));
-                    for (int t = 0; t < take2; t++) S.staging[ex2 + t] = (uint32_t)(q.x + t);
-                    const bool full2 = (lq_pos + lane < lq_n) && (take2 == c2);
-                    const int nf2 = __popc(__ballot_sync(BH_FULL_MASK, full2));
-                    const int nfl = min(__shfl_sync(BH_FULL_MASK, inc2, 31), 32);
+                    const int nfill = min(32, pavail - pbase);
+                    if (lane < nfill)
+                        bh_put_point(S, (ring_head + ring_cnt + lane) & (kRing - 1), LD.part[pbase + lane]);
+                    ring_cnt += nfill;
+                    pbase += nfill;
                     __syncwarp();
-                    if (lane == nf2 && lq_pos + lane < lq_n && take2 > 0)
-                        S.leafq[lq_pos + lane] = make_int2(q.x + take2, c2 - take2);
-                    lq_pos += nf2;
-                    if (lane < nfl)
-                        bh_put_point(S, (ring_head + ring_cnt + lane) & (kRing - 1), P.pos_s[S.staging[lane]]);
-                    ring_cnt += nfl;
-                    __syncwarp();
+                    continue;
                 }
-                continue;
-#endif
-                if (!pending) break;
-                if (!(alive = __all_sync(BH_FULL_MASK, bh_mbar_wait_own(&LD.bar_part, ph_part, ctrl)))) break;
-                ph_part ^= 1u;
-                part_out = false;
-                pending = false;
-                if (lane < nfill) bh_put_point(S, (ring_head + ring_cnt + lane) & (kRing - 1), LD.part[lane]);
-                ring_cnt += nfill;
-                __syncwarp();
                 if (lq_pos < lq_n) {
-                    nfill = fill_issue(lq_pos, lq_n);
+                    pavail = round_issue(lq_pos, lq_n);
+                    pbase = 0;
                     pending = true;
+                    continue;
                 }
+                break;
             }
             if (!alive) break;
         }
