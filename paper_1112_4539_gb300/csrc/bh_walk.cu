@@ -1379,10 +1379,21 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, false>()) bh_walk_t
             if (lane == nf2 && lq_pos + lane < lq_n && take2 > 0)
                 S.leafq[lq_pos + lane] = make_int2(q.x + take2, c2 - take2);
             lq_pos += nf2;
+            // ranges that continue the previous lane's range (sibling leaves are
+            // contiguous in particle order, and so are their landing slots)
+            // join its copy: one copy per run of contiguous ranges
+            const int prev_end = __shfl_up_sync(BH_FULL_MASK, q.x + take2, 1);
+            const bool cont = lane > 0 && take2 > 0 && q.x == prev_end;
+            const unsigned int cm = __ballot_sync(BH_FULL_MASK, cont);
+            const unsigned int after = (lane < 31) ? (~cm & (0xffffffffu << (lane + 1))) : 0u;
+            const int next = after ? __ffs(after) - 1 : 32;
+            const int ex_next = __shfl_sync(BH_FULL_MASK, ex2, next & 31);
+            const int run = (next < 32 ? min(ex_next, nround) : nround) - ex2;
             bh_fence_proxy_async();
             if (lane == 0) bh_mbar_expect_tx(&LD.bar_part, (unsigned int)(nround * 16));
             __syncwarp();
-            if (take2 > 0) bh_bulk_g2s(&LD.part[ex2], P.pos_s + q.x, (unsigned int)(take2 * 16), &LD.bar_part);
+            if (take2 > 0 && !cont)
+                bh_bulk_g2s(&LD.part[ex2], P.pos_s + q.x, (unsigned int)(run * 16), &LD.bar_part);
             part_out = true;
             __syncwarp();
             return nround;
