@@ -1207,7 +1207,10 @@ __device__ __forceinline__ bool bh_mbar_wait_own(unsigned long long* b, unsigned
 }
 
 // Particles of rejected leaves landed per round of copies (a multiple of 32).
-constexpr int kTmaPartCap = 128;
+#ifndef BH_TMA_PART_CAP
+#define BH_TMA_PART_CAP 128
+#endif
+constexpr int kTmaPartCap = BH_TMA_PART_CAP;
 
 template <int ORDER>
 struct TmaLanding {
