@@ -63,7 +63,9 @@ def lib():
         L.or_group_lists.restype = _i64
         L.or_force_particles.argtypes = [_i64, _f32p, _u32p, _i64, _i32p, _i32p, _i32p, _i32p,
                                          _f64p, _vp, _f64p, _i64, _i64, ctypes.c_double,
-                                         ctypes.c_int, _f64p, _vp, _vp, _vp, _vp]
+                                         ctypes.c_int, _vp, _vp, _f64p, _vp, _vp, _vp, _vp]
+        L.or_direct_sym.argtypes = [_i64, _f32p, _f32p, _i64, _f32p, _f32p, _vp, _f64p]
+        L.or_cell_softening.argtypes = [_i64, _f32p, _f32p, _i32p, _i32p, _f64p]
         L.or_force_particles.restype = ctypes.c_int
         L.or_pc_eval.argtypes = [_f64p, _f64p, _vp, ctypes.c_double, _f64p]
         L.or_mlp_nparams.restype = ctypes.c_int
@@ -276,9 +278,14 @@ def group_lists(spos, tree, mom, gfirst, gcount):
 
 
 def force_particles(spos, perm, tree, mom, eps, t0=0, t1=None, unsoftened_pc=False,
-                    want_quad=None):
-    """Per-particle walk of Fig. 3 / Fig. 5 with Eq. (2)'s criterion."""
+                    want_quad=None, eps_s=None, e2bar=None):
+    """Per-particle walk of Fig. 3 / Fig. 5 with Eq. (2)'s criterion.  With
+    eps_s (softening lengths in Morton order) and e2bar (cell_softening) the
+    softening is individual and symmetrized (Sec. 7, after Saitoh & Makino)."""
     spos = _pos(spos)
+    if eps_s is not None:
+        eps_s = np.ascontiguousarray(eps_s, dtype=np.float32)
+        e2bar = np.ascontiguousarray(e2bar, dtype=np.float64)
     n = spos.shape[0]
     t1 = n if t1 is None else t1
     out = np.zeros((n, 4), dtype=np.float64)
@@ -291,7 +298,8 @@ def force_particles(spos, perm, tree, mom, eps, t0=0, t1=None, unsoftened_pc=Fal
                                   tree.n_nodes, tree.first, tree.count, tree.child_first,
                                   tree.nchild, np.ascontiguousarray(mom.com_m), _ptr(quad),
                                   mom.s_eff, int(t0), int(t1), float(eps), int(bool(unsoftened_pc)),
-                                  out, _ptr(n_pp), _ptr(n_pc), _ptr(margin), _ptr(a_abs))
+                                  _ptr(eps_s), _ptr(e2bar), out, _ptr(n_pp), _ptr(n_pc), _ptr(margin),
+                                  _ptr(a_abs))
     if rc != 0:
         raise MemoryError("oracle force_particles")
     return dict(out=out, n_pp=n_pp, n_pc=n_pc, margin=margin, a_abs=a_abs)
@@ -360,6 +368,45 @@ class cell_rounding:
     def __exit__(self, *exc):
         lib().or_set_cell_rounding(1)
         return False
+
+
+def direct_sym(src, eps_src, tgt=None, eps_tgt=None, self_idx=None):
+    """Symmetrized Plummer direct sum (individual softening lengths, pair
+    softening (eps_i^2 + eps_j^2)/2).  With tgt=None the targets are the
+    sources and target i skips source i."""
+    src = _pos(src)
+    eps_src = np.ascontiguousarray(eps_src, dtype=np.float32)
+    if tgt is None:
+        tgt, eps_tgt = src, eps_src
+        self_idx = np.arange(src.shape[0], dtype=np.int64)
+    tgt = _pos(tgt)
+    eps_tgt = np.ascontiguousarray(eps_tgt, dtype=np.float32)
+    if self_idx is not None:
+        self_idx = np.ascontiguousarray(self_idx, dtype=np.int64)
+    out = np.zeros((tgt.shape[0], 4), dtype=np.float64)
+    lib().or_direct_sym(src.shape[0], src, eps_src, tgt.shape[0], tgt, eps_tgt, _ptr(self_idx), out)
+    return out
+
+
+def cell_softening(spos, eps_s, tree):
+    """Per node: the mass-weighted mean of its particles' eps^2."""
+    spos = _pos(spos)
+    e2 = np.zeros(tree.n_nodes, dtype=np.float64)
+    lib().or_cell_softening(tree.n_nodes, spos, np.ascontiguousarray(eps_s, dtype=np.float32), tree.first,
+                            tree.count, e2)
+    return e2
+
+
+def tree_force_sym(pos, eps_len, theta, n_leaf=8, G=32, order=1, curve=CURVE_MORTON, max_level=10,
+                   unsoftened_pc=False):
+    """Per-particle walk with individual, symmetrized softening: eps_len holds
+    each particle's softening length in the caller's order.  Returns (result, Built)."""
+    b = Built(pos, n_leaf, G, theta, order, curve, max_level)
+    eps_s = np.ascontiguousarray(np.asarray(eps_len, dtype=np.float32)[b.perm])
+    e2bar = cell_softening(b.spos, eps_s, b.tree)
+    res = force_particles(b.spos, b.perm, b.tree, b.mom, 0.0, unsoftened_pc=unsoftened_pc, eps_s=eps_s,
+                          e2bar=e2bar)
+    return res, b
 
 
 def pc_eval(x, com_m, quad=None, eps=0.0):

@@ -96,6 +96,65 @@ void or_direct(int64_t n_src, const float* src, int64_t n_tgt, const float* tgt,
 }
 
 /* ------------------------------------------------------------------------
+ * Individual softening with the symmetrized Plummer potential (Sec. 7 names
+ * it as an application of the method, after Saitoh & Makino 2010): particle
+ * i has its own softening length eps_i, and a pair softens with
+ *   eps_ij^2 = (eps_i^2 + eps_j^2) / 2,
+ * so phi_i = -sum_j m_j / sqrt(r^2 + eps_ij^2) and the pair force is the same
+ * for both bodies (total momentum is conserved).  eps_src, eps_tgt: FP32
+ * lengths per source and per target; otherwise as or_direct.
+ * ---------------------------------------------------------------------- */
+void or_direct_sym(int64_t n_src, const float* src, const float* eps_src, int64_t n_tgt, const float* tgt,
+                   const float* eps_tgt, const int64_t* self, double* out)
+{
+    int64_t i;
+#pragma omp parallel for schedule(dynamic, 8)
+    for (i = 0; i < n_tgt; i++) {
+        const double xi = tgt[4 * i], yi = tgt[4 * i + 1], zi = tgt[4 * i + 2];
+        const double ei = eps_tgt[i];
+        const int64_t own = self ? self[i] : -1;
+        double a[4] = {0, 0, 0, 0};
+        for (int64_t j = 0; j < n_src; j++) {
+            if (j == own) continue;
+            const double ej = eps_src[j];
+            const double dx = (double)src[4 * j] - xi;
+            const double dy = (double)src[4 * j + 1] - yi;
+            const double dz = (double)src[4 * j + 2] - zi;
+            const double mj = src[4 * j + 3];
+            const double r2 = dx * dx + dy * dy + dz * dz + 0.5 * (ei * ei + ej * ej);
+            const double g1 = 1.0 / sqrt(r2);
+            const double k = mj * g1 * g1 * g1;
+            a[0] += k * dx;
+            a[1] += k * dy;
+            a[2] += k * dz;
+            a[3] -= mj * g1;
+        }
+        for (int c = 0; c < 4; c++) out[4 * i + c] = a[c];
+    }
+}
+
+/* A node's softening under the symmetrized potential: the mass-weighted mean
+ * of its particles' eps_j^2 (0 for a massless node, whose terms vanish).  With
+ * this mean the term of first order in the spread of eps_j^2 inside the cell
+ * cancels, as the dipole does about the centre of mass.  eps_s: per sorted
+ * particle; e2bar: per node (FP64 direct sums). */
+void or_cell_softening(int64_t nn, const float* spos, const float* eps_s, const int32_t* first,
+                       const int32_t* count, double* e2bar)
+{
+    int64_t v;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (v = 0; v < nn; v++) {
+        double sm = 0.0, se = 0.0;
+        for (int64_t j = first[v]; j < (int64_t)first[v] + count[v]; j++) {
+            const double m = spos[4 * j + 3], e = eps_s[j];
+            sm += m;
+            se += m * e * e;
+        }
+        e2bar[v] = sm != 0.0 ? se / sm : 0.0;
+    }
+}
+
+/* ------------------------------------------------------------------------
  * Sec. 4.1: the root cell is a cube enclosing all particles.  Origin = the
  * per-axis minimum, side L = the largest per-axis extent (FP32, exact min/max,
  * one rounded subtraction).  A degenerate side (0, or one whose 1024/L is not
@@ -704,6 +763,9 @@ int64_t or_group_lists(int64_t nn, const float* spos, const int32_t* first, cons
  * rejected leaf gives particle-particle terms with its members; a rejected
  * internal node is opened.  The self term is skipped by index.  With
  * unsoftened_pc the particle-cell term uses eps = 0 (the Appendix A kernel).
+ * With eps_s (per sorted particle) and e2bar (per node, or_cell_softening)
+ * the softening is individual and symmetrized: a particle term uses
+ * (eps_i^2 + eps_j^2)/2 and a cell term (eps_i^2 + e2bar)/2 (eps is unused).
  * Targets are the Morton positions [t0, t1); out etc. are in caller order.
  * margin (optional): min over the target's criterion decisions (nodes not
  *   holding it) of |d^2 - S_eff| / S_eff; a_abs (optional): sum of |a_term|.
@@ -712,6 +774,7 @@ int or_force_particles(int64_t n, const float* spos, const uint32_t* perm, int64
                        const int32_t* first, const int32_t* count, const int32_t* child_first,
                        const int32_t* nchild, const double* com_m, const double* quad,
                        const double* s_eff, int64_t t0, int64_t t1, double eps, int unsoftened_pc,
+                       const float* eps_s, const double* e2bar,
                        double* out, int64_t* n_pp, int64_t* n_pc, double* margin, double* a_abs)
 {
     const double e2 = eps * eps;
@@ -728,6 +791,7 @@ int or_force_particles(int64_t n, const float* spos, const uint32_t* perm, int64
             continue;
         }
         const double xi = spos[4 * i], yi = spos[4 * i + 1], zi = spos[4 * i + 2];
+        const double ei2 = eps_s ? (double)eps_s[i] * (double)eps_s[i] : 0.0;
         double acc[5] = {0, 0, 0, 0, 0};
         double mmin = INFINITY;
         int64_t cpp = 0, cpc = 0, sp = 0;
@@ -736,7 +800,8 @@ int or_force_particles(int64_t n, const float* spos, const uint32_t* perm, int64
             const int32_t v = stack[--sp];
             if (count[v] == 1) {
                 if (first[v] != i) {
-                    or_pp(xi, yi, zi, spos + 4 * (int64_t)first[v], e2, acc);
+                    const double ej = eps_s ? eps_s[first[v]] : 0.0;
+                    or_pp(xi, yi, zi, spos + 4 * (int64_t)first[v], eps_s ? 0.5 * (ei2 + ej * ej) : e2, acc);
                     cpp++;
                 }
                 continue;
@@ -750,12 +815,14 @@ int or_force_particles(int64_t n, const float* spos, const uint32_t* perm, int64
                 if (mg < mmin) mmin = mg;
             }
             if (d2 > s_eff[v] && !holds_i) {
-                or_pc_cell(xi, yi, zi, c, quad ? quad + 6 * v : NULL, e2c, acc);
+                const double ec = unsoftened_pc ? 0.0 : (eps_s ? 0.5 * (ei2 + e2bar[v]) : e2c);
+                or_pc_cell(xi, yi, zi, c, quad ? quad + 6 * v : NULL, ec, acc);
                 cpc++;
             } else if (nchild[v] == 0) {
                 for (int64_t j = first[v]; j < (int64_t)first[v] + count[v]; j++) {
                     if (j == i) continue;
-                    or_pp(xi, yi, zi, spos + 4 * j, e2, acc);
+                    const double ej = eps_s ? eps_s[j] : 0.0;
+                    or_pp(xi, yi, zi, spos + 4 * j, eps_s ? 0.5 * (ei2 + ej * ej) : e2, acc);
                     cpp++;
                 }
             } else {

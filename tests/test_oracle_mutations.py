@@ -27,6 +27,7 @@ H = "tests/test_oracle_hilbert.py::"
 S = "tests/test_oracle_sph.py::"
 L = "tests/test_oracle_learned_mac.py::"
 F = "tests/test_oracle_leapfrog.py::"
+SO = "tests/test_oracle_softening.py::"
 KD = ("            vel[4 * i + a] = vel[4 * i + a] + acc[4 * i + a] * dt_kick;\n"
       "            pos[4 * i + a] = pos[4 * i + a] + vel[4 * i + a] * dt_drift;")
 
@@ -341,6 +342,23 @@ MUTATIONS = {
         "acc[4 * i + a] * dt_kick;",
         "acc[4 * i + (a + 1) % 3] * dt_kick;",
         [F + "test_one_update_by_hand", F + "test_two_body_circular_orbit"]),
+    "softening_pair_not_symmetrized": (
+        "const double r2 = dx * dx + dy * dy + dz * dz + 0.5 * (ei * ei + ej * ej);",
+        "const double r2 = dx * dx + dy * dy + dz * dz + ej * ej;",
+        [SO + "test_two_bodies_closed_form_and_symmetry", SO + "test_momentum_is_conserved"]),
+    "softening_cell_unweighted_mean": (
+        "            sm += m;\n            se += m * e * e;",
+        "            sm += (m != 0.0);\n            se += (m != 0.0) * e * e;",
+        [SO + "test_cell_softening_is_the_mass_weighted_mean",
+         SO + "test_cell_softening_cancels_the_first_order_term"]),
+    "softening_cell_term_target_only": (
+        "(eps_s ? 0.5 * (ei2 + e2bar[v]) : e2c)",
+        "(eps_s ? ei2 : e2c)",
+        [SO + "test_particle_walk_cell_term_uses_the_pair_mean"]),
+    "softening_particle_node_target_only": (
+        "spos + 4 * (int64_t)first[v], eps_s ? 0.5 * (ei2 + ej * ej) : e2, acc);",
+        "spos + 4 * (int64_t)first[v], eps_s ? ei2 : e2, acc);",
+        [SO + "test_particle_walk_at_theta_to_zero_is_the_direct_sum"]),
 }
 
 
