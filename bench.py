@@ -100,6 +100,9 @@ def parse():
                     help="deepest tree level: 10 (30-bit keys) or 21 (63-bit keys)")
     ap.add_argument("--unsoftened-cells", action="store_true",
                     help="particle walk: cells without softening (the Appendix A kernel)")
+    ap.add_argument("--symmetrized", action="store_true",
+                    help="particle walk with individual softening lengths (log-uniform in [eps/4, 4 eps], seeded) "
+                         "and the symmetrized Plummer potential")
     ap.add_argument("--cpu-report", action="store_true",
                     help="FP64 oracle on the host (1 thread and all threads) against the GPU, N=4096 and N=2^20")
     ap.add_argument("--neighbors", action="store_true",
@@ -196,22 +199,25 @@ def rel_errors(got, ref):
     return da, dp
 
 
-def measure_errors(ctx, x, idx_t, ref, theta, eps, acc, walk="group", unsoftened=False):
+def measure_errors(ctx, x, idx_t, ref, theta, eps, acc, walk="group", unsoftened=False, soft=None):
     import torch
-    ctx.evaluate(x, theta, eps, acc, walk=walk, unsoftened_cells=unsoftened)
+    if soft is not None:
+        ctx.evaluate_symmetrized(x, soft, theta, acc, unsoftened)
+    else:
+        ctx.evaluate(x, theta, eps, acc, walk=walk, unsoftened_cells=unsoftened)
     da, dp = rel_errors(acc[idx_t], ref)
     q = torch.quantile(da, torch.tensor([0.5, 0.99], dtype=torch.float64, device=da.device))
     return dict(p50=float(q[0]), p99=float(q[1]), mean=float(da.mean()), max=float(da.max()),
                 phi_mean=float(dp.mean()), phi_p99=float(torch.quantile(dp, 0.99)))
 
 
-def calibrate(ctx, x, idx_t, ref, eps, acc, lo=0.2, hi=1.2, iters=9, walk="group", unsoftened=False):
+def calibrate(ctx, x, idx_t, ref, eps, acc, lo=0.2, hi=1.2, iters=9, walk="group", unsoftened=False, soft=None):
     """Largest theta (bisection) with p99 relative acceleration error <= 1e-3."""
-    if measure_errors(ctx, x, idx_t, ref, hi, eps, acc, walk, unsoftened)["p99"] <= TARGET_P99:
+    if measure_errors(ctx, x, idx_t, ref, hi, eps, acc, walk, unsoftened, soft)["p99"] <= TARGET_P99:
         return hi
     for _ in range(iters):
         mid = 0.5 * (lo + hi)
-        if measure_errors(ctx, x, idx_t, ref, mid, eps, acc, walk, unsoftened)["p99"] <= TARGET_P99:
+        if measure_errors(ctx, x, idx_t, ref, mid, eps, acc, walk, unsoftened, soft)["p99"] <= TARGET_P99:
             lo = mid
         else:
             hi = mid
@@ -220,7 +226,7 @@ def calibrate(ctx, x, idx_t, ref, eps, acc, lo=0.2, hi=1.2, iters=9, walk="group
 
 # ------------------------------------------------------------ CPU oracle
 def oracle_throughput(pos, theta, eps, leaf, G, order, n_groups_sample, seed=0, walk="group",
-                      unsoftened=False, curve=0, max_level=10):
+                      unsoftened=False, curve=0, max_level=10, soft=None):
     """FP64 CPU oracle (same walk and criterion) on a bounded sample: the
     tree is built once for all particles (timed, reported apart), then the
     walk of a random sample of groups (group walk) or of n_groups_sample *
@@ -236,10 +242,14 @@ def oracle_throughput(pos, theta, eps, leaf, G, order, n_groups_sample, seed=0, 
         chunk = max(1, min(n // 8, n_groups_sample * G // 32))
         starts = np.linspace(0, n - chunk, 8).astype(np.int64)
         I, t_walk = 0, 0.0
+        eps_s = e2bar = None
+        if soft is not None:
+            eps_s = np.ascontiguousarray(soft[b.perm])
+            e2bar = oracle.cell_softening(b.spos, eps_s, b.tree)
         for s0 in starts:
             t0 = time.perf_counter()
             res = oracle.force_particles(b.spos, b.perm, b.tree, b.mom, eps, t0=int(s0), t1=int(s0 + chunk),
-                                         unsoftened_pc=unsoftened)
+                                         unsoftened_pc=unsoftened, eps_s=eps_s, e2bar=e2bar)
             t_walk += time.perf_counter() - t0
             I += int(res["n_pp"].sum() + res["n_pc"].sum())
         scale = n / (8 * chunk)
@@ -331,7 +341,7 @@ def stored_traffic(workload):
         return None
 
 
-def end_to_end(ctx, pos_np, theta, eps, steps, walk="group", unsoftened=False, world=1, dt=None):
+def end_to_end(ctx, pos_np, theta, eps, steps, walk="group", unsoftened=False, world=1, dt=None, soft=None):
     """Whole steps through the public API from and to pinned host memory:
     per step an upload of the particles, the evaluation (Context.evaluate),
     the leapfrog update of the uploaded particles with device-resident
@@ -367,7 +377,10 @@ def end_to_end(ctx, pos_np, theta, eps, steps, walk="group", unsoftened=False, w
                     loaded[nb].record(up)
             comp.wait_event(loaded[b])
             comp.wait_event(fetched[b])            # step k-2's forces are out of this buffer
-            ctx.evaluate(d_pos[b], theta, eps, d_acc[b], walk=walk, unsoftened_cells=unsoftened)
+            if soft is not None:
+                ctx.evaluate_symmetrized(d_pos[b], soft, theta, d_acc[b], unsoftened)
+            else:
+                ctx.evaluate(d_pos[b], theta, eps, d_acc[b], walk=walk, unsoftened_cells=unsoftened)
             if dt is not None:
                 ctx.kick_drift(d_pos[b], d_vel, d_acc[b], dt, dt)
             evaluated[b].record(comp)
@@ -471,24 +484,34 @@ def run_ours(args, W):
                      max_level=args.max_level, walk_variant=variant)
     stream = torch.cuda.current_stream()
 
+    # individual softening lengths (symmetrized potential; the per-particle walk)
+    soft = None
+    if args.symmetrized:
+        args.walk = "particle"
+        soft = torch.from_numpy(workloads.softening_lengths(n, eps, seed=17 + rank)).to(dev)
+
     # FP64 direct sum on 4096 seeded targets: the error judge
     idx = workloads.sample_targets(n, 4096, seed=101)
     idx_t = torch.from_numpy(idx).to(dev)
     ref = torch.empty((idx.size, 4), dtype=torch.float64, device=dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    rc = bh.direct_force(x, x[idx_t].contiguous(), idx_t, eps, ref, 64)
+    if soft is not None:
+        rc = bh.direct_force_sym(x, soft, x[idx_t].contiguous(), soft[idx_t].contiguous(), idx_t, ref, 64)
+    else:
+        rc = bh.direct_force(x, x[idx_t].contiguous(), idx_t, eps, ref, 64)
     torch.cuda.synchronize()
     t_judge = time.perf_counter() - t0
     assert rc == 0, rc
 
     theta = args.theta if args.theta is not None else W["theta"]
     walk, uns = args.walk, args.unsoftened_cells
-    errs = measure_errors(ctx, x, idx_t, ref, theta, eps, acc, walk, uns)
+    errs = measure_errors(ctx, x, idx_t, ref, theta, eps, acc, walk, uns, soft)
     calibrated = False
-    if args.theta is None and (args.calibrate or W.get("calibrate") or errs["p99"] > TARGET_P99):
-        theta = calibrate(ctx, x, idx_t, ref, eps, acc, walk=walk, unsoftened=uns)
-        errs = measure_errors(ctx, x, idx_t, ref, theta, eps, acc, walk, uns)
+    if args.theta is None and (args.calibrate or W.get("calibrate") or errs["p99"] > TARGET_P99 or
+                               soft is not None):
+        theta = calibrate(ctx, x, idx_t, ref, eps, acc, walk=walk, unsoftened=uns, soft=soft)
+        errs = measure_errors(ctx, x, idx_t, ref, theta, eps, acc, walk, uns, soft)
         calibrated = True
     st = ctx.status()
     assert st == 0, st
@@ -499,13 +522,15 @@ def run_ours(args, W):
 
     def step(walk_ev=None):
         ctx.build(x)
+        if soft is not None:
+            ctx.softening(soft)
         ctx.moments(theta)
         if walk_ev is not None:
             walk_ev[0].record(stream)
         if walk == "group":
             ctx.force(eps, acc)
         else:
-            ctx.force_particles(eps, acc, uns)
+            ctx.force_particles(eps, acc, uns, individual_softening=soft is not None)
         if walk_ev is not None:
             walk_ev[1].record(stream)
         ctx.kick_drift(x, vel, acc, dt / 2 if kicks[0] == 0 else dt, dt)
@@ -548,7 +573,7 @@ def run_ours(args, W):
     # particles and downloads its forces; with two buffers per side the copies of neighbouring steps run on
     # their own streams while a step evaluates
     e2e_steps = max(3, args.steps // 2)
-    e2e_ms, e2e_inter = end_to_end(ctx, pos_np, theta, eps, e2e_steps, walk, uns, world, dt=dt)
+    e2e_ms, e2e_inter = end_to_end(ctx, pos_np, theta, eps, e2e_steps, walk, uns, world, dt=dt, soft=soft)
     e2e_inter, e2e_max = whole_job(e2e_inter, e2e_ms, world, dev)
     e2e_value = e2e_inter / (e2e_max * 1e-3) / 1e9
     h_pos_bytes = int(pos_np.size * 4)
@@ -577,6 +602,8 @@ def run_ours(args, W):
                        "curve": args.curve,
                        "max_level": args.max_level,
                        "unsoftened_cells": uns if walk == "particle" else None,
+                       "softening": ("individual, log-uniform in [eps/4, 4 eps], symmetrized" if soft is not None
+                                     else "eps for every particle"),
                        "errors_vs_fp64_direct_4096": errs, "judge_s": t_judge,
                        "interactions_per_step": inter / steps, "pp_per_step": n_pp / steps,
                        "pc_per_step": n_pc / steps, "l2": "inputs larger than L2 (no flush)",
@@ -607,7 +634,8 @@ def run_ours(args, W):
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cb = oracle_throughput(pos_np, theta, eps, leaf, G, order, args.cpu_sample_groups, walk=walk,
-                               unsoftened=uns, curve=curve, max_level=args.max_level)
+                               unsoftened=uns, curve=curve, max_level=args.max_level,
+                               soft=None if soft is None else soft.cpu().numpy())
         unit_s = "groups" if walk == "group" else "targets"
         line["cpu_baseline"] = {"value": cb["value"], "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
                                 "sample": "FP64 oracle %s walk on the same particles and theta: %d of %d %s "

@@ -165,12 +165,34 @@ int tree_force(bh_ctx* ctx, float eps, float* d_acc_pot, void* stream);
  * derived from the current tree on each call.  FP32 terms, Kahan-compensated
  * runs of 32.  bh_stats then counts this walk's interactions.
  * eps >= 0: softening of Eq. (1).  flags: BH_PWALK_UNSOFTENED_CELLS applies
- * particle-cell terms with eps = 0, as the Appendix A kernel does.
+ * particle-cell terms with eps = 0, as the Appendix A kernel does;
+ * BH_PWALK_INDIVIDUAL_SOFTENING uses the per-particle softening lengths set by
+ * tree_softening (the symmetrized potential below; eps is then not used).
  * d_acc_pot: n float4 (ax, ay, az, phi) in the caller's order.
  * Errors: BH_ERR_INVALID, BH_ERR_STATE (tree_moments not run after the last
- * tree_build); device status BH_ERR_CAPACITY for a malformed tree. */
+ * tree_build, or individual softening requested without tree_softening after
+ * it); device status BH_ERR_CAPACITY for a malformed tree. */
 #define BH_PWALK_UNSOFTENED_CELLS 1
+#define BH_PWALK_INDIVIDUAL_SOFTENING 2
 int tree_force_particles(bh_ctx* ctx, float eps, int flags, float* d_acc_pot, void* stream);
+
+/* Individual softening with the symmetrized Plummer potential, the
+ * application Sec. 7 names (after Saitoh & Makino 2010): particle i has its
+ * own softening length eps_i; a pair (i, j) softens with
+ * eps_ij^2 = (eps_i^2 + eps_j^2) / 2, so both bodies feel the same pair force
+ * and momentum is conserved; a cell softens with (eps_i^2 + <eps^2>) / 2,
+ * <eps^2> the mass-weighted mean over its particles (which cancels the term
+ * of first order in the spread of eps^2, as the centre of mass cancels the
+ * dipole; a massless cell takes 0).
+ * Sets the softening of the particles of the tree of the last tree_build
+ * (any later tree_build clears it) for tree_force_particles with
+ * BH_PWALK_INDIVIDUAL_SOFTENING: d_eps holds n floats in the caller's order.
+ * The first call on a context allocates its work arrays (cudaMalloc: 4 bytes
+ * per particle and 20 per node of capacity), so it should come before any
+ * stream capture; later calls allocate nothing.
+ * Errors: BH_ERR_INVALID (bad pointer), BH_ERR_STATE (no tree), BH_ERR_NOMEM;
+ * device status BH_ERR_NONFINITE for an eps that is negative or not finite. */
+int tree_softening(bh_ctx* ctx, const float* d_eps, void* stream);
 
 /* Neighbour search and SPH density, the short-range application of the
  * general tree walk (Sec. 4.3, Fig. 4), on the tree of the last tree_build
@@ -203,6 +225,16 @@ int tree_neighbors(bh_ctx* ctx, const float* d_h, float h, int32_t* d_count, flo
  * BH_ERR_TOO_LARGE (n_src or n_tgt >= 2^31). */
 int direct_force(const float* d_src, int64_t n_src, const float* d_tgt, const int64_t* d_tgt_self,
                  int64_t n_tgt, double eps, void* d_out, int precision, void* stream);
+
+/* direct_force with individual softening lengths and the symmetrized
+ * Plummer potential (Sec. 7, after Saitoh & Makino 2010): the pair (t, j)
+ * softens with (eps_t^2 + eps_j^2) / 2.  d_eps_src: n_src floats (one per
+ * source), d_eps_tgt: n_tgt floats (one per target); the rest as
+ * direct_force (precision 64 is the error judge of the symmetrized walk).
+ * Errors: as direct_force. */
+int direct_force_sym(const float* d_src, const float* d_eps_src, int64_t n_src, const float* d_tgt,
+                     const float* d_eps_tgt, const int64_t* d_tgt_self, int64_t n_tgt, void* d_out, int precision,
+                     void* stream);
 
 /* The orbit loop of Sec. 1 ("compute forces, integrate, repeat"): one
  * leapfrog update per particle, v += a * dt_kick then x += v * dt_drift.

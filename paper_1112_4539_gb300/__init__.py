@@ -34,12 +34,13 @@ SYMBOLS = ["bh_version", "bh_strerror", "bh_config_default", "bh_create", "bh_de
            "tree_moments", "tree_force", "tree_force_particles", "tree_neighbors", "direct_force", "bh_kick_drift",
            "bh_status", "bh_stats", "bh_export", "bh_tree_force_static", "bh_mac_set", "bh_mac_label",
            "bh_mlp_train", "bh_mlp_grad", "bh_mlp_forward", "bh_batch_layout", "bh_force_batched", "bh_graph_capture_batched",
-           "bh_graph_launch", "bh_graph_destroy", "bh_selftest_wait"]
+           "bh_graph_launch", "bh_graph_destroy", "bh_selftest_wait", "tree_softening", "direct_force_sym"]
 BATCH_MAX_N = 65536
 MLP_NPARAM = 1313
 MLP_ACT = 135  # floats of training scratch per sample
 STATIC_MAX_N = 32768
 PWALK_UNSOFTENED_CELLS = 1
+PWALK_INDIVIDUAL_SOFTENING = 2
 CURVE_MORTON = 0
 CURVE_HILBERT = 1
 WALK_ONE_WARP = 0
@@ -109,10 +110,14 @@ def lib():
         L.tree_force.restype = i32
         L.tree_force_particles.argtypes = [vp, ctypes.c_float, i32, vp, vp]
         L.tree_force_particles.restype = i32
+        L.tree_softening.argtypes = [vp, vp, vp]
+        L.tree_softening.restype = i32
         L.tree_neighbors.argtypes = [vp, vp, ctypes.c_float, vp, vp, vp]
         L.tree_neighbors.restype = i32
         L.direct_force.argtypes = [vp, i64, vp, vp, i64, ctypes.c_double, vp, i32, vp]
         L.direct_force.restype = i32
+        L.direct_force_sym.argtypes = [vp, vp, i64, vp, vp, vp, i64, vp, i32, vp]
+        L.direct_force_sym.restype = i32
         L.bh_kick_drift.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, vp]
         L.bh_kick_drift.restype = i32
         L.bh_tree_force_static.argtypes = [vp, i64, ctypes.POINTER(BhConfig), ctypes.c_float, ctypes.c_float, vp,
@@ -201,10 +206,18 @@ def tree_force(h, eps, out, stream=None):
     return lib().tree_force(h, ctypes.c_float(eps), _dptr(out), _stream(stream))
 
 
-def tree_force_particles(h, eps, out, unsoftened_cells=False, stream=None):
-    """The paper's per-particle next/more walk (Fig. 5)."""
-    flags = PWALK_UNSOFTENED_CELLS if unsoftened_cells else 0
+def tree_force_particles(h, eps, out, unsoftened_cells=False, stream=None, individual_softening=False):
+    """The paper's per-particle next/more walk (Fig. 5); with
+    individual_softening the lengths set by tree_softening (symmetrized)."""
+    flags = (PWALK_UNSOFTENED_CELLS if unsoftened_cells else 0) | \
+        (PWALK_INDIVIDUAL_SOFTENING if individual_softening else 0)
     return lib().tree_force_particles(h, ctypes.c_float(eps), int(flags), _dptr(out), _stream(stream))
+
+
+def tree_softening(h, eps, stream=None):
+    """Individual softening lengths (float32 device tensor, caller order) of
+    the current tree's particles, for the symmetrized Plummer potential."""
+    return lib().tree_softening(h, _dptr(eps), _stream(stream))
 
 
 def tree_neighbors(h_ctx, h, count=None, rho=None, stream=None):
@@ -221,6 +234,13 @@ def direct_force(src, tgt, tgt_self, eps, out, precision, stream=None):
     or None, out (m,4) f32 (precision 32) or f64 (precision 64)."""
     return lib().direct_force(_dptr(src), int(src.shape[0]), _dptr(tgt), _dptr(tgt_self),
                               int(tgt.shape[0]), float(eps), _dptr(out), int(precision), _stream(stream))
+
+
+def direct_force_sym(src, eps_src, tgt, eps_tgt, tgt_self, out, precision, stream=None):
+    """direct_force with individual softening lengths (float32, one per source and
+    per target) and the symmetrized Plummer potential."""
+    return lib().direct_force_sym(_dptr(src), _dptr(eps_src), int(src.shape[0]), _dptr(tgt), _dptr(eps_tgt),
+                                  _dptr(tgt_self), int(tgt.shape[0]), _dptr(out), int(precision), _stream(stream))
 
 
 def bh_kick_drift(h, pos, vel, acc, dt_kick, dt_drift, stream=None):
@@ -364,8 +384,24 @@ class Context:
     def force(self, eps, out, stream=None):
         _check(tree_force(self.h, eps, out, stream), "tree_force")
 
-    def force_particles(self, eps, out, unsoftened_cells=False, stream=None):
-        _check(tree_force_particles(self.h, eps, out, unsoftened_cells, stream), "tree_force_particles")
+    def force_particles(self, eps, out, unsoftened_cells=False, stream=None, individual_softening=False):
+        _check(tree_force_particles(self.h, eps, out, unsoftened_cells, stream, individual_softening),
+               "tree_force_particles")
+
+    def softening(self, eps, stream=None):
+        _check(tree_softening(self.h, eps, stream), "tree_softening")
+
+    def evaluate_symmetrized(self, pos, eps, theta, out=None, unsoftened_cells=False, stream=None):
+        """Per-particle walk with individual softening lengths eps (float32,
+        caller order) and the symmetrized Plummer potential."""
+        import torch
+        if out is None:
+            out = torch.empty_like(pos)
+        self.build(pos, stream)
+        self.softening(eps, stream)
+        self.moments(theta, stream)
+        self.force_particles(0.0, out, unsoftened_cells, stream, individual_softening=True)
+        return out
 
     def evaluate(self, pos, theta, eps, out=None, stream=None, walk="group", unsoftened_cells=False):
         """Whole force evaluation (build, moments, walk); returns (n, 4) f32 on the device.

@@ -54,6 +54,10 @@ struct bh_ctx {
     // node bounding boxes of the neighbour search
     float4* blo = nullptr;
     float4* bhi = nullptr;
+    // individual softening (allocated by the first tree_softening call)
+    void* soft_slab = nullptr;
+    bh::bh_soft soft{};
+    bool have_soft = false;
 };
 
 namespace {
@@ -275,6 +279,7 @@ void bh_destroy(bh_ctx* x)
     cudaDeviceSynchronize();
     cudaFreeHost(x->host_ctrl);
     cudaFree(x->slab);
+    if (x->soft_slab) cudaFree(x->soft_slab);
     delete x;
 }
 
@@ -305,6 +310,36 @@ int tree_build(bh_ctx* x, const float* d_pos_mass, int64_t n, void* stream)
     if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
     x->n = n;
     x->have_moments = false;
+    x->have_soft = false;
+    return BH_OK;
+}
+
+int tree_softening(bh_ctx* x, const float* d_eps, void* stream)
+{
+    if (!x) return BH_ERR_INVALID;
+    if (x->n < 0) return BH_ERR_STATE;
+    if (x->n > 0 && (!d_eps || ((uintptr_t)d_eps & 3u) || !is_device_ptr(d_eps, x->device))) return BH_ERR_INVALID;
+    DeviceGuard guard(x->device);
+    if (!x->soft_slab) {
+        const size_t a = ((size_t)x->max_n * sizeof(float) + 255) & ~(size_t)255;
+        const size_t b = ((size_t)x->node_cap * sizeof(double2) + 255) & ~(size_t)255;
+        if (cudaMalloc(&x->soft_slab, a + b + (size_t)x->node_cap * sizeof(float) + 256) != cudaSuccess) {
+            cudaGetLastError();
+            x->soft_slab = nullptr;
+            return BH_ERR_NOMEM;
+        }
+        unsigned char* p = (unsigned char*)x->soft_slab;
+        x->soft.h = (float*)p;
+        x->soft.sums = (double2*)(p + a);
+        x->soft.hbar = (float*)(p + a + b);
+    }
+    if (x->n > 0) {
+        bh::launch_softening(d_eps, x->vals, x->pos_s, x->nd, (int)x->n, x->deep, x->soft, x->ctrl, grid_for(x),
+                             (cudaStream_t)stream);
+        x->launches += bh::launches_softening(x->deep);
+    }
+    if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
+    x->have_soft = true;
     return BH_OK;
 }
 
@@ -353,14 +388,16 @@ int tree_force_particles(bh_ctx* x, float eps, int flags, float* d_acc_pot, void
 {
     if (!x) return BH_ERR_INVALID;
     if (!(eps >= 0.0f) || !std::isfinite(eps)) return BH_ERR_INVALID;
-    if (flags & ~BH_PWALK_UNSOFTENED_CELLS) return BH_ERR_INVALID;
+    if (flags & ~(BH_PWALK_UNSOFTENED_CELLS | BH_PWALK_INDIVIDUAL_SOFTENING)) return BH_ERR_INVALID;
     if (x->n < 0 || !x->have_moments) return BH_ERR_STATE;
+    const bool ind = (flags & BH_PWALK_INDIVIDUAL_SOFTENING) != 0;
+    if (ind && !x->have_soft) return BH_ERR_STATE;
     if (x->n == 0) return BH_OK;
     if (!d_acc_pot || !aligned16(d_acc_pot) || !is_device_ptr(d_acc_pot, x->device)) return BH_ERR_INVALID;
     DeviceGuard guard(x->device);
     int rc = bh::launch_pwalk(x->pos_s, x->vals, x->nd, x->parent, x->next, x->cfg.order, (int)x->n,
                               (int)x->node_cap, eps, (flags & BH_PWALK_UNSOFTENED_CELLS) != 0, (float4*)d_acc_pot,
-                              x->ctrl, x->sm_count, (cudaStream_t)stream);
+                              x->ctrl, x->sm_count, (cudaStream_t)stream, ind ? &x->soft : nullptr);
     if (rc) return rc;
     x->launches += bh::kLaunchesPWalk;
     if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
@@ -417,6 +454,28 @@ int direct_force(const float* d_src, int64_t n_src, const float* d_tgt, const in
     if (d_tgt_self && (((uintptr_t)d_tgt_self & 7u) || !is_device_ptr(d_tgt_self, dev))) return BH_ERR_INVALID;
     return bh::launch_direct((const float4*)d_src, (int)n_src, (const float4*)d_tgt, d_tgt_self, (int)n_tgt, eps,
                              d_out, precision, (cudaStream_t)stream);
+}
+
+int direct_force_sym(const float* d_src, const float* d_eps_src, int64_t n_src, const float* d_tgt,
+                     const float* d_eps_tgt, const int64_t* d_tgt_self, int64_t n_tgt, void* d_out, int precision,
+                     void* stream)
+{
+    if (n_src < 0 || n_tgt < 0) return BH_ERR_INVALID;
+    if (n_src >= ((int64_t)1 << 31) || n_tgt >= ((int64_t)1 << 31)) return BH_ERR_TOO_LARGE;
+    if (precision != 32 && precision != 64) return BH_ERR_INVALID;
+    if (n_tgt == 0) return BH_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BH_ERR_CUDA;
+    if (!d_tgt || !aligned16(d_tgt) || !is_device_ptr(d_tgt, dev)) return BH_ERR_INVALID;
+    if (!d_out || !aligned16(d_out) || !is_device_ptr(d_out, dev)) return BH_ERR_INVALID;
+    if (!d_eps_tgt || ((uintptr_t)d_eps_tgt & 3u) || !is_device_ptr(d_eps_tgt, dev)) return BH_ERR_INVALID;
+    if (n_src > 0 && (!d_src || !aligned16(d_src) || !is_device_ptr(d_src, dev))) return BH_ERR_INVALID;
+    if (n_src > 0 && (!d_eps_src || ((uintptr_t)d_eps_src & 3u) || !is_device_ptr(d_eps_src, dev)))
+        return BH_ERR_INVALID;
+    if (d_tgt_self && (((uintptr_t)d_tgt_self & 7u) || !is_device_ptr(d_tgt_self, dev))) return BH_ERR_INVALID;
+    // (n_src == 0 only zeroes the output)
+    return bh::launch_direct((const float4*)d_src, (int)n_src, (const float4*)d_tgt, d_tgt_self, (int)n_tgt, 0.0,
+                             d_out, precision, (cudaStream_t)stream, d_eps_src, d_eps_tgt);
 }
 
 static int read_ctrl(bh_ctx* x, cudaStream_t s)

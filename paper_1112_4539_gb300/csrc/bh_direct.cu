@@ -5,7 +5,9 @@
 // across tiles.  FP64: the error judge, double throughout with 1/sqrt.  When
 // there are too few targets to fill the GPU the source range is split across
 // blocks and partial sums are combined with atomic adds into the (zeroed)
-// output.  The self term of each target is skipped by index.
+// output.  The self term of each target is skipped by index.  With
+// individual softening lengths (SYM) a pair softens with (eps_i^2 + eps_j^2)/2,
+// the symmetrized Plummer potential (Sec. 7, after Saitoh & Makino 2010).
 #include "bh_internal.cuh"
 
 namespace bh {
@@ -35,13 +37,14 @@ __device__ __forceinline__ void bh_kahan_r(R& s, R& c, R v)
     s = t;
 }
 
-template <typename R, bool ATOMIC>
+template <typename R, bool ATOMIC, bool SYM = false>
 __global__ void __launch_bounds__(kDirThreads)
 bh_direct_kernel(const float4* __restrict__ src, int n_src, const float4* __restrict__ tgt,
                  const int64_t* __restrict__ self, int n_tgt, R eps2, typename Vec4<R>::type* __restrict__ out,
-                 int chunk)
+                 int chunk, const float* __restrict__ eps_src = nullptr, const float* __restrict__ eps_tgt = nullptr)
 {
     __shared__ float4 tile[kDirThreads];
+    __shared__ R tile_e[SYM ? kDirThreads : 1];  // eps_j^2 / 2
     const int i = blockIdx.x * kDirThreads + threadIdx.x;
     const bool valid = i < n_tgt;
     float4 pt = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -51,12 +54,21 @@ bh_direct_kernel(const float4* __restrict__ src, int n_src, const float4* __rest
         if (self) sf = (long long)self[i];
     }
     const R xi = pt.x, yi = pt.y, zi = pt.z;
+    R hi = 0;
+    if (SYM && valid) {
+        const R e = eps_tgt[i];
+        hi = (R)0.5 * (e * e);
+    }
     R ax = 0, ay = 0, az = 0, ph = 0, cx = 0, cy = 0, cz = 0, cp = 0;
     const int s0 = blockIdx.y * chunk;
     const int s1 = min(n_src, s0 + chunk);
     for (int base = s0; base < s1; base += kDirThreads) {
         const int j = base + threadIdx.x;
         tile[threadIdx.x] = (j < s1) ? src[j] : make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+        if (SYM) {
+            const R e = (j < s1) ? (R)eps_src[j] : (R)0;
+            tile_e[threadIdx.x] = (R)0.5 * (e * e);
+        }
         __syncthreads();
         R tx = 0, ty = 0, tz = 0, tp = 0;
         const bool mine = sf >= base && sf < base + kDirThreads;
@@ -65,7 +77,7 @@ bh_direct_kernel(const float4* __restrict__ src, int n_src, const float4* __rest
         for (int k = 0; k < kDirThreads; k++) {
             const float4 s = tile[k];
             const R dx = (R)s.x - xi, dy = (R)s.y - yi, dz = (R)s.z - zi;
-            R r2 = dx * dx + dy * dy + dz * dz + eps2;
+            R r2 = dx * dx + dy * dy + dz * dz + (SYM ? hi + tile_e[k] : eps2);
             R m = s.w;
             if (k == skip) {
                 r2 = 1;
@@ -104,8 +116,9 @@ bh_direct_kernel(const float4* __restrict__ src, int n_src, const float4* __rest
 }
 
 int launch_direct(const float4* src, int n_src, const float4* tgt, const int64_t* self, int n_tgt, double eps,
-                  void* out, int precision, cudaStream_t s)
+                  void* out, int precision, cudaStream_t s, const float* eps_src, const float* eps_tgt)
 {
+    const bool sym = eps_src != nullptr;
     if (n_tgt <= 0) return BH_OK;
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
@@ -124,7 +137,23 @@ int launch_direct(const float4* src, int n_src, const float4* tgt, const int64_t
     const size_t rec = precision == 64 ? sizeof(bh_double4) : sizeof(float4);
     if (split > 1 || n_src == 0) cudaMemsetAsync(out, 0, (size_t)n_tgt * rec, s);
     if (n_src == 0) return BH_OK;
-    if (precision == 64) {
+    if (sym) {
+        if (precision == 64) {
+            if (split > 1)
+                bh_direct_kernel<double, true, true><<<grid, kDirThreads, 0, s>>>(
+                    src, n_src, tgt, self, n_tgt, 0.0, (bh_double4*)out, chunk, eps_src, eps_tgt);
+            else
+                bh_direct_kernel<double, false, true><<<grid, kDirThreads, 0, s>>>(
+                    src, n_src, tgt, self, n_tgt, 0.0, (bh_double4*)out, chunk, eps_src, eps_tgt);
+        } else {
+            if (split > 1)
+                bh_direct_kernel<float, true, true><<<grid, kDirThreads, 0, s>>>(
+                    src, n_src, tgt, self, n_tgt, 0.0f, (float4*)out, chunk, eps_src, eps_tgt);
+            else
+                bh_direct_kernel<float, false, true><<<grid, kDirThreads, 0, s>>>(
+                    src, n_src, tgt, self, n_tgt, 0.0f, (float4*)out, chunk, eps_src, eps_tgt);
+        }
+    } else if (precision == 64) {
         if (split > 1)
             bh_direct_kernel<double, true><<<grid, kDirThreads, 0, s>>>(src, n_src, tgt, self, n_tgt, eps * eps,
                                                                         (bh_double4*)out, chunk);

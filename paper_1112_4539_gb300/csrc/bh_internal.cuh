@@ -367,14 +367,23 @@ void launch_selftest_ring(bh_dev_ctrl* c, cudaStream_t s);
 void launch_selftest_tma(bh_dev_ctrl* c, cudaStream_t s);
 void launch_selftest_lookback(bh_dev_ctrl* c, cudaStream_t s);
 int launch_direct(const float4* src, int n_src, const float4* tgt, const int64_t* self, int n_tgt,
-                  double eps, void* out, int precision, cudaStream_t s);
+                  double eps, void* out, int precision, cudaStream_t s,
+                  const float* eps_src = nullptr, const float* eps_tgt = nullptr);
 void launch_kick_drift(float4* pos, float4* vel, const float4* acc, int n, float dt_kick, float dt_drift, int grid,
                        cudaStream_t s);
 
 // kernel launches enqueued by one call of each stage (for bh_stats.launches)
+// individual softening: h = eps^2 / 2 per particle (key order) and the mass-weighted mean of h per node
+struct bh_soft {
+    float* h = nullptr;        // n
+    double2* sums = nullptr;   // per node: (sum m, sum m h)
+    float* hbar = nullptr;     // per node
+};
 int launch_pwalk(const float4* pos_s, const uint32_t* perm, const bh_nodes& nd, int32_t* parent, int32_t* next,
                  int order, int n, int node_cap, float eps, bool unsoftened_cells, float4* out, bh_dev_ctrl* ctrl,
-                 int sm_count, cudaStream_t s);
+                 int sm_count, cudaStream_t s, const bh_soft* soft = nullptr);
+void launch_softening(const float* eps, const uint32_t* perm, const float4* pos_s, const bh_nodes& nd, int n,
+                      bool deep, const bh_soft& soft, bh_dev_ctrl* ctrl, int grid, cudaStream_t s);
 
 int launch_sph(const float4* pos_s, const uint32_t* perm, const int32_t* g_first, const int32_t* g_count,
                const bh_nodes& nd, float4* blo, float4* bhi, int G, const float* h, float h_const, int32_t* count,
@@ -386,5 +395,6 @@ inline int launches_moments(bool deep) { return (deep ? 22 : 11) + 1; }  // larg
 constexpr int kLaunchesForce = 2;    // counter reset, walk
 constexpr int kLaunchesPWalk = 4;    // parent links, next links, counter reset, walk
 inline int launches_sph(bool deep) { return (deep ? 22 : 11) + 2; }  // node boxes per level, reset, walk
+inline int launches_softening(bool deep) { return (deep ? 22 : 11) + 1; }  // gather, one per level
 
 }  // namespace bh

@@ -59,6 +59,9 @@ __global__ void bh_next_kernel(const int4* __restrict__ rec, const int32_t* __re
 }
 
 struct PWalkParams {
+    const float* soft_h;     // individual softening: eps_i^2 / 2 per particle (key order)
+    const float* soft_hbar;  //   and the mass-weighted mean of it per node
+    bool soft_cells;         //   cells softened (not BH_PWALK_UNSOFTENED_CELLS)
     const float4* pos_s;
     const uint32_t* perm;
     const int4* rec;
@@ -154,7 +157,9 @@ __device__ __forceinline__ void bh_p_pc(float4 c, const float4* __restrict__ q2,
     bh_pcount(S);
 }
 
-template <int ORDER>
+// IND: individual softening (symmetrized): a particle term softens with
+// h_i + h_j, a cell term with h_i + hbar_c (h = eps^2 / 2), instead of eps^2.
+template <int ORDER, bool IND>
 __global__ void __launch_bounds__(kPWalkThreads) bh_pwalk_kernel(PWalkParams P)
 {
     bh_dev_ctrl* ctrl = P.ctrl;
@@ -166,6 +171,7 @@ __global__ void __launch_bounds__(kPWalkThreads) bh_pwalk_kernel(PWalkParams P)
         const int i = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
         if (i < P.n) {
             const float4 xi = P.pos_s[i];
+            const float hi = IND ? P.soft_h[i] : 0.0f;
             PSum S;
             S.x = S.y = S.z = S.p = S.sx = S.sy = S.sz = S.sp = S.cx = S.cy = S.cz = S.cp = 0.0f;
             S.k = 0;
@@ -181,7 +187,7 @@ __global__ void __launch_bounds__(kPWalkThreads) bh_pwalk_kernel(PWalkParams P)
                 const int4 r = P.rec[v];
                 if (r.y == 1) {
                     if (r.x != i) {
-                        bh_p_pp(P.pos_s[r.x], P.eps2, xi.x, xi.y, xi.z, S);
+                        bh_p_pp(P.pos_s[r.x], IND ? hi + P.soft_h[r.x] : P.eps2, xi.x, xi.y, xi.z, S);
                         cnt_pp++;
                     }
                     v = P.next[v];
@@ -192,14 +198,14 @@ __global__ void __launch_bounds__(kPWalkThreads) bh_pwalk_kernel(PWalkParams P)
                 const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
                 const bool holds = (r.x <= i) && (i < r.x + r.y);
                 if (d2 > P.seff[v] && !holds) {
-                    bh_p_pc<ORDER>(c, ORDER >= 2 ? P.quad + 2 * (size_t)v : nullptr, P.eps2c, xi.x, xi.y, xi.z,
-                                   S);
+                    const float e2c = IND ? (P.soft_cells ? hi + P.soft_hbar[v] : 0.0f) : P.eps2c;
+                    bh_p_pc<ORDER>(c, ORDER >= 2 ? P.quad + 2 * (size_t)v : nullptr, e2c, xi.x, xi.y, xi.z, S);
                     cnt_pc++;
                     v = P.next[v];
                 } else if (r.z < 0) {
                     for (int j = r.x; j < r.x + r.y; j++) {
                         if (j == i) continue;
-                        bh_p_pp(P.pos_s[j], P.eps2, xi.x, xi.y, xi.z, S);
+                        bh_p_pp(P.pos_s[j], IND ? hi + P.soft_h[j] : P.eps2, xi.x, xi.y, xi.z, S);
                     }
                     cnt_pp += (unsigned long long)(r.y - (holds ? 1 : 0));
                     v = P.next[v];
@@ -230,9 +236,62 @@ __global__ void bh_pwalk_reset_kernel(bh_dev_ctrl* c)
     c->n_pc = 0ull;
 }
 
+// Individual softening, step 1: h = eps^2 / 2 of every particle in key order
+// (a negative or non-finite length is reported as BH_ERR_NONFINITE).
+__global__ void __launch_bounds__(256) bh_soft_gather_kernel(const float* __restrict__ eps,
+                                                             const uint32_t* __restrict__ perm, int n,
+                                                             float* __restrict__ h, bh_dev_ctrl* c)
+{
+    bool bad = false;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const float e = eps[perm[k]];
+        bad |= !(e >= 0.0f && isfinite(e));
+        h[k] = 0.5f * (e * e);
+    }
+    if (__any_sync(BH_FULL_MASK, bad) && (threadIdx.x & 31) == 0) atomicCAS(&c->status, 0u, (unsigned int)(-BH_ERR_NONFINITE));
+}
+
+// Step 2, one level (deepest first): per node the FP64 sums (sum m, sum m h)
+// over its particles (leaves) or its children, and hbar = sum m h / sum m.
+__global__ void __launch_bounds__(256) bh_soft_level_kernel(const float4* __restrict__ pos_s,
+                                                            const float* __restrict__ h, bh_nodes nd, int lev,
+                                                            double2* __restrict__ sums, float* __restrict__ hbar,
+                                                            const bh_dev_ctrl* __restrict__ c)
+{
+    if (c->n_nodes == 0u) return;
+    const int v0 = (int)c->level_offset[lev], v1 = (int)c->level_offset[lev + 1];
+    for (int v = v0 + blockIdx.x * blockDim.x + threadIdx.x; v < v1; v += gridDim.x * blockDim.x) {
+        const int4 r = nd.rec[v];
+        double sm = 0.0, se = 0.0;
+        if (r.z < 0) {
+            for (int j = r.x; j < r.x + r.y; j++) {
+                const double m = pos_s[j].w;
+                sm += m;
+                se += m * (double)h[j];
+            }
+        } else {
+            for (int k = 0; k < r.w; k++) {
+                const double2 t = sums[r.z + k];
+                sm += t.x;
+                se += t.y;
+            }
+        }
+        sums[v] = make_double2(sm, se);
+        hbar[v] = sm != 0.0 ? (float)(se / sm) : 0.0f;
+    }
+}
+
+void launch_softening(const float* eps, const uint32_t* perm, const float4* pos_s, const bh_nodes& nd, int n,
+                      bool deep, const bh_soft& soft, bh_dev_ctrl* ctrl, int grid, cudaStream_t s)
+{
+    bh_soft_gather_kernel<<<grid, 256, 0, s>>>(eps, perm, n, soft.h, ctrl);
+    for (int lev = deep ? BH_MAX_LEVEL_DEEP : BH_MAX_LEVEL; lev >= 0; lev--)
+        bh_soft_level_kernel<<<grid, 256, 0, s>>>(pos_s, soft.h, nd, lev, soft.sums, soft.hbar, ctrl);
+}
+
 int launch_pwalk(const float4* pos_s, const uint32_t* perm, const bh_nodes& nd, int32_t* parent, int32_t* next,
                  int order, int n, int node_cap, float eps, bool unsoftened_cells, float4* out, bh_dev_ctrl* ctrl,
-                 int sm_count, cudaStream_t s)
+                 int sm_count, cudaStream_t s, const bh_soft* soft)
 {
     const int link_grid = std::max(1, std::min((node_cap + 255) / 256, sm_count * 16));
     bh_parent_kernel<<<link_grid, 256, 0, s>>>(nd.rec, parent, ctrl);
@@ -251,9 +310,17 @@ int launch_pwalk(const float4* pos_s, const uint32_t* perm, const bh_nodes& nd, 
     P.n = n;
     P.eps2 = eps * eps;
     P.eps2c = unsoftened_cells ? 0.0f : eps * eps;
+    P.soft_h = soft ? soft->h : nullptr;
+    P.soft_hbar = soft ? soft->hbar : nullptr;
+    P.soft_cells = !unsoftened_cells;
     const int grid = std::max(1, std::min((n + kPWalkThreads - 1) / kPWalkThreads, sm_count * 64));
-    if (order >= 2) bh_pwalk_kernel<2><<<grid, kPWalkThreads, 0, s>>>(P);
-    else bh_pwalk_kernel<1><<<grid, kPWalkThreads, 0, s>>>(P);
+    if (soft) {
+        if (order >= 2) bh_pwalk_kernel<2, true><<<grid, kPWalkThreads, 0, s>>>(P);
+        else bh_pwalk_kernel<1, true><<<grid, kPWalkThreads, 0, s>>>(P);
+    } else {
+        if (order >= 2) bh_pwalk_kernel<2, false><<<grid, kPWalkThreads, 0, s>>>(P);
+        else bh_pwalk_kernel<1, false><<<grid, kPWalkThreads, 0, s>>>(P);
+    }
     return BH_OK;
 }
 

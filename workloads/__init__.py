@@ -142,6 +142,14 @@ def plummer_search_radii(pos, n_ngb=64):
     return ((3.0 * n_ngb) / (4.0 * np.pi * rho * n)) ** (1.0 / 3.0)
 
 
+def softening_lengths(n, eps, seed=17, spread=4.0):
+    """Individual softening lengths, log-uniform in [eps/spread, eps*spread]
+    (float32, seeded): a stand-in for per-particle softening of mixed mass
+    resolution."""
+    rng = _rng(seed)
+    return (eps * np.exp(rng.uniform(-np.log(spread), np.log(spread), n))).astype(np.float32)
+
+
 def sample_targets(n, n_sample=4096, seed=101):
     """Seeded, sorted, distinct sample of target indices for the FP64 error check."""
     rng = _rng(seed)
