@@ -101,3 +101,30 @@ def test_ten_kick_drift_kick_steps_clumpy(bh, orc):
         _check_update(xs, vs, a, dtk, dt, x.cpu().numpy(), v.cpu().numpy(), orc)
     assert np.abs(x.cpu().numpy()[:, :3] - pos[:, :3]).max() > 0  # the particles moved
     ctx.close()
+
+
+def test_checkpoint_and_resume_give_the_same_bits(bh, tmp_path):
+    """Six leapfrog steps straight through, against three steps, a
+    checkpoint, a resume into a new driver and three more steps."""
+    import torch
+    from paper_1112_4539_gb300 import leapfrog
+    pos = workloads.clumpy(40000, seed=5)
+    cfg = dict(leaf_size=16, group_size=96, order=2)
+    a = leapfrog.Leapfrog(_cuda(pos), dt=1e-4, theta=0.525, eps=1e-3, **cfg)
+    a.step(6)
+    assert a.status() == 0
+    b = leapfrog.Leapfrog(_cuda(pos), dt=1e-4, theta=0.525, eps=1e-3, **cfg)
+    b.step(3)
+    p = str(tmp_path / "ck.npz")
+    b.checkpoint(p)
+    b.close()
+    c = leapfrog.Leapfrog.resume(p)
+    assert c.step_count == 3 and abs(c.time - 3e-4) < 1e-15 and c.cfg == cfg
+    c.step(3)
+    assert c.status() == 0
+    assert torch.equal(a.pos, c.pos) and torch.equal(a.vel, c.vel)
+    # the closing half kick synchronises the velocities without touching the state
+    v = c.synchronised_velocities()
+    assert torch.equal(c.vel, a.vel) and not torch.equal(v, c.vel)
+    a.close()
+    c.close()
