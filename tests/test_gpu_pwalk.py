@@ -149,7 +149,9 @@ def test_particle_walk_small_and_errors(bh):
             np.testing.assert_allclose(got[1, :3], -pos[0, 3] * d / r ** 3, rtol=1e-5)
     out = torch.empty((3, 4), device="cuda:0")
     assert bh.tree_force_particles(ctx.h, -1.0, out) == bh.BH_ERR_INVALID
-    assert bh.lib().tree_force_particles(ctx.h, 0.01, 2, bh._dptr(out), None) == bh.BH_ERR_INVALID
+    assert bh.lib().tree_force_particles(ctx.h, 0.01, 4, bh._dptr(out), None) == bh.BH_ERR_INVALID
+    # individual softening without tree_softening after the build
+    assert bh.lib().tree_force_particles(ctx.h, 0.01, 2, bh._dptr(out), None) == bh.BH_ERR_STATE
     fresh = bh.Context(8)
     assert bh.tree_force_particles(fresh.h, 0.01, out) == bh.BH_ERR_STATE
     fresh.close()
