@@ -815,7 +815,7 @@ int or_force_particles(int64_t n, const float* spos, const uint32_t* perm, int64
                 if (mg < mmin) mmin = mg;
             }
             if (d2 > s_eff[v] && !holds_i) {
-                const double ec = unsoftened_pc ? 0.0 : (eps_s ? 0.5 * (ei2 + e2bar[v]) : e2c);
+                const double ec = eps_s ? (unsoftened_pc ? 0.0 : 0.5 * (ei2 + e2bar[v])) : e2c;
                 or_pc_cell(xi, yi, zi, c, quad ? quad + 6 * v : NULL, ec, acc);
                 cpc++;
             } else if (nchild[v] == 0) {

@@ -352,8 +352,8 @@ MUTATIONS = {
         [SO + "test_cell_softening_is_the_mass_weighted_mean",
          SO + "test_cell_softening_cancels_the_first_order_term"]),
     "softening_cell_term_target_only": (
-        "(eps_s ? 0.5 * (ei2 + e2bar[v]) : e2c)",
-        "(eps_s ? ei2 : e2c)",
+        "(unsoftened_pc ? 0.0 : 0.5 * (ei2 + e2bar[v]))",
+        "(unsoftened_pc ? 0.0 : ei2)",
         [SO + "test_particle_walk_cell_term_uses_the_pair_mean"]),
     "softening_particle_node_target_only": (
         "spos + 4 * (int64_t)first[v], eps_s ? 0.5 * (ei2 + ej * ej) : e2, acc);",
