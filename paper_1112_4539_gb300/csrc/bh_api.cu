@@ -204,7 +204,8 @@ int bh_create(bh_ctx** out, const bh_config* cfg, int64_t max_n, int device)
     const size_t o_quad = c.order >= 2 ? take(NN * 2 * sizeof(float4)) : 0;
     const size_t o_com64 = take(NN * sizeof(bh_double4));
     const size_t o_quad64 = c.order >= 2 ? take(NN * 6 * sizeof(double)) : 0;
-    const size_t o_wrec = take(NN * bh_wrec_f4(c.order) * sizeof(float4));
+    // walk records exist only for the TMA-staged walk (the moments pass writes them when present)
+    const size_t o_wrec = c.walk_variant == BH_WALK_TMA ? take(NN * bh_wrec_f4(c.order) * sizeof(float4)) : 0;
     const size_t o_mfeat = take(NN * sizeof(float4));
     const size_t o_mlp = take(sizeof(bh_mlp_dev));
     const size_t S = (size_t)std::max(1, c.max_systems);
@@ -248,7 +249,7 @@ int bh_create(bh_ctx** out, const bh_config* cfg, int64_t max_n, int device)
     x->nd.quad = c.order >= 2 ? (float4*)(b + o_quad) : nullptr;
     x->nd.com64 = (bh_double4*)(b + o_com64);
     x->nd.quad64 = c.order >= 2 ? (double*)(b + o_quad64) : nullptr;
-    x->nd.wrec = (float4*)(b + o_wrec);
+    x->nd.wrec = c.walk_variant == BH_WALK_TMA ? (float4*)(b + o_wrec) : nullptr;
     x->mfeat = (float4*)(b + o_mfeat);
     x->mlp = (bh_mlp_dev*)(b + o_mlp);
     x->sys_of = (uint32_t*)(b + o_sys);
