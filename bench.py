@@ -87,7 +87,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-criterion comparison")
     ap.add_argument("--no-extra", action="store_true",
-                    help="headline run only: skip the TMA-walk, 512-system and fresh-4M blocks")
+                    help="headline run only: skip the TMA-walk, 512-system, accuracy-sweep and fresh-4M blocks")
     ap.add_argument("--cpu-sample-groups", type=int, default=6000)
     ap.add_argument("--walk", default="group", choices=["group", "particle"],
                     help="group: one warp per particle group; particle: the paper's per-particle walk (Fig. 5)")
@@ -628,6 +628,7 @@ def run_ours(args, W):
         ctx = None
         torch.cuda.empty_cache()
         line["batched512"] = batched_block(local)
+        line["accuracy_sweep_plummer1m"] = accuracy_sweep(local)
         if not args.no_learned and os.path.exists(WEIGHTS):
             line["learned_fresh4m"] = {name: learned_fresh_block(bh, local, name)
                                        for name in ("clumpy4m", "plummer4m")}
@@ -840,45 +841,56 @@ def tma_block(bh, local, x, theta, eps, leaf, G, order, ref_out):
                        "shared memory (mbarrier completion)"}
 
 
-def run_accuracy_sweep(args):
+def accuracy_sweep(local=0, reps=3):
     """Force errors against the FP64 direct sum (4096 seeded targets) and the
     evaluation time over theta in {0.3, 0.5, 0.75} x group size in {32, 64,
     128, 256} x {monopole, quadrupole} on a Plummer sphere of 2^20 particles
-    (seed 1, eps = 0.01, leaf 16).  Prints one JSON object."""
+    (seed 1, eps = 0.01, leaf 16).  Returns a dict."""
     import torch
 
     import paper_1112_4539_gb300 as bh
     bh.lib()
+    dev = torch.device("cuda", local)
     n, eps, leaf = 1 << 20, 0.01, 16
-    x = torch.from_numpy(workloads.make("plummer", n, 1)).cuda()
+    x = torch.from_numpy(workloads.make("plummer", n, 1)).to(dev)
     idx = workloads.sample_targets(n, 4096, seed=101)
-    idx_t = torch.from_numpy(idx).cuda()
-    ref = torch.empty((idx.size, 4), dtype=torch.float64, device=x.device)
+    idx_t = torch.from_numpy(idx).to(dev)
+    ref = torch.empty((idx.size, 4), dtype=torch.float64, device=dev)
     assert bh.direct_force(x, x[idx_t].contiguous(), idx_t, eps, ref, 64) == 0
     acc = torch.empty_like(x)
     rows = []
+    clocks = ClockSampler(local)
+    clocks.start()
     for order in (1, 2):
         for G in (32, 64, 128, 256):
-            ctx = bh.Context(n, leaf_size=leaf, group_size=G, order=order)
+            ctx = bh.Context(n, device=local, leaf_size=leaf, group_size=G, order=order)
             for theta in (0.3, 0.5, 0.75):
                 errs = measure_errors(ctx, x, idx_t, ref, theta, eps, acc)
                 s0 = ctx.stats()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
-                for _ in range(3):
+                for _ in range(reps):
                     ctx.evaluate(x, theta, eps, acc)
                 e1.record()
                 torch.cuda.synchronize()
                 s1 = ctx.stats()
                 assert s1["status"] == 0, s1["status"]
-                inter = (s1["n_pp_total"] - s0["n_pp_total"] + s1["n_pc_total"] - s0["n_pc_total"]) / 3
+                inter = (s1["n_pp_total"] - s0["n_pp_total"] + s1["n_pc_total"] - s0["n_pc_total"]) / reps
                 rows.append(dict(order=order, G=G, theta=theta, p50=errs["p50"], p99=errs["p99"],
                                  mean=errs["mean"], max=errs["max"], phi_p99=errs["phi_p99"],
-                                 ms_per_eval=e0.elapsed_time(e1) / 3, interactions=inter))
+                                 ms_per_eval=e0.elapsed_time(e1) / reps, interactions=inter))
             ctx.close()
-    print(json.dumps({"sweep": "Plummer N=1048576 (seed 1), eps=0.01, leaf 16; errors vs FP64 direct on "
-                               "4096 targets (seed 101); time = whole evaluation (build, moments, walk)",
-                      "gpu": torch.cuda.get_device_name(), "rows": rows}))
+    return {"sweep": "Plummer N=1048576 (seed 1), eps=0.01, leaf 16; errors vs FP64 direct on 4096 targets "
+                     "(seed 101); time = whole evaluation (build, moments, walk)",
+            "rows": rows, "clocks": clocks.stop()}
+
+
+def run_accuracy_sweep(args):
+    """The accuracy sweep alone; prints one JSON object."""
+    import torch
+    out = accuracy_sweep()
+    out["gpu"] = torch.cuda.get_device_name()
+    print(json.dumps(out))
     return 0
 
 
