@@ -518,15 +518,20 @@ __global__ void __launch_bounds__(256) bh_bigleaf_moments_kernel(const float4* _
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     const int nn = (int)c->n_nodes;
-    for (int base = warp * 32; base < nn; base += nw * 32) {
-        const int v = base + lane;
+    // lane l of warp w examines nodes w + nw (l + 32 i): consecutive nodes go to
+    // different warps, so the large leaves of a dense knot (adjacent in the
+    // node order) spread over the grid instead of queueing in one warp
+    for (long long v0 = warp; v0 < nn; v0 += 32ll * nw) {
+        const long long vl = v0 + (long long)nw * lane;
+        const int v = vl < nn ? (int)vl : -1;
         int4 r = make_int4(0, 0, 0, 0);
-        if (v < nn) r = nd.rec[v];
-        unsigned int big = __ballot_sync(BH_FULL_MASK, v < nn && r.z < 0 && r.y > kLeafFp64);
+        if (v >= 0) r = nd.rec[v];
+        unsigned int big = __ballot_sync(BH_FULL_MASK, v >= 0 && r.z < 0 && r.y > kLeafFp64);
         while (big) {
             const int src = __ffs(big) - 1;
             big &= big - 1u;
             const int k = __shfl_sync(BH_FULL_MASK, r.x, src), cnt = __shfl_sync(BH_FULL_MASK, r.y, src);
+            const int vw = __shfl_sync(BH_FULL_MASK, v, src);
             // FP32 lane partials of at most count/32 terms, summed across the
             // warp; the mass with a Kahan compensation and the centre of mass
             // in FP64.  Offsets are taken from the first particle, so the
@@ -572,10 +577,9 @@ __global__ void __launch_bounds__(256) bh_bigleaf_moments_kernel(const float4* _
                 for (int i = 0; i < 6; i++) q[i] = (double)bh_warp_sumf(pq[i]);
             }
             if (lane == 0) {
-                const int w = base + src;
-                nd.com64[w] = bh_double4{cx, cy, cz, M};
+                nd.com64[vw] = bh_double4{cx, cy, cz, M};
                 if (ORDER >= 2)
-                    for (int i = 0; i < 6; i++) nd.quad64[(size_t)w * 6 + i] = q[i];
+                    for (int i = 0; i < 6; i++) nd.quad64[(size_t)vw * 6 + i] = q[i];
             }
         }
     }
@@ -635,92 +639,122 @@ __device__ __forceinline__ void bh_internal_moments(const bh_nodes& nd, int ch, 
     }
 }
 
+// Moments of one node v of level lev (leaves from their particles, internal
+// nodes from their children, which the previous, deeper level wrote).
+template <int ORDER, typename K>
+__device__ __forceinline__ void bh_moment_node(const float4* __restrict__ pos_s, const K* __restrict__ keys,
+                                               const bh_nodes& nd, int v, int lev, float theta, int fp64_threshold,
+                                               int curve, float4 gbox, const uint32_t* __restrict__ sys,
+                                               const float4* __restrict__ sys_box)
+{
+    constexpr int L = bh_key_traits<K>::kMaxLevel;
+    const int4 r = nd.rec[v];
+    // root cube of the node's system (several systems: one cube each)
+    const float4 bx = sys ? sys_box[sys[r.x]] : gbox;
+    const float xmin = bx.x, ymin = bx.y, zmin = bx.z;
+    const float side = ldexpf(bx.w, -lev);  // exact: power-of-two scaling
+    const float opening = side / theta;
+    const bool f64 = bh_node_fp64(r.y, r.z < 0, lev, fp64_threshold);
+    // geometric centre of the node's level-lev cell: the ancestor of the
+    // first particle's cell, decoded from its key
+    unsigned int ix, iy, iz;
+    bh_cell_of<K>(keys[r.x], curve, ix, iy, iz);
+    const int sh = L - lev;
+    const float gx = xmin + ((float)(ix >> sh) + 0.5f) * side;
+    const float gy = ymin + ((float)(iy >> sh) + 0.5f) * side;
+    const float gz = zmin + ((float)(iz >> sh) + 0.5f) * side;
+    float cx, cy, cz, M, q[6];
+    bool massless;
+    if (f64) {
+        bh_mom<double> o;
+        if (r.z < 0 && r.y > kLeafFp64) {
+            // taken by bh_bigleaf_moments_kernel
+            const bh_double4 m4 = nd.com64[v];
+            o.cx = m4.x; o.cy = m4.y; o.cz = m4.z; o.M = m4.w;
+            massless = !(o.M != 0.0);
+            if (ORDER >= 2)
+                for (int i = 0; i < 6; i++) o.q[i] = nd.quad64[(size_t)v * 6 + i];
+        } else if (r.z < 0) {
+            bh_leaf_moments<double, ORDER>(pos_s, r.x, r.y, o, massless);
+        } else {
+            bh_internal_moments<double, ORDER>(nd, r.z, r.w, fp64_threshold, o, massless);
+        }
+        if (massless) {
+            o.cx = gx; o.cy = gy; o.cz = gz;
+        }
+        nd.com64[v] = bh_double4{o.cx, o.cy, o.cz, o.M};
+        cx = (float)o.cx; cy = (float)o.cy; cz = (float)o.cz; M = (float)o.M;
+        if (ORDER >= 2)
+            for (int i = 0; i < 6; i++) {
+                nd.quad64[(size_t)v * 6 + i] = o.q[i];
+                q[i] = (float)o.q[i];
+            }
+    } else {
+        bh_mom<float> o;
+        if (r.z < 0) bh_leaf_moments<float, ORDER>(pos_s, r.x, r.y, o, massless);
+        else bh_internal_moments<float, ORDER>(nd, r.z, r.w, fp64_threshold, o, massless);
+        if (massless) {
+            o.cx = gx; o.cy = gy; o.cz = gz;
+        }
+        cx = o.cx; cy = o.cy; cz = o.cz; M = o.M;
+        if (ORDER >= 2)
+            for (int i = 0; i < 6; i++) q[i] = o.q[i];
+    }
+    nd.com_m[v] = make_float4(cx, cy, cz, M);
+    const float dx = gx - cx, dy = gy - cy, dz = gz - cz;
+    const float s = sqrtf(dx * dx + dy * dy + dz * dz);
+    const float t = opening + s;
+    nd.seff[v] = t * t;
+    float4 qa = make_float4(0.f, 0.f, 0.f, 0.f), qb = qa;
+    if (ORDER >= 2) {
+        const float T = q[0] + q[1] + q[2];
+        qa = make_float4(q[0], q[1], q[2], q[3]);
+        qb = make_float4(q[4], q[5], 1.5f * T, 0.5f * T);
+        nd.quad[2 * (size_t)v] = qa;
+        nd.quad[2 * (size_t)v + 1] = qb;
+    }
+    if (nd.wrec) {
+        float4* w = nd.wrec + (size_t)v * bh_wrec_f4(ORDER);
+        const int chn = r.z < 0 ? -1 : (r.z << 3) | (r.w - 1);
+        w[0] = make_float4(cx, cy, cz, M);
+        w[1] = make_float4(__int_as_float(r.x), __int_as_float(r.y), __int_as_float(chn), t * t);
+        if (ORDER >= 2) {
+            w[2] = qa;
+            w[3] = qb;
+        }
+    }
+}
+
 template <int ORDER, typename K>
 __global__ void __launch_bounds__(256)
 bh_moments_level_kernel(const float4* __restrict__ pos_s, const K* __restrict__ keys, bh_nodes nd, int lev,
                         float theta, int fp64_threshold, int curve, const bh_dev_ctrl* __restrict__ c,
                         const uint32_t* __restrict__ sys, const float4* __restrict__ sys_box)
 {
-    constexpr int L = bh_key_traits<K>::kMaxLevel;
     const int v0 = (int)c->level_offset[lev], v1 = (int)c->level_offset[lev + 1];
     if (c->n_nodes == 0u) return;
     const float4 gbox = make_float4(c->box[0], c->box[1], c->box[2], c->box[3]);
-    for (int v = v0 + blockIdx.x * blockDim.x + threadIdx.x; v < v1; v += gridDim.x * blockDim.x) {
-        const int4 r = nd.rec[v];
-        // root cube of the node's system (several systems: one cube each)
-        const float4 bx = sys ? sys_box[sys[r.x]] : gbox;
-        const float xmin = bx.x, ymin = bx.y, zmin = bx.z;
-        const float side = ldexpf(bx.w, -lev);  // exact: power-of-two scaling
-        const float opening = side / theta;
-        const bool f64 = bh_node_fp64(r.y, r.z < 0, lev, fp64_threshold);
-        // geometric centre of the node's level-lev cell: the ancestor of the
-        // first particle's cell, decoded from its key
-        unsigned int ix, iy, iz;
-        bh_cell_of<K>(keys[r.x], curve, ix, iy, iz);
-        const int sh = L - lev;
-        const float gx = xmin + ((float)(ix >> sh) + 0.5f) * side;
-        const float gy = ymin + ((float)(iy >> sh) + 0.5f) * side;
-        const float gz = zmin + ((float)(iz >> sh) + 0.5f) * side;
-        float cx, cy, cz, M, q[6];
-        bool massless;
-        if (f64) {
-            bh_mom<double> o;
-            if (r.z < 0 && r.y > kLeafFp64) {
-                // taken by bh_bigleaf_moments_kernel
-                const bh_double4 m4 = nd.com64[v];
-                o.cx = m4.x; o.cy = m4.y; o.cz = m4.z; o.M = m4.w;
-                massless = !(o.M != 0.0);
-                if (ORDER >= 2)
-                    for (int i = 0; i < 6; i++) o.q[i] = nd.quad64[(size_t)v * 6 + i];
-            } else if (r.z < 0) {
-                bh_leaf_moments<double, ORDER>(pos_s, r.x, r.y, o, massless);
-            } else {
-                bh_internal_moments<double, ORDER>(nd, r.z, r.w, fp64_threshold, o, massless);
-            }
-            if (massless) {
-                o.cx = gx; o.cy = gy; o.cz = gz;
-            }
-            nd.com64[v] = bh_double4{o.cx, o.cy, o.cz, o.M};
-            cx = (float)o.cx; cy = (float)o.cy; cz = (float)o.cz; M = (float)o.M;
-            if (ORDER >= 2)
-                for (int i = 0; i < 6; i++) {
-                    nd.quad64[(size_t)v * 6 + i] = o.q[i];
-                    q[i] = (float)o.q[i];
-                }
-        } else {
-            bh_mom<float> o;
-            if (r.z < 0) bh_leaf_moments<float, ORDER>(pos_s, r.x, r.y, o, massless);
-            else bh_internal_moments<float, ORDER>(nd, r.z, r.w, fp64_threshold, o, massless);
-            if (massless) {
-                o.cx = gx; o.cy = gy; o.cz = gz;
-            }
-            cx = o.cx; cy = o.cy; cz = o.cz; M = o.M;
-            if (ORDER >= 2)
-                for (int i = 0; i < 6; i++) q[i] = o.q[i];
-        }
-        nd.com_m[v] = make_float4(cx, cy, cz, M);
-        const float dx = gx - cx, dy = gy - cy, dz = gz - cz;
-        const float s = sqrtf(dx * dx + dy * dy + dz * dz);
-        const float t = opening + s;
-        nd.seff[v] = t * t;
-        float4 qa = make_float4(0.f, 0.f, 0.f, 0.f), qb = qa;
-        if (ORDER >= 2) {
-            const float T = q[0] + q[1] + q[2];
-            qa = make_float4(q[0], q[1], q[2], q[3]);
-            qb = make_float4(q[4], q[5], 1.5f * T, 0.5f * T);
-            nd.quad[2 * (size_t)v] = qa;
-            nd.quad[2 * (size_t)v + 1] = qb;
-        }
-        if (nd.wrec) {
-            float4* w = nd.wrec + (size_t)v * bh_wrec_f4(ORDER);
-            const int chn = r.z < 0 ? -1 : (r.z << 3) | (r.w - 1);
-            w[0] = make_float4(cx, cy, cz, M);
-            w[1] = make_float4(__int_as_float(r.x), __int_as_float(r.y), __int_as_float(chn), t * t);
-            if (ORDER >= 2) {
-                w[2] = qa;
-                w[3] = qb;
-            }
-        }
+    for (int v = v0 + blockIdx.x * blockDim.x + threadIdx.x; v < v1; v += gridDim.x * blockDim.x)
+        bh_moment_node<ORDER, K>(pos_s, keys, nd, v, lev, theta, fp64_threshold, curve, gbox, sys, sys_box);
+}
+
+// The top levels (top..0) of a single system's tree in one block: they hold at
+// most 8^top nodes each, too few to fill a grid, and the FP64 sums of their
+// large nodes are latency-bound; one launch with a block barrier between
+// levels replaces one launch per level.
+constexpr int kTopLevels = 4;  // levels 0..kTopLevels
+template <int ORDER, typename K>
+__global__ void __launch_bounds__(1024)
+bh_moments_top_kernel(const float4* __restrict__ pos_s, const K* __restrict__ keys, bh_nodes nd, int top,
+                      float theta, int fp64_threshold, int curve, const bh_dev_ctrl* __restrict__ c)
+{
+    if (c->n_nodes == 0u) return;
+    const float4 gbox = make_float4(c->box[0], c->box[1], c->box[2], c->box[3]);
+    for (int lev = top; lev >= 0; lev--) {
+        const int v0 = (int)c->level_offset[lev], v1 = (int)c->level_offset[lev + 1];
+        for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x)
+            bh_moment_node<ORDER, K>(pos_s, keys, nd, v, lev, theta, fp64_threshold, curve, gbox, nullptr, nullptr);
+        __syncthreads();  // this level's moments are visible to the next (shallower) level's threads
     }
 }
 
@@ -731,13 +765,24 @@ static void bh_moments_t(const float4* pos_s, const K* keys, const bh_nodes& nd,
 {
     if (order >= 2) bh_bigleaf_moments_kernel<2><<<grid, 256, 0, s>>>(pos_s, nd, ctrl);
     else bh_bigleaf_moments_kernel<1><<<grid, 256, 0, s>>>(pos_s, nd, ctrl);
-    for (int lev = bh_key_traits<K>::kMaxLevel; lev >= 0; lev--) {
+    // a single system's top levels in one block; several systems (sys) have
+    // a root per system, so their top levels take the full grid
+    const int last = sys ? 0 : kTopLevels + 1;
+    for (int lev = bh_key_traits<K>::kMaxLevel; lev >= last; lev--) {
         if (order >= 2)
             bh_moments_level_kernel<2, K><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, curve,
                                                                ctrl, sys, sys_box);
         else
             bh_moments_level_kernel<1, K><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, curve,
                                                                ctrl, sys, sys_box);
+    }
+    if (!sys) {
+        if (order >= 2)
+            bh_moments_top_kernel<2, K><<<1, 1024, 0, s>>>(pos_s, keys, nd, kTopLevels, theta, fp64_threshold, curve,
+                                                           ctrl);
+        else
+            bh_moments_top_kernel<1, K><<<1, 1024, 0, s>>>(pos_s, keys, nd, kTopLevels, theta, fp64_threshold, curve,
+                                                           ctrl);
     }
 }
 
