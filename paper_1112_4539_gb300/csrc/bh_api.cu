@@ -753,7 +753,7 @@ int bh_force_batched(bh_ctx* x, const float* d_pos_mass, float theta, float eps,
                              nullptr, x->cfg.walk_variant);
     if (rc) return rc;
     // init, batch sort, 4 tree, 5 groups, moments per level, 2 walk
-    x->launches += 2 + 4 + 5 + bh::launches_moments_batched(x->deep) + bh::kLaunchesForce;
+    x->launches += 2 + 4 + 5 + bh::launches_moments(x->deep) + bh::kLaunchesForce;
     if (cudaGetLastError() != cudaSuccess) return BH_ERR_CUDA;
     x->n = n;
     x->theta = theta;

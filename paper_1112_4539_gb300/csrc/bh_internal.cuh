@@ -391,9 +391,7 @@ int launch_sph(const float4* pos_s, const uint32_t* perm, const int32_t* g_first
 
 // launches per call (deep = 63-bit keys: 8 sort passes, 22 levels)
 inline int launches_build(bool deep) { return deep ? 20 : 16; }  // init, bbox, keys, sort passes, 4 tree, 5 groups
-// large leaves, one per level below the top levels, the top levels in one (a single system)
-inline int launches_moments(bool deep) { return (deep ? 22 : 11) - 5 + 2; }
-inline int launches_moments_batched(bool deep) { return (deep ? 22 : 11) + 1; }  // every level on the grid
+inline int launches_moments(bool deep) { return (deep ? 22 : 11) + 1; }  // large leaves, one per level
 constexpr int kLaunchesForce = 2;    // counter reset, walk
 constexpr int kLaunchesPWalk = 4;    // parent links, next links, counter reset, walk
 inline int launches_sph(bool deep) { return (deep ? 22 : 11) + 2; }  // node boxes per level, reset, walk

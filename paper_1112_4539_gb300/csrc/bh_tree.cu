@@ -738,26 +738,6 @@ bh_moments_level_kernel(const float4* __restrict__ pos_s, const K* __restrict__ 
         bh_moment_node<ORDER, K>(pos_s, keys, nd, v, lev, theta, fp64_threshold, curve, gbox, sys, sys_box);
 }
 
-// The top levels (top..0) of a single system's tree in one block: they hold at
-// most 8^top nodes each, too few to fill a grid, and the FP64 sums of their
-// large nodes are latency-bound; one launch with a block barrier between
-// levels replaces one launch per level.
-constexpr int kTopLevels = 4;  // levels 0..kTopLevels
-template <int ORDER, typename K>
-__global__ void __launch_bounds__(1024)
-bh_moments_top_kernel(const float4* __restrict__ pos_s, const K* __restrict__ keys, bh_nodes nd, int top,
-                      float theta, int fp64_threshold, int curve, const bh_dev_ctrl* __restrict__ c)
-{
-    if (c->n_nodes == 0u) return;
-    const float4 gbox = make_float4(c->box[0], c->box[1], c->box[2], c->box[3]);
-    for (int lev = top; lev >= 0; lev--) {
-        const int v0 = (int)c->level_offset[lev], v1 = (int)c->level_offset[lev + 1];
-        for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x)
-            bh_moment_node<ORDER, K>(pos_s, keys, nd, v, lev, theta, fp64_threshold, curve, gbox, nullptr, nullptr);
-        __syncthreads();  // this level's moments are visible to the next (shallower) level's threads
-    }
-}
-
 template <typename K>
 static void bh_moments_t(const float4* pos_s, const K* keys, const bh_nodes& nd, int order, float theta,
                          int fp64_threshold, int curve, bh_dev_ctrl* ctrl, int grid, cudaStream_t s,
@@ -765,24 +745,13 @@ static void bh_moments_t(const float4* pos_s, const K* keys, const bh_nodes& nd,
 {
     if (order >= 2) bh_bigleaf_moments_kernel<2><<<grid, 256, 0, s>>>(pos_s, nd, ctrl);
     else bh_bigleaf_moments_kernel<1><<<grid, 256, 0, s>>>(pos_s, nd, ctrl);
-    // a single system's top levels in one block; several systems (sys) have
-    // a root per system, so their top levels take the full grid
-    const int last = sys ? 0 : kTopLevels + 1;
-    for (int lev = bh_key_traits<K>::kMaxLevel; lev >= last; lev--) {
+    for (int lev = bh_key_traits<K>::kMaxLevel; lev >= 0; lev--) {
         if (order >= 2)
             bh_moments_level_kernel<2, K><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, curve,
                                                                ctrl, sys, sys_box);
         else
             bh_moments_level_kernel<1, K><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, curve,
                                                                ctrl, sys, sys_box);
-    }
-    if (!sys) {
-        if (order >= 2)
-            bh_moments_top_kernel<2, K><<<1, 1024, 0, s>>>(pos_s, keys, nd, kTopLevels, theta, fp64_threshold, curve,
-                                                           ctrl);
-        else
-            bh_moments_top_kernel<1, K><<<1, 1024, 0, s>>>(pos_s, keys, nd, kTopLevels, theta, fp64_threshold, curve,
-                                                           ctrl);
     }
 }
 
