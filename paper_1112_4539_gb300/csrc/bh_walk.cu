@@ -61,13 +61,13 @@ struct WarpSmem {
     float4 ra[kRing / 2];       // point sources: (-x, -x', -y, -y')
     float4 rb[kRing / 2];       //                (-z, -z', -m, -m')
 };
-struct WarpQuad {               // quadrupole cells, pairs as above
+struct WarpQuad {               // quadrupole cells, pairs as above; Q = 3 I - T 1 (traceless), T = tr I
     float4 a[kRing / 2];        // (-x, -x', -y, -y')      centre of mass
     float4 b[kRing / 2];        // (-z, -z', -M, -M')
-    float4 c[kRing / 2];        // 3 (Ixx, Ixx', Iyy, Iyy')
-    float4 d[kRing / 2];        // 3 (Izz, Izz', Ixy, Ixy')
-    float4 e[kRing / 2];        // 3 (Ixz, Ixz', Iyz, Iyz')
-    float4 f[kRing / 2];        // (1.5 T, 1.5 T', 0.5 T, 0.5 T'),  T = tr I
+    float4 c[kRing / 2];        // (Qxx, Qxx', Qyy, Qyy')
+    float4 d[kRing / 2];        // (Qzz, Qzz', Qxy, Qxy')
+    float4 e[kRing / 2];        // (Qxz, Qxz', Qyz, Qyz')
+    float4 f[kRing / 2];        // (-T eps^2, -T' eps^2, -, -)
 };
 
 __device__ __forceinline__ void bh_put_point(WarpSmem& S, int r, float4 v)
@@ -78,8 +78,9 @@ __device__ __forceinline__ void bh_put_point(WarpSmem& S, int r, float4 v)
     b[0] = -v.z; b[2] = -v.w;
 }
 // cell with centre/mass cm and stored moments qb = (Ixx, Iyy, Izz, Ixy),
-// qc = (Ixz, Iyz, 1.5 T, 0.5 T)
-__device__ __forceinline__ void bh_put_quad(WarpQuad& Q, int r, float4 cm, float4 qb, float4 qc)
+// qc = (Ixz, Iyz, 1.5 T, 0.5 T): staged as the traceless Q = 3 I - T 1 and
+// -T eps^2 (see bh_pq2)
+__device__ __forceinline__ void bh_put_quad(WarpQuad& Q, int r, float4 cm, float4 qb, float4 qc, float eps2)
 {
     const int p = r >> 1, h = r & 1;
     float* a = reinterpret_cast<float*>(&Q.a[p]) + h;
@@ -88,12 +89,13 @@ __device__ __forceinline__ void bh_put_quad(WarpQuad& Q, int r, float4 cm, float
     float* d = reinterpret_cast<float*>(&Q.d[p]) + h;
     float* e = reinterpret_cast<float*>(&Q.e[p]) + h;
     float* f = reinterpret_cast<float*>(&Q.f[p]) + h;
+    const float T = 2.0f * qc.w;  // exact
     a[0] = -cm.x; a[2] = -cm.y;
     b[0] = -cm.z; b[2] = -cm.w;
-    c[0] = 3.0f * qb.x; c[2] = 3.0f * qb.y;
-    d[0] = 3.0f * qb.z; d[2] = 3.0f * qb.w;
+    c[0] = __fmaf_rn(3.0f, qb.x, -T); c[2] = __fmaf_rn(3.0f, qb.y, -T);
+    d[0] = __fmaf_rn(3.0f, qb.z, -T); d[2] = 3.0f * qb.w;
     e[0] = 3.0f * qc.x; e[2] = 3.0f * qc.y;
-    f[0] = qc.z; f[2] = qc.w;
+    f[0] = -T * eps2;
 }
 
 struct WalkParams {
@@ -209,10 +211,14 @@ __device__ __forceinline__ void bh_pp2(float4 sa, float4 sb, f2 eps2, f2 x, f2 y
 }
 
 // A pair of quadrupole cells on one target.  With r = x_i - c, h^2 = r^2 +
-// eps^2, g_n = h^-n, u = 3 I r, q3 = r.u (three times the quadratic form):
-//   a   += g5 u + k r,   k = g5 (1.5 T - 2.5 q3 g2) - M g3
-//   phi += -M g1 + 0.5 T g3 - 0.5 q3 g5
-// the last term accumulated apart (aq) and scaled once per tile.
+// eps^2, g_n = h^-n, the traceless Q = 3 I - T 1, u = Q r and
+// s = r.u - T eps^2, the second-order term of the softened kernel is
+//   a   += g5 u + k r,   k = -M g3 - 2.5 g5 g2 s
+//   phi += -M g1 - 0.5 s g5
+// (the same as  a += 3 g5 I r + (1.5 T g5 - 7.5 q g7) r,
+// phi -= 0.5 (3 q g5 - T g3) with q = r.I.r, since 3 q = r.Q.r + T r^2 and
+// r^2 = h^2 - eps^2); the last term accumulated apart (aq) and scaled once
+// per tile.  33 FP32 operations per source (21 FMA, 9 mul, 3 add).
 __device__ __forceinline__ void bh_pq2(float4 ca, float4 cb, float4 cc, float4 cd, float4 ce, float4 cf, f2 eps2,
                                        f2 x, f2 y, f2 z, f2& ax, f2& ay, f2& az, f2& ap, f2& aq)
 {
@@ -226,14 +232,14 @@ __device__ __forceinline__ void bh_pq2(float4 ca, float4 cb, float4 cc, float4 c
     const f2 u0 = bh_fma2(bh_hi(cd), ry, bh_fma2(bh_lo(ce), rz, bh_mul2(bh_lo(cc), rx)));
     const f2 u1 = bh_fma2(bh_hi(cd), rx, bh_fma2(bh_hi(ce), rz, bh_mul2(bh_hi(cc), ry)));
     const f2 u2 = bh_fma2(bh_lo(ce), rx, bh_fma2(bh_hi(ce), ry, bh_mul2(bh_lo(cd), rz)));
-    const f2 q3 = bh_fma2(rx, u0, bh_fma2(ry, u1, bh_mul2(rz, u2)));
-    const f2 w = bh_fma2(bh_mul2(q3, make_float2(-2.5f, -2.5f)), g2, bh_lo(cf));
+    const f2 sq = bh_fma2(rx, u0, bh_fma2(ry, u1, bh_fma2(rz, u2, bh_lo(cf))));
+    const f2 w = bh_mul2(bh_mul2(sq, make_float2(-2.5f, -2.5f)), g2);
     const f2 k = bh_fma2(g5, w, bh_mul2(mneg, g3));
     ax = bh_fma2(g5, u0, bh_fma2(k, rx, ax));
     ay = bh_fma2(g5, u1, bh_fma2(k, ry, ay));
     az = bh_fma2(g5, u2, bh_fma2(k, rz, az));
-    ap = bh_fma2(bh_hi(cf), g3, bh_fma2(mneg, g1, ap));
-    aq = bh_fma2(q3, g5, aq);
+    ap = bh_fma2(mneg, g1, ap);
+    aq = bh_fma2(sq, g5, aq);
 }
 
 // Targets of a lane: slot t holds (x, x), (y, y), (z, z).
@@ -614,7 +620,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
             if (ORDER >= 2) {
                 if (acc) {
                     const int slot = (q_head + q_cnt + __popc(am & lt)) & (kRing - 1);
-                    bh_put_quad(*Q, slot, cm, P.quad[2 * (size_t)v], P.quad[2 * (size_t)v + 1]);
+                    bh_put_quad(*Q, slot, cm, P.quad[2 * (size_t)v], P.quad[2 * (size_t)v + 1], eps2);
                 }
                 q_cnt += nacc;
             } else {
@@ -689,7 +695,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
         if (ORDER >= 2 && q_cnt > 0) {
             if (lane >= q_cnt)
                 bh_put_quad(*Q, q_head + lane, bh_pad_source(), make_float4(0.f, 0.f, 0.f, 0.f),
-                            make_float4(0.f, 0.f, 0.f, 0.f));
+                            make_float4(0.f, 0.f, 0.f, 0.f), eps2);
             __syncwarp();
             bh_quads<T, WarpQuad>(L, *Q, q_head >> 1, eps2v, X, A);
         }
@@ -971,7 +977,7 @@ __global__ void __launch_bounds__(256, bh_ws_min_blocks<T>()) bh_walk_ws_kernel(
                 if (ORDER >= 2) {
                     if (acc) {
                         const int slot = (q_head + q_cnt + __popc(am & lt)) & (kRing - 1);
-                        bh_put_quad(*Q, slot, cm, P.quad[2 * (size_t)v], P.quad[2 * (size_t)v + 1]);
+                        bh_put_quad(*Q, slot, cm, P.quad[2 * (size_t)v], P.quad[2 * (size_t)v + 1], eps2);
                     }
                     q_cnt += nacc;
                 } else {
@@ -1043,7 +1049,7 @@ __global__ void __launch_bounds__(256, bh_ws_min_blocks<T>()) bh_walk_ws_kernel(
             if (ORDER >= 2 && q_cnt > 0) {
                 if (lane >= q_cnt)
                     bh_put_quad(*Q, q_head + lane, bh_pad_source(), make_float4(0.f, 0.f, 0.f, 0.f),
-                                make_float4(0.f, 0.f, 0.f, 0.f));
+                                make_float4(0.f, 0.f, 0.f, 0.f), eps2);
                 __syncwarp();
                 if (!(alive = send_quads(q_head >> 1))) break;
             }
@@ -1450,7 +1456,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, false>()) bh_walk_t
             const int nacc = __popc(am);
             g_pc += (unsigned int)nacc;
             if (ORDER >= 2) {
-                if (acc) bh_put_quad(*Q, (q_head + q_cnt + __popc(am & lt)) & (kRing - 1), cm, qa, qb);
+                if (acc) bh_put_quad(*Q, (q_head + q_cnt + __popc(am & lt)) & (kRing - 1), cm, qa, qb, eps2);
                 q_cnt += nacc;
             } else {
                 if (acc) bh_put_point(S, (ring_head + ring_cnt + __popc(am & lt)) & (kRing - 1), cm);
@@ -1535,7 +1541,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, false>()) bh_walk_t
         if (ORDER >= 2 && q_cnt > 0) {
             if (lane >= q_cnt)
                 bh_put_quad(*Q, q_head + lane, bh_pad_source(), make_float4(0.f, 0.f, 0.f, 0.f),
-                            make_float4(0.f, 0.f, 0.f, 0.f));
+                            make_float4(0.f, 0.f, 0.f, 0.f), eps2);
             __syncwarp();
             bh_quads<T, WarpQuad>(L, *Q, q_head >> 1, eps2v, X, A);
         }
