@@ -163,12 +163,18 @@ __device__ __forceinline__ bool bh_lookback_wait(const volatile unsigned long lo
     return true;
 }
 
+__device__ __forceinline__ bool bh_lookback_ready(unsigned long long st, unsigned int epoch)
+{
+    return (unsigned int)(st >> 32) == epoch && ((st >> 30) & 3ull) != 0ull;
+}
+
 __device__ __forceinline__ unsigned long long bh_status_word(unsigned int epoch, unsigned int flag, unsigned int v)
 {
     return ((unsigned long long)epoch << 32) | ((unsigned long long)flag << 30) | (unsigned long long)(v & 0x3fffffffu);
 }
 
-// Exclusive scan of one value per thread over a 256-thread block.
+// Exclusive scan over the block's first 256 threads (one value each; the
+// other threads pass 0 and get 0).  Every thread of the block calls it.
 __device__ __forceinline__ unsigned int bh_block_excl_scan256(unsigned int v, unsigned int* warp_tot)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -178,36 +184,78 @@ __device__ __forceinline__ unsigned int bh_block_excl_scan256(unsigned int v, un
         const unsigned int t = __shfl_up_sync(BH_FULL_MASK, incl, o);
         if (lane >= o) incl += t;
     }
-    if (lane == 31) warp_tot[w] = incl;
+    if (w < 8 && lane == 31) warp_tot[w] = incl;
     __syncthreads();
     unsigned int base = 0;
-    for (int i = 0; i < w; i++) base += warp_tot[i];
+    if (w < 8)
+        for (int i = 0; i < w; i++) base += warp_tot[i];
     __syncthreads();
-    return base + incl - v;
+    return w < 8 ? base + incl - v : 0u;
 }
 
-// K = uint32_t (30-bit keys, 16 items per thread) or bh_key64 (63-bit keys,
-// 8 items, so that a tile's keys fit the static shared memory).
-template <typename K, int ITEMS, bool FIRST, bool LAST>
-__global__ void __launch_bounds__(kSortThreads)
+// Sum of the tile aggregates before `tile` for digit d, down to the nearest
+// inclusive prefix (decoupled look-back).  kLookbackBatch predecessors are
+// read at once; the first one not yet published is waited for (bounded).
+__device__ __forceinline__ bool bh_lookback(const unsigned long long* lookback, int tile, int d, unsigned int epoch,
+                                            const bh_dev_ctrl* c, unsigned int& prefix)
+{
+    prefix = 0u;
+    int j = tile - 1;
+    while (j >= 0) {
+        unsigned long long st[kLookbackBatch];
+#pragma unroll
+        for (int u = 0; u < kLookbackBatch; u++)
+            st[u] = j - u >= 0 ? *((const volatile unsigned long long*)lookback + (size_t)(j - u) * 256 + d) : 0ull;
+        int used = 0;
+        bool stop = false;
+#pragma unroll
+        for (int u = 0; u < kLookbackBatch; u++) {
+            if (stop || j - u < 0 || !bh_lookback_ready(st[u], epoch)) {
+                stop = true;
+                continue;
+            }
+            prefix += (unsigned int)(st[u] & 0x3fffffffull);
+            used = u + 1;
+            if (((st[u] >> 30) & 3ull) == kFlagPrefix) return true;
+        }
+        j -= used;
+        if (j < 0) return true;
+        if (used < kLookbackBatch) {  // word j is not published yet
+            unsigned long long w;
+            if (!bh_lookback_wait((const volatile unsigned long long*)lookback + (size_t)j * 256 + d, epoch, c, w))
+                return false;
+            prefix += (unsigned int)(w & 0x3fffffffull);
+            if (((w >> 30) & 3ull) == kFlagPrefix) return true;
+            j--;
+        }
+    }
+    return true;
+}
+
+// One onesweep pass over a tile of TILE keys (4096 30-bit keys, or 2048
+// 63-bit keys so that the tile fits the static shared memory) by THREADS
+// threads, ITEMS = TILE / THREADS keys per thread.
+template <typename K, int TILE, int THREADS, bool FIRST, bool LAST>
+__global__ void __launch_bounds__(THREADS)
 bh_onesweep_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin, K* __restrict__ kout,
                    uint32_t* __restrict__ vout, const float4* __restrict__ pos, float4* __restrict__ pos_s, int n,
                    int shift, int pass, unsigned long long* lookback, bh_dev_ctrl* c)
 {
     const unsigned int epoch = c->build_seq * 8u + (unsigned int)pass + 1u;
-    constexpr int W = kSortThreads / 32;
-    constexpr int TILE = kSortThreads * ITEMS;
+    constexpr int W = THREADS / 32;
+    constexpr int ITEMS = TILE / THREADS;
+    static_assert(ITEMS * THREADS == TILE && THREADS >= 256, "tile shape");
     __shared__ K s_keys[TILE];
     __shared__ uint32_t s_vals[TILE];
-    __shared__ unsigned int s_whist[W][256];
+    __shared__ unsigned short s_whist[W][256];  // per warp and digit: counts, then offsets (< TILE)
     __shared__ unsigned int s_start[256];  // tile-local start of each digit
     __shared__ int s_base[256];            // global position of a digit's first tile-local slot
-    __shared__ unsigned int s_wtot[W];
+    __shared__ unsigned int s_wtot[8];
     __shared__ int s_tile;
 
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     if (tid == 0) s_tile = (int)atomicAdd(&c->tile_ctr[pass], 1u);
-    for (int i = tid; i < W * 256; i += kSortThreads) (&s_whist[0][0])[i] = 0u;
+    for (int i = tid; i < W * 256; i += THREADS) (&s_whist[0][0])[i] = 0;
     __syncthreads();
     const int tile = s_tile;
     const int base = tile * TILE;
@@ -224,18 +272,24 @@ bh_onesweep_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin, 
         key[k] = ok ? kin[p] : ~(K)0;
         val[k] = FIRST ? (uint32_t)p : (ok ? vin[p] : 0u);
     }
-    // stable rank within the warp, item by item
+    // peers of every item first (independent), then the stable rank within
+    // the warp, item by item: earlier items, then lower lanes of this item
     const unsigned int lt = bh_lanemask_lt();
 #pragma unroll
     for (int k = 0; k < ITEMS; k++) {
-        const int p = base + w * (32 * ITEMS) + k * 32 + lane;
-        const bool ok = p < n;
+        const bool ok = base + w * (32 * ITEMS) + k * 32 + lane < n;
         const unsigned int d = ok ? ((unsigned int)(key[k] >> shift) & 255u) : 256u;
-        const unsigned int peers = __match_any_sync(BH_FULL_MASK, d);
+        rank[k] = __match_any_sync(BH_FULL_MASK, d);
+    }
+#pragma unroll
+    for (int k = 0; k < ITEMS; k++) {
+        const bool ok = base + w * (32 * ITEMS) + k * 32 + lane < n;
+        const unsigned int d = (unsigned int)(key[k] >> shift) & 255u;
+        const unsigned int peers = rank[k];
         unsigned int prior = 0u;
         if (ok) prior = s_whist[w][d];
         __syncwarp();
-        if (ok && lane == __ffs(peers) - 1) s_whist[w][d] = prior + __popc(peers);
+        if (ok && lane == __ffs(peers) - 1) s_whist[w][d] = (unsigned short)(prior + __popc(peers));
         __syncwarp();
         rank[k] = prior + __popc(peers & lt);
     }
@@ -243,43 +297,31 @@ bh_onesweep_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin, 
 
     // per digit (thread = digit): exclusive over warps, tile count
     const int d = tid;
-    unsigned int run = 0u;
+    unsigned int tile_cnt = 0u;
+    if (d < 256) {
 #pragma unroll
-    for (int i = 0; i < W; i++) {
-        const unsigned int t = s_whist[i][d];
-        s_whist[i][d] = run;
-        run += t;
-    }
-    const unsigned int tile_cnt = run;
-    unsigned long long* my = lookback + (size_t)tile * 256 + d;
-    if (tile == 0) {
-        *(volatile unsigned long long*)my = bh_status_word(epoch, kFlagPrefix, tile_cnt);
-    } else {
-        *(volatile unsigned long long*)my = bh_status_word(epoch, kFlagAgg, tile_cnt);
+        for (int i = 0; i < W; i++) {
+            const unsigned int t = s_whist[i][d];
+            s_whist[i][d] = (unsigned short)tile_cnt;
+            tile_cnt += t;
+        }
+        unsigned long long* my = lookback + (size_t)tile * 256 + d;
+        *(volatile unsigned long long*)my = bh_status_word(epoch, tile == 0 ? kFlagPrefix : kFlagAgg, tile_cnt);
     }
     const unsigned int tstart = bh_block_excl_scan256(tile_cnt, s_wtot);
-    const unsigned int goff = bh_block_excl_scan256(c->hist[pass][d], s_wtot);
+    const unsigned int goff = bh_block_excl_scan256(d < 256 ? c->hist[pass][d] : 0u, s_wtot);
 
     // decoupled look-back over earlier tiles (bounded waits)
-    unsigned int prefix = 0u;
-    if (tile > 0) {
-        int j = tile - 1;
-        bool timed_out = false;
-        while (j >= 0) {
-            unsigned long long st;
-            if (!bh_lookback_wait(lookback + (size_t)j * 256 + d, epoch, c, st)) {
-                timed_out = true;
-                break;
-            }
-            prefix += (unsigned int)(st & 0x3fffffffull);
-            if (((st >> 30) & 3ull) == kFlagPrefix) break;
-            j--;
+    if (d < 256) {
+        unsigned int prefix = 0u;
+        if (tile > 0) {
+            if (!bh_lookback(lookback, tile, d, epoch, c, prefix)) bh_set_error(c, BH_ERR_DEVICE_TIMEOUT);
+            *(volatile unsigned long long*)(lookback + (size_t)tile * 256 + d) =
+                bh_status_word(epoch, kFlagPrefix, prefix + tile_cnt);
         }
-        if (timed_out) bh_set_error(c, BH_ERR_DEVICE_TIMEOUT);
-        *(volatile unsigned long long*)my = bh_status_word(epoch, kFlagPrefix, prefix + tile_cnt);
+        s_start[d] = tstart;
+        s_base[d] = (int)(goff + prefix) - (int)tstart;
     }
-    s_start[d] = tstart;
-    s_base[d] = (int)(goff + prefix) - (int)tstart;
     __syncthreads();
 
     // scatter into shared memory in sorted order
@@ -294,43 +336,60 @@ bh_onesweep_kernel(const K* __restrict__ kin, const uint32_t* __restrict__ vin, 
         }
     }
     __syncthreads();
-    // write out: runs of equal digits go to consecutive global positions
-    for (int i = tid; i < tile_n; i += kSortThreads) {
-        const K kk = s_keys[i];
-        const uint32_t vv = s_vals[i];
-        const int dest = s_base[(unsigned int)(kk >> shift) & 255u] + i;
-        if (dest >= 0 && dest < n) {
-            kout[dest] = kk;
-            vout[dest] = vv;
-            if (LAST) pos_s[dest] = pos[vv < (uint32_t)n ? vv : 0u];
+    // write out: runs of equal digits go to consecutive global positions;
+    // every load of a thread (the particle gathers of the last pass among
+    // them) is issued before its first store
+    int dst[ITEMS];
+#pragma unroll
+    for (int k = 0; k < ITEMS; k++) {
+        const int i = tid + k * THREADS;
+        dst[k] = -1;
+        if (i < tile_n) {
+            key[k] = s_keys[i];
+            val[k] = s_vals[i];
+            const int dd = s_base[(unsigned int)(key[k] >> shift) & 255u] + i;
+            if (dd >= 0 && dd < n) dst[k] = dd;
         }
     }
+    if (LAST) {
+        float4 pv[ITEMS];
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++)
+            if (dst[k] >= 0) pv[k] = pos[val[k] < (uint32_t)n ? val[k] : 0u];
+#pragma unroll
+        for (int k = 0; k < ITEMS; k++)
+            if (dst[k] >= 0) pos_s[dst[k]] = pv[k];
+    }
+#pragma unroll
+    for (int k = 0; k < ITEMS; k++)
+        if (dst[k] >= 0) {
+            kout[dst[k]] = key[k];
+            vout[dst[k]] = val[k];
+        }
 }
 
 // Passes of 8 bits from the lowest (4 for 30-bit keys, 8 for 63-bit keys;
 // an even count, so keys/vals end where they started); the last pass also
 // gathers the particles.  vals[k] = caller index of the k-th particle in key order.
-template <typename K, int ITEMS>
+// THREADS0: block size of pass 0 (keys only: fewer registers per key).
+template <typename K, int TILE, int THREADS0, int THREADS>
 static void bh_sort_passes(K* keys, K* keys_alt, uint32_t* vals, uint32_t* vals_alt, const float4* pos,
                            float4* pos_s, int n, unsigned long long* lookback, bh_dev_ctrl* ctrl, cudaStream_t s)
 {
     constexpr int NP = bh_key_traits<K>::kPasses;
-    const int tiles = (n + kSortThreads * ITEMS - 1) / (kSortThreads * ITEMS);
+    const int tiles = (n + TILE - 1) / TILE;
     K *ka = keys, *kb = keys_alt;
     uint32_t *va = vals, *vb = vals_alt;
     for (int p = 0; p < NP; p++) {
         if (p == 0)
-            bh_onesweep_kernel<K, ITEMS, true, false><<<tiles, kSortThreads, 0, s>>>(ka, nullptr, kb, vb, pos, pos_s,
-                                                                                     n, 0, 0, lookback,
-                                                                                     ctrl);
+            bh_onesweep_kernel<K, TILE, THREADS0, true, false>
+                <<<tiles, THREADS0, 0, s>>>(ka, nullptr, kb, vb, pos, pos_s, n, 0, 0, lookback, ctrl);
         else if (p == NP - 1)
-            bh_onesweep_kernel<K, ITEMS, false, true><<<tiles, kSortThreads, 0, s>>>(ka, va, kb, vb, pos, pos_s, n,
-                                                                                     8 * p, p, lookback,
-                                                                                     ctrl);
+            bh_onesweep_kernel<K, TILE, THREADS, false, true>
+                <<<tiles, THREADS, 0, s>>>(ka, va, kb, vb, pos, pos_s, n, 8 * p, p, lookback, ctrl);
         else
-            bh_onesweep_kernel<K, ITEMS, false, false><<<tiles, kSortThreads, 0, s>>>(ka, va, kb, vb, pos, pos_s, n,
-                                                                                      8 * p, p, lookback,
-                                                                                      ctrl);
+            bh_onesweep_kernel<K, TILE, THREADS, false, false>
+                <<<tiles, THREADS, 0, s>>>(ka, va, kb, vb, pos, pos_s, n, 8 * p, p, lookback, ctrl);
         K* tk = ka; ka = kb; kb = tk;
         uint32_t* tv = va; va = vb; vb = tv;
     }
@@ -341,11 +400,11 @@ void launch_sort(void* keys, void* keys_alt, uint32_t* vals, uint32_t* vals_alt,
 {
     if (n <= 0) return;
     if (deep)
-        bh_sort_passes<bh_key64, kSortItems / 2>((bh_key64*)keys, (bh_key64*)keys_alt, vals, vals_alt, pos, pos_s,
-                                                 n, lookback, ctrl, s);
+        bh_sort_passes<bh_key64, kSortTileDeep, kSortThreadsDeep, kSortThreadsDeep>(
+            (bh_key64*)keys, (bh_key64*)keys_alt, vals, vals_alt, pos, pos_s, n, lookback, ctrl, s);
     else
-        bh_sort_passes<uint32_t, kSortItems>((uint32_t*)keys, (uint32_t*)keys_alt, vals, vals_alt, pos, pos_s, n,
-                                             lookback, ctrl, s);
+        bh_sort_passes<uint32_t, kSortTile, kSortThreadsFirst, kSortThreads>(
+            (uint32_t*)keys, (uint32_t*)keys_alt, vals, vals_alt, pos, pos_s, n, lookback, ctrl, s);
 }
 
 // Self-test of the failure path: one look-back wait on a word that no block

@@ -65,14 +65,42 @@ bh_levels_kernel(const K* __restrict__ keys, const uint32_t* __restrict__ sys, i
     unsigned int cnt[L + 1];
 #pragma unroll
     for (int l = 0; l <= L; l++) cnt[l] = 0u;
+    // W_k = max of w_j over j in [k - n_leaf, k], i.e. sw[k - base .. k - base + n_leaf]
+    // (entries for j < 0 hold -1).  A thread's positions k0 + r (r < kLvlPer)
+    // share the core sw[t0 + kLvlPer - 1 .. t0 + n_leaf] when n_leaf >= kLvlPer - 1;
+    // the rest of window r is a suffix of sw[t0 .. t0 + kLvlPer - 2] and a
+    // prefix of sw[t0 + n_leaf + 1 ..] (the same maxima, fewer loads).
+    const int t0 = tid * kLvlPer;
+    int Wr[kLvlPer];
+    if (n_leaf >= kLvlPer - 1) {
+        int core = -1;
+        for (int i = t0 + kLvlPer - 1; i <= t0 + n_leaf; i++) core = max(core, (int)sw[i]);
+        int suf = -1;
+#pragma unroll
+        for (int r = kLvlPer - 1; r >= 0; r--) {
+            if (r < kLvlPer - 1) suf = max(suf, (int)sw[t0 + r]);
+            Wr[r] = max(core, suf);
+        }
+        int pre = -1;
+#pragma unroll
+        for (int r = 1; r < kLvlPer; r++) {
+            pre = max(pre, (int)sw[t0 + n_leaf + r]);
+            Wr[r] = max(Wr[r], pre);
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < kLvlPer; r++) {
+            int W = -1;
+            for (int i = t0 + r; i <= t0 + r + n_leaf; i++) W = max(W, (int)sw[i]);
+            Wr[r] = W;
+        }
+    }
+#pragma unroll
     for (int r = 0; r < kLvlPer; r++) {
-        const int k = base + tid * kLvlPer + r;
+        const int k = base + t0 + r;
         if (k >= n) break;
         const int d = (k == 0 || ss[k - 1 - lo] != ss[k - lo]) ? -1 : bh_common_level(sk[k - 1 - lo], sk[k - lo]);
-        int W = -1;
-        const int j0 = max(0, k - n_leaf);
-        for (int j = j0; j <= k; j++) W = max(W, (int)sw[j - (base - n_leaf)]);
-        const int lam = min(L, W + 1);
+        const int lam = min(L, Wr[r] + 1);
         dl[k] = (uint16_t)((d + 1) | (lam << 5));
 #pragma unroll
         for (int l = 0; l <= L; l++) cnt[l] += (l > d && l <= lam) ? 1u : 0u;
