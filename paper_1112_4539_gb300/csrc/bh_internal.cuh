@@ -47,7 +47,8 @@ struct bh_dev_ctrl {
     unsigned long long cum_pc;
     unsigned int build_seq;      // builds since the block was zeroed (never reset): the sort
                                  // passes of build b use look-back epochs 8 b + 1 .. 8 b + 8
-    unsigned int pad[7];
+    unsigned int scan_done;      // level-scan blocks finished (the last one writes the offsets)
+    unsigned int pad[6];
 };
 
 // Record a device-side error (first one wins) and raise the abort flag.

@@ -23,6 +23,7 @@ __global__ void bh_init_kernel(bh_dev_ctrl* c)
     }
     for (int i = t; i < 8 * 256; i += blockDim.x) (&c->hist[0][0])[i] = 0u;
     if (t < 8) c->tile_ctr[t] = 0u;
+    if (t == 0) c->scan_done = 0u;
     if (t < BH_LEVEL_SLOTS) {
         c->level_total[t] = 0u;
         c->level_offset[t] = 0u;

@@ -171,32 +171,37 @@ __device__ unsigned int bh_scan_segment(uint32_t* a, int len, unsigned int* wtot
 }
 
 // ------------------------------------------------------------ pass 2
-// nlev = deepest level + 1; level_offset[l] for l >= nlev holds the node count.
+// One block per level (nlev = deepest level + 1 blocks) scans that level's
+// per-block node counts; the block that finishes last turns the level totals
+// into level offsets.  level_offset[l] for l >= nlev holds the node count.
 __global__ void __launch_bounds__(1024) bh_level_scan_kernel(uint32_t* blk_lvl, int nblk, int nlev, bh_dev_ctrl* c,
                                                              long long node_cap)
 {
     __shared__ unsigned int wtot[33];
-    __shared__ unsigned int tot[BH_LEVEL_SLOTS];
-    for (int l = 0; l < nlev; l++) {
-        const unsigned int t = bh_scan_segment(blk_lvl + (size_t)l * nblk, nblk, wtot);
-        if (threadIdx.x == 0) tot[l] = t;
+    __shared__ bool last;
+    const int l = blockIdx.x;
+    const unsigned int t = bh_scan_segment(blk_lvl + (size_t)l * nblk, nblk, wtot);
+    if (threadIdx.x == 0) {
+        c->level_total[l] = t;
+        __threadfence();
+        last = atomicAdd(&c->scan_done, 1u) == (unsigned int)(nlev - 1);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long run = 0ull;
-        for (int l = 0; l < nlev; l++) {
-            c->level_total[l] = tot[l];
-            c->level_offset[l] = (unsigned int)run;
-            run += tot[l];
-        }
-        if ((long long)run > node_cap) {
-            bh_set_error(c, BH_ERR_CAPACITY);
-            run = 0ull;  // later kernels see an empty tree
-            for (int l = 0; l < nlev; l++) c->level_offset[l] = 0u;
-        }
-        for (int l = nlev; l < BH_LEVEL_SLOTS; l++) c->level_offset[l] = (unsigned int)run;
-        c->n_nodes = (unsigned int)run;
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    const volatile unsigned int* tot = c->level_total;
+    unsigned long long run = 0ull;
+    for (int k = 0; k < nlev; k++) {
+        c->level_offset[k] = (unsigned int)run;
+        run += tot[k];
     }
+    if ((long long)run > node_cap) {
+        bh_set_error(c, BH_ERR_CAPACITY);
+        run = 0ull;  // later kernels see an empty tree
+        for (int k = 0; k < nlev; k++) c->level_offset[k] = 0u;
+    }
+    for (int k = nlev; k < BH_LEVEL_SLOTS; k++) c->level_offset[k] = (unsigned int)run;
+    c->n_nodes = (unsigned int)run;
 }
 
 // ------------------------------------------------------------ pass 3
@@ -326,7 +331,7 @@ static void bh_tree_t(const K* keys, int n, int n_leaf, uint16_t* dl, uint32_t* 
     constexpr int L = bh_key_traits<K>::kMaxLevel;
     const int nblk = (n + kLevelTile - 1) / kLevelTile;
     bh_levels_kernel<K><<<nblk, kLvlThreads, 0, s>>>(keys, sys, n, n_leaf, dl, blk_lvl, nblk);
-    bh_level_scan_kernel<<<1, 1024, 0, s>>>(blk_lvl, nblk, L + 1, ctrl, (long long)node_cap);
+    bh_level_scan_kernel<<<L + 1, 1024, 0, s>>>(blk_lvl, nblk, L + 1, ctrl, (long long)node_cap);
     bh_node_write_kernel<L><<<nblk, kLvlThreads, 0, s>>>(dl, n, blk_lvl, nblk, ctrl, nd.first, nd.level, nd.child);
     bh_node_finalize_kernel<K><<<grid, 256, 0, s>>>(keys, sys, sys_off, n, nd, ctrl);
 }
@@ -633,19 +638,24 @@ __device__ __forceinline__ void bh_child_moments(const bh_nodes& nd, int cidx, i
     }
 }
 
+// Two passes over the children (centre of mass, then second moments about
+// it), each re-reading the children's records: no per-thread copy of the
+// children (which lived in local memory and spilled to L2 at full occupancy).
 template <typename R, int ORDER>
 __device__ __forceinline__ void bh_internal_moments(const bh_nodes& nd, int ch, int nch, int fp64_threshold,
                                                     bh_mom<R>& o, bool& massless)
 {
-    bh_mom<R> cm[8];
-    for (int i = 0; i < nch; i++) bh_child_moments<R>(nd, ch + i, fp64_threshold, ORDER, cm[i]);
-    const R x0 = cm[0].cx, y0 = cm[0].cy, z0 = cm[0].cz;
+    bh_mom<R> c0;
+    bh_child_moments<R>(nd, ch, fp64_threshold, 1, c0);
+    const R x0 = c0.cx, y0 = c0.cy, z0 = c0.cz;
     R M = 0, sx = 0, sy = 0, sz = 0;
     for (int i = 0; i < nch; i++) {
-        M += cm[i].M;
-        sx += cm[i].M * (cm[i].cx - x0);
-        sy += cm[i].M * (cm[i].cy - y0);
-        sz += cm[i].M * (cm[i].cz - z0);
+        bh_mom<R> cm;
+        bh_child_moments<R>(nd, ch + i, fp64_threshold, 1, cm);
+        M += cm.M;
+        sx += cm.M * (cm.cx - x0);
+        sy += cm.M * (cm.cy - y0);
+        sz += cm.M * (cm.cz - z0);
     }
     massless = !(M != (R)0);
     o.M = M;
@@ -655,13 +665,15 @@ __device__ __forceinline__ void bh_internal_moments(const bh_nodes& nd, int ch, 
     if (ORDER >= 2) {
         R q[6] = {0, 0, 0, 0, 0, 0};
         for (int i = 0; i < nch; i++) {
-            const R a = cm[i].cx - o.cx, b = cm[i].cy - o.cy, e = cm[i].cz - o.cz, m = cm[i].M;
-            q[0] += cm[i].q[0] + m * a * a;
-            q[1] += cm[i].q[1] + m * b * b;
-            q[2] += cm[i].q[2] + m * e * e;
-            q[3] += cm[i].q[3] + m * a * b;
-            q[4] += cm[i].q[4] + m * a * e;
-            q[5] += cm[i].q[5] + m * b * e;
+            bh_mom<R> cm;
+            bh_child_moments<R>(nd, ch + i, fp64_threshold, 2, cm);
+            const R a = cm.cx - o.cx, b = cm.cy - o.cy, e = cm.cz - o.cz, m = cm.M;
+            q[0] += cm.q[0] + m * a * a;
+            q[1] += cm.q[1] + m * b * b;
+            q[2] += cm.q[2] + m * e * e;
+            q[3] += cm.q[3] + m * a * b;
+            q[4] += cm.q[4] + m * a * e;
+            q[5] += cm.q[5] + m * b * e;
         }
         for (int i = 0; i < 6; i++) o.q[i] = q[i];
     }
