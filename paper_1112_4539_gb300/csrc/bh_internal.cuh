@@ -317,18 +317,12 @@ __host__ __device__ constexpr int bh_wrec_f4(int order) { return order >= 2 ? 5 
 // (bodies in the .cu files; all are stream-ordered and take device pointers)
 namespace bh {
 
-#ifndef BH_SORT_THREADS
-#define BH_SORT_THREADS 512
-#endif
-#ifndef BH_LOOKBACK_BATCH
-#define BH_LOOKBACK_BATCH 4
-#endif
-constexpr int kSortThreads = BH_SORT_THREADS;          // threads of an onesweep block (30-bit keys)
-constexpr int kSortThreadsFirst = 256;                 // threads of pass 0 (30-bit keys)
-constexpr int kSortThreadsDeep = 256;                  // threads of an onesweep block (63-bit keys)
-constexpr int kLookbackBatch = BH_LOOKBACK_BATCH;      // predecessors read per look-back step
-constexpr int kSortTile = 4096;                        // keys per tile (30-bit keys)
-constexpr int kSortTileDeep = 2048;                    // keys per tile (63-bit keys)
+constexpr int kSortThreads = 512;       // threads of an onesweep block, passes 1-3 (30-bit keys)
+constexpr int kSortThreadsFirst = 256;  // threads of pass 0 (30-bit keys: 16 keys per thread)
+constexpr int kSortThreadsDeep = 256;   // threads of an onesweep block (63-bit keys)
+constexpr int kLookbackBatch = 4;       // predecessors read per look-back step
+constexpr int kSortTile = 4096;         // keys per tile (30-bit keys)
+constexpr int kSortTileDeep = 2048;     // keys per tile (63-bit keys)
 constexpr int kLevelTile = 2048;                       // positions per node-build block
 constexpr int kFlagTile = 4096;                        // positions per group-compaction block
 
