@@ -483,6 +483,7 @@ __device__ __forceinline__ void bh_leaf_moments(const float4* __restrict__ pos_s
     const float4 p0 = pos_s[k];
     const R x0 = p0.x, y0 = p0.y, z0 = p0.z;
     R M = 0, sx = 0, sy = 0, sz = 0;
+#pragma unroll 4
     for (int j = k; j < k + cnt; j++) {
         const float4 p = pos_s[j];
         const R m = p.w;
@@ -498,6 +499,7 @@ __device__ __forceinline__ void bh_leaf_moments(const float4* __restrict__ pos_s
     o.cz = massless ? z0 : z0 + sz / M;
     if (ORDER >= 2) {
         R q0 = 0, q1 = 0, q2 = 0, q3 = 0, q4 = 0, q5 = 0;
+#pragma unroll 4
         for (int j = k; j < k + cnt; j++) {
             const float4 p = pos_s[j];
             const R m = p.w;
@@ -765,8 +767,10 @@ __device__ __forceinline__ void bh_moment_node(const float4* __restrict__ pos_s,
     }
 }
 
+// 4 blocks per SM (at most 64 registers): the level passes are bound by the
+// latency of their loads, so more resident warps beat the few spilled words.
 template <int ORDER, typename K>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 bh_moments_level_kernel(const float4* __restrict__ pos_s, const K* __restrict__ keys, bh_nodes nd, int lev,
                         float theta, int fp64_threshold, int curve, const bh_dev_ctrl* __restrict__ c,
                         const uint32_t* __restrict__ sys, const float4* __restrict__ sys_box)
