@@ -56,21 +56,42 @@ __global__ void __launch_bounds__(256) bh_bbox_kernel(const float4* __restrict__
         lo0 = min(lo0, ox); lo1 = min(lo1, oy); lo2 = min(lo2, oz);
         hi0 = max(hi0, ox); hi1 = max(hi1, oy); hi2 = max(hi2, oz);
     }
+    // warp, then block reduction: one set of atomics per block (the six
+    // words are shared by every block, so per-warp atomics contended in L2)
+    __shared__ unsigned int red[8][7];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     lo0 = __reduce_min_sync(BH_FULL_MASK, lo0);
     lo1 = __reduce_min_sync(BH_FULL_MASK, lo1);
     lo2 = __reduce_min_sync(BH_FULL_MASK, lo2);
     hi0 = __reduce_max_sync(BH_FULL_MASK, hi0);
     hi1 = __reduce_max_sync(BH_FULL_MASK, hi1);
     hi2 = __reduce_max_sync(BH_FULL_MASK, hi2);
-    const bool anybad = __any_sync(BH_FULL_MASK, bad);
-    if ((threadIdx.x & 31) == 0) {
-        atomicMin(&c->minmax[0], lo0);
-        atomicMin(&c->minmax[1], lo1);
-        atomicMin(&c->minmax[2], lo2);
-        atomicMax(&c->minmax[3], hi0);
-        atomicMax(&c->minmax[4], hi1);
-        atomicMax(&c->minmax[5], hi2);
-        if (anybad) atomicCAS(&c->status, 0u, (unsigned int)(-BH_ERR_NONFINITE));
+    const unsigned int anybad = __any_sync(BH_FULL_MASK, bad) ? 1u : 0u;
+    if (lane == 0) {
+        red[w][0] = lo0; red[w][1] = lo1; red[w][2] = lo2;
+        red[w][3] = hi0; red[w][4] = hi1; red[w][5] = hi2;
+        red[w][6] = anybad;
+    }
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        const bool ok = lane < nw;
+        lo0 = __reduce_min_sync(BH_FULL_MASK, ok ? red[lane][0] : 0xffffffffu);
+        lo1 = __reduce_min_sync(BH_FULL_MASK, ok ? red[lane][1] : 0xffffffffu);
+        lo2 = __reduce_min_sync(BH_FULL_MASK, ok ? red[lane][2] : 0xffffffffu);
+        hi0 = __reduce_max_sync(BH_FULL_MASK, ok ? red[lane][3] : 0u);
+        hi1 = __reduce_max_sync(BH_FULL_MASK, ok ? red[lane][4] : 0u);
+        hi2 = __reduce_max_sync(BH_FULL_MASK, ok ? red[lane][5] : 0u);
+        const unsigned int nb = __reduce_or_sync(BH_FULL_MASK, ok ? red[lane][6] : 0u);
+        if (lane == 0) {
+            atomicMin(&c->minmax[0], lo0);
+            atomicMin(&c->minmax[1], lo1);
+            atomicMin(&c->minmax[2], lo2);
+            atomicMax(&c->minmax[3], hi0);
+            atomicMax(&c->minmax[4], hi1);
+            atomicMax(&c->minmax[5], hi2);
+            if (nb) atomicCAS(&c->status, 0u, (unsigned int)(-BH_ERR_NONFINITE));
+        }
     }
 }
 
