@@ -297,6 +297,26 @@ def test_coincident_and_clustered(bh, orc):
     ctx.close()
 
 
+@pytest.mark.parametrize("order,G", [(1, 64), (2, 96)])
+def test_group_walk_without_softening(bh, orc, order, G):
+    # eps = 0: each target is among its own group's sources, and the self tile
+    # must mask it (a 0/0 otherwise); ragged groups, split slots, odd source counts
+    pos = workloads.plummer(6007, seed=21)
+    ctx, got, rc = _run(bh, pos, 0.5, 0.0, leaf_size=16, group_size=G, order=order)
+    assert rc == 0 and np.isfinite(got).all()
+    ref, b = orc.tree_force(pos, 0.5, 0.0, n_leaf=16, G=G, order=order, walk="group")
+    _check_force(got, ref["out"], ref["margin"], a_abs=ref["a_abs"], case="plummer 6007 eps=0 order %d" % order)
+    ctx.close()
+    # one group of 1, 2 and 3 particles: the closed form of Eq. 1
+    ctx = bh.Context(8, leaf_size=8, group_size=G, order=order)
+    for n in (1, 2, 3):
+        pos = workloads.plummer(8, seed=3)[:n].copy()
+        got = ctx.evaluate(_cuda(pos), 0.5, 0.0).cpu().numpy()
+        assert ctx.status() == 0 and np.isfinite(got).all()
+        np.testing.assert_allclose(got, orc.direct(pos, eps=0.0), rtol=1e-5, atol=0)
+    ctx.close()
+
+
 def test_errors(bh):
     import torch
     ctx = bh.Context(1000, device=0)
