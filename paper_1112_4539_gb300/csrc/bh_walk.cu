@@ -252,16 +252,20 @@ struct Tgt {
 // the pair loop unrolled PU times.
 template <int T, int NF, int PU>
 __device__ __forceinline__ void bh_eval_points(const float4* __restrict__ ra, const float4* __restrict__ rb,
-                                               f2 eps2, const Tgt<T>& X, Acc<T>& A)
+                                               f2 eps2, const Tgt<T>& X, Acc<T>& A, int np)
 {
     Part<T> P;
 #pragma unroll
     for (int t = 0; t < NF; t++) P.x[t] = P.y[t] = P.z[t] = P.p[t] = make_float2(0.f, 0.f);
-#pragma unroll PU
-    for (int j = 0; j < 16; j++) {
-        const float4 sa = ra[j], sb = rb[j];
+#pragma unroll 1
+    for (int j0 = 0; j0 < np; j0 += PU) {
 #pragma unroll
-        for (int t = 0; t < NF; t++) bh_pp2(sa, sb, eps2, X.x[t], X.y[t], X.z[t], P.x[t], P.y[t], P.z[t], P.p[t]);
+        for (int j = j0; j < j0 + PU; j++) {
+            const float4 sa = ra[j], sb = rb[j];
+#pragma unroll
+            for (int t = 0; t < NF; t++)
+                bh_pp2(sa, sb, eps2, X.x[t], X.y[t], X.z[t], P.x[t], P.y[t], P.z[t], P.p[t]);
+        }
     }
     bh_add_tile<T, NF>(A, P, false);
 }
@@ -269,13 +273,13 @@ __device__ __forceinline__ void bh_eval_points(const float4* __restrict__ ra, co
 // One tile (16 pairs) of quadrupole cells on the first NF slots of every lane.
 // QC: any staging with the six pair arrays a..f of WarpQuad (pairs p0..p0+15).
 template <int T, int NF, class QC>
-__device__ __forceinline__ void bh_eval_quads(const QC& Q, int p0, f2 eps2, const Tgt<T>& X, Acc<T>& A)
+__device__ __forceinline__ void bh_eval_quads(const QC& Q, int p0, f2 eps2, const Tgt<T>& X, Acc<T>& A, int np)
 {
     Part<T> P;
 #pragma unroll
     for (int t = 0; t < NF; t++) P.x[t] = P.y[t] = P.z[t] = P.p[t] = P.q[t] = make_float2(0.f, 0.f);
 #pragma unroll kQuadUnroll
-    for (int j = p0; j < p0 + 16; j++) {
+    for (int j = p0; j < p0 + np; j++) {
         const float4 ca = Q.a[j], cb = Q.b[j], cc = Q.c[j], cd = Q.d[j], ce = Q.e[j], cf = Q.f[j];
 #pragma unroll
         for (int t = 0; t < NF; t++)
@@ -337,25 +341,30 @@ __device__ __forceinline__ void bh_split_quads(const Layout& L, const QC& Q, int
 // from one call site only (they are inlined: a second site would double the
 // code of the hottest loop).
 template <int T, int PU = kPointUnroll>
+// A point tile; np: pairs evaluated on the full slots (16, or fewer for a
+// group's last, partly padded tile: the padding pairs add exact zeros), a
+// multiple of PU.  The split slot always takes the whole tile.
 __device__ __forceinline__ void bh_points(const Layout& L, const float4* __restrict__ ra,
-                                          const float4* __restrict__ rb, f2 eps2, const Tgt<T>& X, Acc<T>& A)
+                                          const float4* __restrict__ rb, f2 eps2, const Tgt<T>& X, Acc<T>& A,
+                                          int np = 16)
 {
-    if (T > 1 && L.nf == 1) bh_eval_points<T, 1, PU>(ra, rb, eps2, X, A);
-    else if (T > 2 && L.nf == 2) bh_eval_points<T, (T > 2 ? 2 : T), PU>(ra, rb, eps2, X, A);
-    else if (T > 3 && L.nf == 3) bh_eval_points<T, (T > 3 ? 3 : T), PU>(ra, rb, eps2, X, A);
-    else if (T > 4 && L.nf == 4) bh_eval_points<T, (T > 4 ? 4 : T), PU>(ra, rb, eps2, X, A);
-    else if (L.nf > 0) bh_eval_points<T, T, PU>(ra, rb, eps2, X, A);
+    if (T > 1 && L.nf == 1) bh_eval_points<T, 1, PU>(ra, rb, eps2, X, A, np);
+    else if (T > 2 && L.nf == 2) bh_eval_points<T, (T > 2 ? 2 : T), PU>(ra, rb, eps2, X, A, np);
+    else if (T > 3 && L.nf == 3) bh_eval_points<T, (T > 3 ? 3 : T), PU>(ra, rb, eps2, X, A, np);
+    else if (T > 4 && L.nf == 4) bh_eval_points<T, (T > 4 ? 4 : T), PU>(ra, rb, eps2, X, A, np);
+    else if (L.nf > 0) bh_eval_points<T, T, PU>(ra, rb, eps2, X, A, np);
     if (L.split) bh_split_points<T>(L, ra, rb, eps2, X, A);
 }
 template <int T, class QC>
+// A quadrupole tile (pairs p0 ..); np as for bh_points (any count).
 __device__ __forceinline__ void bh_quads(const Layout& L, const QC& Q, int p0, f2 eps2, const Tgt<T>& X,
-                                         Acc<T>& A)
+                                         Acc<T>& A, int np = 16)
 {
-    if (T > 1 && L.nf == 1) bh_eval_quads<T, 1, QC>(Q, p0, eps2, X, A);
-    else if (T > 2 && L.nf == 2) bh_eval_quads<T, (T > 2 ? 2 : T), QC>(Q, p0, eps2, X, A);
-    else if (T > 3 && L.nf == 3) bh_eval_quads<T, (T > 3 ? 3 : T), QC>(Q, p0, eps2, X, A);
-    else if (T > 4 && L.nf == 4) bh_eval_quads<T, (T > 4 ? 4 : T), QC>(Q, p0, eps2, X, A);
-    else if (L.nf > 0) bh_eval_quads<T, T, QC>(Q, p0, eps2, X, A);
+    if (T > 1 && L.nf == 1) bh_eval_quads<T, 1, QC>(Q, p0, eps2, X, A, np);
+    else if (T > 2 && L.nf == 2) bh_eval_quads<T, (T > 2 ? 2 : T), QC>(Q, p0, eps2, X, A, np);
+    else if (T > 3 && L.nf == 3) bh_eval_quads<T, (T > 3 ? 3 : T), QC>(Q, p0, eps2, X, A, np);
+    else if (T > 4 && L.nf == 4) bh_eval_quads<T, (T > 4 ? 4 : T), QC>(Q, p0, eps2, X, A, np);
+    else if (L.nf > 0) bh_eval_quads<T, T, QC>(Q, p0, eps2, X, A, np);
     if (L.split) bh_split_quads<T, QC>(L, Q, p0, eps2, X, A);
 }
 
@@ -697,13 +706,14 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
                 bh_put_quad(*Q, q_head + lane, bh_pad_source(), make_float4(0.f, 0.f, 0.f, 0.f),
                             make_float4(0.f, 0.f, 0.f, 0.f), eps2);
             __syncwarp();
-            bh_quads<T, WarpQuad>(L, *Q, q_head >> 1, eps2v, X, A);
+            bh_quads<T, WarpQuad>(L, *Q, q_head >> 1, eps2v, X, A, (q_cnt + 1) >> 1);
         }
         if (ring_cnt > 0) {
             if (lane >= ring_cnt) bh_put_point(S, ring_head + lane, bh_pad_source());
             __syncwarp();
-            bh_points<T, LEARNED ? kPointUnrollLearned : kPointUnroll>(L, S.ra + (ring_head >> 1), S.rb + (ring_head >> 1),
-                                                                        eps2v, X, A);
+            constexpr int PU = LEARNED ? kPointUnrollLearned : kPointUnroll;
+            bh_points<T, PU>(L, S.ra + (ring_head >> 1), S.rb + (ring_head >> 1), eps2v, X, A,
+                             (((ring_cnt + 1) >> 1) + PU - 1) / PU * PU);
         }
         __syncwarp();
         // ---- write (ax, ay, az, phi) in the caller's order; a split slot first
@@ -1543,12 +1553,13 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, false>()) bh_walk_t
                 bh_put_quad(*Q, q_head + lane, bh_pad_source(), make_float4(0.f, 0.f, 0.f, 0.f),
                             make_float4(0.f, 0.f, 0.f, 0.f), eps2);
             __syncwarp();
-            bh_quads<T, WarpQuad>(L, *Q, q_head >> 1, eps2v, X, A);
+            bh_quads<T, WarpQuad>(L, *Q, q_head >> 1, eps2v, X, A, (q_cnt + 1) >> 1);
         }
         if (ring_cnt > 0) {
             if (lane >= ring_cnt) bh_put_point(S, ring_head + lane, bh_pad_source());
             __syncwarp();
-            bh_points<T, kPointUnroll>(L, S.ra + (ring_head >> 1), S.rb + (ring_head >> 1), eps2v, X, A);
+            bh_points<T, kPointUnroll>(L, S.ra + (ring_head >> 1), S.rb + (ring_head >> 1), eps2v, X, A,
+                                       (((ring_cnt + 1) >> 1) + kPointUnroll - 1) / kPointUnroll * kPointUnroll);
         }
         __syncwarp();
 #pragma unroll
