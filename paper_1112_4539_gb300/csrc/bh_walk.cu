@@ -11,10 +11,11 @@
 // group member; accepted nodes become particle-cell sources, rejected leaves
 // contribute their particles as particle-particle sources, other rejected
 // nodes are opened.
-// Sources go through a 64-entry ring in shared memory and are evaluated in
-// tiles of 32: every lane applies each source to its T targets in FP32 with
+// Sources go through a 128-entry ring in shared memory and are evaluated in
+// tiles of 64: every lane applies each source to its T targets in FP32 with
 // rsqrtf, two sources per packed f32x2 instruction; each tile's partial sums
-// are added to the running totals with Kahan compensation.  A target slot
+// (plain FP32 sums of 32 terms per pair half) are added to the running totals
+// with Kahan compensation.  A target slot
 // holding few targets is split across source phases (see Layout).  The
 // group's own particles are applied once, as a masked "self" tile, so the
 // target itself is excluded by index.
@@ -31,7 +32,9 @@
 namespace bh {
 
 constexpr int kStackCap = 704;
-constexpr int kRing = 64;   // sources per ring (two tiles of 32), stored as 32 even/odd pairs
+constexpr int kTile = 64;              // sources per tile (one Kahan-compensated addition per tile)
+constexpr int kTilePairs = kTile / 2;  // a tile as even/odd source pairs
+constexpr int kRing = 2 * kTile;       // sources per ring (two tiles), stored as even/odd pairs
 // unroll factors of the per-tile pair loops (tuning constants, measured:
 // larger factors overflow the instruction cache, as every T-slot variant of
 // the loops is live at once across the SM's warps)
@@ -144,9 +147,9 @@ __host__ __device__ constexpr size_t bh_kahan_smem_bytes()
 // (warp-uniform).  Slots 0..nf-1 hold targets t*32 + lane.  When the last
 // slot would hold at most kSplitMax targets (k = gc - 32*nf) it is "split":
 // lane l holds target nf*32 + (l mod m), m = 2^lg >= k, and evaluates only
-// the m sources of each tile in its phase (l / m); the phases' partial sums
+// the 2m sources of each tile in its phase (l / m); the phases' partial sums
 // are added across lanes once, when the group ends.  A slot with 4 targets
-// then costs 4 evaluations per tile instead of 32.
+// then costs 8 evaluations per tile instead of 64.
 #ifndef BH_SPLIT_MAX
 #define BH_SPLIT_MAX 16
 #endif
@@ -248,7 +251,7 @@ struct Tgt {
     f2 x[T], y[T], z[T];
 };
 
-// One tile (16 pairs) of point sources on the first NF slots of every lane,
+// One tile (np <= kTilePairs pairs) of point sources on the first NF slots of every lane,
 // the pair loop unrolled PU times.
 template <int T, int NF, int PU>
 __device__ __forceinline__ void bh_eval_points(const float4* __restrict__ ra, const float4* __restrict__ rb,
@@ -270,7 +273,7 @@ __device__ __forceinline__ void bh_eval_points(const float4* __restrict__ ra, co
     bh_add_tile<T, NF>(A, P, false);
 }
 
-// One tile (16 pairs) of quadrupole cells on the first NF slots of every lane.
+// One tile (np <= kTilePairs pairs) of quadrupole cells on the first NF slots of every lane.
 // QC: any staging with the six pair arrays a..f of WarpQuad (pairs p0..p0+15).
 template <int T, int NF, class QC>
 __device__ __forceinline__ void bh_eval_quads(const QC& Q, int p0, f2 eps2, const Tgt<T>& X, Acc<T>& A, int np)
@@ -298,10 +301,10 @@ __device__ __forceinline__ void bh_split_target(const Layout& L, const Tgt<T>& X
     for (int t = 1; t < T; t++)
         if (t == L.nf) { x = X.x[t]; y = X.y[t]; z = X.z[t]; }
 }
-__device__ __forceinline__ float bh_split_sum(const Layout& L, f2 v)
-{
-    return L.lg ? v.x + v.y : ((threadIdx.x & 1) ? v.y : v.x);
-}
+// With kTilePairs = 32 pairs per tile and 32 / m phases, a phase (and each
+// of its lanes) takes m whole pairs: pairs (l / m) * m .. + m - 1.
+static_assert(kTilePairs == 32, "split phases assume 32 pairs per tile");
+__device__ __forceinline__ float bh_split_sum(const Layout&, f2 v) { return v.x + v.y; }
 template <int T>
 __device__ __forceinline__ void bh_split_add(const Layout& L, Acc<T>& A, float ax, float ay, float az, float ap)
 {
@@ -320,7 +323,7 @@ __device__ __forceinline__ void bh_split_points(const Layout& L, const float4* _
 {
     f2 x, y, z, ax = make_float2(0.f, 0.f), ay = ax, az = ax, ap = ax;
     bh_split_target<T>(L, X, x, y, z);
-    const int p = ((threadIdx.x & 31) >> L.lg) << L.lg >> 1, np = L.lg ? 1 << (L.lg - 1) : 1;
+    const int p = ((threadIdx.x & 31) >> L.lg) << L.lg, np = 1 << L.lg;
     for (int i = p; i < p + np; i++) bh_pp2(ra[i], rb[i], eps2, x, y, z, ax, ay, az, ap);
     bh_split_add<T>(L, A, bh_split_sum(L, ax), bh_split_sum(L, ay), bh_split_sum(L, az), bh_split_sum(L, ap));
 }
@@ -330,7 +333,7 @@ __device__ __forceinline__ void bh_split_quads(const Layout& L, const QC& Q, int
 {
     f2 x, y, z, ax = make_float2(0.f, 0.f), ay = ax, az = ax, ap = ax, aq = ax;
     bh_split_target<T>(L, X, x, y, z);
-    const int p = p0 + (((threadIdx.x & 31) >> L.lg) << L.lg >> 1), np = L.lg ? 1 << (L.lg - 1) : 1;
+    const int p = p0 + (((threadIdx.x & 31) >> L.lg) << L.lg), np = 1 << L.lg;
     for (int i = p; i < p + np; i++)
         bh_pq2(Q.a[i], Q.b[i], Q.c[i], Q.d[i], Q.e[i], Q.f[i], eps2, x, y, z, ax, ay, az, ap, aq);
     bh_split_add<T>(L, A, bh_split_sum(L, ax), bh_split_sum(L, ay), bh_split_sum(L, az),
@@ -341,12 +344,12 @@ __device__ __forceinline__ void bh_split_quads(const Layout& L, const QC& Q, int
 // from one call site only (they are inlined: a second site would double the
 // code of the hottest loop).
 template <int T, int PU = kPointUnroll>
-// A point tile; np: pairs evaluated on the full slots (16, or fewer for a
-// group's last, partly padded tile: the padding pairs add exact zeros), a
-// multiple of PU.  The split slot always takes the whole tile.
+// A point tile; np: pairs evaluated on the full slots (kTilePairs, or fewer
+// for a group's last, partly padded tile: the padding pairs add exact zeros),
+// a multiple of PU.  The split slot always takes the whole tile.
 __device__ __forceinline__ void bh_points(const Layout& L, const float4* __restrict__ ra,
                                           const float4* __restrict__ rb, f2 eps2, const Tgt<T>& X, Acc<T>& A,
-                                          int np = 16)
+                                          int np = kTilePairs)
 {
     if (T > 1 && L.nf == 1) bh_eval_points<T, 1, PU>(ra, rb, eps2, X, A, np);
     else if (T > 2 && L.nf == 2) bh_eval_points<T, (T > 2 ? 2 : T), PU>(ra, rb, eps2, X, A, np);
@@ -358,7 +361,7 @@ __device__ __forceinline__ void bh_points(const Layout& L, const float4* __restr
 template <int T, class QC>
 // A quadrupole tile (pairs p0 ..); np as for bh_points (any count).
 __device__ __forceinline__ void bh_quads(const Layout& L, const QC& Q, int p0, f2 eps2, const Tgt<T>& X,
-                                         Acc<T>& A, int np = 16)
+                                         Acc<T>& A, int np = kTilePairs)
 {
     if (T > 1 && L.nf == 1) bh_eval_quads<T, 1, QC>(Q, p0, eps2, X, A, np);
     else if (T > 2 && L.nf == 2) bh_eval_quads<T, (T > 2 ? 2 : T), QC>(Q, p0, eps2, X, A, np);
@@ -653,19 +656,19 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
 
             // ---- drain: quadrupole tiles, point tiles, particle fills
             if (ORDER >= 2) {
-                while (q_cnt >= 32) {
+                while (q_cnt >= kTile) {
                     bh_quads<T, WarpQuad>(L, *Q, q_head >> 1, eps2v, X, A);
-                    q_head ^= 32;
-                    q_cnt -= 32;
+                    q_head ^= kTile;
+                    q_cnt -= kTile;
                 }
             }
             int lq_pos = 0;
             for (;;) {
-                if (ring_cnt >= 32) {
+                if (ring_cnt >= kTile) {
                     bh_points<T, LEARNED ? kPointUnrollLearned : kPointUnroll>(L, S.ra + (ring_head >> 1), S.rb + (ring_head >> 1),
                                                                         eps2v, X, A);
-                    ring_head ^= 32;
-                    ring_cnt -= 32;
+                    ring_head ^= kTile;
+                    ring_cnt -= kTile;
                     continue;
                 }
                 if (lq_pos >= lq_n) break;
@@ -702,14 +705,16 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
         }
         // ---- flush the partial tiles (padded with far, massless sources)
         if (ORDER >= 2 && q_cnt > 0) {
-            if (lane >= q_cnt)
-                bh_put_quad(*Q, q_head + lane, bh_pad_source(), make_float4(0.f, 0.f, 0.f, 0.f),
-                            make_float4(0.f, 0.f, 0.f, 0.f), eps2);
+            for (int i = lane; i < kTile; i += 32)
+                if (i >= q_cnt)
+                    bh_put_quad(*Q, q_head + i, bh_pad_source(), make_float4(0.f, 0.f, 0.f, 0.f),
+                                make_float4(0.f, 0.f, 0.f, 0.f), eps2);
             __syncwarp();
             bh_quads<T, WarpQuad>(L, *Q, q_head >> 1, eps2v, X, A, (q_cnt + 1) >> 1);
         }
         if (ring_cnt > 0) {
-            if (lane >= ring_cnt) bh_put_point(S, ring_head + lane, bh_pad_source());
+            for (int i = lane; i < kTile; i += 32)
+                if (i >= ring_cnt) bh_put_point(S, ring_head + i, bh_pad_source());
             __syncwarp();
             constexpr int PU = LEARNED ? kPointUnrollLearned : kPointUnroll;
             bh_points<T, PU>(L, S.ra + (ring_head >> 1), S.rb + (ring_head >> 1), eps2v, X, A,
@@ -765,8 +770,8 @@ constexpr int kWsSpinLimit = 1 << 22;
 constexpr unsigned long long kWsTimeoutNs = 1000000000ull;
 enum : int { kWsPoints = 0, kWsQuads = 1, kWsBegin = 2, kWsEnd = 3, kWsExit = 4 };
 
-struct WsTile {  // 32 sources as 16 pairs, laid out as WarpSmem (points: a, b) and WarpQuad (cells: a..f)
-    float4 a[16], b[16], c[16], d[16], e[16], f[16];
+struct WsTile {  // kTile sources as pairs, laid out as WarpSmem (points: a, b) and WarpQuad (cells: a..f)
+    float4 a[kTilePairs], b[kTilePairs], c[kTilePairs], d[kTilePairs], e[kTilePairs], f[kTilePairs];
 };
 struct WsChannel {
     WsTile tile[kWsSlots];
@@ -883,7 +888,7 @@ __global__ void __launch_bounds__(256, bh_ws_min_blocks<T>()) bh_walk_ws_kernel(
         bool alive = true;
         auto send_quads = [&](int p0) {
             return bh_ws_send(C, item, kWsQuads, 0, ctrl, [&](WsTile& t) {
-                if (lane < 16) {
+                if (lane < kTilePairs) {
                     t.a[lane] = Q->a[p0 + lane]; t.b[lane] = Q->b[p0 + lane]; t.c[lane] = Q->c[p0 + lane];
                     t.d[lane] = Q->d[p0 + lane]; t.e[lane] = Q->e[p0 + lane]; t.f[lane] = Q->f[p0 + lane];
                 }
@@ -891,7 +896,7 @@ __global__ void __launch_bounds__(256, bh_ws_min_blocks<T>()) bh_walk_ws_kernel(
         };
         auto send_points = [&](int p0) {
             return bh_ws_send(C, item, kWsPoints, 0, ctrl, [&](WsTile& t) {
-                if (lane < 16) {
+                if (lane < kTilePairs) {
                     t.a[lane] = S.ra[p0 + lane];
                     t.b[lane] = S.rb[p0 + lane];
                 }
@@ -1010,20 +1015,20 @@ __global__ void __launch_bounds__(256, bh_ws_min_blocks<T>()) bh_walk_ws_kernel(
                 __syncwarp();
 
                 if (ORDER >= 2) {
-                    while (q_cnt >= 32 && alive) {
+                    while (q_cnt >= kTile && alive) {
                         __syncwarp();
                         alive = send_quads(q_head >> 1);
-                        q_head ^= 32;
-                        q_cnt -= 32;
+                        q_head ^= kTile;
+                        q_cnt -= kTile;
                     }
                 }
                 int lq_pos = 0;
                 while (alive) {
-                    if (ring_cnt >= 32) {
+                    if (ring_cnt >= kTile) {
                         __syncwarp();
                         alive = send_points(ring_head >> 1);
-                        ring_head ^= 32;
-                        ring_cnt -= 32;
+                        ring_head ^= kTile;
+                        ring_cnt -= kTile;
                         continue;
                     }
                     if (lq_pos >= lq_n) break;
@@ -1057,14 +1062,16 @@ __global__ void __launch_bounds__(256, bh_ws_min_blocks<T>()) bh_walk_ws_kernel(
             }
             // flush the partial tiles (padded with far, massless sources), then close the group
             if (ORDER >= 2 && q_cnt > 0) {
-                if (lane >= q_cnt)
-                    bh_put_quad(*Q, q_head + lane, bh_pad_source(), make_float4(0.f, 0.f, 0.f, 0.f),
-                                make_float4(0.f, 0.f, 0.f, 0.f), eps2);
+                for (int i = lane; i < kTile; i += 32)
+                    if (i >= q_cnt)
+                        bh_put_quad(*Q, q_head + i, bh_pad_source(), make_float4(0.f, 0.f, 0.f, 0.f),
+                                    make_float4(0.f, 0.f, 0.f, 0.f), eps2);
                 __syncwarp();
                 if (!(alive = send_quads(q_head >> 1))) break;
             }
             if (ring_cnt > 0) {
-                if (lane >= ring_cnt) bh_put_point(S, ring_head + lane, bh_pad_source());
+                for (int i = lane; i < kTile; i += 32)
+                    if (i >= ring_cnt) bh_put_point(S, ring_head + i, bh_pad_source());
                 __syncwarp();
                 if (!(alive = send_points(ring_head >> 1))) break;
             }
@@ -1498,17 +1505,17 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, false>()) bh_walk_t
 
             // ---- drain: quadrupole tiles, then point tiles fed from the landed rounds
             if (ORDER >= 2) {
-                while (q_cnt >= 32) {
+                while (q_cnt >= kTile) {
                     bh_quads<T, WarpQuad>(L, *Q, q_head >> 1, eps2v, X, A);
-                    q_head ^= 32;
-                    q_cnt -= 32;
+                    q_head ^= kTile;
+                    q_cnt -= kTile;
                 }
             }
             for (;;) {
-                if (ring_cnt >= 32) {
+                if (ring_cnt >= kTile) {
                     bh_points<T, kPointUnroll>(L, S.ra + (ring_head >> 1), S.rb + (ring_head >> 1), eps2v, X, A);
-                    ring_head ^= 32;
-                    ring_cnt -= 32;
+                    ring_head ^= kTile;
+                    ring_cnt -= kTile;
                     continue;
                 }
                 if (pbase < pavail) {
@@ -1549,14 +1556,16 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, false>()) bh_walk_t
         }
         // ---- flush the partial tiles (padded with far, massless sources)
         if (ORDER >= 2 && q_cnt > 0) {
-            if (lane >= q_cnt)
-                bh_put_quad(*Q, q_head + lane, bh_pad_source(), make_float4(0.f, 0.f, 0.f, 0.f),
-                            make_float4(0.f, 0.f, 0.f, 0.f), eps2);
+            for (int i = lane; i < kTile; i += 32)
+                if (i >= q_cnt)
+                    bh_put_quad(*Q, q_head + i, bh_pad_source(), make_float4(0.f, 0.f, 0.f, 0.f),
+                                make_float4(0.f, 0.f, 0.f, 0.f), eps2);
             __syncwarp();
             bh_quads<T, WarpQuad>(L, *Q, q_head >> 1, eps2v, X, A, (q_cnt + 1) >> 1);
         }
         if (ring_cnt > 0) {
-            if (lane >= ring_cnt) bh_put_point(S, ring_head + lane, bh_pad_source());
+            for (int i = lane; i < kTile; i += 32)
+                if (i >= ring_cnt) bh_put_point(S, ring_head + i, bh_pad_source());
             __syncwarp();
             bh_points<T, kPointUnroll>(L, S.ra + (ring_head >> 1), S.rb + (ring_head >> 1), eps2v, X, A,
                                        (((ring_cnt + 1) >> 1) + kPointUnroll - 1) / kPointUnroll * kPointUnroll);
