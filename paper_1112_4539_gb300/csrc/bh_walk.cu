@@ -143,6 +143,15 @@ __host__ __device__ constexpr size_t bh_kahan_smem_bytes()
     return BH_KAHAN_SMEM ? (size_t)T * 4 * 32 * sizeof(float) : 0;
 }
 
+// Squared distance of a node's centre of mass from the group's box, as
+// explicit round-to-nearest operations: every walk kernel takes the same
+// opening decisions bit for bit (an expression left to the compiler may be
+// contracted into FMAs differently in each kernel, which flips near ties).
+__device__ __forceinline__ float bh_dist2(float dx, float dy, float dz)
+{
+    return __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+}
+
 // Target layout of a group of gc particles on the warp's T slots per lane
 // (warp-uniform).  Slots 0..nf-1 hold targets t*32 + lane.  When the last
 // slot would hold at most kSplitMax targets (k = gc - 32*nf) it is "split":
@@ -398,12 +407,12 @@ __device__ __forceinline__ void bh_eval_self(int gc, const Layout& L, float eps2
                 float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
                 r2 = self ? 1.0f : r2;
                 const float ri = rsqrtf(r2);
-                const float mr = (self ? 0.0f : sm) * ri;
-                const float mr3 = mr * ri * ri;
+                const float mr = __fmul_rn(self ? 0.0f : sm, ri);
+                const float mr3 = __fmul_rn(__fmul_rn(mr, ri), ri);
                 tx[t] = fmaf(mr3, dx, tx[t]);
                 ty[t] = fmaf(mr3, dy, ty[t]);
                 tz[t] = fmaf(mr3, dz, tz[t]);
-                tp[t] -= mr;
+                tp[t] = __fsub_rn(tp[t], mr);
             }
         }
     }
@@ -594,7 +603,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
             const float dx = fmaxf(fmaxf(bx0 - cm.x, cm.x - bx1), 0.0f);
             const float dy = fmaxf(fmaxf(by0 - cm.y, cm.y - by1), 0.0f);
             const float dz = fmaxf(fmaxf(bz0 - cm.z, cm.z - bz1), 0.0f);
-            const float d2 = dx * dx + dy * dy + dz * dz;
+            const float d2 = bh_dist2(dx, dy, dz);
             const bool member = (r.x < ge) && (r.x + r.y > gb);
             bool acc = has && (d2 > se) && !member;
             if (LEARNED && __ballot_sync(BH_FULL_MASK, acc)) {
@@ -971,7 +980,7 @@ __global__ void __launch_bounds__(256, bh_ws_min_blocks<T>()) bh_walk_ws_kernel(
                 const float dx = fmaxf(fmaxf(bx0 - cm.x, cm.x - bx1), 0.0f);
                 const float dy = fmaxf(fmaxf(by0 - cm.y, cm.y - by1), 0.0f);
                 const float dz = fmaxf(fmaxf(bz0 - cm.z, cm.z - bz1), 0.0f);
-                const float d2 = dx * dx + dy * dy + dz * dz;
+                const float d2 = bh_dist2(dx, dy, dz);
                 const bool member = (r.x < ge) && (r.x + r.y > gb);
                 const bool acc = has && (d2 > se) && !member;
                 const bool leaf = has && !acc && (r.z < 0);
@@ -1452,7 +1461,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, false>()) bh_walk_t
             const float dx = fmaxf(fmaxf(gb0.x - cm.x, cm.x - gb1.x), 0.0f);
             const float dy = fmaxf(fmaxf(gb0.y - cm.y, cm.y - gb1.y), 0.0f);
             const float dz = fmaxf(fmaxf(gb0.z - cm.z, cm.z - gb1.z), 0.0f);
-            const float d2 = dx * dx + dy * dy + dz * dz;
+            const float d2 = bh_dist2(dx, dy, dz);
             const bool member = (rfirst < ge) && (rfirst + rcount > gb);
             const bool acc = has && (d2 > se) && !member;
             const bool leaf = has && !acc && (rchn < 0);
