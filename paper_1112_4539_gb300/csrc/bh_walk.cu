@@ -45,12 +45,14 @@ constexpr int kRing = 2 * kTile;       // sources per ring (two tiles), stored a
 #define BH_POINT_UNROLL_LEARNED 2
 #endif
 #ifndef BH_QUAD_UNROLL
-#define BH_QUAD_UNROLL 1
+#define BH_QUAD_UNROLL 2           // one-warp kernel (the paired and TMA kernels keep 1)
 #endif
 constexpr int kPointUnroll = BH_POINT_UNROLL;
 constexpr int kPointUnrollLearned = BH_POINT_UNROLL_LEARNED;
 constexpr int kPointUnrollPaired = 2;
 constexpr int kQuadUnroll = BH_QUAD_UNROLL;
+constexpr int kQuadUnrollPaired = 1;
+constexpr int kQuadUnrollTma = 1;
 
 // Sources are staged negated and as pairs (ring positions 2p, 2p+1 side by
 // side) so that the interaction arithmetic runs on packed f32x2 operations:
@@ -284,13 +286,13 @@ __device__ __forceinline__ void bh_eval_points(const float4* __restrict__ ra, co
 
 // One tile (np <= kTilePairs pairs) of quadrupole cells on the first NF slots of every lane.
 // QC: any staging with the six pair arrays a..f of WarpQuad (pairs p0..p0+15).
-template <int T, int NF, class QC>
+template <int T, int NF, class QC, int QU>
 __device__ __forceinline__ void bh_eval_quads(const QC& Q, int p0, f2 eps2, const Tgt<T>& X, Acc<T>& A, int np)
 {
     Part<T> P;
 #pragma unroll
     for (int t = 0; t < NF; t++) P.x[t] = P.y[t] = P.z[t] = P.p[t] = P.q[t] = make_float2(0.f, 0.f);
-#pragma unroll kQuadUnroll
+#pragma unroll QU
     for (int j = p0; j < p0 + np; j++) {
         const float4 ca = Q.a[j], cb = Q.b[j], cc = Q.c[j], cd = Q.d[j], ce = Q.e[j], cf = Q.f[j];
 #pragma unroll
@@ -367,16 +369,17 @@ __device__ __forceinline__ void bh_points(const Layout& L, const float4* __restr
     else if (L.nf > 0) bh_eval_points<T, T, PU>(ra, rb, eps2, X, A, np);
     if (L.split) bh_split_points<T>(L, ra, rb, eps2, X, A);
 }
-template <int T, class QC>
-// A quadrupole tile (pairs p0 ..); np as for bh_points (any count).
+// A quadrupole tile (pairs p0 ..); np as for bh_points (any count); QU: the
+// unroll factor of the pair loop.
+template <int T, class QC, int QU = kQuadUnroll>
 __device__ __forceinline__ void bh_quads(const Layout& L, const QC& Q, int p0, f2 eps2, const Tgt<T>& X,
                                          Acc<T>& A, int np = kTilePairs)
 {
-    if (T > 1 && L.nf == 1) bh_eval_quads<T, 1, QC>(Q, p0, eps2, X, A, np);
-    else if (T > 2 && L.nf == 2) bh_eval_quads<T, (T > 2 ? 2 : T), QC>(Q, p0, eps2, X, A, np);
-    else if (T > 3 && L.nf == 3) bh_eval_quads<T, (T > 3 ? 3 : T), QC>(Q, p0, eps2, X, A, np);
-    else if (T > 4 && L.nf == 4) bh_eval_quads<T, (T > 4 ? 4 : T), QC>(Q, p0, eps2, X, A, np);
-    else if (L.nf > 0) bh_eval_quads<T, T, QC>(Q, p0, eps2, X, A, np);
+    if (T > 1 && L.nf == 1) bh_eval_quads<T, 1, QC, QU>(Q, p0, eps2, X, A, np);
+    else if (T > 2 && L.nf == 2) bh_eval_quads<T, (T > 2 ? 2 : T), QC, QU>(Q, p0, eps2, X, A, np);
+    else if (T > 3 && L.nf == 3) bh_eval_quads<T, (T > 3 ? 3 : T), QC, QU>(Q, p0, eps2, X, A, np);
+    else if (T > 4 && L.nf == 4) bh_eval_quads<T, (T > 4 ? 4 : T), QC, QU>(Q, p0, eps2, X, A, np);
+    else if (L.nf > 0) bh_eval_quads<T, T, QC, QU>(Q, p0, eps2, X, A, np);
     if (L.split) bh_split_quads<T, QC>(L, Q, p0, eps2, X, A);
 }
 
@@ -1144,7 +1147,7 @@ __global__ void __launch_bounds__(256, bh_ws_min_blocks<T>()) bh_walk_ws_kernel(
                 X.z[t] = make_float2(zi[t], zi[t]);
             }
         } else if (kind == kWsQuads) {
-            if (ORDER >= 2) bh_quads<T, WsTile>(L, C.tile[s], 0, eps2v, X, A);
+            if (ORDER >= 2) bh_quads<T, WsTile, kQuadUnrollPaired>(L, C.tile[s], 0, eps2v, X, A);
         } else if (kind == kWsPoints) {
             bh_points<T, kPointUnrollPaired>(L, C.tile[s].a, C.tile[s].b, eps2v, X, A);
         } else if (kind == kWsEnd) {
@@ -1515,7 +1518,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, false>()) bh_walk_t
             // ---- drain: quadrupole tiles, then point tiles fed from the landed rounds
             if (ORDER >= 2) {
                 while (q_cnt >= kTile) {
-                    bh_quads<T, WarpQuad>(L, *Q, q_head >> 1, eps2v, X, A);
+                    bh_quads<T, WarpQuad, kQuadUnrollTma>(L, *Q, q_head >> 1, eps2v, X, A);
                     q_head ^= kTile;
                     q_cnt -= kTile;
                 }
@@ -1570,7 +1573,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, false>()) bh_walk_t
                     bh_put_quad(*Q, q_head + i, bh_pad_source(), make_float4(0.f, 0.f, 0.f, 0.f),
                                 make_float4(0.f, 0.f, 0.f, 0.f), eps2);
             __syncwarp();
-            bh_quads<T, WarpQuad>(L, *Q, q_head >> 1, eps2v, X, A, (q_cnt + 1) >> 1);
+            bh_quads<T, WarpQuad, kQuadUnrollTma>(L, *Q, q_head >> 1, eps2v, X, A, (q_cnt + 1) >> 1);
         }
         if (ring_cnt > 0) {
             for (int i = lane; i < kTile; i += 32)
