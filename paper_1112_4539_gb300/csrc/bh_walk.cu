@@ -39,18 +39,22 @@ constexpr int kRing = 2 * kTile;       // sources per ring (two tiles), stored a
 // larger factors overflow the instruction cache, as every T-slot variant of
 // the loops is live at once across the SM's warps)
 #ifndef BH_POINT_UNROLL
-#define BH_POINT_UNROLL 4          // plain criterion (the learned walk's larger code keeps 2)
+#define BH_POINT_UNROLL 4
 #endif
 #ifndef BH_POINT_UNROLL_LEARNED
-#define BH_POINT_UNROLL_LEARNED 2
+#define BH_POINT_UNROLL_LEARNED 4
 #endif
 #ifndef BH_QUAD_UNROLL
 #define BH_QUAD_UNROLL 2           // one-warp kernel (the paired and TMA kernels keep 1)
+#endif
+#ifndef BH_QUAD_UNROLL_LEARNED
+#define BH_QUAD_UNROLL_LEARNED 1    // the learned walk (more registers for the network)
 #endif
 constexpr int kPointUnroll = BH_POINT_UNROLL;
 constexpr int kPointUnrollLearned = BH_POINT_UNROLL_LEARNED;
 constexpr int kPointUnrollPaired = 2;
 constexpr int kQuadUnroll = BH_QUAD_UNROLL;
+constexpr int kQuadUnrollLearned = BH_QUAD_UNROLL_LEARNED;
 constexpr int kQuadUnrollPaired = 1;
 constexpr int kQuadUnrollTma = 1;
 
@@ -669,7 +673,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
             // ---- drain: quadrupole tiles, point tiles, particle fills
             if (ORDER >= 2) {
                 while (q_cnt >= kTile) {
-                    bh_quads<T, WarpQuad>(L, *Q, q_head >> 1, eps2v, X, A);
+                    bh_quads<T, WarpQuad, LEARNED ? kQuadUnrollLearned : kQuadUnroll>(L, *Q, q_head >> 1, eps2v, X, A);
                     q_head ^= kTile;
                     q_cnt -= kTile;
                 }
@@ -722,7 +726,8 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
                     bh_put_quad(*Q, q_head + i, bh_pad_source(), make_float4(0.f, 0.f, 0.f, 0.f),
                                 make_float4(0.f, 0.f, 0.f, 0.f), eps2);
             __syncwarp();
-            bh_quads<T, WarpQuad>(L, *Q, q_head >> 1, eps2v, X, A, (q_cnt + 1) >> 1);
+            bh_quads<T, WarpQuad, LEARNED ? kQuadUnrollLearned : kQuadUnroll>(L, *Q, q_head >> 1, eps2v, X, A,
+                                                                             (q_cnt + 1) >> 1);
         }
         if (ring_cnt > 0) {
             for (int i = lane; i < kTile; i += 32)
