@@ -58,6 +58,11 @@ constexpr int kQuadUnrollLearned = BH_QUAD_UNROLL_LEARNED;
 constexpr int kQuadUnrollPaired = 1;
 constexpr int kQuadUnrollTma = 1;
 
+// Quadrupole-pair unroll of the one-warp kernel: 2 up to 3 slots per lane;
+// the 4-slot and learned kernels, with more registers live, keep 1.
+template <int T, bool LEARNED>
+__host__ __device__ constexpr int bh_quad_unroll() { return LEARNED ? kQuadUnrollLearned : (T <= 3 ? kQuadUnroll : 1); }
+
 // Sources are staged negated and as pairs (ring positions 2p, 2p+1 side by
 // side) so that the interaction arithmetic runs on packed f32x2 operations:
 // one instruction computes the same step for two sources.
@@ -673,7 +678,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
             // ---- drain: quadrupole tiles, point tiles, particle fills
             if (ORDER >= 2) {
                 while (q_cnt >= kTile) {
-                    bh_quads<T, WarpQuad, LEARNED ? kQuadUnrollLearned : kQuadUnroll>(L, *Q, q_head >> 1, eps2v, X, A);
+                    bh_quads<T, WarpQuad, bh_quad_unroll<T, LEARNED>()>(L, *Q, q_head >> 1, eps2v, X, A);
                     q_head ^= kTile;
                     q_cnt -= kTile;
                 }
@@ -726,7 +731,7 @@ __global__ void __launch_bounds__(128, bh_walk_min_blocks<T, LEARNED>())
                     bh_put_quad(*Q, q_head + i, bh_pad_source(), make_float4(0.f, 0.f, 0.f, 0.f),
                                 make_float4(0.f, 0.f, 0.f, 0.f), eps2);
             __syncwarp();
-            bh_quads<T, WarpQuad, LEARNED ? kQuadUnrollLearned : kQuadUnroll>(L, *Q, q_head >> 1, eps2v, X, A,
+            bh_quads<T, WarpQuad, bh_quad_unroll<T, LEARNED>()>(L, *Q, q_head >> 1, eps2v, X, A,
                                                                              (q_cnt + 1) >> 1);
         }
         if (ring_cnt > 0) {
