@@ -26,6 +26,10 @@ constexpr int kLvlThreads = 256;
 constexpr int kLvlPer = kLevelTile / kLvlThreads;  // 8 positions per thread
 constexpr int kMaxLeaf = 64;
 constexpr int kLeafFp64 = 32;
+#ifndef BH_WARP_MOMENT_LEVELS
+#define BH_WARP_MOMENT_LEVELS 4
+#endif
+constexpr int kWarpMomentLevels = BH_WARP_MOMENT_LEVELS;  // levels 0..this: a warp per node
 
 // ------------------------------------------------------------ pass 1
 // dl[k] = (d_k + 1) | (lambda_k << 5); per-block node counts per level.
@@ -681,9 +685,79 @@ __device__ __forceinline__ void bh_internal_moments(const bh_nodes& nd, int ch, 
     }
 }
 
+// The same sums with a warp per node (the levels near the root: few nodes,
+// mostly FP64): lane j takes particle j of a leaf (at most kLeafFp64 = 32;
+// larger leaves come from bh_bigleaf_moments_kernel) or child j of an
+// internal node, and the sums are butterfly reductions, so every lane ends
+// with the same values.  Offsets from the first particle / first child, as
+// in the per-thread form; only the order of the additions differs.
+template <typename R>
+__device__ __forceinline__ R bh_wsum(R x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(BH_FULL_MASK, x, o);
+    return x;
+}
+
+template <typename R, int ORDER>
+__device__ __forceinline__ void bh_leaf_moments_warp(const float4* __restrict__ pos_s, int k, int cnt, bh_mom<R>& o,
+                                                     bool& massless)
+{
+    const int lane = threadIdx.x & 31;
+    const float4 p0 = pos_s[k];
+    const float4 p = lane < cnt ? pos_s[k + lane] : p0;
+    const R m = lane < cnt ? (R)p.w : (R)0;
+    const R x0 = p0.x, y0 = p0.y, z0 = p0.z;
+    const R M = bh_wsum<R>(m);
+    const R sx = bh_wsum<R>(m * ((R)p.x - x0)), sy = bh_wsum<R>(m * ((R)p.y - y0)), sz = bh_wsum<R>(m * ((R)p.z - z0));
+    massless = !(M != (R)0);
+    o.M = M;
+    o.cx = massless ? x0 : x0 + sx / M;
+    o.cy = massless ? y0 : y0 + sy / M;
+    o.cz = massless ? z0 : z0 + sz / M;
+    if (ORDER >= 2) {
+        const R a = (R)p.x - o.cx, b = (R)p.y - o.cy, e = (R)p.z - o.cz;
+        o.q[0] = bh_wsum<R>(m * a * a);
+        o.q[1] = bh_wsum<R>(m * b * b);
+        o.q[2] = bh_wsum<R>(m * e * e);
+        o.q[3] = bh_wsum<R>(m * a * b);
+        o.q[4] = bh_wsum<R>(m * a * e);
+        o.q[5] = bh_wsum<R>(m * b * e);
+    }
+}
+
+template <typename R, int ORDER>
+__device__ __forceinline__ void bh_internal_moments_warp(const bh_nodes& nd, int ch, int nch, int fp64_threshold,
+                                                         bh_mom<R>& o, bool& massless)
+{
+    const int lane = threadIdx.x & 31;
+    bh_mom<R> c;
+    bh_child_moments<R>(nd, ch + (lane < nch ? lane : 0), fp64_threshold, ORDER, c);
+    const R m = lane < nch ? c.M : (R)0;
+    const R x0 = __shfl_sync(BH_FULL_MASK, c.cx, 0), y0 = __shfl_sync(BH_FULL_MASK, c.cy, 0),
+            z0 = __shfl_sync(BH_FULL_MASK, c.cz, 0);
+    const R M = bh_wsum<R>(m);
+    const R sx = bh_wsum<R>(m * (c.cx - x0)), sy = bh_wsum<R>(m * (c.cy - y0)), sz = bh_wsum<R>(m * (c.cz - z0));
+    massless = !(M != (R)0);
+    o.M = M;
+    o.cx = massless ? x0 : x0 + sx / M;
+    o.cy = massless ? y0 : y0 + sy / M;
+    o.cz = massless ? z0 : z0 + sz / M;
+    if (ORDER >= 2) {
+        const R a = c.cx - o.cx, b = c.cy - o.cy, e = c.cz - o.cz;
+        const R own = lane < nch ? (R)1 : (R)0;
+        o.q[0] = bh_wsum<R>(own * c.q[0] + m * a * a);
+        o.q[1] = bh_wsum<R>(own * c.q[1] + m * b * b);
+        o.q[2] = bh_wsum<R>(own * c.q[2] + m * e * e);
+        o.q[3] = bh_wsum<R>(own * c.q[3] + m * a * b);
+        o.q[4] = bh_wsum<R>(own * c.q[4] + m * a * e);
+        o.q[5] = bh_wsum<R>(own * c.q[5] + m * b * e);
+    }
+}
+
 // Moments of one node v of level lev (leaves from their particles, internal
 // nodes from their children, which the previous, deeper level wrote).
-template <int ORDER, typename K>
+template <int ORDER, typename K, bool WARP>
 __device__ __forceinline__ void bh_moment_node(const float4* __restrict__ pos_s, const K* __restrict__ keys,
                                                const bh_nodes& nd, int v, int lev, float theta, int fp64_threshold,
                                                int curve, float4 gbox, const uint32_t* __restrict__ sys,
@@ -707,6 +781,7 @@ __device__ __forceinline__ void bh_moment_node(const float4* __restrict__ pos_s,
     const float gz = zmin + ((float)(iz >> sh) + 0.5f) * side;
     float cx, cy, cz, M, q[6];
     bool massless;
+    const bool writer = !WARP || (threadIdx.x & 31) == 0;  // a warp's lanes hold the same sums
     if (f64) {
         bh_mom<double> o;
         if (r.z < 0 && r.y > kLeafFp64) {
@@ -717,24 +792,31 @@ __device__ __forceinline__ void bh_moment_node(const float4* __restrict__ pos_s,
             if (ORDER >= 2)
                 for (int i = 0; i < 6; i++) o.q[i] = nd.quad64[(size_t)v * 6 + i];
         } else if (r.z < 0) {
-            bh_leaf_moments<double, ORDER>(pos_s, r.x, r.y, o, massless);
+            if (WARP) bh_leaf_moments_warp<double, ORDER>(pos_s, r.x, r.y, o, massless);
+            else bh_leaf_moments<double, ORDER>(pos_s, r.x, r.y, o, massless);
         } else {
-            bh_internal_moments<double, ORDER>(nd, r.z, r.w, fp64_threshold, o, massless);
+            if (WARP) bh_internal_moments_warp<double, ORDER>(nd, r.z, r.w, fp64_threshold, o, massless);
+            else bh_internal_moments<double, ORDER>(nd, r.z, r.w, fp64_threshold, o, massless);
         }
         if (massless) {
             o.cx = gx; o.cy = gy; o.cz = gz;
         }
-        nd.com64[v] = bh_double4{o.cx, o.cy, o.cz, o.M};
+        if (writer) nd.com64[v] = bh_double4{o.cx, o.cy, o.cz, o.M};
         cx = (float)o.cx; cy = (float)o.cy; cz = (float)o.cz; M = (float)o.M;
         if (ORDER >= 2)
             for (int i = 0; i < 6; i++) {
-                nd.quad64[(size_t)v * 6 + i] = o.q[i];
+                if (writer) nd.quad64[(size_t)v * 6 + i] = o.q[i];
                 q[i] = (float)o.q[i];
             }
     } else {
         bh_mom<float> o;
-        if (r.z < 0) bh_leaf_moments<float, ORDER>(pos_s, r.x, r.y, o, massless);
-        else bh_internal_moments<float, ORDER>(nd, r.z, r.w, fp64_threshold, o, massless);
+        if (r.z < 0) {
+            if (WARP) bh_leaf_moments_warp<float, ORDER>(pos_s, r.x, r.y, o, massless);
+            else bh_leaf_moments<float, ORDER>(pos_s, r.x, r.y, o, massless);
+        } else {
+            if (WARP) bh_internal_moments_warp<float, ORDER>(nd, r.z, r.w, fp64_threshold, o, massless);
+            else bh_internal_moments<float, ORDER>(nd, r.z, r.w, fp64_threshold, o, massless);
+        }
         if (massless) {
             o.cx = gx; o.cy = gy; o.cz = gz;
         }
@@ -742,6 +824,7 @@ __device__ __forceinline__ void bh_moment_node(const float4* __restrict__ pos_s,
         if (ORDER >= 2)
             for (int i = 0; i < 6; i++) q[i] = o.q[i];
     }
+    if (!writer) return;
     nd.com_m[v] = make_float4(cx, cy, cz, M);
     const float dx = gx - cx, dy = gy - cy, dz = gz - cz;
     const float s = sqrtf(dx * dx + dy * dy + dz * dz);
@@ -767,10 +850,13 @@ __device__ __forceinline__ void bh_moment_node(const float4* __restrict__ pos_s,
     }
 }
 
-// 4 blocks per SM (at most 64 registers): the level passes are bound by the
-// latency of their loads, so more resident warps beat the few spilled words.
-template <int ORDER, typename K>
-__global__ void __launch_bounds__(256, 4)
+// One launch per level, deepest first.  Per thread (WARP = false, 4 blocks
+// per SM, at most 64 registers: the deep levels are bound by the latency of
+// their loads, so more resident warps beat the few spilled words) or per
+// warp (WARP = true, the levels near the root, kWarpMomentLevels: few nodes,
+// FP64 sums whose dependent chains a warp shortens to a few reductions).
+template <int ORDER, typename K, bool WARP>
+__global__ void __launch_bounds__(256, WARP ? 1 : 4)
 bh_moments_level_kernel(const float4* __restrict__ pos_s, const K* __restrict__ keys, bh_nodes nd, int lev,
                         float theta, int fp64_threshold, int curve, const bh_dev_ctrl* __restrict__ c,
                         const uint32_t* __restrict__ sys, const float4* __restrict__ sys_box)
@@ -778,8 +864,10 @@ bh_moments_level_kernel(const float4* __restrict__ pos_s, const K* __restrict__ 
     const int v0 = (int)c->level_offset[lev], v1 = (int)c->level_offset[lev + 1];
     if (c->n_nodes == 0u) return;
     const float4 gbox = make_float4(c->box[0], c->box[1], c->box[2], c->box[3]);
-    for (int v = v0 + blockIdx.x * blockDim.x + threadIdx.x; v < v1; v += gridDim.x * blockDim.x)
-        bh_moment_node<ORDER, K>(pos_s, keys, nd, v, lev, theta, fp64_threshold, curve, gbox, sys, sys_box);
+    const int per = WARP ? 32 : 1;
+    const int first = (blockIdx.x * blockDim.x + threadIdx.x) / per, stride = gridDim.x * blockDim.x / per;
+    for (int v = v0 + first; v < v1; v += stride)
+        bh_moment_node<ORDER, K, WARP>(pos_s, keys, nd, v, lev, theta, fp64_threshold, curve, gbox, sys, sys_box);
 }
 
 template <typename K>
@@ -790,12 +878,22 @@ static void bh_moments_t(const float4* pos_s, const K* keys, const bh_nodes& nd,
     if (order >= 2) bh_bigleaf_moments_kernel<2><<<grid, 256, 0, s>>>(pos_s, nd, ctrl);
     else bh_bigleaf_moments_kernel<1><<<grid, 256, 0, s>>>(pos_s, nd, ctrl);
     for (int lev = bh_key_traits<K>::kMaxLevel; lev >= 0; lev--) {
-        if (order >= 2)
-            bh_moments_level_kernel<2, K><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, curve,
-                                                               ctrl, sys, sys_box);
-        else
-            bh_moments_level_kernel<1, K><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold, curve,
-                                                               ctrl, sys, sys_box);
+        const bool warp = lev <= kWarpMomentLevels;
+        if (order >= 2) {
+            if (warp)
+                bh_moments_level_kernel<2, K, true><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold,
+                                                                         curve, ctrl, sys, sys_box);
+            else
+                bh_moments_level_kernel<2, K, false><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold,
+                                                                          curve, ctrl, sys, sys_box);
+        } else {
+            if (warp)
+                bh_moments_level_kernel<1, K, true><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold,
+                                                                         curve, ctrl, sys, sys_box);
+            else
+                bh_moments_level_kernel<1, K, false><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold,
+                                                                          curve, ctrl, sys, sys_box);
+        }
     }
 }
 
