@@ -29,7 +29,7 @@ constexpr int kLeafFp64 = 32;
 #ifndef BH_WARP_MOMENT_LEVELS
 #define BH_WARP_MOMENT_LEVELS 4
 #endif
-constexpr int kWarpMomentLevels = BH_WARP_MOMENT_LEVELS;  // levels 0..this: a warp per node
+constexpr int kWarpMomentLevels = BH_WARP_MOMENT_LEVELS;  // levels 0..this: a warp per node, below a thread
 
 // ------------------------------------------------------------ pass 1
 // dl[k] = (d_k + 1) | (lambda_k << 5); per-block node counts per level.
@@ -685,59 +685,94 @@ __device__ __forceinline__ void bh_internal_moments(const bh_nodes& nd, int ch, 
     }
 }
 
-// The same sums with a warp per node (the levels near the root: few nodes,
-// mostly FP64): lane j takes particle j of a leaf (at most kLeafFp64 = 32;
-// larger leaves come from bh_bigleaf_moments_kernel) or child j of an
-// internal node, and the sums are butterfly reductions, so every lane ends
-// with the same values.  Offsets from the first particle / first child, as
-// in the per-thread form; only the order of the additions differs.
-template <typename R>
+// The same sums with a group of W lanes per node (used with W = 32, a warp,
+// on the levels near the root: few nodes, mostly FP64; on the deep levels of
+// small leaves groups of 8 or 16 lanes were slower than a thread per node):
+// lane j of the group takes particles j, j + W, ... of a leaf (at most
+// kLeafFp64 = 32; larger leaves come from bh_bigleaf_moments_kernel) or
+// child j of an internal node, and the sums are butterfly reductions within
+// the group, so each of its lanes ends with the same values.  Offsets from
+// the first particle / first child, as in the per-thread form; only the
+// order of the additions differs.
+// The lanes of this thread's group of W (all of them take the same path: one node).
+template <int W>
+__device__ __forceinline__ unsigned int bh_group_mask()
+{
+    return W == 32 ? BH_FULL_MASK : ((1u << W) - 1u) << ((threadIdx.x & 31) & ~(W - 1));
+}
+template <int W, typename R>
 __device__ __forceinline__ R bh_wsum(R x)
 {
+    const unsigned int mask = bh_group_mask<W>();
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(BH_FULL_MASK, x, o);
+    for (int o = W / 2; o > 0; o >>= 1) x += __shfl_xor_sync(mask, x, o);
     return x;
 }
 
-template <typename R, int ORDER>
+template <int W, typename R, int ORDER>
 __device__ __forceinline__ void bh_leaf_moments_warp(const float4* __restrict__ pos_s, int k, int cnt, bh_mom<R>& o,
                                                      bool& massless)
 {
-    const int lane = threadIdx.x & 31;
+    constexpr int NP = 32 / W;  // particles per lane
+    const int j = threadIdx.x & (W - 1);
     const float4 p0 = pos_s[k];
-    const float4 p = lane < cnt ? pos_s[k + lane] : p0;
-    const R m = lane < cnt ? (R)p.w : (R)0;
+    float4 p[NP];
+    R m[NP];
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+        const int jj = j + i * W;
+        p[i] = jj < cnt ? pos_s[k + jj] : p0;
+        m[i] = jj < cnt ? (R)p[i].w : (R)0;
+    }
     const R x0 = p0.x, y0 = p0.y, z0 = p0.z;
-    const R M = bh_wsum<R>(m);
-    const R sx = bh_wsum<R>(m * ((R)p.x - x0)), sy = bh_wsum<R>(m * ((R)p.y - y0)), sz = bh_wsum<R>(m * ((R)p.z - z0));
+    R M = 0, sx = 0, sy = 0, sz = 0;
+#pragma unroll
+    for (int i = 0; i < NP; i++) {
+        M += m[i];
+        sx += m[i] * ((R)p[i].x - x0);
+        sy += m[i] * ((R)p[i].y - y0);
+        sz += m[i] * ((R)p[i].z - z0);
+    }
+    M = bh_wsum<W>(M);
+    sx = bh_wsum<W>(sx);
+    sy = bh_wsum<W>(sy);
+    sz = bh_wsum<W>(sz);
     massless = !(M != (R)0);
     o.M = M;
     o.cx = massless ? x0 : x0 + sx / M;
     o.cy = massless ? y0 : y0 + sy / M;
     o.cz = massless ? z0 : z0 + sz / M;
     if (ORDER >= 2) {
-        const R a = (R)p.x - o.cx, b = (R)p.y - o.cy, e = (R)p.z - o.cz;
-        o.q[0] = bh_wsum<R>(m * a * a);
-        o.q[1] = bh_wsum<R>(m * b * b);
-        o.q[2] = bh_wsum<R>(m * e * e);
-        o.q[3] = bh_wsum<R>(m * a * b);
-        o.q[4] = bh_wsum<R>(m * a * e);
-        o.q[5] = bh_wsum<R>(m * b * e);
+        R q[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int i = 0; i < NP; i++) {
+            const R a = (R)p[i].x - o.cx, b = (R)p[i].y - o.cy, e = (R)p[i].z - o.cz;
+            q[0] += m[i] * a * a;
+            q[1] += m[i] * b * b;
+            q[2] += m[i] * e * e;
+            q[3] += m[i] * a * b;
+            q[4] += m[i] * a * e;
+            q[5] += m[i] * b * e;
+        }
+#pragma unroll
+        for (int i = 0; i < 6; i++) o.q[i] = bh_wsum<W>(q[i]);
     }
 }
 
-template <typename R, int ORDER>
+template <int W, typename R, int ORDER>
 __device__ __forceinline__ void bh_internal_moments_warp(const bh_nodes& nd, int ch, int nch, int fp64_threshold,
                                                          bh_mom<R>& o, bool& massless)
 {
-    const int lane = threadIdx.x & 31;
+    static_assert(W >= 8, "a lane per child");
+    const int j = threadIdx.x & (W - 1);
+    const int base = (threadIdx.x & 31) & ~(W - 1);  // the group's first lane
     bh_mom<R> c;
-    bh_child_moments<R>(nd, ch + (lane < nch ? lane : 0), fp64_threshold, ORDER, c);
-    const R m = lane < nch ? c.M : (R)0;
-    const R x0 = __shfl_sync(BH_FULL_MASK, c.cx, 0), y0 = __shfl_sync(BH_FULL_MASK, c.cy, 0),
-            z0 = __shfl_sync(BH_FULL_MASK, c.cz, 0);
-    const R M = bh_wsum<R>(m);
-    const R sx = bh_wsum<R>(m * (c.cx - x0)), sy = bh_wsum<R>(m * (c.cy - y0)), sz = bh_wsum<R>(m * (c.cz - z0));
+    bh_child_moments<R>(nd, ch + (j < nch ? j : 0), fp64_threshold, ORDER, c);
+    const R m = j < nch ? c.M : (R)0;
+    const unsigned int mask = bh_group_mask<W>();
+    const R x0 = __shfl_sync(mask, c.cx, base), y0 = __shfl_sync(mask, c.cy, base), z0 = __shfl_sync(mask, c.cz, base);
+    const R M = bh_wsum<W>(m);
+    const R sx = bh_wsum<W>(m * (c.cx - x0)), sy = bh_wsum<W>(m * (c.cy - y0)), sz = bh_wsum<W>(m * (c.cz - z0));
     massless = !(M != (R)0);
     o.M = M;
     o.cx = massless ? x0 : x0 + sx / M;
@@ -745,19 +780,19 @@ __device__ __forceinline__ void bh_internal_moments_warp(const bh_nodes& nd, int
     o.cz = massless ? z0 : z0 + sz / M;
     if (ORDER >= 2) {
         const R a = c.cx - o.cx, b = c.cy - o.cy, e = c.cz - o.cz;
-        const R own = lane < nch ? (R)1 : (R)0;
-        o.q[0] = bh_wsum<R>(own * c.q[0] + m * a * a);
-        o.q[1] = bh_wsum<R>(own * c.q[1] + m * b * b);
-        o.q[2] = bh_wsum<R>(own * c.q[2] + m * e * e);
-        o.q[3] = bh_wsum<R>(own * c.q[3] + m * a * b);
-        o.q[4] = bh_wsum<R>(own * c.q[4] + m * a * e);
-        o.q[5] = bh_wsum<R>(own * c.q[5] + m * b * e);
+        const R own = j < nch ? (R)1 : (R)0;
+        o.q[0] = bh_wsum<W>(own * c.q[0] + m * a * a);
+        o.q[1] = bh_wsum<W>(own * c.q[1] + m * b * b);
+        o.q[2] = bh_wsum<W>(own * c.q[2] + m * e * e);
+        o.q[3] = bh_wsum<W>(own * c.q[3] + m * a * b);
+        o.q[4] = bh_wsum<W>(own * c.q[4] + m * a * e);
+        o.q[5] = bh_wsum<W>(own * c.q[5] + m * b * e);
     }
 }
 
 // Moments of one node v of level lev (leaves from their particles, internal
 // nodes from their children, which the previous, deeper level wrote).
-template <int ORDER, typename K, bool WARP>
+template <int ORDER, typename K, int W>
 __device__ __forceinline__ void bh_moment_node(const float4* __restrict__ pos_s, const K* __restrict__ keys,
                                                const bh_nodes& nd, int v, int lev, float theta, int fp64_threshold,
                                                int curve, float4 gbox, const uint32_t* __restrict__ sys,
@@ -781,7 +816,7 @@ __device__ __forceinline__ void bh_moment_node(const float4* __restrict__ pos_s,
     const float gz = zmin + ((float)(iz >> sh) + 0.5f) * side;
     float cx, cy, cz, M, q[6];
     bool massless;
-    const bool writer = !WARP || (threadIdx.x & 31) == 0;  // a warp's lanes hold the same sums
+    const bool writer = (threadIdx.x & (W - 1)) == 0;  // the lanes of a node's group hold the same sums
     if (f64) {
         bh_mom<double> o;
         if (r.z < 0 && r.y > kLeafFp64) {
@@ -792,10 +827,10 @@ __device__ __forceinline__ void bh_moment_node(const float4* __restrict__ pos_s,
             if (ORDER >= 2)
                 for (int i = 0; i < 6; i++) o.q[i] = nd.quad64[(size_t)v * 6 + i];
         } else if (r.z < 0) {
-            if (WARP) bh_leaf_moments_warp<double, ORDER>(pos_s, r.x, r.y, o, massless);
+            if (W > 1) bh_leaf_moments_warp<(W > 1 ? W : 8), double, ORDER>(pos_s, r.x, r.y, o, massless);
             else bh_leaf_moments<double, ORDER>(pos_s, r.x, r.y, o, massless);
         } else {
-            if (WARP) bh_internal_moments_warp<double, ORDER>(nd, r.z, r.w, fp64_threshold, o, massless);
+            if (W > 1) bh_internal_moments_warp<(W > 1 ? W : 8), double, ORDER>(nd, r.z, r.w, fp64_threshold, o, massless);
             else bh_internal_moments<double, ORDER>(nd, r.z, r.w, fp64_threshold, o, massless);
         }
         if (massless) {
@@ -811,10 +846,10 @@ __device__ __forceinline__ void bh_moment_node(const float4* __restrict__ pos_s,
     } else {
         bh_mom<float> o;
         if (r.z < 0) {
-            if (WARP) bh_leaf_moments_warp<float, ORDER>(pos_s, r.x, r.y, o, massless);
+            if (W > 1) bh_leaf_moments_warp<(W > 1 ? W : 8), float, ORDER>(pos_s, r.x, r.y, o, massless);
             else bh_leaf_moments<float, ORDER>(pos_s, r.x, r.y, o, massless);
         } else {
-            if (WARP) bh_internal_moments_warp<float, ORDER>(nd, r.z, r.w, fp64_threshold, o, massless);
+            if (W > 1) bh_internal_moments_warp<(W > 1 ? W : 8), float, ORDER>(nd, r.z, r.w, fp64_threshold, o, massless);
             else bh_internal_moments<float, ORDER>(nd, r.z, r.w, fp64_threshold, o, massless);
         }
         if (massless) {
@@ -850,13 +885,12 @@ __device__ __forceinline__ void bh_moment_node(const float4* __restrict__ pos_s,
     }
 }
 
-// One launch per level, deepest first.  Per thread (WARP = false, 4 blocks
-// per SM, at most 64 registers: the deep levels are bound by the latency of
-// their loads, so more resident warps beat the few spilled words) or per
-// warp (WARP = true, the levels near the root, kWarpMomentLevels: few nodes,
-// FP64 sums whose dependent chains a warp shortens to a few reductions).
-template <int ORDER, typename K, bool WARP>
-__global__ void __launch_bounds__(256, WARP ? 1 : 4)
+// One launch per level, deepest first, W lanes per node: 32 on the levels near
+// the root (kWarpMomentLevels: few nodes, FP64 sums whose dependent chains a
+// warp shortens to a few reductions), 1 below (4 blocks per SM, at most 64
+// registers: the deep levels are bound by the latency of their loads).
+template <int ORDER, typename K, int W>
+__global__ void __launch_bounds__(256, W == 32 ? 1 : 4)
 bh_moments_level_kernel(const float4* __restrict__ pos_s, const K* __restrict__ keys, bh_nodes nd, int lev,
                         float theta, int fp64_threshold, int curve, const bh_dev_ctrl* __restrict__ c,
                         const uint32_t* __restrict__ sys, const float4* __restrict__ sys_box)
@@ -864,10 +898,10 @@ bh_moments_level_kernel(const float4* __restrict__ pos_s, const K* __restrict__ 
     const int v0 = (int)c->level_offset[lev], v1 = (int)c->level_offset[lev + 1];
     if (c->n_nodes == 0u) return;
     const float4 gbox = make_float4(c->box[0], c->box[1], c->box[2], c->box[3]);
-    const int per = WARP ? 32 : 1;
-    const int first = (blockIdx.x * blockDim.x + threadIdx.x) / per, stride = gridDim.x * blockDim.x / per;
+    // the W lanes of a group share one node per iteration (and so one path)
+    const int first = (blockIdx.x * blockDim.x + threadIdx.x) / W, stride = gridDim.x * blockDim.x / W;
     for (int v = v0 + first; v < v1; v += stride)
-        bh_moment_node<ORDER, K, WARP>(pos_s, keys, nd, v, lev, theta, fp64_threshold, curve, gbox, sys, sys_box);
+        bh_moment_node<ORDER, K, W>(pos_s, keys, nd, v, lev, theta, fp64_threshold, curve, gbox, sys, sys_box);
 }
 
 template <typename K>
@@ -881,18 +915,18 @@ static void bh_moments_t(const float4* pos_s, const K* keys, const bh_nodes& nd,
         const bool warp = lev <= kWarpMomentLevels;
         if (order >= 2) {
             if (warp)
-                bh_moments_level_kernel<2, K, true><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold,
-                                                                         curve, ctrl, sys, sys_box);
+                bh_moments_level_kernel<2, K, 32><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold,
+                                                                       curve, ctrl, sys, sys_box);
             else
-                bh_moments_level_kernel<2, K, false><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold,
-                                                                          curve, ctrl, sys, sys_box);
+                bh_moments_level_kernel<2, K, 1><<<grid, 256, 0, s>>>(
+                    pos_s, keys, nd, lev, theta, fp64_threshold, curve, ctrl, sys, sys_box);
         } else {
             if (warp)
-                bh_moments_level_kernel<1, K, true><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold,
-                                                                         curve, ctrl, sys, sys_box);
+                bh_moments_level_kernel<1, K, 32><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold,
+                                                                       curve, ctrl, sys, sys_box);
             else
-                bh_moments_level_kernel<1, K, false><<<grid, 256, 0, s>>>(pos_s, keys, nd, lev, theta, fp64_threshold,
-                                                                          curve, ctrl, sys, sys_box);
+                bh_moments_level_kernel<1, K, 1><<<grid, 256, 0, s>>>(
+                    pos_s, keys, nd, lev, theta, fp64_threshold, curve, ctrl, sys, sys_box);
         }
     }
 }
