@@ -147,8 +147,10 @@ def test_groups_identical(bh, orc, G):
 
 @pytest.mark.parametrize("order", [1, 2])
 @pytest.mark.parametrize("fp64_threshold", [4096, 1])
-def test_moments(bh, orc, order, fp64_threshold):
-    pos = workloads.clumpy(60000, seed=6)
+@pytest.mark.parametrize("kind,n", [("clumpy", 60000), ("uniform", 300)])
+def test_moments(bh, orc, order, fp64_threshold, kind, n):
+    # the sparse uniform set has its leaves on levels 1-3, where a warp takes each node
+    pos = workloads.make(kind, n, 6)
     theta = 0.6
     ctx = bh.Context(pos.shape[0], device=0, leaf_size=8, group_size=64, order=order,
                      fp64_node_threshold=fp64_threshold)
