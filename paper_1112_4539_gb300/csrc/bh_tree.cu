@@ -210,6 +210,9 @@ __global__ void __launch_bounds__(1024) bh_level_scan_kernel(uint32_t* blk_lvl, 
 
 // ------------------------------------------------------------ pass 3
 // Write (first, level, child) of every node at its breadth-first index.
+// Position k starts the nodes of levels d_k+1 .. lambda_k (usually none): the
+// per-level counts and running indices of a thread live in its own column of
+// shared memory, so counting and writing loop over those levels only.
 template <int L>
 __global__ void __launch_bounds__(kLvlThreads)
 bh_node_write_kernel(const uint16_t* __restrict__ dl, int n, const uint32_t* __restrict__ blk_lvl, int nblk,
@@ -217,32 +220,31 @@ bh_node_write_kernel(const uint16_t* __restrict__ dl, int n, const uint32_t* __r
                      int32_t* __restrict__ nchildidx)
 {
     __shared__ unsigned int swt[kLvlThreads / 32][L + 1];
+    __shared__ unsigned int sx[L + 1][kLvlThreads];  // per level and thread: count, then next node index
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int base = blockIdx.x * kLevelTile;
     if (c->n_nodes == 0u) return;  // capacity error (or empty)
-    uint16_t my[kLvlPer];
-    unsigned int cnt[L + 1];
 #pragma unroll
-    for (int l = 0; l <= L; l++) cnt[l] = 0u;
+    for (int l = 0; l <= L; l++) sx[l][tid] = 0u;
+    uint16_t my[kLvlPer];
 #pragma unroll
     for (int r = 0; r < kLvlPer; r++) {
         const int k = base + tid * kLvlPer + r;
         my[r] = (k < n) ? dl[k] : (uint16_t)(L + 1);  // d+1 = L+1 > lambda = 0: no node
         const int d = (int)(my[r] & 31) - 1, lam = my[r] >> 5;
-#pragma unroll
-        for (int l = 0; l <= L; l++) cnt[l] += (l > d && l <= lam) ? 1u : 0u;
+        for (int l = d + 1; l <= lam; l++) sx[l][tid]++;
     }
     // per-level exclusive scan over the block (thread order = position order)
-    unsigned int ex[L + 1];
 #pragma unroll
     for (int l = 0; l <= L; l++) {
-        unsigned int incl = cnt[l];
+        const unsigned int cnt = sx[l][tid];
+        unsigned int incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned int t = __shfl_up_sync(BH_FULL_MASK, incl, o);
             if (lane >= o) incl += t;
         }
-        ex[l] = incl - cnt[l];
+        sx[l][tid] = incl - cnt;
         if (lane == 31) swt[w][l] = incl;
     }
     __syncthreads();
@@ -250,22 +252,19 @@ bh_node_write_kernel(const uint16_t* __restrict__ dl, int n, const uint32_t* __r
     for (int l = 0; l <= L; l++) {
         unsigned int b = c->level_offset[l] + blk_lvl[(size_t)l * nblk + blockIdx.x];
         for (int i = 0; i < w; i++) b += swt[i][l];
-        ex[l] += b;
+        sx[l][tid] += b;
     }
 #pragma unroll
     for (int r = 0; r < kLvlPer; r++) {
         const int k = base + tid * kLvlPer + r;
         const int d = (int)(my[r] & 31) - 1, lam = my[r] >> 5;
         int below = -1;  // index of node (k, l+1)
-#pragma unroll
-        for (int l = L; l >= 0; l--) {
-            if (l > d && l <= lam) {
-                const int idx = (int)ex[l]++;
-                nfirst[idx] = k;
-                nlevel[idx] = (uint8_t)l;
-                nchildidx[idx] = (l < lam) ? below : -1;
-                below = idx;
-            }
+        for (int l = lam; l > d; l--) {
+            const int idx = (int)sx[l][tid]++;
+            nfirst[idx] = k;
+            nlevel[idx] = (uint8_t)l;
+            nchildidx[idx] = (l < lam) ? below : -1;
+            below = idx;
         }
     }
 }
