@@ -45,9 +45,10 @@ bh_levels_kernel(const K* __restrict__ keys, const uint32_t* __restrict__ sys, i
     __shared__ K sk[kLevelTile + 2 * kMaxLeaf + 2];
     __shared__ uint32_t ss[kLevelTile + 2 * kMaxLeaf + 2];
     __shared__ int8_t sw[kLevelTile + kMaxLeaf + 1];
-    __shared__ unsigned int scnt[kLvlThreads / 32][L + 1];
+    __shared__ unsigned int sblk[L + 1];  // the block's node count per level
     const int tid = threadIdx.x;
     const int base = blockIdx.x * kLevelTile;
+    if (tid <= L) sblk[tid] = 0u;
     const int lo = base - n_leaf - 1;
     const int span = kLevelTile + 2 * n_leaf + 1;
     for (int i = tid; i < span; i += kLvlThreads) {
@@ -66,9 +67,6 @@ bh_levels_kernel(const K* __restrict__ keys, const uint32_t* __restrict__ sys, i
         sw[i] = (int8_t)wv;
     }
     __syncthreads();
-    unsigned int cnt[L + 1];
-#pragma unroll
-    for (int l = 0; l <= L; l++) cnt[l] = 0u;
     // W_k = max of w_j over j in [k - n_leaf, k], i.e. sw[k - base .. k - base + n_leaf]
     // (entries for j < 0 hold -1).  A thread's positions k0 + r (r < kLvlPer)
     // share the core sw[t0 + kLvlPer - 1 .. t0 + n_leaf] when n_leaf >= kLvlPer - 1;
@@ -106,21 +104,10 @@ bh_levels_kernel(const K* __restrict__ keys, const uint32_t* __restrict__ sys, i
         const int d = (k == 0 || ss[k - 1 - lo] != ss[k - lo]) ? -1 : bh_common_level(sk[k - 1 - lo], sk[k - lo]);
         const int lam = min(L, Wr[r] + 1);
         dl[k] = (uint16_t)((d + 1) | (lam << 5));
-#pragma unroll
-        for (int l = 0; l <= L; l++) cnt[l] += (l > d && l <= lam) ? 1u : 0u;
-    }
-    const int lane = tid & 31, w = tid >> 5;
-#pragma unroll
-    for (int l = 0; l <= L; l++) {
-        const unsigned int s = __reduce_add_sync(BH_FULL_MASK, cnt[l]);
-        if (lane == 0) scnt[w][l] = s;
+        for (int l = d + 1; l <= lam; l++) atomicAdd(&sblk[l], 1u);  // the nodes starting at k (usually none)
     }
     __syncthreads();
-    if (tid <= L) {
-        unsigned int s = 0u;
-        for (int i = 0; i < kLvlThreads / 32; i++) s += scnt[i][tid];
-        blk_lvl[(size_t)tid * nblk + blockIdx.x] = s;
-    }
+    if (tid <= L) blk_lvl[(size_t)tid * nblk + blockIdx.x] = sblk[tid];
 }
 
 // 1024-thread block: exclusive scan of v (one per thread), returns the total.
