@@ -216,6 +216,20 @@ def test_tree_force_parity(bh, orc, kind, n, seed, theta, eps, leaf, G, order):
     ctx.close()
 
 
+@pytest.mark.parametrize("G,order", [(40, 1), (72, 2), (100, 2), (33, 2)])
+def test_split_slots_of_every_width(bh, orc, G, order):
+    # group sizes whose last 32-target slot holds 1..16 targets in many groups:
+    # the split slot's phases (m = 1, 2, 4, 8, 16 lanes, m pairs of each tile)
+    pos = workloads.clumpy(30011, seed=19)
+    ctx, got, rc = _run(bh, pos, 0.55, 1e-3, leaf_size=8, group_size=G, order=order)
+    assert rc == 0
+    ref, b = orc.tree_force(pos, 0.55, 1e-3, n_leaf=8, G=G, order=order, walk="group")
+    last = b.g_count - 32 * ((b.g_count - 1) // 32)
+    assert ((last >= 1) & (last <= 16)).sum() > 50
+    _check_force(got, ref["out"], ref["margin"], a_abs=ref["a_abs"], case="clumpy 30011 G=%d split slots" % G)
+    ctx.close()
+
+
 def test_repeated_evaluations_are_identical(bh):
     import torch
     pos = workloads.plummer(50000, seed=9)
